@@ -1,0 +1,417 @@
+"""Benchmark: compressed-VDB path tracing on one GB300 (or N replicas).
+
+Workload (the 512^3 turbulent medium): a seeded 512^3 float32 volume (6-octave
+fBm x spherical falloff, ~50 % exactly 0), encoded at 1:10 into the VDB grid
+(409 of 4096 32^3 bricks), path traced at 1024x1024 x 16 spp with delta
+tracking, albedo 0.9, Henyey-Greenstein g = 0.6, up to 16 bounces, one
+directional light plus a constant environment; the same renderer on the dense
+volume in a 3D CUDA texture is the comparator.
+
+A step is one pass of the whole hot path over the input already in HBM:
+encode (histogram/background, brick ranges, scores, selection, tree build,
+prune, macrocell ranges) + render (majorants, DDA, Woodcock tracking,
+ratio-tracked light, scattering, accumulation).  `value` is Mpaths/s of those
+steps, timed with CUDA events on the launching stream (the 512 MiB input is
+larger than L2, and every step re-reads it, so L2 holds no stale grid).
+`e2e` runs the same step through the C ABI with host buffers: the volume is
+copied from pinned host memory inside vdbc_encode and the image is read back
+to the host inside vdbc_render.
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands)
+on the host cores over a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s and density lookups/s vs dense-texture render at stated PSNR; HBM GB/s"
+WORKLOAD = "turbulence512_r10_pt1024sq_16spp"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vdbc", choices=["vdbc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("render.cu", "vdbc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2504_04564_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the path-tracing kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_pt_vdb_turbulence512.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    src, traffic = None, None
+    for line in txt.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch_full_size:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    if src == kernel_source_hash() and traffic is not None:
+        return traffic
+    return None
+
+
+def scene(w):
+    from volgen import scenes
+    cam = scenes.pinhole_orbit(w["dims"], w["width"], w["height"])
+    return cam, w["medium"]
+
+
+def run_vdbc(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2504_04564_gb300 as v
+    import volgen
+    from volgen import scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = scenes.TURBULENCE_512
+    cam_args, med_args = scene(w)
+    cam = v.make_camera(*cam_args)
+    med = v.make_medium(v.MODE_PT, **med_args)
+    p = volgen.make_params(w["kind"], w["dims"], w["seed"])
+    vol = volgen.generate_torch(p, dev)
+    stream = torch.cuda.current_stream(dev)
+    H, W = w["height"], w["width"]
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    paths_per_step = H * W * w["spp"]
+    seed = 2024
+
+    def step():
+        g = v.vdbc_encode(vol, w["ratio"], stream=stream)
+        v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
+        return g
+
+    for _ in range(max(args.warmup, 3)):
+        g = step()
+        g.close()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- timed region: K whole steps; the render launch is also bracketed alone
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = v.vdbc_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    grids = []
+    for i in range(args.steps):
+        a, b, c = ev[i]
+        a.record(stream)
+        g = v.vdbc_encode(vol, w["ratio"], stream=stream)
+        b.record(stream)
+        v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
+        c.record(stream)
+        grids.append(g)
+    t_end.record(stream)
+    barrier()
+    launches = v.vdbc_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    enc_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    ren_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    stats = v.vdbc_render_stats_get(grids[-1], stream=stream)
+    info = grids[-1].info
+    for g in grids:
+        g.close()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * paths_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    render_ms = sum(ren_ms) / len(ren_ms)
+    lookups = int(stats.lookups)
+    vdb_img = img.clone()
+
+    # --- roofline of the dominant kernel (the path tracer): algorithmic bytes
+    # per density lookup = 8 FP32 voxel values = 32 B
+    peak, peak_kind = measured_peaks()
+    achieved = lookups * 32.0 / (render_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+            "kernel": "k_pt<VdbSampler>", "peak_source": peak_kind,
+            "algorithmic_bytes_per_lookup": 32}
+
+    # --- comparator: the same renderer on the dense 3D texture; PSNR
+    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, stream=stream)
+    dimg = torch.empty_like(img)
+    for _ in range(2):
+        v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(reps):
+        v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dense_ms = e0.elapsed_time(e1) / reps
+    dstats = v.vdbc_volume_render_stats_get(tex, stream=stream)
+    tex.close()
+    g1 = v.vdbc_encode(vol, 1.0, stream=stream)          # the uncompressed (lossless) render
+    ref_img = torch.empty_like(img)
+    v.vdbc_render(g1, cam, med, w["spp"], seed, ref_img, stream=stream)
+    torch.cuda.synchronize()
+    g1.close()
+
+    def psnr(a, b):
+        mse = float(((a[..., :3] - b[..., :3]) ** 2).mean().item())
+        return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_vol = vol.cpu().pin_memory()
+        host_img = np.empty((H, W, 4), dtype=np.float32)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            g = v.vdbc_encode(host_vol, w["ratio"], stream=stream)
+            v.vdbc_render(g, cam, med, w["spp"], seed, host_img, stream=stream)
+            g.close()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g = v.vdbc_encode(host_vol, w["ratio"], stream=stream)
+            v.vdbc_render(g, cam, med, w["spp"], seed, host_img, stream=stream)
+            g.close()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": round(world * paths_per_step * args.steps / e2e_s / 1e6, 3), "unit": "Mpaths/s",
+               "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
+                   "ratio": "1:10", "payload": "fp32", "image": "1024x1024", "spp": 16, "max_bounces": 16,
+                   "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "input 512 MiB > L2, re-read every step"},
+        "render_ms": round(render_ms, 3), "encode_ms": round(sum(enc_ms) / len(enc_ms), 3),
+        "lookups_per_step": lookups, "glookups_per_s": round(lookups / (render_ms * 1e-3) / 1e9, 3),
+        "dense_texture": {"ms_render": round(dense_ms, 3),
+                          "mpaths_per_s": round(paths_per_step / (dense_ms * 1e-3) / 1e6, 3),
+                          "vdb_over_dense_render_only": round(dense_ms / render_ms, 4),
+                          "vdb_over_dense_step": round(dense_ms / ms_per_step, 4),
+                          "lookups": int(dstats.lookups)},
+        "psnr_db": {"vdb_r10_vs_uncompressed_r1": round(psnr(vdb_img, ref_img), 3),
+                    "vdb_r10_vs_dense_texture": round(psnr(vdb_img, dimg), 3)},
+        "grid": {"total_bytes": int(info.total_bytes), "payload_bytes": int(info.payload_bytes),
+                 "n_active_bricks": int(info.n_active), "n_leaves": int(info.n_leaves)},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+class CpuOracle:
+    """The FP64 oracle (unchanged) on the host cores: the full 512^3 volume is
+    encoded once; a measurement then traces a fixed pixel sample (every 16th
+    row and column, all 16 spp) for about budget_s seconds."""
+
+    def __init__(self):
+        import numpy as np
+
+        import oracle
+        import volgen
+        from volgen import scenes
+
+        self.np, self.oracle = np, oracle
+        self.w = w = scenes.TURBULENCE_512
+        self.cores = os.cpu_count() or 1
+        p = volgen.make_params(w["kind"], w["dims"], w["seed"])
+        host = volgen.generate_host(p, threads=self.cores)
+        t0 = time.perf_counter()
+        e = oracle.encode(host, w["ratio"])
+        self.D = oracle.decode_dense(host, e["active"], e["background_bits"])
+        self.mx = oracle.macrocell_minmax(self.D, 8)[1]
+        self.enc_s = time.perf_counter() - t0
+        cam_args, med_args = scene(w)
+        self.cam = oracle.make_camera(*cam_args)
+        self.med = oracle.make_medium(1, macrocell=8, **med_args)
+        W, H = w["width"], w["height"]
+        ys, xs = np.meshgrid(np.arange(0, H, 16), np.arange(0, W, 16), indexing="ij")
+        pix = (ys * W + xs).ravel().astype(np.int64)
+        np.random.default_rng(0).shuffle(pix)
+        self.pix = pix
+        self.n = min(128, pix.size)
+
+    def measure(self, budget_s):
+        w = self.w
+        t0 = time.perf_counter()
+        self.oracle.render_pixels(self.D, self.mx, self.cam, self.med, w["spp"], 2024, self.pix[:self.n],
+                                  threads=self.cores)
+        dt = time.perf_counter() - t0
+        # size the next sample to about budget_s
+        self.n = int(min(self.pix.size, max(16, self.n * budget_s / max(dt, 1e-3))))
+        paths = self.n * w["spp"]
+        t0 = time.perf_counter()
+        self.oracle.render_pixels(self.D, self.mx, self.cam, self.med, w["spp"], 2024, self.pix[:self.n],
+                                  threads=self.cores)
+        dt = time.perf_counter() - t0
+        return {"value": round(paths / dt / 1e6, 6), "unit": "Mpaths/s", "cores": self.cores, "kind": "oracle",
+                "sample": "%d pixels of the every-16th-row/column subset of the 1024^2 image x %d spp "
+                          "(%d paths) in %.1f s; oracle encode+decode+macrocells of the full 512^3 volume "
+                          "took %.1f s (not in the rate)" % (self.n, w["spp"], paths, dt, self.enc_s)}
+
+
+def cpu_baseline(budget_s):
+    return CpuOracle().measure(budget_s)
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    co = CpuOracle()
+    per = max(2.0, min(20.0, 150.0 / (2 * (steps + max(args.warmup, 0)))))
+    for _ in range(max(args.warmup, 0)):
+        co.measure(per)
+    vals, cb = [], None
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cb = co.measure(per)
+        vals.append(cb["value"])
+    total = time.perf_counter() - t0
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Mpaths/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": round(value, 6),
+                             "unit": "Mpaths/s"},
+            "e2e": {"value": round(value, 6), "unit": "Mpaths/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_vdbc(a)

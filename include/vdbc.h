@@ -1,0 +1,245 @@
+/*
+ * vdbc.h -- C ABI of the GB300 (sm_103a) compressed-VDB volume renderer.
+ *
+ * Method: Zellmann et al., "GPU Volume Rendering with Hierarchical
+ * Compression Using VDB" (arXiv 2504.04564).  A dense float32 volume is
+ * encoded at a fixed rate into a four-level VDB tree by activating whole
+ * 32^3 bricks in order of their distance from the background value
+ * (Section 3.1, Algorithm 1, Eq. f1-f3; Section 3.2.1); a renderer then
+ * samples the tree at arbitrary positions, decoding every lookup on the fly
+ * (Section 3.2.2), with a macrocell majorant grid, a 3D-DDA and Woodcock
+ * tracking (Section 4).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a vdbc_status; nothing throws across the ABI.  On an
+ *    error, vdbc_last_error() gives a message for the calling thread.
+ *  - Volumes are x-fastest float32 arrays of dims[0]*dims[1]*dims[2] values.
+ *    Voxel (i,j,k) sits at index coordinate (i,j,k); the volume is the box
+ *    [-1/2, dim-1/2]^3.  World space scales index space so that the longest
+ *    axis spans one unit: index = world * max(dims) - 1/2.
+ *  - Pointers passed in are borrowed for the duration of the call (or until
+ *    the work enqueued on `stream` completes, for device pointers).  Grids
+ *    and plain-form volumes are owned by the library and freed only by their
+ *    *_free call.  Image buffers are owned by the caller.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that return device results enqueue their work on it and return without
+ *    waiting; calls that return host results wait for it, polling with a
+ *    wall-clock limit (VDBC_TIMEOUT_MS, default 600000 ms) after which they
+ *    return VDBC_ERR_TIMEOUT.
+ *  - Device kernels bound every loop; a path or lookup that exceeds its bound
+ *    sets a device error word, which the next host-synchronizing call of the
+ *    same handle reports as VDBC_ERR_DEVICE_FLAG.
+ *  - A handle may be used from several threads only if the calls are
+ *    serialized by the caller.
+ */
+#ifndef VDBC_H
+#define VDBC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VDBC_OK = 0,
+    VDBC_ERR_INVALID_ARG = 1,   /* a null pointer, a bad size or an out-of-range parameter */
+    VDBC_ERR_OOM = 2,           /* a device or host allocation failed */
+    VDBC_ERR_CUDA = 3,          /* a CUDA runtime call failed; see vdbc_last_error() */
+    VDBC_ERR_FORMAT = 4,        /* a grid file is truncated, of another version or corrupt */
+    VDBC_ERR_TIMEOUT = 5,       /* a host wait ran past its wall-clock limit */
+    VDBC_ERR_DEVICE_FLAG = 6,   /* a kernel hit one of its loop bounds */
+    VDBC_ERR_UNSUPPORTED = 7    /* valid request the build does not implement */
+} vdbc_status;
+
+/* similarity of a brick's value range [lo,hi] to the background B (Eq. f1-f3) */
+enum { VDBC_F1 = 1,  /* closest:  min(|lo-B|, |hi-B|)  */
+       VDBC_F2 = 2,  /* farthest: max(|lo-B|, |hi-B|)  */
+       VDBC_F3 = 3   /* median:   |(lo+hi)/2 - B|      */ };
+
+/* leaf payload: FP32 as in the paper; FP16 / FP8 (E4M3) with a per-leaf
+ * FP32 scale and offset are a project extension (not in the paper) */
+enum { VDBC_FP32 = 0, VDBC_FP16 = 1, VDBC_FP8 = 2 };
+
+enum { VDBC_CAM_ORTHO = 0, VDBC_CAM_PINHOLE = 1 };
+enum { VDBC_MODE_EA = 0,   /* emission-absorption ray marching (fixed step) */
+       VDBC_MODE_PT = 1    /* delta tracking, ratio-tracked light, scattering */ };
+enum { VDBC_FILTER_TEXTURE = 0,  /* plain form: 3D CUDA texture, hardware trilinear */
+       VDBC_FILTER_LINEAR = 1    /* plain form: linear device array, software trilinear */ };
+
+typedef struct vdbc_grid vdbc_grid;      /* compressed grid: opaque, library-owned */
+typedef struct vdbc_volume vdbc_volume;  /* plain form of a dense volume: opaque, library-owned */
+
+/* a dense input volume, x fastest; data is a device pointer if on_device != 0 */
+typedef struct {
+    int32_t dims[3];
+    int32_t on_device;
+    const float* data;
+} vdbc_dense;
+
+typedef struct {
+    double  ratio;      /* R of the target rate 1:R, R >= 1; 1 keeps every non-empty brick */
+    int32_t metric;     /* VDBC_F1, VDBC_F2 (default when 0) or VDBC_F3 */
+    int32_t payload;    /* VDBC_FP32, VDBC_FP16 or VDBC_FP8 */
+    int32_t macrocell;  /* edge of a majorant macrocell in voxels, 1..64; 0 means 8 */
+    int32_t reserved;
+} vdbc_encode_params;
+
+typedef struct {
+    int32_t  dims[3];
+    int32_t  payload;
+    int32_t  macrocell;
+    int32_t  metric;
+    uint32_t background_bits;  /* bit pattern of the background value B */
+    int32_t  reserved;
+    double   ratio;
+    int64_t  n_bricks;         /* ceil(dims / 32) brick grid size */
+    int64_t  n_nonempty;       /* bricks whose range is not exactly [B,B] */
+    int64_t  budget;           /* N = floor(n_bricks * 131072 / (ratio * brick payload bytes)) */
+    int64_t  n_active;         /* bricks activated = min(budget, n_nonempty) */
+    int64_t  n_upper, n_lower, n_leaves, n_tiles;
+    uint64_t payload_bytes;    /* leaf values plus per-leaf scale/offset */
+    uint64_t node_bytes;       /* root, upper and lower tables plus tile values */
+    uint64_t total_bytes;      /* everything the grid holds on the device, incl. majorants */
+} vdbc_grid_info;
+
+typedef struct {
+    int32_t kind;              /* VDBC_CAM_ORTHO or VDBC_CAM_PINHOLE */
+    int32_t width, height;     /* image size in pixels, 1..16384 each */
+    int32_t reserved;
+    double  eye[3];            /* world space */
+    double  look[3];           /* a world point the camera looks at */
+    double  up[3];
+    double  fovy_or_height;    /* vertical field of view in degrees (pinhole) or
+                                  world height of the image (ortho) */
+} vdbc_camera;
+
+typedef struct {
+    int32_t mode;              /* VDBC_MODE_EA or VDBC_MODE_PT */
+    int32_t tf_n;              /* EA: number of RGBA entries of the transfer function, 2..2048 */
+    const float* tf_rgba;      /* EA: host pointer to tf_n RGBA float entries; alpha is
+                                  the extinction per voxel length */
+    float   step;              /* EA: step in voxels (> 0) */
+    float   density_scale;     /* PT: extinction per world unit at density 1 */
+    float   albedo;            /* PT: single-scattering albedo in [0,1] */
+    float   g;                 /* PT: Henyey-Greenstein asymmetry in (-1,1) */
+    int32_t max_bounces;       /* PT: scattering events per path, 1..4096 */
+    int32_t reserved;
+    float   sun_dir[3];        /* PT: unit direction toward the directional light */
+    float   sun_rad[3];        /* PT: its irradiance (RGB) */
+    float   env_rad[3];        /* PT: constant environment radiance (RGB) */
+} vdbc_medium;
+
+/* counters of the last render on a handle (read after the stream completes) */
+typedef struct {
+    uint64_t lookups;          /* density lookups (trilinear reconstructions) */
+    uint64_t paths;
+    uint64_t error_flags;      /* nonzero if a kernel hit one of its bounds */
+} vdbc_render_stats;
+
+/*
+ * vdbc_encode -- fixed-rate compression of a dense volume into a VDB grid.
+ * Paper: Section 3.1, Algorithm 1 (histogram -> background B, 32^3 brick
+ * ranges, sort by Eq. f1-f3, activate the first bricks up to the rate) and
+ * Section 3.2.1 (always set the two extreme corner voxels; prune).
+ *   in      dense volume (host or device pointer, x fastest); borrowed.
+ *   params  rate, metric, payload, macrocell edge.
+ *   stream  work is enqueued here; the call waits once for the tree sizes.
+ *   out     receives a new grid handle; free with vdbc_grid_free.
+ * Errors: INVALID_ARG for null pointers, dims < 1 or > 8192, ratio < 1 or not
+ * finite, unknown metric/payload, or non-finite voxel values; OOM; CUDA.
+ */
+vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_params* params, void* stream,
+                        vdbc_grid** out);
+
+/* vdbc_grid_get_info -- sizes and counts of a grid (host struct, no device work). */
+vdbc_status vdbc_grid_get_info(const vdbc_grid* grid, vdbc_grid_info* info);
+
+/*
+ * vdbc_grid_decode -- the decoded grid D at every voxel (the value the
+ * sampler of Section 3.2.2 reconstructs from: the voxel where the tree holds
+ * it, a tile or the background elsewhere), x fastest.
+ *   out        dims[0]*dims[1]*dims[2] floats, device pointer if out_on_device else host.
+ * Errors: INVALID_ARG; CUDA; TIMEOUT (host output only).
+ */
+vdbc_status vdbc_grid_decode(const vdbc_grid* grid, float* out, int32_t out_on_device, void* stream);
+
+/* vdbc_grid_active_bricks -- 1 byte per brick (x fastest): 1 if Algorithm 1
+ * activated it.  host_out holds info.n_bricks bytes. */
+vdbc_status vdbc_grid_active_bricks(const vdbc_grid* grid, uint8_t* host_out);
+
+/* vdbc_grid_macrocells -- per macrocell min and max of D over the cell's voxels
+ * dilated by one voxel (the majorant ranges of Section 4); host arrays of
+ * prod(ceil(dims / macrocell)) floats each. */
+vdbc_status vdbc_grid_macrocells(const vdbc_grid* grid, float* host_min, float* host_max);
+
+/*
+ * vdbc_grid_save / vdbc_grid_load -- the grid as one linear, pointer-free
+ * block (the property Section 2.3 and Section 3.2.1 rely on for copying
+ * NanoVDB grids with memcpy), behind a versioned header and a checksum.  No
+ * entropy coding, so the file keeps random access (Section 5.5).
+ * Errors: INVALID_ARG; FORMAT (bad magic, version, size or checksum); OOM; CUDA.
+ */
+vdbc_status vdbc_grid_save(const vdbc_grid* grid, const char* path);
+vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid** out);
+void        vdbc_grid_free(vdbc_grid* grid);
+
+/*
+ * vdbc_render -- render the compressed grid, one thread per light path,
+ * every density lookup decoded on the fly (Section 3.2.2: tree descent with
+ * a cached accessor, leaf decode, trilinear reconstruction; Section 4:
+ * macrocell majorants, 3D-DDA, Woodcock tracking, volumetric scattering).
+ *   mode EA: one ray per pixel through the pixel centre, front-to-back
+ *            emission-absorption with a fixed step; spp must be 1.
+ *   mode PT: spp paths per pixel, Philox counter (pixel, sample, call,
+ *            stream) keyed by seed; light from a directional source by ratio
+ *            tracking plus a constant environment.
+ *   rgba_out width*height*4 floats (RGBA per pixel, row 0 at the top),
+ *            device pointer if out_on_device else host (the call then waits).
+ * Errors: INVALID_ARG; OOM; CUDA; TIMEOUT; DEVICE_FLAG.
+ */
+vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* camera, const vdbc_medium* medium,
+                        int32_t spp, uint64_t seed, float* rgba_out, int32_t out_on_device,
+                        void* stream);
+
+/* vdbc_render_stats_get -- counters of the last vdbc_render on this grid;
+ * waits for `stream`. */
+vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream, vdbc_render_stats* stats);
+
+/*
+ * vdbc_volume_create -- the plain form the paper compares against (Section
+ * 5.3: the structured volume in a 3D CUDA texture) or, with
+ * VDBC_FILTER_LINEAR, a linear device copy sampled by the same software
+ * trilinear as the grid.  Builds the same macrocell majorant grid from the
+ * dense values.
+ */
+vdbc_status vdbc_volume_create(const vdbc_dense* in, int32_t filter, int32_t macrocell,
+                               void* stream, vdbc_volume** out);
+void        vdbc_volume_free(vdbc_volume* vol);
+
+/* vdbc_render_dense -- vdbc_render on the plain form; identical arguments and
+ * tracking code, only the sampler differs. */
+vdbc_status vdbc_render_dense(const vdbc_volume* vol, const vdbc_camera* camera,
+                              const vdbc_medium* medium, int32_t spp, uint64_t seed,
+                              float* rgba_out, int32_t out_on_device, void* stream);
+vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void* stream,
+                                         vdbc_render_stats* stats);
+
+/* vdbc_philox -- n outputs of the device Philox4x32-10 (the generator every
+ * render draws from), for checking it against its published definition.
+ * ctr: 4*n counters, key: 2 words, out: 4*n words; all host arrays. */
+vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int32_t n);
+
+/* number of kernels this library has launched in the process so far (every
+ * launch increments it on the host); for counting device work per step */
+uint64_t    vdbc_kernel_launches(void);
+
+/* message of the last failed call on this thread ("" if none) */
+const char* vdbc_last_error(void);
+/* library version, e.g. "vdbc 0.1.0 sm_103a" */
+const char* vdbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

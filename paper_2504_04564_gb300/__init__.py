@@ -1,0 +1,340 @@
+"""Python binding of libvdbc (include/vdbc.h): argument marshalling only.
+
+Every step of encoding and rendering runs in the library's CUDA kernels.  The
+binding converts torch tensors (device memory, via ``data_ptr()``), numpy
+arrays (host memory) and plain Python values into the C structs, and turns a
+non-OK status into ``VdbcError``.  There is no fallback: if ``libvdbc.so`` is
+missing the import of :func:`lib` raises.
+
+Functions keep the C names: ``vdbc_encode``, ``vdbc_render``,
+``vdbc_render_dense``, ``vdbc_volume_create``, ``vdbc_grid_decode`` ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_FORMAT, ERR_TIMEOUT, ERR_DEVICE_FLAG, ERR_UNSUPPORTED = range(8)
+F1, F2, F3 = 1, 2, 3
+FP32, FP16, FP8 = 0, 1, 2
+CAM_ORTHO, CAM_PINHOLE = 0, 1
+MODE_EA, MODE_PT = 0, 1
+FILTER_TEXTURE, FILTER_LINEAR = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "FORMAT", 5: "TIMEOUT",
+                6: "DEVICE_FLAG", 7: "UNSUPPORTED"}
+
+
+class VdbcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class Dense(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("on_device", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class EncodeParams(ctypes.Structure):
+    _fields_ = [("ratio", ctypes.c_double), ("metric", ctypes.c_int32), ("payload", ctypes.c_int32),
+                ("macrocell", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("payload", ctypes.c_int32), ("macrocell", ctypes.c_int32),
+                ("metric", ctypes.c_int32), ("background_bits", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("ratio", ctypes.c_double), ("n_bricks", ctypes.c_int64), ("n_nonempty", ctypes.c_int64),
+                ("budget", ctypes.c_int64), ("n_active", ctypes.c_int64), ("n_upper", ctypes.c_int64),
+                ("n_lower", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("payload_bytes", ctypes.c_uint64), ("node_bytes", ctypes.c_uint64),
+                ("total_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if name == "dims" else v
+        return d
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("eye", ctypes.c_double * 3), ("look", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fovy_or_height", ctypes.c_double)]
+
+
+class Medium(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tf_n", ctypes.c_int32), ("tf_rgba", ctypes.c_void_p),
+                ("step", ctypes.c_float), ("density_scale", ctypes.c_float), ("albedo", ctypes.c_float),
+                ("g", ctypes.c_float), ("max_bounces", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sun_dir", ctypes.c_float * 3), ("sun_rad", ctypes.c_float * 3), ("env_rad", ctypes.c_float * 3)]
+
+
+class RenderStats(ctypes.Structure):
+    _fields_ = [("lookups", ctypes.c_uint64), ("paths", ctypes.c_uint64), ("error_flags", ctypes.c_uint64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported surface of include/vdbc.h
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "vdbc_encode": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.POINTER(EncodeParams), _vp, ctypes.POINTER(_vp)]),
+    "vdbc_grid_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(GridInfo)]),
+    "vdbc_grid_decode": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp]),
+    "vdbc_grid_active_bricks": (ctypes.c_int, [_vp, _vp]),
+    "vdbc_grid_macrocells": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vdbc_grid_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "vdbc_grid_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
+    "vdbc_grid_free": (None, [_vp]),
+    "vdbc_render": (ctypes.c_int, [_vp, ctypes.POINTER(Camera), ctypes.POINTER(Medium), ctypes.c_int32,
+                                   ctypes.c_uint64, _vp, ctypes.c_int32, _vp]),
+    "vdbc_render_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
+    "vdbc_volume_create": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.c_int32, ctypes.c_int32, _vp,
+                                          ctypes.POINTER(_vp)]),
+    "vdbc_volume_free": (None, [_vp]),
+    "vdbc_render_dense": (ctypes.c_int, [_vp, ctypes.POINTER(Camera), ctypes.POINTER(Medium), ctypes.c_int32,
+                                         ctypes.c_uint64, _vp, ctypes.c_int32, _vp]),
+    "vdbc_volume_render_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
+    "vdbc_philox": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "vdbc_kernel_launches": (ctypes.c_uint64, []),
+    "vdbc_last_error": (ctypes.c_char_p, []),
+    "vdbc_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libvdbc.so.  Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libvdbc.so is not built (%s); run __graft_entry__.build() "
+                              "or python -m paper_2504_04564_gb300.build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        msg = lib().vdbc_last_error()
+        raise VdbcError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor or a numpy array."""
+    if _is_torch(x):
+        return x.data_ptr(), int(x.is_cuda)
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, 0
+    raise TypeError("expected a torch tensor or a numpy array, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_dense(vol) -> Dense:
+    """Descriptor of an x-fastest (nz, ny, nx) float32 volume (torch or numpy)."""
+    if _is_torch(vol):
+        assert vol.dtype.__str__() == "torch.float32" and vol.is_contiguous()
+    else:
+        assert vol.dtype == np.float32 and vol.flags["C_CONTIGUOUS"]
+    nz, ny, nx = vol.shape
+    d = Dense()
+    d.dims[0], d.dims[1], d.dims[2] = nx, ny, nz
+    p, on_dev = _ptr(vol)
+    d.data = p
+    d.on_device = on_dev
+    return d
+
+
+def make_camera(kind, width, height, eye, look, up, fovy_or_height) -> Camera:
+    c = Camera()
+    c.kind, c.width, c.height = int(kind), int(width), int(height)
+    for a in range(3):
+        c.eye[a], c.look[a], c.up[a] = float(eye[a]), float(look[a]), float(up[a])
+    c.fovy_or_height = float(fovy_or_height)
+    return c
+
+
+def make_medium(mode, tf=None, step=0.5, density_scale=1.0, albedo=0.9, g=0.0, max_bounces=1,
+                sun_dir=(0, 0, 1), sun_rad=(0, 0, 0), env_rad=(0, 0, 0)) -> Medium:
+    m = Medium()
+    m.mode = int(mode)
+    m._tf = None
+    if tf is not None:
+        m._tf = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1, 4)
+        m.tf_n = m._tf.shape[0]
+        m.tf_rgba = m._tf.ctypes.data
+    m.step, m.density_scale, m.albedo, m.g = float(step), float(density_scale), float(albedo), float(g)
+    m.max_bounces = int(max_bounces)
+    for a in range(3):
+        m.sun_dir[a], m.sun_rad[a], m.env_rad[a] = float(sun_dir[a]), float(sun_rad[a]), float(env_rad[a])
+    return m
+
+
+# ---------------------------------------------------------------- the C entry points
+class Grid:
+    """Owning wrapper of a vdbc_grid*; frees it on close()/garbage collection."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @property
+    def info(self) -> GridInfo:
+        return vdbc_grid_get_info(self)
+
+    def close(self):
+        if self.handle:
+            lib().vdbc_grid_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Volume:
+    """Owning wrapper of a vdbc_volume* (the plain dense form)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().vdbc_volume_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vdbc_encode(vol, ratio, metric=F2, payload=FP32, macrocell=8, stream=None) -> Grid:
+    d = make_dense(vol)
+    p = EncodeParams(float(ratio), int(metric), int(payload), int(macrocell), 0)
+    h = ctypes.c_void_p()
+    _check(lib().vdbc_encode(ctypes.byref(d), ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+    return Grid(h.value)
+
+
+def vdbc_grid_get_info(grid: Grid) -> GridInfo:
+    info = GridInfo()
+    _check(lib().vdbc_grid_get_info(grid.handle, ctypes.byref(info)))
+    return info
+
+
+def vdbc_grid_decode(grid: Grid, out, stream=None):
+    p, on_dev = _ptr(out)
+    _check(lib().vdbc_grid_decode(grid.handle, p, on_dev, _stream(stream)))
+    return out
+
+
+def vdbc_grid_active_bricks(grid: Grid) -> np.ndarray:
+    out = np.zeros(grid.info.n_bricks, dtype=np.uint8)
+    _check(lib().vdbc_grid_active_bricks(grid.handle, out.ctypes.data))
+    return out
+
+
+def vdbc_grid_macrocells(grid: Grid):
+    i = grid.info
+    mc = i.macrocell
+    n = int(np.prod([(d + mc - 1) // mc for d in i.dims]))
+    mn = np.zeros(n, dtype=np.float32)
+    mx = np.zeros(n, dtype=np.float32)
+    _check(lib().vdbc_grid_macrocells(grid.handle, mn.ctypes.data, mx.ctypes.data))
+    return mn, mx
+
+
+def vdbc_grid_save(grid: Grid, path: str) -> None:
+    _check(lib().vdbc_grid_save(grid.handle, path.encode()))
+
+
+def vdbc_grid_load(path: str, stream=None) -> Grid:
+    h = ctypes.c_void_p()
+    _check(lib().vdbc_grid_load(path.encode(), _stream(stream), ctypes.byref(h)))
+    return Grid(h.value)
+
+
+def vdbc_render(grid: Grid, camera: Camera, medium: Medium, spp, seed, out, stream=None):
+    p, on_dev = _ptr(out)
+    _check(lib().vdbc_render(grid.handle, ctypes.byref(camera), ctypes.byref(medium), int(spp),
+                             ctypes.c_uint64(int(seed)), p, on_dev, _stream(stream)))
+    return out
+
+
+def vdbc_render_stats_get(grid: Grid, stream=None) -> RenderStats:
+    s = RenderStats()
+    _check(lib().vdbc_render_stats_get(grid.handle, _stream(stream), ctypes.byref(s)))
+    return s
+
+
+def vdbc_volume_create(vol, filter=FILTER_TEXTURE, macrocell=8, stream=None) -> Volume:
+    d = make_dense(vol)
+    h = ctypes.c_void_p()
+    _check(lib().vdbc_volume_create(ctypes.byref(d), int(filter), int(macrocell), _stream(stream),
+                                    ctypes.byref(h)))
+    return Volume(h.value)
+
+
+def vdbc_render_dense(volume: Volume, camera: Camera, medium: Medium, spp, seed, out, stream=None):
+    p, on_dev = _ptr(out)
+    _check(lib().vdbc_render_dense(volume.handle, ctypes.byref(camera), ctypes.byref(medium), int(spp),
+                                   ctypes.c_uint64(int(seed)), p, on_dev, _stream(stream)))
+    return out
+
+
+def vdbc_volume_render_stats_get(volume: Volume, stream=None) -> RenderStats:
+    s = RenderStats()
+    _check(lib().vdbc_volume_render_stats_get(volume.handle, _stream(stream), ctypes.byref(s)))
+    return s
+
+
+def vdbc_philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _check(lib().vdbc_philox(c.ctypes.data, k.ctypes.data, out.ctypes.data, c.shape[0]))
+    return out
+
+
+def vdbc_kernel_launches() -> int:
+    return int(lib().vdbc_kernel_launches())
+
+
+def vdbc_last_error() -> str:
+    return lib().vdbc_last_error().decode()
+
+
+def vdbc_version() -> str:
+    return lib().vdbc_version().decode()

@@ -1,0 +1,976 @@
+// encode.cu -- fixed-rate VDB encoding on the GPU.
+//
+// Section 3.1, Algorithm 1: histogram -> background B; 32^3 brick value
+// ranges; sort by similarity f1/f2/f3 (Eq. f1-f3); activate the first bricks
+// up to the rate.  Section 3.2.1: always keep the two extreme corner voxels,
+// then prune (constant leaves become tiles).  Readings (shared with the
+// CPU oracle, which is separate code): two-level bit-pattern histogram for B
+// (ties to the smaller pattern), ceil brick grid, empty = range exactly
+// [B,B], largest f first with ties to the lower brick index, exactly
+// N = floor(numBricks * 131072 / (ratio * brick payload bytes)) bricks.
+//
+// Kernels, in order (every one is HBM- or latency-bound, none is a
+// contraction):
+//   k_pass1        one CTA per brick: min/max (total order) + upper-16-bit
+//                  histogram (warp-aggregated atomics) + non-finite check
+//   k_argmax       one CTA: most frequent bin, ties to the smaller index
+//   k_pass2        one CTA per brick overlapping the winning bin: lower-16-bit
+//                  histogram inside it
+//   k_scores       one thread per brick: FP64 f with no contraction
+//   k_select       one CTA: threshold bisection over the FP64 keys (the N-th
+//                  largest), ties by brick index
+//   k_leaf_status  one warp per candidate leaf: constant? (prune) tile value?
+//   scans, k_fill_* tree tables, k_fill_leaves payload copy / quantization
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "vdbc_host.h"
+
+namespace vdbc {
+namespace {
+
+__device__ __forceinline__ uint32_t okey(uint32_t b) { return (b & 0x80000000u) ? ~b : (b | 0x80000000u); }
+__device__ __forceinline__ uint32_t okey_inv(uint32_t k) { return (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k; }
+
+struct Dims {
+    int nx, ny, nz;
+    int bx, by, bz;     // brick grid
+};
+
+__device__ __forceinline__ void brick_coords(const Dims& d, int b, int& bx, int& by, int& bz)
+{
+    bx = b % d.bx;
+    by = (b / d.bx) % d.by;
+    bz = b / (d.bx * d.by);
+}
+
+// ---------------------------------------------------------------- pass 1
+constexpr int kPassThreads = 256;
+
+__global__ void __launch_bounds__(kPassThreads) k_pass1(const float* __restrict__ v, Dims d,
+                                                        uint32_t* __restrict__ lo_key,
+                                                        uint32_t* __restrict__ hi_key,
+                                                        unsigned long long* __restrict__ hist,
+                                                        int* __restrict__ nonfinite)
+{
+    __shared__ uint32_t s_min[kPassThreads / 32], s_max[kPassThreads / 32];
+    __shared__ int s_bad;
+    const int b = blockIdx.x;
+    int bx, by, bz;
+    brick_coords(d, b, bx, by, bz);
+    const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
+    const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_bad = 0;
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    bool bad = false;
+    const bool valid = lane < ex;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const int rows = ey * ez;
+    constexpr int U = 4;   // rows in flight per warp
+    for (int r0 = warp * U; r0 < rows; r0 += (kPassThreads / 32) * U) {
+        uint32_t u[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            int row = r0 + q;
+            u[q] = 0;
+            if (valid && row < rows) {
+                int y = row % ey, z = row / ey;
+                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (r0 + q >= rows) break;               // warp-uniform
+            if (valid) {
+                uint32_t w = u[q];
+                bad |= ((w & 0x7f800000u) == 0x7f800000u);
+                uint32_t k = okey(w);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+                unsigned peers = __match_any_sync(vmask, w >> 16);
+                if (lane == __ffs(peers) - 1) atomicAdd(hist + (w >> 16), (unsigned long long)__popc(peers));
+            }
+        }
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
+    if (lane == 0) { s_min[warp] = kmin; s_max[warp] = kmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = s_min[0], c = s_max[0];
+        for (int w = 1; w < kPassThreads / 32; ++w) { a = min(a, s_min[w]); c = max(c, s_max[w]); }
+        lo_key[b] = a;
+        hi_key[b] = c;
+        if (s_bad) atomicOr(nonfinite, 1);
+    }
+}
+
+// most frequent of 65536 bins, ties to the smaller index; writes (out_base | idx)
+__global__ void __launch_bounds__(1024) k_argmax(const unsigned long long* __restrict__ hist,
+                                                 uint32_t* __restrict__ out, int stage)
+{
+    __shared__ unsigned long long s[32];
+    unsigned long long best = 0;
+    for (int i = threadIdx.x; i < 65536; i += 1024) {
+        unsigned long long p = (hist[i] << 16) | (unsigned long long)(0xffffu - (uint32_t)i);
+        best = p > best ? p : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+        best = t > best ? t : best;
+    }
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 32; ++w) best = s[w] > best ? s[w] : best;
+        s[0] = best > s[0] ? best : s[0];
+        uint32_t idx = 0xffffu - (uint32_t)(s[0] & 0xffffu);
+        // stage 0 -> upper 16 bits; stage 1 -> B = upper << 16 | lower
+        if (stage == 0) out[0] = idx;
+        else out[1] = (out[0] << 16) | idx;
+    }
+}
+
+// ---------------------------------------------------------------- pass 2
+__global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict__ v, Dims d,
+                                                        const uint32_t* __restrict__ lo_key,
+                                                        const uint32_t* __restrict__ hi_key,
+                                                        const uint32_t* __restrict__ bsel,
+                                                        unsigned long long* __restrict__ hist)
+{
+    const int b = blockIdx.x;
+    const uint32_t H = bsel[0];
+    // key range of the bit patterns [H<<16, H<<16 | 0xffff]
+    const uint32_t p0 = H << 16, p1 = (H << 16) | 0xffffu;
+    const uint32_t ka = min(okey(p0), okey(p1)), kb = max(okey(p0), okey(p1));
+    if (hi_key[b] < ka || lo_key[b] > kb) return;       // no value of this brick is in the bin
+    int bx, by, bz;
+    brick_coords(d, b, bx, by, bz);
+    const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
+    const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool valid = lane < ex;
+    const int rows = ey * ez;
+    for (int row = warp; row < rows; row += kPassThreads / 32) {
+        uint32_t w = 0;
+        if (valid) {
+            int y = row % ey, z = row / ey;
+            w = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+        }
+        bool in = valid && (w >> 16) == H;
+        unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            unsigned peers = __match_any_sync(m, w & 0xffffu);
+            if (lane == __ffs(peers) - 1) atomicAdd(hist + (w & 0xffffu), (unsigned long long)__popc(peers));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- scores (Eq. f1-f3)
+__global__ void k_scores(const uint32_t* __restrict__ lo_key, const uint32_t* __restrict__ hi_key,
+                         int nb, const uint32_t* __restrict__ bsel, int metric,
+                         unsigned long long* __restrict__ fkey, uint8_t* __restrict__ empty)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    uint32_t bb = bsel[1];
+    uint32_t lb = okey_inv(lo_key[i]), hb = okey_inv(hi_key[i]);
+    double B = (double)__uint_as_float(bb);
+    double lo = (double)__uint_as_float(lb), hi = (double)__uint_as_float(hb);
+    double dl = fabs(__dsub_rn(lo, B)), dh = fabs(__dsub_rn(hi, B));
+    double f;
+    if (metric == VDBC_F1) f = dl < dh ? dl : dh;
+    else if (metric == VDBC_F3) f = fabs(__dsub_rn(__ddiv_rn(__dadd_rn(lo, hi), 2.0), B));
+    else f = dl > dh ? dl : dh;
+    fkey[i] = (unsigned long long)__double_as_longlong(f);   // f >= 0: bits are monotone
+    empty[i] = (uint8_t)(lb == bb && hb == bb);
+}
+
+// ---------------------------------------------------------------- selection
+template <typename T>
+__device__ T block_sum(T x, T* s)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
+    __syncthreads();
+    T t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    return t;
+}
+
+// the N largest keys among non-empty bricks, ties to the lower index; one CTA
+__global__ void __launch_bounds__(1024) k_select(const unsigned long long* __restrict__ fkey,
+                                                 const uint8_t* __restrict__ empty, int nb,
+                                                 long long budget, uint8_t* __restrict__ active,
+                                                 long long* __restrict__ counts)
+{
+    __shared__ long long s[32];
+    __shared__ long long s_run;
+    long long m = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) m += empty[i] ? 0 : 1;
+    m = block_sum(m, s);
+    long long take = budget < m ? budget : m;
+    if (take == m || take == 0) {
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) active[i] = (take > 0 && !empty[i]) ? 1 : 0;
+        if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
+        return;
+    }
+    // bisection on the bits of the threshold T: the largest T with #{key >= T} >= take
+    unsigned long long T = 0;
+    for (int bit = 63; bit >= 0; --bit) {
+        unsigned long long cand = T | (1ull << bit);
+        long long c = 0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) c += (!empty[i] && fkey[i] >= cand) ? 1 : 0;
+        c = block_sum(c, s);
+        if (c >= take) T = cand;
+    }
+    long long gt = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) gt += (!empty[i] && fkey[i] > T) ? 1 : 0;
+    gt = block_sum(gt, s);
+    const long long need = take - gt;   // keys equal to T, lowest brick indices first
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        bool eq = i < nb && !empty[i] && fkey[i] == T;
+        // exclusive rank of this thread's tie within the chunk
+        unsigned bal = __ballot_sync(0xffffffffu, eq);
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int in_warp = __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();
+        if (lane == 0) s[w] = __popc(bal);
+        __syncthreads();
+        long long before = s_run;
+        for (int q = 0; q < w; ++q) before += s[q];
+        before += in_warp;
+        if (i < nb) active[i] = (!empty[i] && (fkey[i] > T || (eq && before < need))) ? 1 : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s[q];
+            s_run += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
+}
+
+// ---------------------------------------------------------------- exclusive scan (u32)
+constexpr int kScanBlock = 1024, kScanItems = 4;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(const uint32_t* __restrict__ in, long long n,
+                                                          uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t s[32];
+    long long base = (long long)blockIdx.x * kScanBlock * kScanItems;
+    uint32_t t = 0;
+    for (int q = 0; q < kScanItems; ++q) {
+        long long i = base + (long long)q * kScanBlock + threadIdx.x;
+        if (i < n) t += in[i];
+    }
+    t = block_sum(t, s);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(uint32_t* __restrict__ sums, int nblocks,
+                                                         uint32_t* __restrict__ total)
+{
+    __shared__ uint32_t s[32];
+    __shared__ uint32_t run;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    for (int base = 0; base < nblocks; base += kScanBlock) {
+        int i = base + threadIdx.x;
+        uint32_t x = i < nblocks ? sums[i] : 0;
+        uint32_t incl = x;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s[w] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int q = 0; q < w; ++q) wbase += s[q];
+        uint32_t r0 = run;
+        if (i < nblocks) sums[i] = r0 + wbase + incl - x;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) run = r0 + wbase + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) total[0] = run;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(const uint32_t* __restrict__ in, long long n,
+                                                           const uint32_t* __restrict__ sums,
+                                                           uint32_t* __restrict__ out)
+{
+    __shared__ uint32_t s[32];
+    __shared__ uint32_t run;
+    if (threadIdx.x == 0) run = sums[blockIdx.x];
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kScanBlock * kScanItems;
+    for (int q = 0; q < kScanItems; ++q) {
+        long long i = base + (long long)q * kScanBlock + threadIdx.x;
+        uint32_t x = i < n ? in[i] : 0;
+        uint32_t incl = x;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s[w] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int qq = 0; qq < w; ++qq) wbase += s[qq];
+        uint32_t r0 = run;
+        if (i < n) out[i] = r0 + wbase + incl - x;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) run = r0 + wbase + incl;
+        __syncthreads();
+    }
+}
+
+// exclusive scan of n u32 values; total written to total_dev[0]; tmp holds >= scan_tmp_words(n)
+long long scan_blocks(long long n) { return (n + kScanBlock * kScanItems - 1) / (kScanBlock * kScanItems); }
+
+void scan_exclusive(const uint32_t* in, uint32_t* out, long long n, uint32_t* tmp, uint32_t* total_dev,
+                    cudaStream_t s)
+{
+    long long nb = scan_blocks(n);
+    if (nb == 0) {
+        cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    KLAUNCH(k_scan_sums<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, tmp));
+    KLAUNCH(k_scan_top<<<1, kScanBlock, 0, s>>>(tmp, (int)nb, total_dev));
+    KLAUNCH(k_scan_apply<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, tmp, out));
+}
+
+// ---------------------------------------------------------------- tree build
+__global__ void k_active_list(const uint8_t* __restrict__ active, const uint32_t* __restrict__ rank, int nb,
+                              int* __restrict__ list)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb && active[i]) list[rank[i]] = i;
+}
+
+__global__ void k_u8_to_u32(const uint8_t* __restrict__ a, uint32_t* __restrict__ b, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+struct Cand {
+    int li, lj, lk;       // leaf slot (voxel >> 3)
+    int corner;           // -1 for a leaf of an active brick, 0/1 for a corner leaf
+};
+
+__device__ __forceinline__ Cand candidate(const Dims& d, const int* __restrict__ list, long long nact, long long c)
+{
+    Cand r;
+    if (c < nact * 64) {
+        int b = list[c >> 6];
+        int local = (int)(c & 63);
+        int bx, by, bz;
+        brick_coords(d, b, bx, by, bz);
+        r.li = bx * 4 + (local & 3);
+        r.lj = by * 4 + ((local >> 2) & 3);
+        r.lk = bz * 4 + (local >> 4);
+        r.corner = -1;
+    } else {
+        r.corner = (int)(c - nact * 64);
+        if (r.corner == 0) { r.li = 0; r.lj = 0; r.lk = 0; }
+        else { r.li = (d.nx - 1) >> 3; r.lj = (d.ny - 1) >> 3; r.lk = (d.nz - 1) >> 3; }
+    }
+    return r;
+}
+
+// value n (x fastest in the 8^3 leaf) of the decoded grid inside candidate leaf `c`
+__device__ __forceinline__ float cand_value(const float* __restrict__ v, const Dims& d, const Cand& c, int n,
+                                            float B)
+{
+    int x = c.li * 8 + (n & 7), y = c.lj * 8 + ((n >> 3) & 7), z = c.lk * 8 + (n >> 6);
+    if (x >= d.nx || y >= d.ny || z >= d.nz) return B;
+    if (c.corner < 0) return __ldg(v + ((size_t)z * d.ny + y) * d.nx + x);
+    bool at = (c.corner == 0) ? (x == 0 && y == 0 && z == 0)
+                              : (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
+    return at ? __ldg(v + ((size_t)z * d.ny + y) * d.nx + x) : B;
+}
+
+// status: 0 background (or inside an active brick's leaf that already holds the
+// corner), 1 constant non-background (a tile after prune), 2 a leaf
+__global__ void k_leaf_status(const float* __restrict__ v, Dims d, const int* __restrict__ list,
+                              const long long* __restrict__ counts, long long ncand_cap,
+                              const uint8_t* __restrict__ active, const uint32_t* __restrict__ bsel,
+                              uint32_t* __restrict__ is_leaf, uint32_t* __restrict__ is_tile,
+                              float* __restrict__ tval, int* __restrict__ lowslot, int lx, int ly)
+{
+    long long nact = counts[1];
+    long long ncand = nact * 64 + 2;
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= ncand_cap) return;
+    if (c >= ncand) {   // unused capacity
+        if (lane == 0) { is_leaf[c] = 0; is_tile[c] = 0; lowslot[c] = -1; }
+        return;
+    }
+    float B = __uint_as_float(bsel[1]);
+    Cand cd = candidate(d, list, nact, c);
+    if (cd.corner >= 0) {
+        int x = cd.corner == 0 ? 0 : d.nx - 1, y = cd.corner == 0 ? 0 : d.ny - 1, z = cd.corner == 0 ? 0 : d.nz - 1;
+        int b = ((z >> 5) * d.by + (y >> 5)) * d.bx + (x >> 5);
+        bool dup = active[b] || (cd.corner == 1 && d.nx <= 8 && d.ny <= 8 && d.nz <= 8);
+        if (dup) {   // covered by an active brick, or the same leaf as corner 0
+            if (lane == 0) { is_leaf[c] = 0; is_tile[c] = 0; lowslot[c] = -1; }
+            return;
+        }
+    }
+    uint32_t first = 0;
+    bool same = true;
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r) {
+        int n = lane + 32 * r;
+        float val;
+        if (cd.corner == 0 && d.nx <= 8 && d.ny <= 8 && d.nz <= 8) {
+            // a single leaf holds both corners
+            int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
+            bool at = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
+            val = (x < d.nx && y < d.ny && z < d.nz && at) ? __ldg(v + ((size_t)z * d.ny + y) * d.nx + x) : B;
+        } else {
+            val = cand_value(v, d, cd, n, B);
+        }
+        uint32_t u = __float_as_uint(val);
+        if (r == 0) first = __shfl_sync(0xffffffffu, u, 0);
+        same &= (u == first);
+    }
+    bool constant = __all_sync(0xffffffffu, same);
+    if (lane == 0) {
+        uint32_t st;
+        if (!constant) st = 2;
+        else st = (first == bsel[1]) ? 0 : 1;
+        is_leaf[c] = st == 2;
+        is_tile[c] = st == 1;
+        tval[c] = __uint_as_float(first);
+        lowslot[c] = st ? (((cd.lk >> 4) * ly + (cd.lj >> 4)) * lx + (cd.li >> 4)) : -1;
+    }
+}
+
+__global__ void k_mark_lower(const int* __restrict__ lowslot, long long ncand, uint32_t* __restrict__ lflag)
+{
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncand && lowslot[c] >= 0) lflag[lowslot[c]] = 1;
+}
+
+__global__ void k_mark_root(const uint32_t* __restrict__ lflag, int nlow, int lx, int ly, int rx, int ry,
+                            uint32_t* __restrict__ rflag)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nlow || !lflag[s]) return;
+    int li = s % lx, lj = (s / lx) % ly, lk = s / (lx * ly);
+    rflag[((lk >> 5) * ry + (lj >> 5)) * rx + (li >> 5)] = 1;
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ p, long long n, uint32_t value)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = value;
+}
+
+__global__ void k_fill_root(uint32_t* __restrict__ root, const uint32_t* __restrict__ rflag,
+                            const uint32_t* __restrict__ rrank, int nroot)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nroot) root[s] = rflag[s] ? rrank[s] : kBackgroundEntry;
+}
+
+__global__ void k_fill_upper(uint32_t* __restrict__ upper, const uint32_t* __restrict__ lflag,
+                             const uint32_t* __restrict__ lrank, const uint32_t* __restrict__ rrank, int nlow,
+                             int lx, int ly, int rx, int ry)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nlow || !lflag[s]) return;
+    int li = s % lx, lj = (s / lx) % ly, lk = s / (lx * ly);
+    uint32_t u = rrank[((lk >> 5) * ry + (lj >> 5)) * rx + (li >> 5)];
+    upper[(size_t)u * kUpperN + ((lk & 31) << 10) + ((lj & 31) << 5) + (li & 31)] = lrank[s];
+}
+
+__global__ void k_fill_lower(uint32_t* __restrict__ lower, float* __restrict__ tiles, Dims d,
+                             const int* __restrict__ list, const long long* __restrict__ counts,
+                             const int* __restrict__ lowslot, const uint32_t* __restrict__ is_leaf,
+                             const uint32_t* __restrict__ leaf_rank, const uint32_t* __restrict__ tile_rank,
+                             const float* __restrict__ tval, const uint32_t* __restrict__ lrank,
+                             const uint32_t* __restrict__ bsel)
+{
+    long long nact = counts[1];
+    long long ncand = nact * 64 + 2;
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) tiles[0] = __uint_as_float(bsel[1]);
+    if (c >= ncand || lowslot[c] < 0) return;
+    Cand cd = candidate(d, list, nact, c);
+    uint32_t entry;
+    if (is_leaf[c]) entry = leaf_rank[c];
+    else {
+        uint32_t t = 1 + tile_rank[c];
+        tiles[t] = tval[c];
+        entry = kTile | t;
+    }
+    lower[(size_t)lrank[lowslot[c]] * kLowerN + ((cd.lk & 15) << 8) + ((cd.lj & 15) << 4) + (cd.li & 15)] = entry;
+}
+
+// payload of every leaf: a copy (FP32) or the per-leaf quantized codes
+__global__ void k_fill_leaves(const float* __restrict__ v, Dims d, const int* __restrict__ list,
+                              const long long* __restrict__ counts, const uint32_t* __restrict__ is_leaf,
+                              const uint32_t* __restrict__ leaf_rank, const uint32_t* __restrict__ bsel,
+                              int payload, void* __restrict__ leaves, float2* __restrict__ meta)
+{
+    long long nact = counts[1];
+    long long ncand = nact * 64 + 2;
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= ncand || !is_leaf[c]) return;
+    float B = __uint_as_float(bsel[1]);
+    Cand cd = candidate(d, list, nact, c);
+    bool both = cd.corner == 0 && d.nx <= 8 && d.ny <= 8 && d.nz <= 8;
+    float vals[16];
+    uint32_t kmin = 0xffffffffu, kmax = 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int n = lane + 32 * r;
+        float val;
+        if (both) {
+            int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
+            bool at = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
+            val = (x < d.nx && y < d.ny && z < d.nz && at) ? __ldg(v + ((size_t)z * d.ny + y) * d.nx + x) : B;
+        } else {
+            val = cand_value(v, d, cd, n, B);
+        }
+        vals[r] = val;
+        uint32_t k = okey(__float_as_uint(val));
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+    }
+    size_t base = (size_t)leaf_rank[c] * kLeafN;
+    if (payload == VDBC_FP32) {
+        float* out = reinterpret_cast<float*>(leaves) + base;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) out[lane + 32 * r] = vals[r];
+        return;
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    float off = __uint_as_float(okey_inv(kmin));
+    float scale = __fsub_rn(__uint_as_float(okey_inv(kmax)), off);
+    if (lane == 0) meta[leaf_rank[c]] = make_float2(scale, off);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        float t = scale != 0.0f ? __fdiv_rn(__fsub_rn(vals[r], off), scale) : 0.0f;
+        int n = lane + 32 * r;
+        if (payload == VDBC_FP16) {
+            reinterpret_cast<__half*>(leaves)[base + n] = __float2half_rn(t);
+        } else {
+            reinterpret_cast<uint8_t*>(leaves)[base + n] =
+                (uint8_t)__nv_cvt_float_to_fp8(t, __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- macrocells
+// min/max of the decoded grid over each macrocell's voxels dilated by one
+// voxel (Section 4: the majorant ranges); one warp per macrocell
+__global__ void k_macrocells(GridView g, float* __restrict__ mcmin, float* __restrict__ mcmax, long long ncell)
+{
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= ncell) return;
+    int cx = (int)(c % g.mx), cy = (int)((c / g.mx) % g.my), cz = (int)(c / ((long long)g.mx * g.my));
+    int x0 = max(cx * g.mc - 1, 0), x1 = min(cx * g.mc + g.mc, g.nx - 1);
+    int y0 = max(cy * g.mc - 1, 0), y1 = min(cy * g.mc + g.mc, g.ny - 1);
+    int z0 = max(cz * g.mc - 1, 0), z1 = min(cz * g.mc + g.mc, g.nz - 1);
+    // leaf slots under the box: if all are tiles, the answer is the min/max of their values
+    int lx0 = x0 >> 3, lx1 = x1 >> 3, ly0 = y0 >> 3, ly1 = y1 >> 3, lz0 = z0 >> 3, lz1 = z1 >> 3;
+    int nl = (lx1 - lx0 + 1) * (ly1 - ly0 + 1) * (lz1 - lz0 + 1);
+    float vmin = INFINITY, vmax = -INFINITY;
+    bool all_tiles = true;
+    for (int q = lane; q < nl; q += 32) {
+        int a = lx0 + q % (lx1 - lx0 + 1);
+        int b = ly0 + (q / (lx1 - lx0 + 1)) % (ly1 - ly0 + 1);
+        int e = lz0 + q / ((lx1 - lx0 + 1) * (ly1 - ly0 + 1));
+        uint32_t en = descend_to_leaf(g, a, b, e);
+        if (en & kTile) {
+            float t = __ldg(g.tiles + (en & ~kTile));
+            vmin = fminf(vmin, t);
+            vmax = fmaxf(vmax, t);
+        } else {
+            all_tiles = false;
+        }
+    }
+    if (!__all_sync(0xffffffffu, all_tiles)) {
+        Accessor acc;
+        acc.reset();
+        int ex = x1 - x0 + 1, ey = y1 - y0 + 1, ez = z1 - z0 + 1;
+        int n = ex * ey * ez;
+        for (int q = lane; q < n; q += 32) {
+            int x = x0 + q % ex, y = y0 + (q / ex) % ey, z = z0 + q / (ex * ey);
+            float val = voxel(g, acc, x, y, z);
+            vmin = fminf(vmin, val);
+            vmax = fmaxf(vmax, val);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if (lane == 0) { mcmin[c] = vmin; mcmax[c] = vmax; }
+}
+
+// full decode, one thread per voxel (tests and the decode entry point)
+__global__ void k_decode(GridView g, float* __restrict__ out, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+        Accessor acc;
+        acc.reset();
+        out[i] = voxel(g, acc, x, y, z);
+    }
+}
+
+unsigned grid1d(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int64_t brick_bytes(int payload)
+{
+    if (payload == VDBC_FP16) return 32768 * 2 + 64 * 8;
+    if (payload == VDBC_FP8) return 32768 * 1 + 64 * 8;
+    return 32768 * 4;
+}
+
+static int payload_elem(int payload) { return payload == VDBC_FP32 ? 4 : (payload == VDBC_FP16 ? 2 : 1); }
+
+void bind_view(vdbc_grid* g)
+{
+    GridView& v = g->view;
+    const vdbc_grid_info& in = g->info;
+    char* base = static_cast<char*>(g->block);
+    v.nx = in.dims[0]; v.ny = in.dims[1]; v.nz = in.dims[2];
+    v.rx = (v.nx + 4095) / 4096; v.ry = (v.ny + 4095) / 4096; v.rz = (v.nz + 4095) / 4096;
+    v.payload = in.payload;
+    v.mc = in.macrocell;
+    v.mx = (v.nx + v.mc - 1) / v.mc; v.my = (v.ny + v.mc - 1) / v.mc; v.mz = (v.nz + v.mc - 1) / v.mc;
+    int m = std::max(v.nx, std::max(v.ny, v.nz));
+    v.inv_m = 1.0f / (float)m;
+    v.root = reinterpret_cast<const uint32_t*>(base + g->off_root);
+    v.upper = reinterpret_cast<const uint32_t*>(base + g->off_upper);
+    v.lower = reinterpret_cast<const uint32_t*>(base + g->off_lower);
+    v.tiles = reinterpret_cast<const float*>(base + g->off_tiles);
+    v.leaves = base + g->off_leaves;
+    v.meta = reinterpret_cast<const float2*>(base + g->off_meta);
+    v.mcmin = reinterpret_cast<const float*>(base + g->off_mcmin);
+    v.mcmax = reinterpret_cast<const float*>(base + g->off_mcmax);
+}
+
+// offsets of every table inside the one linear block, from the counts in g->info
+static void layout(vdbc_grid* g)
+{
+    vdbc_grid_info& in = g->info;
+    long long rx = (in.dims[0] + 4095) / 4096, ry = (in.dims[1] + 4095) / 4096, rz = (in.dims[2] + 4095) / 4096;
+    long long mc = in.macrocell;
+    long long ncell = ((in.dims[0] + mc - 1) / mc) * ((in.dims[1] + mc - 1) / mc) * ((in.dims[2] + mc - 1) / mc);
+    size_t off = 0;
+    g->off_root = off;   off = align256(off + (size_t)(rx * ry * rz) * 4);
+    g->off_upper = off;  off = align256(off + (size_t)in.n_upper * kUpperN * 4);
+    g->off_lower = off;  off = align256(off + (size_t)in.n_lower * kLowerN * 4);
+    g->off_tiles = off;  off = align256(off + (size_t)in.n_tiles * 4);
+    g->off_leaves = off; off = align256(off + (size_t)in.n_leaves * kLeafN * payload_elem(in.payload));
+    g->off_meta = off;   off = align256(off + (in.payload != VDBC_FP32 ? (size_t)in.n_leaves * 8 : 0));
+    g->off_mcmin = off;  off = align256(off + (size_t)ncell * 4);
+    g->off_mcmax = off;  off = align256(off + (size_t)ncell * 4);
+    g->block_bytes = off;
+    in.payload_bytes = (uint64_t)in.n_leaves * kLeafN * payload_elem(in.payload) +
+                       (in.payload != VDBC_FP32 ? (uint64_t)in.n_leaves * 8 : 0);
+    in.node_bytes = (uint64_t)(rx * ry * rz) * 4 + (uint64_t)in.n_upper * kUpperN * 4 +
+                    (uint64_t)in.n_lower * kLowerN * 4 + (uint64_t)in.n_tiles * 4;
+    in.total_bytes = off;
+}
+
+vdbc_status build_macrocells(vdbc_grid* g, cudaStream_t s)
+{
+    const GridView& v = g->view;
+    long long ncell = (long long)v.mx * v.my * v.mz;
+    char* base = static_cast<char*>(g->block);
+    KLAUNCH(k_macrocells<<<grid1d(ncell * 32, 256), 256, 0, s>>>(v, reinterpret_cast<float*>(base + g->off_mcmin),
+                                                          reinterpret_cast<float*>(base + g->off_mcmax), ncell));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
+
+}  // namespace vdbc
+
+using namespace vdbc;
+
+namespace {
+// scratch allocations of one encode call, released on every exit path
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    vdbc_status get(T** p, size_t count)
+    {
+        void* q = nullptr;
+        vdbc_status st = dev_alloc(&q, std::max<size_t>(count * sizeof(T), 16), s);
+        if (st != VDBC_OK) return st;
+        ptrs.push_back(q);
+        *p = static_cast<T*>(q);
+        return VDBC_OK;
+    }
+    ~Scratch()
+    {
+        for (void* q : ptrs) dev_free(q, s);
+    }
+};
+}  // namespace
+
+extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_params* params, void* stream,
+                                   vdbc_grid** out)
+{
+    clear_error();
+    if (!in || !params || !out || !in->data) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: null argument");
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a)
+        if (in->dims[a] < 1 || in->dims[a] > kMaxDim)
+            return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: dims[%d]=%d outside 1..%d", a, in->dims[a], kMaxDim);
+    double ratio = params->ratio;
+    if (!(ratio >= 1.0) || !std::isfinite(ratio))
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: ratio must be a finite value >= 1");
+    int metric = params->metric == 0 ? VDBC_F2 : params->metric;
+    if (metric < VDBC_F1 || metric > VDBC_F3) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: unknown metric %d", metric);
+    int payload = params->payload;
+    if (payload < VDBC_FP32 || payload > VDBC_FP8)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: unknown payload %d", payload);
+    int mc = params->macrocell == 0 ? 8 : params->macrocell;
+    if (mc < 1 || mc > 64) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: macrocell %d outside 1..64", mc);
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch sc(s);
+    Dims d;
+    d.nx = in->dims[0]; d.ny = in->dims[1]; d.nz = in->dims[2];
+    d.bx = (d.nx + 31) / 32; d.by = (d.ny + 31) / 32; d.bz = (d.nz + 31) / 32;
+    const long long nvox = (long long)d.nx * d.ny * d.nz;
+    const int nb = d.bx * d.by * d.bz;
+
+    const float* vol = in->data;
+    if (!in->on_device) {
+        float* dv = nullptr;
+        VDBC_TRY(sc.get(&dv, (size_t)nvox));
+        VDBC_CUDA(cudaMemcpyAsync(dv, in->data, (size_t)nvox * 4, cudaMemcpyHostToDevice, s));
+        vol = dv;
+    }
+    uint32_t *lo_key, *hi_key, *bsel, *scan_tmp, *total;
+    unsigned long long *hist, *fkey;
+    uint8_t *empty, *active;
+    int *nonfinite, *list;
+    long long* counts;
+    VDBC_TRY(sc.get(&lo_key, nb));
+    VDBC_TRY(sc.get(&hi_key, nb));
+    VDBC_TRY(sc.get(&bsel, 2));
+    VDBC_TRY(sc.get(&hist, 65536));
+    VDBC_TRY(sc.get(&fkey, nb));
+    VDBC_TRY(sc.get(&empty, nb));
+    VDBC_TRY(sc.get(&active, nb));
+    VDBC_TRY(sc.get(&nonfinite, 1));
+    VDBC_TRY(sc.get(&counts, 2));
+    VDBC_TRY(sc.get(&total, 8));
+
+    // phase 1: histogram -> B (two levels), brick ranges
+    VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
+    VDBC_CUDA(cudaMemsetAsync(nonfinite, 0, 4, s));
+    KLAUNCH(k_pass1<<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, hist, nonfinite));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0));
+    VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
+    KLAUNCH(k_pass2<<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 1));
+    // phase 2: f per brick, selection of N bricks
+    KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(lo_key, hi_key, nb, bsel, metric, fkey, empty));
+    double nbud = std::floor((double)nb * 131072.0 / (ratio * (double)brick_bytes(payload)));
+    const long long budget = nbud > (double)nb ? (long long)nb : (long long)nbud;
+    KLAUNCH(k_select<<<1, 1024, 0, s>>>(fkey, empty, nb, budget, active, counts));
+    VDBC_CUDA(cudaGetLastError());
+
+    // compact list of active bricks (x-fastest brick order)
+    uint32_t *act32, *brank;
+    VDBC_TRY(sc.get(&act32, nb));
+    VDBC_TRY(sc.get(&brank, nb));
+    long long tmp_words = std::max<long long>(scan_blocks(std::max<long long>(nb, (long long)budget * 64 + 2)) + 1, 1024);
+    VDBC_TRY(sc.get(&scan_tmp, (size_t)tmp_words + 4096));
+    KLAUNCH(k_u8_to_u32<<<grid1d(nb, 256), 256, 0, s>>>(active, act32, nb));
+    scan_exclusive(act32, brank, nb, scan_tmp, total, s);
+    VDBC_TRY(sc.get(&list, (size_t)std::max<long long>(std::min<long long>(budget, nb), 1)));
+    KLAUNCH(k_active_list<<<grid1d(nb, 256), 256, 0, s>>>(active, brank, nb, list));
+
+    // candidate leaves: 64 per active brick + the two corner leaves
+    const long long cap = std::min<long long>(budget, nb) * 64 + 2;
+    const int lx = (d.nx + 127) / 128, ly = (d.ny + 127) / 128, lz = (d.nz + 127) / 128;
+    const int nlow = lx * ly * lz;
+    const int rx = (d.nx + 4095) / 4096, ry = (d.ny + 4095) / 4096, rz = (d.nz + 4095) / 4096;
+    const int nroot = rx * ry * rz;
+    uint32_t *is_leaf, *is_tile, *leaf_rank, *tile_rank, *lflag, *lrank, *rflag, *rrank;
+    float* tval;
+    int* lowslot;
+    VDBC_TRY(sc.get(&is_leaf, cap));
+    VDBC_TRY(sc.get(&is_tile, cap));
+    VDBC_TRY(sc.get(&leaf_rank, cap));
+    VDBC_TRY(sc.get(&tile_rank, cap));
+    VDBC_TRY(sc.get(&tval, cap));
+    VDBC_TRY(sc.get(&lowslot, cap));
+    VDBC_TRY(sc.get(&lflag, nlow));
+    VDBC_TRY(sc.get(&lrank, nlow));
+    VDBC_TRY(sc.get(&rflag, nroot));
+    VDBC_TRY(sc.get(&rrank, nroot));
+    KLAUNCH(k_leaf_status<<<grid1d(cap * 32, 256), 256, 0, s>>>(vol, d, list, counts, cap, active, bsel, is_leaf, is_tile,
+                                                         tval, lowslot, lx, ly));
+    scan_exclusive(is_leaf, leaf_rank, cap, scan_tmp, total + 1, s);
+    scan_exclusive(is_tile, tile_rank, cap, scan_tmp, total + 2, s);
+    VDBC_CUDA(cudaMemsetAsync(lflag, 0, (size_t)nlow * 4, s));
+    VDBC_CUDA(cudaMemsetAsync(rflag, 0, (size_t)nroot * 4, s));
+    KLAUNCH(k_mark_lower<<<grid1d(cap, 256), 256, 0, s>>>(lowslot, cap, lflag));
+    scan_exclusive(lflag, lrank, nlow, scan_tmp, total + 3, s);
+    KLAUNCH(k_mark_root<<<grid1d(nlow, 256), 256, 0, s>>>(lflag, nlow, lx, ly, rx, ry, rflag));
+    scan_exclusive(rflag, rrank, nroot, scan_tmp, total + 4, s);
+    VDBC_CUDA(cudaGetLastError());
+
+    // the one host wait of the encoder: table sizes
+    uint32_t h_total[8] = {0};
+    long long h_counts[2] = {0, 0};
+    int h_bad = 0;
+    uint32_t h_bsel[2] = {0, 0};
+    VDBC_CUDA(cudaMemcpyAsync(h_total, total, sizeof(h_total), cudaMemcpyDeviceToHost, s));
+    VDBC_CUDA(cudaMemcpyAsync(h_counts, counts, sizeof(h_counts), cudaMemcpyDeviceToHost, s));
+    VDBC_CUDA(cudaMemcpyAsync(&h_bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VDBC_CUDA(cudaMemcpyAsync(h_bsel, bsel, sizeof(h_bsel), cudaMemcpyDeviceToHost, s));
+    vdbc_grid* g = new vdbc_grid();
+    g->active.resize(nb);
+    VDBC_CUDA(cudaMemcpyAsync(g->active.data(), active, nb, cudaMemcpyDeviceToHost, s));
+    vdbc_status ws = wait_stream(s);
+    if (ws != VDBC_OK) { delete g; return ws; }
+    if (h_bad) {
+        delete g;
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: the volume holds non-finite values");
+    }
+    cudaGetDevice(&g->device);
+    vdbc_grid_info& info = g->info;
+    info.dims[0] = d.nx; info.dims[1] = d.ny; info.dims[2] = d.nz;
+    info.payload = payload;
+    info.macrocell = mc;
+    info.metric = metric;
+    info.background_bits = h_bsel[1];
+    info.ratio = ratio;
+    info.n_bricks = nb;
+    info.n_nonempty = h_counts[0];
+    info.budget = budget;
+    info.n_active = h_counts[1];
+    info.n_leaves = h_total[1];
+    info.n_tiles = 1 + (int64_t)h_total[2];
+    info.n_lower = h_total[3];
+    info.n_upper = h_total[4];
+    layout(g);
+    vdbc_status st = dev_alloc(&g->block, g->block_bytes, s);
+    if (st != VDBC_OK) { delete g; return st; }
+    bind_view(g);
+    char* base = static_cast<char*>(g->block);
+    uint32_t* root = reinterpret_cast<uint32_t*>(base + g->off_root);
+    uint32_t* upper = reinterpret_cast<uint32_t*>(base + g->off_upper);
+    uint32_t* lower = reinterpret_cast<uint32_t*>(base + g->off_lower);
+    float* tiles = reinterpret_cast<float*>(base + g->off_tiles);
+    long long nup = (long long)info.n_upper * kUpperN, nlo = (long long)info.n_lower * kLowerN;
+    if (nup) KLAUNCH(k_fill_u32<<<grid1d(std::min<long long>(nup, 1 << 22), 256), 256, 0, s>>>(upper, nup, kBackgroundEntry));
+    if (nlo) KLAUNCH(k_fill_u32<<<grid1d(std::min<long long>(nlo, 1 << 22), 256), 256, 0, s>>>(lower, nlo, kBackgroundEntry));
+    KLAUNCH(k_fill_root<<<grid1d(nroot, 256), 256, 0, s>>>(root, rflag, rrank, nroot));
+    KLAUNCH(k_fill_upper<<<grid1d(nlow, 256), 256, 0, s>>>(upper, lflag, lrank, rrank, nlow, lx, ly, rx, ry));
+    KLAUNCH(k_fill_lower<<<grid1d(cap, 256), 256, 0, s>>>(lower, tiles, d, list, counts, lowslot, is_leaf, leaf_rank,
+                                                  tile_rank, tval, lrank, bsel));
+    KLAUNCH(k_fill_leaves<<<grid1d(cap * 32, 256), 256, 0, s>>>(vol, d, list, counts, is_leaf, leaf_rank, bsel, payload,
+                                                        base + g->off_leaves,
+                                                        reinterpret_cast<float2*>(base + g->off_meta)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: tree kernels"); }
+    st = build_macrocells(g, s);
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
+    if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: stats"); }
+    *out = g;
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_grid_decode(const vdbc_grid* g, float* out, int32_t out_on_device, void* stream)
+{
+    clear_error();
+    if (!g || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_decode: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    long long n = (long long)g->info.dims[0] * g->info.dims[1] * g->info.dims[2];
+    float* dst = out;
+    void* tmp = nullptr;
+    if (!out_on_device) {
+        VDBC_TRY(dev_alloc(&tmp, (size_t)n * 4, s));
+        dst = static_cast<float*>(tmp);
+    }
+    KLAUNCH(k_decode<<<grid1d(std::min<long long>(n, 152LL * 2048), 256), 256, 0, s>>>(g->view, dst, n));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, dst, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) { if (tmp) dev_free(tmp, s); return cuda_status(e, "vdbc_grid_decode"); }
+    if (!out_on_device) {
+        vdbc_status st = wait_stream(s);
+        dev_free(tmp, s);
+        return st;
+    }
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_grid_active_bricks(const vdbc_grid* g, uint8_t* host_out)
+{
+    clear_error();
+    if (!g || !host_out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_active_bricks: null argument");
+    std::memcpy(host_out, g->active.data(), g->active.size());
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_grid_macrocells(const vdbc_grid* g, float* host_min, float* host_max)
+{
+    clear_error();
+    if (!g || !host_min || !host_max) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_macrocells: null argument");
+    long long n = (long long)g->view.mx * g->view.my * g->view.mz;
+    const char* base = static_cast<const char*>(g->block);
+    VDBC_CUDA(cudaMemcpy(host_min, base + g->off_mcmin, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    VDBC_CUDA(cudaMemcpy(host_max, base + g->off_mcmax, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_grid_get_info(const vdbc_grid* g, vdbc_grid_info* info)
+{
+    clear_error();
+    if (!g || !info) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_get_info: null argument");
+    *info = g->info;
+    return VDBC_OK;
+}
+
+extern "C" void vdbc_grid_free(vdbc_grid* g)
+{
+    if (!g) return;
+    if (g->block) cudaFree(g->block);
+    if (g->stats) cudaFree(g->stats);
+    delete g;
+}

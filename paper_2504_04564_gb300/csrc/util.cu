@@ -1,0 +1,253 @@
+// util.cu -- error reporting, allocation, bounded waits, grid save/load and
+// the Philox entry point of libvdbc.
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+
+#include "vdbc_host.h"
+
+namespace vdbc {
+
+static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+vdbc_status set_error(vdbc_status s, const char* fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+vdbc_status cuda_status(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(VDBC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(VDBC_ERR_CUDA, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+bool fault_injected(const char* name)
+{
+    const char* f = std::getenv("VDBC_FAULT");
+    return f && std::strstr(f, name) != nullptr;
+}
+
+static void keep_pool_memory()
+{
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+vdbc_status dev_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (fault_injected("oom")) return set_error(VDBC_ERR_OOM, "device allocation of %zu bytes refused (VDBC_FAULT=oom)", bytes);
+    keep_pool_memory();
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return cuda_status(e, "cudaMallocAsync");
+    }
+    return VDBC_OK;
+}
+
+void dev_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+vdbc_status wait_stream(cudaStream_t s)
+{
+    long long limit_ms = 600000;
+    if (const char* t = std::getenv("VDBC_TIMEOUT_MS")) limit_ms = std::atoll(t);
+    if (fault_injected("timeout")) limit_ms = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int spin = 0;; ++spin) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return VDBC_OK;
+        if (e != cudaErrorNotReady) return cuda_status(e, "stream wait");
+        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (ms >= limit_ms)
+            return set_error(VDBC_ERR_TIMEOUT, "stream wait exceeded %lld ms", limit_ms);
+        if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace vdbc
+
+using namespace vdbc;
+
+extern "C" const char* vdbc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* vdbc_version(void) { return "vdbc 0.1.0 sm_103a"; }
+
+extern "C" uint64_t vdbc_kernel_launches(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- Philox
+namespace {
+__global__ void k_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    U4 r = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+}  // namespace
+
+extern "C" vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int32_t n)
+{
+    clear_error();
+    if (!ctr || !key || !out || n < 0) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_philox: bad argument");
+    if (n == 0) return VDBC_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    VDBC_CUDA(cudaMalloc(&dc, (size_t)n * 16));
+    cudaError_t e = cudaMalloc(&dout, (size_t)n * 16);
+    if (e != cudaSuccess) { cudaFree(dc); return cuda_status(e, "vdbc_philox"); }
+    e = cudaMemcpy(dc, ctr, (size_t)n * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        KLAUNCH(k_philox<<<(n + 255) / 256, 256>>>(dc, key[0], key[1], dout, n));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)n * 16, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    if (e != cudaSuccess) return cuda_status(e, "vdbc_philox");
+    return VDBC_OK;
+}
+
+// ---------------------------------------------------------------- save / load
+// File: 64-byte header {magic "VDBCGRD1", version, header bytes, info bytes,
+// block bytes, offsets[8], FNV-1a 64 of info+active+block}, then the
+// vdbc_grid_info struct, the activation flags and the linear block.
+namespace {
+constexpr char kMagic[8] = {'V', 'D', 'B', 'C', 'G', 'R', 'D', '1'};
+constexpr uint32_t kVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t info_bytes;
+    uint64_t active_bytes;
+    uint64_t block_bytes;
+    uint64_t offsets[8];
+    uint64_t checksum;
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const uint8_t* b = static_cast<const uint8_t*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 0x100000001b3ull; }
+    return h;
+}
+}  // namespace
+
+extern "C" vdbc_status vdbc_grid_save(const vdbc_grid* g, const char* path)
+{
+    clear_error();
+    if (!g || !path) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_save: null argument");
+    std::vector<uint8_t> host(g->block_bytes);
+    VDBC_CUDA(cudaMemcpy(host.data(), g->block, g->block_bytes, cudaMemcpyDeviceToHost));
+    FileHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = kVersion;
+    h.info_bytes = sizeof(vdbc_grid_info);
+    h.active_bytes = g->active.size();
+    h.block_bytes = g->block_bytes;
+    size_t offs[8] = {g->off_root, g->off_upper, g->off_lower, g->off_tiles, g->off_leaves, g->off_meta,
+                      g->off_mcmin, g->off_mcmax};
+    for (int i = 0; i < 8; ++i) h.offsets[i] = offs[i];
+    uint64_t c = 0xcbf29ce484222325ull;
+    c = fnv1a(c, &g->info, sizeof(vdbc_grid_info));
+    c = fnv1a(c, g->active.data(), g->active.size());
+    c = fnv1a(c, host.data(), host.size());
+    h.checksum = c;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_save: cannot open %s", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+              std::fwrite(&g->info, sizeof(vdbc_grid_info), 1, f) == 1 &&
+              (g->active.empty() || std::fwrite(g->active.data(), g->active.size(), 1, f) == 1) &&
+              std::fwrite(host.data(), host.size(), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_save: write to %s failed", path);
+    return VDBC_OK;
+}
+
+// Validation of the whole file happens on the host before any device work,
+// so a corrupt file is rejected without touching the GPU.
+extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid** out)
+{
+    clear_error();
+    if (!path || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_load: null argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_grid_load: cannot open %s", path);
+    FileHeader h{};
+    vdbc_grid_info info{};
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+    if (ok && (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion || h.info_bytes != sizeof(info) ||
+               h.block_bytes > (1ull << 40) || h.active_bytes > (1ull << 32))) {
+        std::fclose(f);
+        return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: %s is not a version-%u grid file", path, kVersion);
+    }
+    ok = ok && std::fread(&info, sizeof(info), 1, f) == 1;
+    std::vector<uint8_t> active(ok ? h.active_bytes : 0), host(ok ? h.block_bytes : 0);
+    ok = ok && (active.empty() || std::fread(active.data(), active.size(), 1, f) == 1);
+    ok = ok && (host.empty() || std::fread(host.data(), host.size(), 1, f) == 1);
+    bool trailing = ok && std::fgetc(f) != EOF;
+    std::fclose(f);
+    if (!ok || trailing) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: %s is truncated or too long", path);
+    uint64_t c = 0xcbf29ce484222325ull;
+    c = fnv1a(c, &info, sizeof(info));
+    c = fnv1a(c, active.data(), active.size());
+    c = fnv1a(c, host.data(), host.size());
+    if (fault_injected("format")) c ^= 1;
+    if (c != h.checksum) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: checksum mismatch in %s", path);
+    for (int a = 0; a < 3; ++a)
+        if (info.dims[a] < 1 || info.dims[a] > kMaxDim) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad dims");
+    if ((long long)active.size() != info.n_bricks || info.macrocell < 1 || info.macrocell > 64 ||
+        info.payload < VDBC_FP32 || info.payload > VDBC_FP8)
+        return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: inconsistent header");
+    for (int i = 0; i < 8; ++i)
+        if (h.offsets[i] > h.block_bytes || (h.offsets[i] & 255)) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad offsets");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    vdbc_grid* g = new vdbc_grid();
+    g->info = info;
+    g->active = std::move(active);
+    g->block_bytes = h.block_bytes;
+    g->off_root = h.offsets[0]; g->off_upper = h.offsets[1]; g->off_lower = h.offsets[2];
+    g->off_tiles = h.offsets[3]; g->off_leaves = h.offsets[4]; g->off_meta = h.offsets[5];
+    g->off_mcmin = h.offsets[6]; g->off_mcmax = h.offsets[7];
+    cudaGetDevice(&g->device);
+    vdbc_status st = dev_alloc(&g->block, g->block_bytes, s);
+    if (st == VDBC_OK) st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    cudaError_t e = cudaMemcpyAsync(g->block, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
+    if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_grid_load"); }
+    bind_view(g);
+    st = wait_stream(s);     // `host` must outlive the copy
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    *out = g;
+    return VDBC_OK;
+}

@@ -1,0 +1,191 @@
+// vdbc_device.cuh -- device-side data layout and lookup code of the grid.
+//
+// Layout (this library's own; the paper's NanoVDB is prior art, not copied):
+//   one linear device block holds, at 256-byte aligned offsets,
+//   root   u32[nroot]               dense table over the 4096^3 regions
+//   upper  u32[n_upper * 32768]     32^3 children of 128^3 voxels each
+//   lower  u32[n_lower * 4096]      16^3 children of 8^3 voxels each
+//   tiles  f32[n_tiles]             tile values; tiles[0] is the background
+//   leaves payload[n_leaves * 512]  8^3 values, x fastest (f32, f16 or e4m3)
+//   meta   float2[n_leaves]         (scale, offset) of quantized leaves
+//   mcmin, mcmax f32[n_macrocells]  min/max of the decoded grid per macrocell
+// An entry of root/upper/lower is a child index (bit 31 clear) or a tile
+// (bit 31 set, low bits index `tiles`).  This is the {5,4,3} tree of Section
+// 2.3 with the root made a dense table because the input is a bounded
+// structured-regular volume.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace vdbc {
+
+constexpr uint32_t kTile = 0x80000000u;
+constexpr uint32_t kBackgroundEntry = 0x80000000u;   // tile 0
+constexpr int kUpperN = 32768, kLowerN = 4096, kLeafN = 512;
+constexpr int kMaxDim = 8192;
+
+struct GridView {
+    int nx, ny, nz;
+    int rx, ry, rz;           // root table size = ceil(dims / 4096)
+    int payload;              // 0 f32, 1 f16, 2 e4m3
+    int mc;                   // macrocell edge
+    int mx, my, mz;           // macrocell grid
+    float inv_m;              // 1 / max(dims)
+    const uint32_t* root;
+    const uint32_t* upper;
+    const uint32_t* lower;
+    const float* tiles;
+    const void* leaves;
+    const float2* meta;
+    const float* mcmin;
+    const float* mcmax;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: 10 rounds of two 32x32 multiplies, key bumped by the
+// Weyl constants between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ float u01(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------- leaf payload decode
+__device__ __forceinline__ float e4m3_to_float(uint8_t b)
+{
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+__device__ __forceinline__ float leaf_value(const GridView& g, uint32_t leaf, int off, float2 sm)
+{
+    if (g.payload == 0) return __ldg(reinterpret_cast<const float*>(g.leaves) + (size_t)leaf * kLeafN + off);
+    if (g.payload == 1) {
+        __half h = reinterpret_cast<const __half*>(g.leaves)[(size_t)leaf * kLeafN + off];
+        return __fmaf_rn(sm.x, __half2float(h), sm.y);
+    }
+    uint8_t b = reinterpret_cast<const uint8_t*>(g.leaves)[(size_t)leaf * kLeafN + off];
+    return __fmaf_rn(sm.x, e4m3_to_float(b), sm.y);
+}
+
+// ---------------------------------------------------------------- descent
+// entry of the lower level that covers voxel-leaf (li,lj,lk) = (i>>3, j>>3, k>>3)
+__device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, int lj, int lk)
+{
+    int i = li << 3, j = lj << 3, k = lk << 3;
+    uint32_t e = __ldg(g.root + ((k >> 12) * g.ry + (j >> 12)) * g.rx + (i >> 12));
+    if (e & kTile) return e;
+    e = __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
+    if (e & kTile) return e;
+    return __ldg(g.lower + (size_t)e * kLowerN + (((k >> 3) & 15) << 8) + (((j >> 3) & 15) << 4) + ((i >> 3) & 15));
+}
+
+// per-thread cached accessor: remembers the last leaf-level entry (Section
+// 3.2.2: NanoVDB's accessors cache the path of the last lookup)
+struct Accessor {
+    int li, lj, lk;
+    uint32_t entry;
+    float2 sm;
+    __device__ __forceinline__ void reset() { li = -1; lj = -1; lk = -1; entry = kBackgroundEntry; sm = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ uint32_t leaf(const GridView& g, int a, int b, int c)
+    {
+        if (a != li || b != lj || c != lk) {
+            li = a; lj = b; lk = c;
+            entry = descend_to_leaf(g, a, b, c);
+            if (g.payload != 0 && !(entry & kTile)) sm = __ldg(g.meta + entry);
+        }
+        return entry;
+    }
+};
+
+__device__ __forceinline__ float voxel(const GridView& g, Accessor& acc, int i, int j, int k)
+{
+    uint32_t e = acc.leaf(g, i >> 3, j >> 3, k >> 3);
+    if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
+    return leaf_value(g, e, ((k & 7) << 6) | ((j & 7) << 3) | (i & 7), acc.sm);
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
+
+// trilinear reconstruction at index-space position p, clamp to edge
+struct VdbSampler {
+    GridView g;
+    __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor& acc) const
+    {
+        float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+        float tx = px - fx, ty = py - fy, tz = pz - fz;
+        int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
+        int x0 = min(max(i0, 0), g.nx - 1), x1 = min(max(i0 + 1, 0), g.nx - 1);
+        int y0 = min(max(j0, 0), g.ny - 1), y1 = min(max(j0 + 1, 0), g.ny - 1);
+        int z0 = min(max(k0, 0), g.nz - 1), z1 = min(max(k0 + 1, 0), g.nz - 1);
+        float v000, v100, v010, v110, v001, v101, v011, v111;
+        if ((x0 >> 3) == (x1 >> 3) && (y0 >> 3) == (y1 >> 3) && (z0 >> 3) == (z1 >> 3)) {
+            uint32_t e = acc.leaf(g, x0 >> 3, y0 >> 3, z0 >> 3);
+            if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
+            int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
+            int az = (z0 & 7) << 6, bz = (z1 & 7) << 6;
+            float2 sm = acc.sm;
+            v000 = leaf_value(g, e, az | ay | ax, sm); v100 = leaf_value(g, e, az | ay | bx, sm);
+            v010 = leaf_value(g, e, az | by | ax, sm); v110 = leaf_value(g, e, az | by | bx, sm);
+            v001 = leaf_value(g, e, bz | ay | ax, sm); v101 = leaf_value(g, e, bz | ay | bx, sm);
+            v011 = leaf_value(g, e, bz | by | ax, sm); v111 = leaf_value(g, e, bz | by | bx, sm);
+        } else {
+            v000 = voxel(g, acc, x0, y0, z0); v100 = voxel(g, acc, x1, y0, z0);
+            v010 = voxel(g, acc, x0, y1, z0); v110 = voxel(g, acc, x1, y1, z0);
+            v001 = voxel(g, acc, x0, y0, z1); v101 = voxel(g, acc, x1, y0, z1);
+            v011 = voxel(g, acc, x0, y1, z1); v111 = voxel(g, acc, x1, y1, z1);
+        }
+        float c00 = lerpf(v000, v100, tx), c10 = lerpf(v010, v110, tx);
+        float c01 = lerpf(v001, v101, tx), c11 = lerpf(v011, v111, tx);
+        float c0 = lerpf(c00, c10, ty), c1 = lerpf(c01, c11, ty);
+        return lerpf(c0, c1, tz);
+    }
+};
+
+// plain form, linear device array, the same software trilinear
+struct LinearSampler {
+    const float* d;
+    int nx, ny, nz;
+    __device__ __forceinline__ float at(int i, int j, int k) const
+    {
+        return __ldg(d + ((size_t)k * ny + j) * nx + i);
+    }
+    __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor&) const
+    {
+        float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+        float tx = px - fx, ty = py - fy, tz = pz - fz;
+        int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
+        int x0 = min(max(i0, 0), nx - 1), x1 = min(max(i0 + 1, 0), nx - 1);
+        int y0 = min(max(j0, 0), ny - 1), y1 = min(max(j0 + 1, 0), ny - 1);
+        int z0 = min(max(k0, 0), nz - 1), z1 = min(max(k0 + 1, 0), nz - 1);
+        float c00 = lerpf(at(x0, y0, z0), at(x1, y0, z0), tx), c10 = lerpf(at(x0, y1, z0), at(x1, y1, z0), tx);
+        float c01 = lerpf(at(x0, y0, z1), at(x1, y0, z1), tx), c11 = lerpf(at(x0, y1, z1), at(x1, y1, z1), tx);
+        return lerpf(lerpf(c00, c10, ty), lerpf(c01, c11, ty), tz);
+    }
+};
+
+// plain form, 3D CUDA texture with hardware trilinear and clamp addressing
+// (unnormalized coordinates: texel centres sit at i + 1/2)
+struct TexSampler {
+    cudaTextureObject_t tex;
+    __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor&) const
+    {
+        return tex3D<float>(tex, px + 0.5f, py + 0.5f, pz + 0.5f);
+    }
+};
+
+}  // namespace vdbc

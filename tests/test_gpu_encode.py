@@ -1,0 +1,190 @@
+"""GPU encoder parity against the CPU oracle (bit-exact: the background value,
+the activated brick set, every decoded voxel, the macrocell ranges, the leaf
+count), plus the input generator's device build against its host build."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import oracle
+    import paper_2504_04564_gb300 as v
+    import volgen
+    return dict(torch=torch, v=v, orc=oracle, vg=volgen, dev=torch.device("cuda:0"))
+
+
+def encode_both(env, host, ratio, metric=2, payload=0, macrocell=8):
+    torch, v, orc = env["torch"], env["v"], env["orc"]
+    vol = torch.from_numpy(host).to(env["dev"])
+    grid = v.vdbc_encode(vol, ratio, metric=metric, payload=payload, macrocell=macrocell)
+    e = orc.encode(host, ratio, metric=metric, payload=payload)
+    return vol, grid, e
+
+
+def check_encoding(env, host, ratio, metric=2, payload=0, macrocell=8):
+    torch, v, orc = env["torch"], env["v"], env["orc"]
+    vol, grid, e = encode_both(env, host, ratio, metric, payload, macrocell)
+    info = grid.info
+    assert info.background_bits == e["background_bits"]
+    assert info.n_bricks == e["lo"].size
+    assert info.budget == e["budget"] and info.n_active == e["n_active"]
+    assert info.n_nonempty == int((e["empty"] == 0).sum())
+    assert np.array_equal(v.vdbc_grid_active_bricks(grid), e["active"])
+    D = orc.decode_dense(host, e["active"], e["background_bits"], payload)
+    dec = torch.empty_like(vol)
+    v.vdbc_grid_decode(grid, dec)
+    got = dec.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), D.view(np.uint32))
+    # host-output decode path as well
+    got2 = np.empty_like(host)
+    v.vdbc_grid_decode(grid, got2)
+    assert np.array_equal(got2.view(np.uint32), D.view(np.uint32))
+    # leaf count after prune equals the oracle tree's
+    t = orc.Tree(host, e["active"], e["background_bits"], payload)
+    c = t.counts()
+    assert info.n_leaves == c["leaves"]
+    assert info.n_lower == c["lower"] and info.n_upper == c["upper"]
+    # macrocell min/max of the decoded grid
+    mn, mx = v.vdbc_grid_macrocells(grid)
+    omn, omx = orc.macrocell_minmax(D, macrocell)
+    assert np.array_equal(mn, omn) and np.array_equal(mx, omx)
+    return grid, e, D
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (40, 33, 17), (97, 70, 33), (1, 1, 1), (3, 70, 9), (130, 8, 129)])
+@pytest.mark.parametrize("ratio", [1.0, 4.0, 10.0])
+def test_encoder_bit_exact_fp32(env, dims, ratio):
+    host = env["vg"].generate_host(env["vg"].make_params("blobs", dims, 1))
+    check_encoding(env, host, ratio)
+
+
+@pytest.mark.parametrize("metric", [1, 2, 3])
+@pytest.mark.parametrize("payload", [1, 2])
+def test_encoder_bit_exact_metrics_and_quantized_payloads(env, metric, payload):
+    host = env["vg"].generate_host(env["vg"].make_params("turbulence", (96, 80, 72), 3))
+    check_encoding(env, host, 6.0, metric=metric, payload=payload)
+
+
+@pytest.mark.parametrize("macrocell", [4, 8, 13])
+def test_macrocell_sizes(env, macrocell):
+    host = env["vg"].generate_host(env["vg"].make_params("blobs", (50, 41, 66), 2))
+    check_encoding(env, host, 2.0, macrocell=macrocell)
+
+
+def test_degenerate_volumes(env):
+    vg = env["vg"]
+    # all zero: every brick is empty, only the (background) corners remain -> no leaves
+    z = np.zeros((37, 20, 45), dtype=np.float32)
+    grid, e, D = check_encoding(env, z, 1.0)
+    assert grid.info.n_leaves == 0 and grid.info.n_active == 0
+    # constant non-zero bricks prune to tiles; ties in f everywhere
+    c = np.zeros((64, 64, 64), dtype=np.float32)
+    c[:32] = 0.5
+    grid, e, D = check_encoding(env, c, 1.0)
+    assert grid.info.n_leaves == 0 and grid.info.n_tiles > 1
+    # corner values differing from the background with nothing activated
+    k = np.zeros((40, 33, 17), dtype=np.float32)
+    k[0, 0, 0], k[-1, -1, -1], k[20, 20, 10] = 0.3, 0.7, 0.9
+    grid, e, D = check_encoding(env, k, 1000.0)
+    assert grid.info.n_active == 0 and grid.info.n_leaves == 2
+    # both corners inside one leaf
+    s = np.arange(27, dtype=np.float32).reshape(3, 3, 3) / 27
+    check_encoding(env, s, 100.0)
+    # dense noise, lossless (the paper's worst case)
+    n = vg.generate_host(vg.make_params("noise", (64, 64, 64), 5))
+    grid, e, D = check_encoding(env, n, 1.0)
+    assert grid.info.n_active == 8 and grid.info.n_leaves == 512
+
+
+def test_encoder_rejects_non_finite(env):
+    torch, v = env["torch"], env["v"]
+    a = np.zeros((16, 16, 16), dtype=np.float32)
+    a[3, 4, 5] = np.inf
+    with pytest.raises(v.VdbcError) as ex:
+        v.vdbc_encode(torch.from_numpy(a).to(env["dev"]), 2.0)
+    assert ex.value.status == v.ERR_INVALID_ARG
+
+
+def test_host_input_equals_device_input(env):
+    v = env["v"]
+    host = env["vg"].generate_host(env["vg"].make_params("blobs", (70, 64, 50), 9))
+    g1 = v.vdbc_encode(host, 4.0)
+    vol, g2, _ = encode_both(env, host, 4.0)
+    a = np.empty_like(host)
+    b = np.empty_like(host)
+    v.vdbc_grid_decode(g1, a)
+    v.vdbc_grid_decode(g2, b)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_save_load_roundtrip_and_corruption(env, tmp_path):
+    v = env["v"]
+    host = env["vg"].generate_host(env["vg"].make_params("turbulence", (64, 48, 80), 4))
+    g1 = v.vdbc_encode(host, 3.0, payload=1)
+    path = str(tmp_path / "g.vdbc")
+    v.vdbc_grid_save(g1, path)
+    g2 = v.vdbc_grid_load(path)
+    assert g2.info.as_dict() == g1.info.as_dict()
+    a = np.empty_like(host)
+    b = np.empty_like(host)
+    v.vdbc_grid_decode(g1, a)
+    v.vdbc_grid_decode(g2, b)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert np.array_equal(v.vdbc_grid_macrocells(g1)[1], v.vdbc_grid_macrocells(g2)[1])
+    raw = bytearray(open(path, "rb").read())
+    raw[len(raw) // 2] ^= 0x40
+    bad = str(tmp_path / "bad.vdbc")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(v.VdbcError) as ex:
+        v.vdbc_grid_load(bad)
+    assert ex.value.status == v.ERR_FORMAT
+
+
+def test_injected_allocation_failure(env, monkeypatch):
+    """Host-side fault injection: VDBC_FAULT=oom refuses every device allocation
+    before it is made; the call reports OOM and the context stays usable."""
+    v = env["v"]
+    host = env["vg"].generate_host(env["vg"].make_params("blobs", (32, 32, 32), 0))
+    monkeypatch.setenv("VDBC_FAULT", "oom")
+    with pytest.raises(v.VdbcError) as ex:
+        v.vdbc_encode(host, 2.0)
+    assert ex.value.status == v.ERR_OOM
+    monkeypatch.delenv("VDBC_FAULT")
+    g = v.vdbc_encode(host, 2.0)
+    assert g.info.n_active > 0
+
+
+def test_device_generator_matches_host(env):
+    torch, vg = env["torch"], env["vg"]
+    for kind, dims in (("blobs", (64, 64, 64)), ("turbulence", (72, 64, 80)), ("cloud", (66, 45, 81)),
+                       ("noise", (33, 17, 9))):
+        p = vg.make_params(kind, dims, 2)
+        h = vg.generate_host(p)
+        d = vg.generate_torch(p).cpu().numpy()
+        assert np.array_equal(h.view(np.uint32), d.view(np.uint32)), kind
+
+
+def test_full_size_turbulence_encoding(env):
+    """The 512^3 medium at 1:10, as the benchmark encodes it: B, the 409
+    activated bricks and sampled decoded voxels against the oracle."""
+    torch, v, orc, vg = env["torch"], env["v"], env["orc"], env["vg"]
+    p = vg.make_params("turbulence", (512, 512, 512), 0)
+    host = vg.generate_host(p)
+    vol = vg.generate_torch(p)
+    grid = v.vdbc_encode(vol, 10.0)
+    e = orc.encode(host, 10.0)
+    assert grid.info.n_active == 409 == e["n_active"]
+    assert grid.info.background_bits == e["background_bits"]
+    assert np.array_equal(v.vdbc_grid_active_bricks(grid), e["active"])
+    dec = torch.empty_like(vol)
+    v.vdbc_grid_decode(grid, dec)
+    D = orc.decode_dense(host, e["active"], e["background_bits"])
+    got = dec.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), D.view(np.uint32))

@@ -1,0 +1,50 @@
+"""Scene definitions shared by the tests, smoke and the benchmark.
+
+Each workload is named by what it is; camera and light follow the readings
+listed in the design doc (pinhole at the volume centre + 1.6 x normalize(0.6, 0.4,
+0.7), fov 40 deg; sun along normalize(1, 1, 0.5) with irradiance 3; constant
+environment 0.25; transfer function a linear grey ramp).
+"""
+import math
+
+import numpy as np
+
+SUN = tuple(np.array([1.0, 1.0, 0.5]) / np.linalg.norm([1.0, 1.0, 0.5]))
+
+
+def world_extent(dims):
+    M = max(dims)
+    return tuple(d / M for d in dims)
+
+
+def ortho_plus_z(dims, width, height):
+    """(kind, w, h, eye, look, up, height) of an orthographic camera on the +z
+    axis whose image covers the volume's x-y extent."""
+    ex, ey, ez = world_extent(dims)
+    return (0, width, height, (0.5 * ex, 0.5 * ey, -1.0), (0.5 * ex, 0.5 * ey, 0.0), (0, 1, 0), ey)
+
+
+def pinhole_orbit(dims, width, height, dist=1.6, direction=(0.6, 0.4, 0.7), fovy=40.0):
+    ex, ey, ez = world_extent(dims)
+    c = np.array([0.5 * ex, 0.5 * ey, 0.5 * ez])
+    d = np.array(direction, dtype=np.float64)
+    d /= np.linalg.norm(d)
+    eye = c + dist * d
+    return (1, width, height, tuple(eye), tuple(c), (0, 1, 0), fovy)
+
+
+def linear_ramp_tf(n=256):
+    r = np.arange(n, dtype=np.float64) / (n - 1)
+    return np.stack([r, r, r, r], axis=1).astype(np.float32)
+
+
+def pt_medium_args(density_scale=20.0, albedo=0.9, g=0.6, max_bounces=16):
+    return dict(density_scale=density_scale, albedo=albedo, g=g, max_bounces=max_bounces, sun_dir=SUN,
+                sun_rad=(3.0, 3.0, 3.0), env_rad=(0.25, 0.25, 0.25))
+
+
+# the 512^3 turbulent medium at 1:10, 1024^2 x 16 spp, albedo 0.9, g 0.6, 16 bounces
+TURBULENCE_512 = dict(kind="turbulence", dims=(512, 512, 512), seed=0, ratio=10.0, width=1024, height=1024,
+                      spp=16, medium=pt_medium_args())
+# the 64^3 blobs volume at 1:4, EA, 128^2, step 0.5, ortho +z
+BLOBS_64_EA = dict(kind="blobs", dims=(64, 64, 64), seed=0, ratio=4.0, width=128, height=128, step=0.5)
