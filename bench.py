@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="the ncu capture case: the same workload at a 256x256 image, two renders")
     return ap.parse_args()
 
 
@@ -244,7 +246,7 @@ def run_vdbc(args):
     achieved = lookups * 32.0 / (render_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-            "kernel": "k_pt<VdbSampler>", "peak_source": peak_kind,
+            "kernel": "k_pt<VdbSamplerT<0>>", "peak_source": peak_kind,
             "algorithmic_bytes_per_lookup": 32}
 
     # --- comparator: the same renderer on the dense 3D texture; PSNR
@@ -409,9 +411,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case():
+    """The capture case for `ncu --set full`: the 512^3 medium at 1:10 (same
+    grid as the benchmark), rendered twice at 256x256 x 16 spp so that a
+    full-section capture of the second launch stays small."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2504_04564_gb300 as v
+    import volgen
+    from volgen import scenes
+
+    w = scenes.TURBULENCE_512
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 256, 256))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
+    g = v.vdbc_encode(vol, w["ratio"])
+    img = torch.empty((256, 256, 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        v.vdbc_render(g, cam, med, w["spp"], 2024, img)
+    torch.cuda.synchronize()
+    st = v.vdbc_render_stats_get(g)
+    print(json.dumps({"profile_case": "turbulence512_r10_pt256sq_16spp", "lookups": int(st.lookups),
+                      "paths": int(st.paths)}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_case:
+        run_profile_case()
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_vdbc(a)

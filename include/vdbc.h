@@ -135,6 +135,9 @@ typedef struct {
     uint64_t lookups;          /* density lookups (trilinear reconstructions) */
     uint64_t paths;
     uint64_t error_flags;      /* nonzero if a kernel hit one of its bounds */
+    uint64_t events[6];        /* only in builds with VDBC_STATS defined, else 0: tracker loop
+                                  iterations, DDA cells examined, coarse blocks crossed, free
+                                  flights drawn, rays started, paths fetched */
 } vdbc_render_stats;
 
 /*

@@ -13,13 +13,15 @@
  *    (the support of trilinear reconstruction inside the cell);
  *  - majorant of a cell = density_scale * max / M per index unit;
  *  - 3D-DDA over macrocells (Section 4, Amanatides-Woo stepping); Woodcock
- *    (delta) tracking inside each non-empty cell, restarting at the next
- *    cell on overshoot (Section 4); cells of zero majorant or zero length
- *    draw no random numbers;
+ *    (delta) tracking with one optical depth per free flight carried across
+ *    the non-empty cells (the majorant-grid free-path sampling of
+ *    Szirmay-Kalos et al. 2011 that Section 4 cites for its DDA); cells of
+ *    zero majorant or zero length consume nothing;
  *  - ratio tracking for the transmittance toward the directional light;
  *  - Philox counter = (pixel, sample, call, stream), key = seed; stream 0 is
  *    the camera and the scattering walk, stream 1 the light rays; each call
- *    gives u0 (distance), u1 (accept test), u2/u3 (phase function);
+ *    gives u0 (optical depth of a free flight), u1 (accept test), u2/u3
+ *    (phase function);
  *  - Henyey-Greenstein phase function; orthonormal basis of Duff et al.,
  *    "Building an Orthonormal Basis, Revisited" (JCGT 2017);
  *  - a path scatters at most max_bounces times; each scattering event adds
@@ -310,24 +312,33 @@ static double majorant(const walk_ctx* w, int64_t cell)
     return w->m->density_scale * (double)w->cmax[cell] * w->inv_m;
 }
 
-/* Woodcock tracking through the macrocells; returns 1 on a real collision
- * with its distance and the phase-function numbers of that step */
+/* Woodcock tracking over the macrocell grid (Section 4, with the DDA of
+ * Szirmay-Kalos et al. 2011 that it cites): one optical depth
+ * tau = -ln(1 - u0) is drawn per tentative collision and spent along the
+ * ray, majorant times length per non-empty cell; where it runs out inside a
+ * cell, the density there decides (u1) between a real collision (phase
+ * function numbers u2, u3) and a new draw from that point.  Cells of zero
+ * majorant neither consume tau nor draw.  Returns 1 on a real collision. */
 static int delta_track(const walk_ctx* w, const double o[3], const double dir[3], double tmin,
                        double tmax, uint32_t* call, double* thit, double xi[2])
 {
     dda_t s;
     dda_init(&s, w->dims, w->m->macrocell, o, dir, tmin, tmax);
     int64_t cell;
-    double texit;
+    double texit, tau = -1.0, u[4] = {0, 0, 0, 0};
     while (dda_cell(&s, &cell, &texit)) {
         double mj = majorant(w, cell);
         if (mj > 0.0 && texit > s.t) {
             double t = s.t;
             for (;;) {
-                double u[4];
-                rng(w, (*call)++, 0, u);
-                t = t - log(1.0 - u[0]) / mj;
-                if (t >= texit) break;
+                if (tau < 0.0) {
+                    rng(w, (*call)++, 0, u);
+                    tau = -log(1.0 - u[0]);
+                }
+                double reach = mj * (texit - t);
+                if (!(tau < reach)) { tau -= reach; break; }
+                t = t + tau / mj;
+                tau = -1.0;
                 if (u[1] * mj < sigma_at(w, o, dir, t)) {
                     *thit = t; xi[0] = u[2]; xi[1] = u[3];
                     return 1;
@@ -339,23 +350,28 @@ static int delta_track(const walk_ctx* w, const double o[3], const double dir[3]
     return 0;
 }
 
-/* ratio tracking: product of (1 - sigma/majorant) over tentative collisions */
+/* ratio tracking: the same free flights; every tentative collision
+ * multiplies the transmittance by (1 - sigma / majorant) */
 static double ratio_track(const walk_ctx* w, const double o[3], const double dir[3],
                           double tmin, double tmax, uint32_t* call)
 {
     dda_t s;
     dda_init(&s, w->dims, w->m->macrocell, o, dir, tmin, tmax);
     int64_t cell;
-    double texit, T = 1.0;
+    double texit, T = 1.0, tau = -1.0, u[4] = {0, 0, 0, 0};
     while (dda_cell(&s, &cell, &texit)) {
         double mj = majorant(w, cell);
         if (mj > 0.0 && texit > s.t) {
             double t = s.t;
             for (;;) {
-                double u[4];
-                rng(w, (*call)++, 1, u);
-                t = t - log(1.0 - u[0]) / mj;
-                if (t >= texit) break;
+                if (tau < 0.0) {
+                    rng(w, (*call)++, 1, u);
+                    tau = -log(1.0 - u[0]);
+                }
+                double reach = mj * (texit - t);
+                if (!(tau < reach)) { tau -= reach; break; }
+                t = t + tau / mj;
+                tau = -1.0;
                 T *= 1.0 - sigma_at(w, o, dir, t) / mj;
             }
         }

@@ -77,7 +77,8 @@ class Medium(ctypes.Structure):
 
 
 class RenderStats(ctypes.Structure):
-    _fields_ = [("lookups", ctypes.c_uint64), ("paths", ctypes.c_uint64), ("error_flags", ctypes.c_uint64)]
+    _fields_ = [("lookups", ctypes.c_uint64), ("paths", ctypes.c_uint64), ("error_flags", ctypes.c_uint64),
+                ("events", ctypes.c_uint64 * 6)]
 
 
 _lib = None

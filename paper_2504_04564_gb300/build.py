@@ -17,6 +17,9 @@ LIB = os.path.join(BUILD, "libvdbc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["encode.cu", "render.cu", "util.cu"]
+# render.cu fuses multiply-adds only where the source says so (__fmaf_rn), so
+# every sampler instantiation of the tracker computes the same bits
+PER_FILE_FLAGS = {"render.cu": ["--fmad=false"]}
 HEADERS = ["vdbc_device.cuh", "vdbc_host.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -48,7 +51,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = ["nvcc"] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = ["nvcc"] + flags + PER_FILE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for cmd, p in procs:
         out, _ = p.communicate()

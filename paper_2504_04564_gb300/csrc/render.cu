@@ -3,21 +3,25 @@
 //
 //   k_ea  emission-absorption marching, fixed step, front to back; one
 //         thread per pixel (the project's sci-vis mode)
-//   k_pt  Monte Carlo path tracing: 3D-DDA over the macrocell majorant grid,
-//         Woodcock (delta) tracking inside every non-empty cell with a restart
-//         at the next cell on overshoot, Henyey-Greenstein scattering, the
-//         directional light's transmittance by ratio tracking, a constant
-//         environment on escape.  One thread per pixel loops over its spp
-//         paths so the per-pixel sum has a fixed order.
-// Both are templated on the sampler: VdbSampler (tree descent + leaf decode +
-// trilinear, every lookup), LinearSampler (dense array, the same software
-// trilinear) and TexSampler (3D CUDA texture, hardware trilinear).
+//   k_pt  Monte Carlo path tracing: 3D-DDA over the macrocell majorant grid
+//         (with a coarse occupancy level that crosses empty 8^3 blocks of
+//         macrocells in one step), Woodcock (delta) tracking with one optical
+//         depth per free flight carried across the non-empty cells (the
+//         free-path sampling of Szirmay-Kalos et al. 2011 that Section 4 cites),
+//         Henyey-Greenstein scattering, the directional light's transmittance
+//         by ratio tracking, a constant environment on escape.  Persistent
+//         lanes each carry one path and fetch the next when it ends; path
+//         radiance is averaged per pixel in sample order by k_pt_reduce.
+// Both are templated on the sampler: VdbSamplerT<payload> (tree descent + leaf
+// decode + trilinear, every lookup), LinearSampler (dense array, the same
+// software trilinear) and TexSampler (3D CUDA texture, hardware trilinear).
 //
 // Random numbers: Philox4x32-10, counter (pixel, sample, call, stream), key =
 // seed; stream 0 for the camera and the walk, 1 for the light rays; one call
-// per event, u0 = distance, u1 = accept, u2/u3 = phase function.
+// per free flight: u0 = optical depth, u1 = accept, u2/u3 = phase function.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "vdbc_host.h"
@@ -49,6 +53,10 @@ struct Majorants {
     int mx, my, mz;
     int nx, ny, nz;
 };
+
+// coarse occupancy level over kCoarse^3 macrocells: a ray crosses an empty
+// coarse cell in one step instead of one step per macrocell
+constexpr int kCoarse = 8;
 
 constexpr int kMaxStepsPerCell = 1 << 20;
 
@@ -82,21 +90,24 @@ __device__ __forceinline__ bool clip_box(const Majorants& m, float3 o, float3 d,
     return t0 < t1;
 }
 
-// 3D-DDA over the macrocells (Amanatides-Woo stepping, boundaries recomputed
-// from the cell index every step so no error accumulates)
+// 3D-DDA over the macrocells (Amanatides-Woo stepping).  The next boundary of
+// each axis is kept and only the stepped axis is recomputed, from its cell
+// index (-1/2 + (c + [s > 0]) * cell - o) / d, so no error accumulates.
 struct Dda {
     int cx, cy, cz, sx, sy, sz;
+    float ix, iy, iz;       // 1 / d per axis
+    float nx, ny, nz;       // t of the next boundary per axis
     float t, tmax;
-    __device__ __forceinline__ static float bnd(int c, int s, float mc, float o, float d)
+    __device__ __forceinline__ static float bnd(int c, int s, float mc, float o, float inv)
     {
         if (s == 0) return INFINITY;
-        float b = -0.5f + (float)(c + (s > 0 ? 1 : 0)) * mc;
-        return (b - o) / d;
+        float b = __fadd_rn(-0.5f, __fmul_rn((float)(c + (s > 0 ? 1 : 0)), mc));
+        return __fmul_rn(__fsub_rn(b, o), inv);
     }
     __device__ __forceinline__ static int first_cell(float o, float d, float tmin, float mc, int n)
     {
-        float p = o + tmin * d;
-        int ci = (int)floorf((p + 0.5f) / mc);
+        float p = __fmaf_rn(tmin, d, o);
+        int ci = (int)floorf(__fdiv_rn(__fadd_rn(p, 0.5f), mc));
         return min(max(ci, 0), n - 1);
     }
     __device__ __forceinline__ void init(const Majorants& m, float3 o, float3 d, float tmin, float tmax_)
@@ -107,36 +118,64 @@ struct Dda {
         sx = d.x > 0.0f ? 1 : (d.x < 0.0f ? -1 : 0);
         sy = d.y > 0.0f ? 1 : (d.y < 0.0f ? -1 : 0);
         sz = d.z > 0.0f ? 1 : (d.z < 0.0f ? -1 : 0);
+        ix = 1.0f / d.x; iy = 1.0f / d.y; iz = 1.0f / d.z;
         cx = first_cell(o.x, d.x, tmin, mc, m.mx);
         cy = first_cell(o.y, d.y, tmin, mc, m.my);
         cz = first_cell(o.z, d.z, tmin, mc, m.mz);
+        nx = bnd(cx, sx, mc, o.x, ix);
+        ny = bnd(cy, sy, mc, o.y, iy);
+        nz = bnd(cz, sz, mc, o.z, iz);
     }
     // current cell and its exit distance; false once the ray left the grid
-    __device__ __forceinline__ bool cell(const Majorants& m, float3 o, float3 d, int& id, float& texit) const
+    __device__ __forceinline__ bool cell(const Majorants& m, int& id, float& texit) const
     {
         if (t >= tmax) return false;
-        if (cx < 0 || cx >= m.mx || cy < 0 || cy >= m.my || cz < 0 || cz >= m.mz) return false;
-        float mc = (float)m.mc;
-        float te = fminf(tmax, bnd(cx, sx, mc, o.x, d.x));
-        te = fminf(te, bnd(cy, sy, mc, o.y, d.y));
-        te = fminf(te, bnd(cz, sz, mc, o.z, d.z));
+        if ((unsigned)cx >= (unsigned)m.mx || (unsigned)cy >= (unsigned)m.my || (unsigned)cz >= (unsigned)m.mz)
+            return false;
+        texit = fminf(fminf(tmax, nx), fminf(ny, nz));
         id = (cz * m.my + cy) * m.mx + cx;
-        texit = te;
+        return true;
+    }
+    // Cross the whole kCoarse^3 block of macrocells around the current cell,
+    // which holds no positive majorant.  The state becomes what cell-by-cell
+    // stepping would reach: the block's exit time is the boundary formula of
+    // the last macrocell on the exit face, and every other axis crosses the
+    // boundaries whose times are <= that exit.  False if the ray ends first.
+    __device__ __forceinline__ bool skip_block(const Majorants& m, float3 o)
+    {
+        float mc = (float)m.mc;
+        int fx = sx > 0 ? min((cx / kCoarse) * kCoarse + kCoarse - 1, m.mx - 1) : (cx / kCoarse) * kCoarse;
+        int fy = sy > 0 ? min((cy / kCoarse) * kCoarse + kCoarse - 1, m.my - 1) : (cy / kCoarse) * kCoarse;
+        int fz = sz > 0 ? min((cz / kCoarse) * kCoarse + kCoarse - 1, m.mz - 1) : (cz / kCoarse) * kCoarse;
+        float tx = bnd(fx, sx, mc, o.x, ix), ty = bnd(fy, sy, mc, o.y, iy), tz = bnd(fz, sz, mc, o.z, iz);
+        float T = tx;
+        int axis = 0;
+        if (ty < T) { T = ty; axis = 1; }
+        if (tz < T) { T = tz; axis = 2; }
+        if (!(T < tmax)) { t = tmax; return false; }
+        if (axis == 0) cx = fx + sx; else { for (int k = 0; k < kCoarse && bnd(cx, sx, mc, o.x, ix) <= T; ++k) cx += sx; }
+        if (axis == 1) cy = fy + sy; else { for (int k = 0; k < kCoarse && bnd(cy, sy, mc, o.y, iy) <= T; ++k) cy += sy; }
+        if (axis == 2) cz = fz + sz; else { for (int k = 0; k < kCoarse && bnd(cz, sz, mc, o.z, iz) <= T; ++k) cz += sz; }
+        nx = bnd(cx, sx, mc, o.x, ix);
+        ny = bnd(cy, sy, mc, o.y, iy);
+        nz = bnd(cz, sz, mc, o.z, iz);
+        if (T > t) t = T;
         return true;
     }
     // step the axis whose boundary is nearest (x, then y, then z on ties)
-    __device__ __forceinline__ void advance(const Majorants& m, float3 o, float3 d, float texit)
+    __device__ __forceinline__ void advance(const Majorants& m, float3 o, float texit)
     {
         float mc = (float)m.mc;
-        float bx = bnd(cx, sx, mc, o.x, d.x), by = bnd(cy, sy, mc, o.y, d.y), bz = bnd(cz, sz, mc, o.z, d.z);
-        float bt = bx;
-        int best = 0;
-        if (by < bt) { bt = by; best = 1; }
-        if (bz < bt) { bt = bz; best = 2; }
-        if (!(bt < tmax)) { t = tmax; return; }
-        if (best == 0) cx += sx;
-        else if (best == 1) cy += sy;
-        else cz += sz;
+        if (nx <= ny && nx <= nz) {
+            if (!(nx < tmax)) { t = tmax; return; }
+            cx += sx; nx = bnd(cx, sx, mc, o.x, ix);
+        } else if (ny <= nz) {
+            if (!(ny < tmax)) { t = tmax; return; }
+            cy += sy; ny = bnd(cy, sy, mc, o.y, iy);
+        } else {
+            if (!(nz < tmax)) { t = tmax; return; }
+            cz += sz; nz = bnd(cz, sz, mc, o.z, iz);
+        }
         if (texit > t) t = texit;
     }
 };
@@ -175,14 +214,16 @@ __device__ __forceinline__ void camera_ray(const CamDev& cam, int px, int py, fl
     float sy = 1.0f - 2.0f * ((float)py + jy) / (float)cam.h;
     if (cam.kind == VDBC_CAM_ORTHO) {
         float a = sx * cam.sxs, b = sy * cam.sys;
-        o = f3(cam.eye.x + a * cam.right.x + b * cam.up.x, cam.eye.y + a * cam.right.y + b * cam.up.y,
-               cam.eye.z + a * cam.right.z + b * cam.up.z);
+        o = f3(__fmaf_rn(b, cam.up.x, __fmaf_rn(a, cam.right.x, cam.eye.x)),
+               __fmaf_rn(b, cam.up.y, __fmaf_rn(a, cam.right.y, cam.eye.y)),
+               __fmaf_rn(b, cam.up.z, __fmaf_rn(a, cam.right.z, cam.eye.z)));
         d = cam.fwd;
     } else {
         float a = sx * cam.sxs, b = sy * cam.sys;
         o = cam.eye;
-        d = norm3(f3(cam.fwd.x + a * cam.right.x + b * cam.up.x, cam.fwd.y + a * cam.right.y + b * cam.up.y,
-                     cam.fwd.z + a * cam.right.z + b * cam.up.z));
+        d = norm3(f3(__fmaf_rn(b, cam.up.x, __fmaf_rn(a, cam.right.x, cam.fwd.x)),
+                     __fmaf_rn(b, cam.up.y, __fmaf_rn(a, cam.right.y, cam.fwd.y)),
+                     __fmaf_rn(b, cam.up.z, __fmaf_rn(a, cam.right.z, cam.fwd.z))));
     }
 }
 
@@ -197,121 +238,18 @@ struct Rng {
 struct Walk {
     unsigned long long lookups;
     unsigned long long flags;
+#ifdef VDBC_STATS
+    // loop iterations, DDA cells examined, coarse blocks crossed, free flights
+    // drawn, rays started, paths fetched
+    unsigned int ev[6];
+#endif
 };
 
-// Woodcock tracking through the macrocells; true on a real collision
-template <class S>
-__device__ __forceinline__ bool delta_track(const S& smp, Accessor& acc, const Majorants& m, const MedDev& med,
-                                            const Rng& rng, float3 o, float3 d, float tmin, float tmax,
-                                            uint32_t& call, float& thit, float& xi0, float& xi1, Walk& w)
-{
-    Dda dda;
-    dda.init(m, o, d, tmin, tmax);
-    int cell;
-    float texit;
-    int guard = m.mx + m.my + m.mz + 8;
-    while (dda.cell(m, o, d, cell, texit)) {
-        if (--guard < 0) { w.flags |= kErrDdaSteps; return false; }
-        float mj = med.sigma_scale * __ldg(m.mcmax + cell);
-        if (mj > 0.0f && texit > dda.t) {
-            float t = dda.t;
-            for (int it = 0;; ++it) {
-                if (it >= kMaxStepsPerCell) { w.flags |= kErrTrackSteps; return false; }
-                U4 r = rng.draw(call++, 0);
-                t = t - logf(1.0f - u01(r.x)) / mj;
-                if (t >= texit) break;
-                float3 p = f3(o.x + t * d.x, o.y + t * d.y, o.z + t * d.z);
-                float sigma = med.sigma_scale * smp(p.x, p.y, p.z, acc);
-                ++w.lookups;
-                if (u01(r.y) * mj < sigma) {
-                    thit = t;
-                    xi0 = u01(r.z);
-                    xi1 = u01(r.w);
-                    return true;
-                }
-            }
-        }
-        dda.advance(m, o, d, texit);
-    }
-    return false;
-}
-
-// ratio tracking: product of (1 - sigma / majorant) over the tentative collisions
-template <class S>
-__device__ __forceinline__ float ratio_track(const S& smp, Accessor& acc, const Majorants& m, const MedDev& med,
-                                             const Rng& rng, float3 o, float3 d, float tmin, float tmax,
-                                             uint32_t& call, Walk& w)
-{
-    Dda dda;
-    dda.init(m, o, d, tmin, tmax);
-    int cell;
-    float texit, T = 1.0f;
-    int guard = m.mx + m.my + m.mz + 8;
-    while (dda.cell(m, o, d, cell, texit)) {
-        if (--guard < 0) { w.flags |= kErrDdaSteps; return T; }
-        float mj = med.sigma_scale * __ldg(m.mcmax + cell);
-        if (mj > 0.0f && texit > dda.t) {
-            float t = dda.t;
-            for (int it = 0;; ++it) {
-                if (it >= kMaxStepsPerCell) { w.flags |= kErrTrackSteps; return T; }
-                U4 r = rng.draw(call++, 1);
-                t = t - logf(1.0f - u01(r.x)) / mj;
-                if (t >= texit) break;
-                float3 p = f3(o.x + t * d.x, o.y + t * d.y, o.z + t * d.z);
-                float sigma = med.sigma_scale * smp(p.x, p.y, p.z, acc);
-                ++w.lookups;
-                T *= 1.0f - sigma / mj;
-            }
-        }
-        dda.advance(m, o, d, texit);
-    }
-    return T;
-}
-
-template <class S>
-__device__ float3 trace_path(const S& smp, Accessor& acc, const Majorants& m, const CamDev& cam,
-                             const MedDev& med, const Rng& rng, int px, int py, Walk& w)
-{
-    uint32_t call = 0, lcall = 0;
-    U4 r = rng.draw(call++, 0);
-    float3 o, d;
-    camera_ray(cam, px, py, u01(r.x), u01(r.y), o, d);
-    float3 L = f3(0.f, 0.f, 0.f);
-    float beta = 1.0f;
-    float tin, tout;
-    if (!clip_box(m, o, d, tin, tout)) return med.env_rad;
-    for (int bounce = 0; bounce < med.max_bounces; ++bounce) {
-        float thit, xi0, xi1;
-        if (!delta_track(smp, acc, m, med, rng, o, d, tin, tout, call, thit, xi0, xi1, w)) {
-            L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
-            return L;
-        }
-        float3 x = f3(o.x + thit * d.x, o.y + thit * d.y, o.z + thit * d.z);
-        beta *= med.albedo;
-        float ltin, ltout, T = 1.0f;
-        if (clip_box(m, x, med.sun_dir, ltin, ltout))
-            T = ratio_track(smp, acc, m, med, rng, x, med.sun_dir, ltin, ltout, lcall, w);
-        float ph = hg_eval(dot3(d, med.sun_dir), med.g);
-        float wgt = beta * ph * T;
-        L.x += wgt * med.sun_rad.x; L.y += wgt * med.sun_rad.y; L.z += wgt * med.sun_rad.z;
-        if (bounce + 1 == med.max_bounces) return L;
-        float mu = hg_sample_mu(med.g, xi0);
-        float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
-        float sphi, cphi;
-        sincospif(2.0f * xi1, &sphi, &cphi);   // phi = 2 pi xi1, reduction-free form
-        float3 b1, b2;
-        onb(d, b1, b2);
-        float3 nd = f3(st * cphi * b1.x + st * sphi * b2.x + mu * d.x, st * cphi * b1.y + st * sphi * b2.y + mu * d.y,
-                       st * cphi * b1.z + st * sphi * b2.z + mu * d.z);
-        d = norm3(nd);
-        o = x;
-        if (!clip_box(m, o, d, tin, tout)) {
-            L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
-            return L;
-        }
-    }
-    return L;
-}
+#ifdef VDBC_STATS
+#define VDBC_EVENT(w, k) ((w).ev[k]++)
+#else
+#define VDBC_EVENT(w, k) ((void)0)
+#endif
 
 __device__ __forceinline__ void flush_stats(DevStats* st, const Walk& w, unsigned long long paths)
 {
@@ -327,32 +265,320 @@ __device__ __forceinline__ void flush_stats(DevStats* st, const Walk& w, unsigne
         atomicAdd(&st->paths, p);
         if (f) atomicOr(&st->error_flags, f);
     }
+#ifdef VDBC_STATS
+    for (int k = 0; k < 6; ++k) atomicAdd(&st->ev[k], (unsigned long long)w.ev[k]);
+#endif
 }
 
-template <class S>
-__global__ void __launch_bounds__(128, 4) k_pt(S smp, Majorants m, CamDev cam, MedDev med, int spp, uint32_t k0,
-                                            uint32_t k1, float4* __restrict__ out, DevStats* __restrict__ st)
+// ---------------------------------------------------------------- path tracer
+// One lane carries one light path at a time and fetches the next path as soon
+// as its own ends (persistent threads, warp-aggregated work counter), so the
+// lanes of a warp stay busy until the work runs out.  Delta tracking and the
+// light ray's ratio tracking are one loop: every iteration a lane either
+// moves to its next non-empty macrocell or takes one tentative step with a
+// density lookup, whichever its path needs; lanes therefore issue their
+// lookups together.  Random-number use per path is the oracle's: the camera
+// takes call 0 of stream 0, each tentative step of the walk the next call of
+// stream 0, each tentative step of a light ray the next call of stream 1.
+// Path radiance goes to path_out[sample * npix + pixel]; k_pt_reduce averages
+// the samples of every pixel in sample order (deterministic).
+
+enum : int { kNeed = 0, kDone = 1, kDelta = 2, kRatio = 3 };
+
+struct Track {
+    Dda dda;
+    float tcur, texit, mj;
+};
+
+// next macrocell with a positive majorant at or after the current DDA cell;
+// false when the ray leaves the grid.  Blocks of kCoarse^3 macrocells whose
+// coarse bit is clear are crossed in one step; inside an occupied block,
+// cells whose own bit is clear (majorant <= 0) are passed without loading
+// their majorant.
+__device__ __forceinline__ bool next_cell(Track& tr, const Majorants& m, const MedDev& med, float3 o,
+                                          const uint32_t* bits, const uint32_t* cbits, int cx_n, int cy_n,
+                                          int& guard, Walk& w)
 {
-    const int npix = cam.w * cam.h;
-    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-    Walk w{0, 0};
-    unsigned long long paths = 0;
-    if (pix < npix) {
-        Accessor acc;
-        acc.reset();
-        Rng rng{(uint32_t)pix, 0, k0, k1};
-        const int px = pix % cam.w, py = pix / cam.w;
-        float3 acc_l = f3(0.f, 0.f, 0.f);
-        for (int s = 0; s < spp; ++s) {
-            rng.sample = (uint32_t)s;
-            float3 L = trace_path(smp, acc, m, cam, med, rng, px, py, w);
-            acc_l.x += L.x; acc_l.y += L.y; acc_l.z += L.z;
+    int id;
+    float texit;
+    while (tr.dda.cell(m, id, texit)) {
+        VDBC_EVENT(w, 1);
+        if (--guard < 0) return false;
+        int cid = ((tr.dda.cz / kCoarse) * cy_n + tr.dda.cy / kCoarse) * cx_n + tr.dda.cx / kCoarse;
+        if (!((cbits[cid >> 5] >> (cid & 31)) & 1u)) {
+            VDBC_EVENT(w, 2);
+            if (!tr.dda.skip_block(m, o)) return false;
+            continue;
         }
-        float inv = 1.0f / (float)spp;
-        out[pix] = make_float4(acc_l.x * inv, acc_l.y * inv, acc_l.z * inv, 1.0f);
-        paths = (unsigned long long)spp;
+        if (((bits[id >> 5] >> (id & 31)) & 1u) && texit > tr.dda.t) {
+            float mj = __fmul_rn(med.sigma_scale, __ldg(m.mcmax + id));
+            if (mj > 0.0f) {
+                tr.mj = mj;
+                tr.texit = texit;
+                tr.tcur = tr.dda.t;
+                return true;
+            }
+        }
+        tr.dda.advance(m, o, texit);
+    }
+    return false;
+}
+
+// gbits: nwords fine occupancy words followed by ncwords coarse words; the
+// parts that fit in `smem_words` are staged in shared memory (coarse first)
+template <class S>
+__global__ void __launch_bounds__(256, 2)
+    k_pt(S smp, Majorants m, CamDev cam, MedDev med, int spp, uint32_t k0, uint32_t k1,
+         const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
+         float4* __restrict__ path_out, DevStats* __restrict__ st, unsigned long long nitems, int tiles_x, int chunk)
+{
+    extern __shared__ uint32_t s_bits[];
+    const uint32_t* cbits = gbits + nwords;
+    const uint32_t* bits = gbits;
+    if (ncwords <= smem_words) {
+        for (int i = threadIdx.x; i < ncwords; i += blockDim.x) s_bits[i] = gbits[nwords + i];
+        cbits = s_bits;
+        if (ncwords + nwords <= smem_words) {
+            for (int i = threadIdx.x; i < nwords; i += blockDim.x) s_bits[ncwords + i] = gbits[i];
+            bits = s_bits + ncwords;
+        }
+    }
+    __syncthreads();
+    const int cx_n = (m.mx + kCoarse - 1) / kCoarse, cy_n = (m.my + kCoarse - 1) / kCoarse;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int npix = cam.w * cam.h;
+    const int dda_guard = m.mx + m.my + m.mz + 8;
+    Walk w{};
+    unsigned long long paths = 0;
+
+    int mode = kNeed;
+    uint32_t pixel = 0, sample = 0, call = 0, lcall = 0;
+    int bounce = 0;
+    float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), nd = d, L = f3(0.f, 0.f, 0.f);
+    float beta = 1.0f, T = 1.0f, ph = 0.0f;
+    float tau = -1.0f, ua = 0.0f, ub = 0.0f, uc = 0.0f;   // current free flight: optical depth left, u1..u3
+    int steps_in_cell = 0, guard = 0;
+    unsigned long long pool_next = 0, pool_end = 0;   // this warp's share of the work counter
+    Track tr;
+    Accessor acc;
+    acc.reset();
+
+    for (;;) {
+        if (mode != kDone) VDBC_EVENT(w, 0);
+        // ---- fetch work for lanes without a path: each warp takes `chunk`
+        // items at a time from the global counter and hands them out to its
+        // lanes in order, so the counter is touched once per chunk
+        const unsigned need = __ballot_sync(0xffffffffu, mode == kNeed);
+        if (need) {
+            const unsigned n = (unsigned)__popc(need);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long fresh = 0;
+            if (avail < n) {
+                if (lane == 0) fresh = atomicAdd(&st->work_next, (unsigned long long)chunk);
+                fresh = __shfl_sync(0xffffffffu, fresh, 0);
+            }
+            if (mode == kNeed) {
+                const unsigned long long r = (unsigned long long)__popc(need & lt_mask);
+                unsigned long long item = r < avail ? pool_next + r : fresh + (r - avail);
+                if (item >= nitems) {
+                    mode = kDone;
+                } else {
+                    // item -> (sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
+                    unsigned long long per = nitems / (unsigned long long)spp;
+                    sample = (uint32_t)(item / per);
+                    uint32_t q = (uint32_t)(item % per), tile = q >> 5, in = q & 31;
+                    int px = (int)(tile % tiles_x) * 8 + (int)(in & 7);
+                    int py = (int)(tile / tiles_x) * 4 + (int)(in >> 3);
+                    if (px < cam.w && py < cam.h) {
+                        VDBC_EVENT(w, 5);
+                        pixel = (uint32_t)(py * cam.w + px);
+                        Rng rng{pixel, sample, k0, k1};
+                        call = 0;
+                        lcall = 0;
+                        U4 r = rng.draw(call++, 0);
+                        camera_ray(cam, px, py, u01(r.x), u01(r.y), o, d);
+                        L = f3(0.f, 0.f, 0.f);
+                        beta = 1.0f;
+                        bounce = 0;
+                        float tin, tout;
+                        if (!clip_box(m, o, d, tin, tout)) {
+                            path_out[(size_t)sample * npix + pixel] = make_float4(med.env_rad.x, med.env_rad.y,
+                                                                                 med.env_rad.z, 1.0f);
+                            ++paths;
+                        } else {
+                            tr.dda.init(m, o, d, tin, tout);
+                            tau = -1.0f;   // every ray starts a new free flight
+                            VDBC_EVENT(w, 4);
+                            guard = dda_guard;
+                            steps_in_cell = 0;
+                            mode = kDelta;
+                            if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kDelta;   // leaves at once
+                        }
+                    }
+                }
+            }
+            if (avail < n) { pool_next = fresh + (n - avail); pool_end = fresh + (unsigned long long)chunk; }
+            else pool_next += n;
+        }
+        if (__all_sync(0xffffffffu, mode == kDone)) break;
+
+        // ---- one free flight per lane: draw tau, spend it over the cells, and
+        // where it runs out evaluate the density (delta: accept or not;
+        // ratio: attenuate)
+        if (mode == kDelta || mode == kRatio) {
+            if (tau < 0.0f) {
+                Rng rng{pixel, sample, k0, k1};
+                U4 r = (mode == kDelta) ? rng.draw(call++, 0) : rng.draw(lcall++, 1);
+                VDBC_EVENT(w, 3);
+                tau = -logf(1.0f - u01(r.x));
+                ua = u01(r.y); ub = u01(r.z); uc = u01(r.w);
+            }
+            // spend tau over as many cells as it lasts (cheap inner walk), so
+            // that the draw and the lookup below run once per iteration
+            bool ended = false;
+            for (;;) {
+                float reach = __fmul_rn(tr.mj, __fsub_rn(tr.texit, tr.tcur));
+                if (tau < reach) break;
+                tau = __fsub_rn(tau, reach);
+                tr.dda.advance(m, o, tr.texit);
+                steps_in_cell = 0;
+                if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) {
+                    if (guard < 0) w.flags |= kErrDdaSteps;
+                    ended = true;
+                    break;
+                }
+            }
+            if (ended) {
+                mode = -mode;            // ray ended
+            } else if (++steps_in_cell > kMaxStepsPerCell) {
+                w.flags |= kErrTrackSteps;
+                mode = -mode;            // give up on this ray (reported through the error word)
+            } else {
+                float t = __fadd_rn(tr.tcur, __fdiv_rn(tau, tr.mj));
+                tr.tcur = t;
+                tau = -1.0f;
+                float3 x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
+                float sigma = __fmul_rn(med.sigma_scale, smp(x.x, x.y, x.z, acc));
+                ++w.lookups;
+                if (mode == kRatio) {
+                    T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
+                } else if (__fmul_rn(ua, tr.mj) < sigma) {
+                    // real collision: scatter, then trace the light ray from here
+                    beta *= med.albedo;
+                    ph = hg_eval(dot3(d, med.sun_dir), med.g);
+                    float mu = hg_sample_mu(med.g, ub);
+                    float st_ = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+                    float sphi, cphi;
+                    sincospif(2.0f * uc, &sphi, &cphi);
+                    float3 b1, b2;
+                    onb(d, b1, b2);
+                    nd = norm3(f3(st_ * cphi * b1.x + st_ * sphi * b2.x + mu * d.x,
+                                  st_ * cphi * b1.y + st_ * sphi * b2.y + mu * d.y,
+                                  st_ * cphi * b1.z + st_ * sphi * b2.z + mu * d.z));
+                    o = x;
+                    d = med.sun_dir;
+                    T = 1.0f;
+                    float tin, tout;
+                    mode = kRatio;
+                    if (clip_box(m, o, d, tin, tout)) {
+                        tr.dda.init(m, o, d, tin, tout);
+                        tau = -1.0f;   // every ray starts a new free flight
+                        VDBC_EVENT(w, 4);
+                        guard = dda_guard;
+                        steps_in_cell = 0;
+                        if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kRatio;
+                    } else {
+                        mode = -kRatio;
+                    }
+                }
+            }
+        }
+        // ---- a ray ended (negative mode): escape, or the light ray's contribution
+        if (mode < 0) {
+            bool finished = false;
+            if (mode == -kDelta) {
+                L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
+                finished = true;
+            } else {
+                float wgt = beta * ph * T;
+                L.x += wgt * med.sun_rad.x; L.y += wgt * med.sun_rad.y; L.z += wgt * med.sun_rad.z;
+                if (++bounce >= med.max_bounces) {
+                    finished = true;
+                } else {
+                    d = nd;
+                    float tin, tout;
+                    if (!clip_box(m, o, d, tin, tout)) {
+                        L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
+                        finished = true;
+                    } else {
+                        tr.dda.init(m, o, d, tin, tout);
+                        tau = -1.0f;   // every ray starts a new free flight
+                        VDBC_EVENT(w, 4);
+                        guard = dda_guard;
+                        steps_in_cell = 0;
+                        mode = kDelta;
+                        if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kDelta;
+                        if (mode == -kDelta) {
+                            L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
+                            finished = true;
+                        }
+                    }
+                }
+            }
+            if (finished) {
+                path_out[(size_t)sample * npix + pixel] = make_float4(L.x, L.y, L.z, 1.0f);
+                ++paths;
+                mode = kNeed;
+            }
+        }
     }
     flush_stats(st, w, paths);
+}
+
+// average of the spp path radiances of each pixel, in sample order
+__global__ void k_pt_reduce(const float4* __restrict__ path_out, int npix, int spp, float4* __restrict__ out)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    float r = 0.f, g = 0.f, b = 0.f;
+    for (int s = 0; s < spp; ++s) {
+        float4 v = path_out[(size_t)s * npix + p];
+        r += v.x; g += v.y; b += v.z;
+    }
+    float inv = 1.0f / (float)spp;
+    out[p] = make_float4(r * inv, g * inv, b * inv, 1.0f);
+}
+
+// coarse occupancy: a bit per kCoarse^3 block of macrocells, set if any
+// macrocell inside has its occupancy bit
+__global__ void k_coarse_occupancy(const uint32_t* __restrict__ bits, int mx, int my, int mz,
+                                   uint32_t* __restrict__ cbits, int cxn, int cyn, int czn)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = cxn * cyn * czn;
+    bool on = false;
+    if (c < n) {
+        int bx = c % cxn, by = (c / cxn) % cyn, bz = c / (cxn * cyn);
+        for (int z = bz * kCoarse; z < min(bz * kCoarse + kCoarse, mz) && !on; ++z)
+            for (int y = by * kCoarse; y < min(by * kCoarse + kCoarse, my) && !on; ++y)
+                for (int x = bx * kCoarse; x < min(bx * kCoarse + kCoarse, mx); ++x) {
+                    long long id = ((long long)z * my + y) * mx + x;
+                    if ((bits[id >> 5] >> (id & 31)) & 1u) { on = true; break; }
+                }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, on);
+    if ((threadIdx.x & 31) == 0 && c < n) cbits[c >> 5] = b;
+}
+
+// occupancy bit per macrocell: majorant > 0
+__global__ void k_occupancy(const float* __restrict__ mcmax, long long ncell, float sigma_scale,
+                            uint32_t* __restrict__ bits)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool on = i < ncell && sigma_scale * mcmax[i] > 0.0f;
+    unsigned b = __ballot_sync(0xffffffffu, on);
+    if ((threadIdx.x & 31) == 0 && i < ncell) bits[i >> 5] = b;
 }
 
 template <class S>
@@ -364,7 +590,7 @@ __global__ void __launch_bounds__(128) k_ea(S smp, Majorants m, CamDev cam, MedD
     __syncthreads();
     const int npix = cam.w * cam.h;
     const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-    Walk w{0, 0};
+    Walk w{};
     unsigned long long paths = 0;
     if (pix < npix) {
         Accessor acc;
@@ -496,6 +722,58 @@ vdbc_status make_med(const vdbc_medium* m, const int dims[3], int spp, cudaStrea
     return VDBC_OK;
 }
 
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+constexpr int kPtThreads = 256;
+
+// crossing empty 8^3 blocks of macrocells in one step; VDBC_PT_COARSE=0 turns it off
+bool coarse_skipping()
+{
+    const char* e = std::getenv("VDBC_PT_COARSE");
+    return !(e && e[0] == '0');
+}
+
+// items a warp takes from the work counter at once (>= 32); VDBC_PT_CHUNK overrides
+int work_chunk()
+{
+    int c = 256;
+    if (const char* e = std::getenv("VDBC_PT_CHUNK")) c = std::atoi(e);
+    return c < 32 ? 32 : c;
+}
+constexpr size_t kSmemBitsMax = 96 * 1024;
+
+template <class S>
+vdbc_status launch_pt(const S& smp, const Majorants& mj, const CamDev& cam, const MedDev& med, int spp,
+                      uint64_t seed, const uint32_t* bits, int nwords, int ncwords, float4* path_out,
+                      DevStats* stats, unsigned long long nitems, int tiles_x, int chunk, cudaStream_t s)
+{
+    int smem_words = std::min<int>(nwords + ncwords, (int)(kSmemBitsMax / 4));
+    if (smem_words < ncwords) smem_words = 0;
+    size_t smem = (size_t)smem_words * 4;
+    auto kern = k_pt<S>;
+    if (smem > 48 * 1024) VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    long long want = (nitems + kPtThreads - 1) / kPtThreads;
+    long long blocks = std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
+    KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, mj, cam, med, spp, (uint32_t)seed,
+                                                            (uint32_t)(seed >> 32), bits, nwords, ncwords,
+                                                            smem_words, path_out, stats, nitems, tiles_x, chunk));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
+
 template <class S>
 vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const MedDev& med, int spp, uint64_t seed,
                    float4* out, DevStats* stats, cudaStream_t s)
@@ -504,12 +782,37 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     VDBC_CUDA(cudaMemsetAsync(stats, 0, sizeof(DevStats), s));
     if (med.mode == VDBC_MODE_EA) {
         KLAUNCH(k_ea<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out, stats));
-    } else {
-        KLAUNCH(k_pt<S><<<blocks_for(npix, 128), 128, 0, s>>>(smp, mj, cam, med, spp, (uint32_t)seed,
-                                                      (uint32_t)(seed >> 32), out, stats));
+        VDBC_CUDA(cudaGetLastError());
+        return VDBC_OK;
     }
-    VDBC_CUDA(cudaGetLastError());
-    return VDBC_OK;
+    long long ncell = (long long)mj.mx * mj.my * mj.mz;
+    int nwords = (int)((ncell + 31) / 32);
+    int cxn = (mj.mx + kCoarse - 1) / kCoarse, cyn = (mj.my + kCoarse - 1) / kCoarse, czn = (mj.mz + kCoarse - 1) / kCoarse;
+    int ncwords = (cxn * cyn * czn + 31) / 32;
+    int tiles_x = (cam.w + 7) / 8, tiles_y = (cam.h + 3) / 4;
+    unsigned long long nitems = (unsigned long long)spp * tiles_x * tiles_y * 32;
+    uint32_t* bits = nullptr;
+    float4* path_out = nullptr;
+    VDBC_TRY(dev_alloc(reinterpret_cast<void**>(&bits), (size_t)(nwords + ncwords) * 4, s));
+    vdbc_status st = dev_alloc(reinterpret_cast<void**>(&path_out), (size_t)spp * npix * sizeof(float4), s);
+    if (st != VDBC_OK) { dev_free(bits, s); return st; }
+    KLAUNCH(k_occupancy<<<blocks_for(ncell, 256), 256, 0, s>>>(mj.mcmax, ncell, med.sigma_scale, bits));
+    if (coarse_skipping()) {
+        KLAUNCH(k_coarse_occupancy<<<blocks_for((long long)cxn * cyn * czn, 256), 256, 0, s>>>(
+            bits, mj.mx, mj.my, mj.mz, bits + nwords, cxn, cyn, czn));
+    } else {
+        VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
+    }
+    st = launch_pt<S>(smp, mj, cam, med, spp, seed, bits, nwords, ncwords, path_out, stats, nitems, tiles_x,
+                      work_chunk(), s);
+    if (st == VDBC_OK) {
+        KLAUNCH(k_pt_reduce<<<blocks_for(npix, 256), 256, 0, s>>>(path_out, (int)npix, spp, out));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_status(e, "k_pt_reduce");
+    }
+    dev_free(path_out, s);
+    dev_free(bits, s);
+    return st;
 }
 
 template <class S>
@@ -586,10 +889,15 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
     clear_error();
     if (!grid) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_render: grid is null");
     const GridView& g = grid->view;
-    VdbSampler smp{g};
     Majorants mj{g.mcmax, g.mc, g.mx, g.my, g.mz, g.nx, g.ny, g.nz};
-    return render_common(smp, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out, out_on_device,
-                         stream);
+    if (g.payload == VDBC_FP16)
+        return render_common(VdbSamplerT<1>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
+                             out_on_device, stream);
+    if (g.payload == VDBC_FP8)
+        return render_common(VdbSamplerT<2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
+                             out_on_device, stream);
+    return render_common(VdbSamplerT<0>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
+                         out_on_device, stream);
 }
 
 extern "C" vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream, vdbc_render_stats* out)
@@ -602,6 +910,7 @@ extern "C" vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream
     out->lookups = h.lookups;
     out->paths = h.paths;
     out->error_flags = h.error_flags;
+    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
     return VDBC_OK;
 }
 
@@ -713,5 +1022,6 @@ extern "C" vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void
     out->lookups = h.lookups;
     out->paths = h.paths;
     out->error_flags = h.error_flags;
+    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
     return VDBC_OK;
 }

@@ -71,15 +71,24 @@ __device__ __forceinline__ float e4m3_to_float(uint8_t b)
     return __half2float(__half(h));
 }
 
-__device__ __forceinline__ float leaf_value(const GridView& g, uint32_t leaf, int off, float2 sm)
+// value `off` of leaf `leaf`; P is the payload (0 f32, 1 f16, 2 e4m3) or -1
+// to read it from the grid at run time
+template <int P>
+__device__ __forceinline__ float leaf_value_t(const GridView& g, uint32_t leaf, int off, float2 sm)
 {
-    if (g.payload == 0) return __ldg(reinterpret_cast<const float*>(g.leaves) + (size_t)leaf * kLeafN + off);
-    if (g.payload == 1) {
+    const int pay = P >= 0 ? P : g.payload;
+    if (pay == 0) return __ldg(reinterpret_cast<const float*>(g.leaves) + (size_t)leaf * kLeafN + off);
+    if (pay == 1) {
         __half h = reinterpret_cast<const __half*>(g.leaves)[(size_t)leaf * kLeafN + off];
         return __fmaf_rn(sm.x, __half2float(h), sm.y);
     }
     uint8_t b = reinterpret_cast<const uint8_t*>(g.leaves)[(size_t)leaf * kLeafN + off];
     return __fmaf_rn(sm.x, e4m3_to_float(b), sm.y);
+}
+
+__device__ __forceinline__ float leaf_value(const GridView& g, uint32_t leaf, int off, float2 sm)
+{
+    return leaf_value_t<-1>(g, leaf, off, sm);
 }
 
 // ---------------------------------------------------------------- descent
@@ -112,17 +121,26 @@ struct Accessor {
     }
 };
 
-__device__ __forceinline__ float voxel(const GridView& g, Accessor& acc, int i, int j, int k)
+template <int P>
+__device__ __forceinline__ float voxel_t(const GridView& g, Accessor& acc, int i, int j, int k)
 {
     uint32_t e = acc.leaf(g, i >> 3, j >> 3, k >> 3);
     if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
-    return leaf_value(g, e, ((k & 7) << 6) | ((j & 7) << 3) | (i & 7), acc.sm);
+    return leaf_value_t<P>(g, e, ((k & 7) << 6) | ((j & 7) << 3) | (i & 7), acc.sm);
+}
+
+__device__ __forceinline__ float voxel(const GridView& g, Accessor& acc, int i, int j, int k)
+{
+    return voxel_t<-1>(g, acc, i, j, k);
 }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// trilinear reconstruction at index-space position p, clamp to edge
-struct VdbSampler {
+// trilinear reconstruction at index-space position p, clamp to edge; every
+// call descends the tree (through the accessor's cached leaf) and decodes the
+// eight voxels; P is the payload type of the grid
+template <int P>
+struct VdbSamplerT {
     GridView g;
     __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor& acc) const
     {
@@ -139,15 +157,15 @@ struct VdbSampler {
             int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
             int az = (z0 & 7) << 6, bz = (z1 & 7) << 6;
             float2 sm = acc.sm;
-            v000 = leaf_value(g, e, az | ay | ax, sm); v100 = leaf_value(g, e, az | ay | bx, sm);
-            v010 = leaf_value(g, e, az | by | ax, sm); v110 = leaf_value(g, e, az | by | bx, sm);
-            v001 = leaf_value(g, e, bz | ay | ax, sm); v101 = leaf_value(g, e, bz | ay | bx, sm);
-            v011 = leaf_value(g, e, bz | by | ax, sm); v111 = leaf_value(g, e, bz | by | bx, sm);
+            v000 = leaf_value_t<P>(g, e, az | ay | ax, sm); v100 = leaf_value_t<P>(g, e, az | ay | bx, sm);
+            v010 = leaf_value_t<P>(g, e, az | by | ax, sm); v110 = leaf_value_t<P>(g, e, az | by | bx, sm);
+            v001 = leaf_value_t<P>(g, e, bz | ay | ax, sm); v101 = leaf_value_t<P>(g, e, bz | ay | bx, sm);
+            v011 = leaf_value_t<P>(g, e, bz | by | ax, sm); v111 = leaf_value_t<P>(g, e, bz | by | bx, sm);
         } else {
-            v000 = voxel(g, acc, x0, y0, z0); v100 = voxel(g, acc, x1, y0, z0);
-            v010 = voxel(g, acc, x0, y1, z0); v110 = voxel(g, acc, x1, y1, z0);
-            v001 = voxel(g, acc, x0, y0, z1); v101 = voxel(g, acc, x1, y0, z1);
-            v011 = voxel(g, acc, x0, y1, z1); v111 = voxel(g, acc, x1, y1, z1);
+            v000 = voxel_t<P>(g, acc, x0, y0, z0); v100 = voxel_t<P>(g, acc, x1, y0, z0);
+            v010 = voxel_t<P>(g, acc, x0, y1, z0); v110 = voxel_t<P>(g, acc, x1, y1, z0);
+            v001 = voxel_t<P>(g, acc, x0, y0, z1); v101 = voxel_t<P>(g, acc, x1, y0, z1);
+            v011 = voxel_t<P>(g, acc, x0, y1, z1); v111 = voxel_t<P>(g, acc, x1, y1, z1);
         }
         float c00 = lerpf(v000, v100, tx), c10 = lerpf(v010, v110, tx);
         float c01 = lerpf(v001, v101, tx), c11 = lerpf(v011, v111, tx);

@@ -16,7 +16,8 @@ struct DevStats {
     unsigned long long lookups;
     unsigned long long paths;
     unsigned long long error_flags;
-    unsigned long long pad;
+    unsigned long long work_next;    // persistent-kernel work counter
+    unsigned long long ev[6];        // event counts of builds with VDBC_STATS (else 0)
 };
 
 enum : unsigned long long {

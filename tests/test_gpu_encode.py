@@ -154,11 +154,11 @@ def test_injected_allocation_failure(env, monkeypatch):
     host = env["vg"].generate_host(env["vg"].make_params("blobs", (32, 32, 32), 0))
     monkeypatch.setenv("VDBC_FAULT", "oom")
     with pytest.raises(v.VdbcError) as ex:
-        v.vdbc_encode(host, 2.0)
+        v.vdbc_encode(host, 1.0)
     assert ex.value.status == v.ERR_OOM
     monkeypatch.delenv("VDBC_FAULT")
-    g = v.vdbc_encode(host, 2.0)
-    assert g.info.n_active > 0
+    g = v.vdbc_encode(host, 1.0)        # one 32^3 brick: the budget at 1:1 is that brick
+    assert g.info.n_active == 1
 
 
 def test_device_generator_matches_host(env):
