@@ -18,7 +18,7 @@ copied from pinned host memory inside vdbc_encode and the image is read back
 to the host inside vdbc_render.
 
 --impl reference times the FP64 CPU oracle (the test oracle, as it stands)
-on the host cores over a bounded pixel sample of the same workload.
+on the host cores over a bounded pixel sample of the same frame.
 """
 from __future__ import annotations
 
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--profile-case", action="store_true",
-                    help="the ncu capture case: the same workload at a 256x256 image, two renders")
+                    help="the ncu capture case: the same workload at a 512x512 image, two renders")
     return ap.parse_args()
 
 
@@ -184,7 +184,7 @@ def run_vdbc(args):
     seed = 2024
 
     def step():
-        g = v.vdbc_encode(vol, w["ratio"], stream=stream)
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
         v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
         return g
 
@@ -213,7 +213,7 @@ def run_vdbc(args):
     for i in range(args.steps):
         a, b, c = ev[i]
         a.record(stream)
-        g = v.vdbc_encode(vol, w["ratio"], stream=stream)
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
         b.record(stream)
         v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
         c.record(stream)
@@ -250,7 +250,7 @@ def run_vdbc(args):
             "algorithmic_bytes_per_lookup": 32}
 
     # --- comparator: the same renderer on the dense 3D texture; PSNR
-    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, stream=stream)
+    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w["macrocell"], stream=stream)
     dimg = torch.empty_like(img)
     for _ in range(2):
         v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
@@ -265,7 +265,7 @@ def run_vdbc(args):
     dense_ms = e0.elapsed_time(e1) / reps
     dstats = v.vdbc_volume_render_stats_get(tex, stream=stream)
     tex.close()
-    g1 = v.vdbc_encode(vol, 1.0, stream=stream)          # the uncompressed (lossless) render
+    g1 = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"], stream=stream)   # the uncompressed (lossless) render
     ref_img = torch.empty_like(img)
     v.vdbc_render(g1, cam, med, w["spp"], seed, ref_img, stream=stream)
     torch.cuda.synchronize()
@@ -282,13 +282,13 @@ def run_vdbc(args):
         host_img = np.empty((H, W, 4), dtype=np.float32)
         torch.cuda.synchronize()
         for _ in range(2):
-            g = v.vdbc_encode(host_vol, w["ratio"], stream=stream)
+            g = v.vdbc_encode(host_vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
             v.vdbc_render(g, cam, med, w["spp"], seed, host_img, stream=stream)
             g.close()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            g = v.vdbc_encode(host_vol, w["ratio"], stream=stream)
+            g = v.vdbc_encode(host_vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
             v.vdbc_render(g, cam, med, w["spp"], seed, host_img, stream=stream)
             g.close()
         barrier()
@@ -301,7 +301,8 @@ def run_vdbc(args):
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
-                   "ratio": "1:10", "payload": "fp32", "image": "1024x1024", "spp": 16, "max_bounces": 16,
+                   "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"], "image": "1024x1024", "spp": 16,
+                   "max_bounces": 16,
                    "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "input 512 MiB > L2, re-read every step"},
         "render_ms": round(render_ms, 3), "encode_ms": round(sum(enc_ms) / len(enc_ms), 3),
@@ -331,8 +332,8 @@ def run_vdbc(args):
 
 class CpuOracle:
     """The FP64 oracle (unchanged) on the host cores: the full 512^3 volume is
-    encoded once; a measurement then traces a fixed pixel sample (every 16th
-    row and column, all 16 spp) for about budget_s seconds."""
+    encoded once; a measurement then traces a random pixel sample of the frame
+    (all 16 spp), sized to about budget_s seconds and capped at the whole frame."""
 
     def __init__(self):
         import numpy as np
@@ -349,17 +350,16 @@ class CpuOracle:
         t0 = time.perf_counter()
         e = oracle.encode(host, w["ratio"])
         self.D = oracle.decode_dense(host, e["active"], e["background_bits"])
-        self.mx = oracle.macrocell_minmax(self.D, 8)[1]
+        self.mx = oracle.macrocell_minmax(self.D, w["macrocell"])[1]
         self.enc_s = time.perf_counter() - t0
         cam_args, med_args = scene(w)
         self.cam = oracle.make_camera(*cam_args)
-        self.med = oracle.make_medium(1, macrocell=8, **med_args)
+        self.med = oracle.make_medium(1, macrocell=w["macrocell"], **med_args)
         W, H = w["width"], w["height"]
-        ys, xs = np.meshgrid(np.arange(0, H, 16), np.arange(0, W, 16), indexing="ij")
-        pix = (ys * W + xs).ravel().astype(np.int64)
-        np.random.default_rng(0).shuffle(pix)
+        pix = np.arange(W * H, dtype=np.int64)
+        np.random.default_rng(0).shuffle(pix)     # an unbiased subset of the frame at any size
         self.pix = pix
-        self.n = min(128, pix.size)
+        self.n = min(4096, pix.size)
 
     def measure(self, budget_s):
         w = self.w
@@ -375,9 +375,10 @@ class CpuOracle:
                                   threads=self.cores)
         dt = time.perf_counter() - t0
         return {"value": round(paths / dt / 1e6, 6), "unit": "Mpaths/s", "cores": self.cores, "kind": "oracle",
-                "sample": "%d pixels of the every-16th-row/column subset of the 1024^2 image x %d spp "
-                          "(%d paths) in %.1f s; oracle encode+decode+macrocells of the full 512^3 volume "
-                          "took %.1f s (not in the rate)" % (self.n, w["spp"], paths, dt, self.enc_s)}
+                "sample": "%d random pixels of the 1024^2 frame (all of it when it fits the %.0f s budget) "
+                          "x %d spp = %d paths in %.2f s; oracle encode+decode+macrocells of the full 512^3 "
+                          "volume took %.1f s (not in the rate)" % (self.n, budget_s, w["spp"], paths, dt,
+                                                                     self.enc_s)}
 
 
 def cpu_baseline(budget_s):
@@ -413,7 +414,7 @@ def run_reference(args):
 
 def run_profile_case():
     """The capture case for `ncu --set full`: the 512^3 medium at 1:10 (same
-    grid as the benchmark), rendered twice at 256x256 x 16 spp so that a
+    grid as the benchmark), rendered twice at 512x512 x 16 spp so that a
     full-section capture of the second launch stays small."""
     import torch
 
@@ -424,16 +425,16 @@ def run_profile_case():
     from volgen import scenes
 
     w = scenes.TURBULENCE_512
-    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 256, 256))
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 512, 512))
     med = v.make_medium(v.MODE_PT, **w["medium"])
     vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
-    g = v.vdbc_encode(vol, w["ratio"])
-    img = torch.empty((256, 256, 4), dtype=torch.float32, device="cuda")
+    g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"])
+    img = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
     for _ in range(2):
         v.vdbc_render(g, cam, med, w["spp"], 2024, img)
     torch.cuda.synchronize()
     st = v.vdbc_render_stats_get(g)
-    print(json.dumps({"profile_case": "turbulence512_r10_pt256sq_16spp", "lookups": int(st.lookups),
+    print(json.dumps({"profile_case": "turbulence512_r10_pt512sq_16spp", "lookups": int(st.lookups),
                       "paths": int(st.paths)}))
 
 

@@ -327,7 +327,10 @@ __device__ __forceinline__ bool next_cell(Track& tr, const Majorants& m, const M
 // gbits: nwords fine occupancy words followed by ncwords coarse words; the
 // parts that fit in `smem_words` are staged in shared memory (coarse first)
 template <class S>
-__global__ void __launch_bounds__(256, 2)
+#ifndef VDBC_PT_MIN_BLOCKS
+#define VDBC_PT_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
     k_pt(S smp, Majorants m, CamDev cam, MedDev med, int spp, uint32_t k0, uint32_t k1,
          const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
          float4* __restrict__ path_out, DevStats* __restrict__ st, unsigned long long nitems, int tiles_x, int chunk)

@@ -111,6 +111,24 @@ def test_pt_turbulence_matches_oracle(env, payload):
     assert st.paths == 48 * 40 * 4 and st.error_flags == 0 and st.lookups > 48 * 40 * 4
 
 
+@pytest.mark.parametrize("macrocell", [16, 5])
+def test_pt_macrocell_sizes_match_oracle(env, macrocell):
+    """Majorant macrocells of other sizes (the benchmark uses 16^3) change the
+    free flights but not the parity with the oracle."""
+    torch, v, orc, vg, sc = env["torch"], env["v"], env["orc"], env["vg"], env["sc"]
+    dims = (112, 96, 80)
+    host = vg.generate_host(vg.make_params("turbulence", dims, 4))
+    grid = v.vdbc_encode(torch.from_numpy(host).to(env["dev"]), 6.0, macrocell=macrocell)
+    e = orc.encode(host, 6.0)
+    D = orc.decode_dense(host, e["active"], e["background_bits"])
+    cam = sc.pinhole_orbit(dims, 40, 36)
+    med = sc.pt_medium_args()
+    got = gpu_image(env, grid, cam, v.make_medium(v.MODE_PT, **med), 4, 77)
+    ref = oracle_image(env, D, cam, 1, 4, 77, macrocell=macrocell, **med)
+    err = np.abs(got[..., :3] - ref[..., :3]).mean(axis=(0, 1))
+    assert np.all(err <= PT_MEAN_ABS), err
+
+
 def test_pt_blobs_lossless_vdb_equals_dense_linear(env):
     """At 1:1 the decoded grid is the input, so the grid render and the linear
     plain-form render run the same arithmetic on the same values."""
@@ -226,17 +244,17 @@ def test_full_size_turbulence_sampled_pixels(env):
     w = sc.TURBULENCE_512
     p = vg.make_params(w["kind"], w["dims"], w["seed"])
     host = vg.generate_host(p)
-    grid = v.vdbc_encode(vg.generate_torch(p), w["ratio"])
+    grid = v.vdbc_encode(vg.generate_torch(p), w["ratio"], macrocell=w["macrocell"])
     cam_args = sc.pinhole_orbit(w["dims"], w["width"], w["height"])
     out = torch.empty((w["height"], w["width"], 4), dtype=torch.float32, device=env["dev"])
     v.vdbc_render(grid, v.make_camera(*cam_args), v.make_medium(v.MODE_PT, **w["medium"]), w["spp"], 2024, out)
     img = out.cpu().numpy().reshape(-1, 4).astype(np.float64)
     e = orc.encode(host, w["ratio"])
     D = orc.decode_dense(host, e["active"], e["background_bits"])
-    mx = orc.macrocell_minmax(D, 8)[1]
+    mx = orc.macrocell_minmax(D, w["macrocell"])[1]
     rng = np.random.default_rng(11)
     pix = np.sort(rng.choice(w["width"] * w["height"], 256, replace=False))
-    ref = orc.render_pixels(D, mx, orc.make_camera(*cam_args), orc.make_medium(1, macrocell=8, **w["medium"]),
+    ref = orc.render_pixels(D, mx, orc.make_camera(*cam_args), orc.make_medium(1, macrocell=w["macrocell"], **w["medium"]),
                             w["spp"], 2024, pix, threads=8)
     err = np.abs(img[pix, :3] - ref[:, :3]).mean(axis=0)
     assert np.all(err <= PT_MEAN_ABS), err

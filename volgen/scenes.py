@@ -43,8 +43,9 @@ def pt_medium_args(density_scale=20.0, albedo=0.9, g=0.6, max_bounces=16):
                 sun_rad=(3.0, 3.0, 3.0), env_rad=(0.25, 0.25, 0.25))
 
 
-# the 512^3 turbulent medium at 1:10, 1024^2 x 16 spp, albedo 0.9, g 0.6, 16 bounces
+# the 512^3 turbulent medium at 1:10, 1024^2 x 16 spp, albedo 0.9, g 0.6, 16 bounces;
+# majorant macrocells of 16^3 voxels (for grid and dense texture alike)
 TURBULENCE_512 = dict(kind="turbulence", dims=(512, 512, 512), seed=0, ratio=10.0, width=1024, height=1024,
-                      spp=16, medium=pt_medium_args())
+                      spp=16, medium=pt_medium_args(), macrocell=16)
 # the 64^3 blobs volume at 1:4, EA, 128^2, step 0.5, ortho +z
 BLOBS_64_EA = dict(kind="blobs", dims=(64, 64, 64), seed=0, ratio=4.0, width=128, height=128, step=0.5)
