@@ -228,6 +228,36 @@ vdbc_status vdbc_render_dense(const vdbc_volume* vol, const vdbc_camera* camera,
 vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void* stream,
                                          vdbc_render_stats* stats);
 
+/*
+ * vdbc_select_bricks_noalloc -- for callers that cannot allocate device memory
+ * while they run (a renderer inside a host application that owns the whole
+ * device-memory budget and forbids allocation after start-up, or a frame loop
+ * that cannot afford the implicit synchronization of cudaMalloc / cudaFree).
+ * The paper has no counterpart: this is the brick-selection phase of
+ * vdbc_encode (the histogram for the background B, the 32^3 brick ranges, the
+ * f scores and the choice of the bricks to activate) with all its scratch in
+ * one fixed array inside the library (about 1.6 MiB, held on every GPU that
+ * loads the library until the process exits).  Nothing is allocated.
+ *   in                    dense volume in DEVICE memory (on_device must be 1)
+ *   params                ratio, metric and payload as for vdbc_encode
+ *   background_bits_out   device pointer to one uint32: bit pattern of B
+ *   active_out            device pointer to n_bricks bytes: 1 = activated
+ *   counts_out            device pointer to three int64: number of non-empty
+ *                         bricks, number activated, nonzero if the volume held
+ *                         non-finite values (the other outputs are then invalid)
+ * Results equal vdbc_encode's (vdbc_grid_get_info, vdbc_grid_active_bricks).
+ * The work is enqueued on `stream`; the call does not wait.  The first call on
+ * a device looks up the array's device address; make that call before any
+ * stream capture.  Every call reuses the same array, so calls whose GPU work
+ * overlaps (different streams, or unordered threads) race: serialize them.
+ * Errors: INVALID_ARG for null pointers, a host volume, dims outside 1..8192,
+ * bad ratio/metric/payload, or more than 65,536 bricks (the array's limit,
+ * e.g. a 1024 x 1024 x 2048 volume); CUDA.
+ */
+vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vdbc_encode_params* params,
+                                       uint32_t* background_bits_out, uint8_t* active_out,
+                                       int64_t* counts_out, void* stream);
+
 /* vdbc_philox -- n outputs of the device Philox4x32-10 (the generator every
  * render draws from), for checking it against its published definition.
  * ctr: 4*n counters, key: 2 words, out: 4*n words; all host arrays. */

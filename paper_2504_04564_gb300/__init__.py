@@ -104,6 +104,8 @@ SIGNATURES = {
                                          ctypes.c_uint64, _vp, ctypes.c_int32, _vp]),
     "vdbc_volume_render_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
     "vdbc_philox": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "vdbc_select_bricks_noalloc": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.POINTER(EncodeParams), _vp, _vp,
+                                                  _vp, _vp]),
     "vdbc_kernel_launches": (ctypes.c_uint64, []),
     "vdbc_last_error": (ctypes.c_char_p, []),
     "vdbc_version": (ctypes.c_char_p, []),
@@ -319,6 +321,16 @@ def vdbc_volume_render_stats_get(volume: Volume, stream=None) -> RenderStats:
     s = RenderStats()
     _check(lib().vdbc_volume_render_stats_get(volume.handle, _stream(stream), ctypes.byref(s)))
     return s
+
+
+def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, counts_out, metric=F2, payload=FP32,
+                               stream=None):
+    """Brick selection of vdbc_encode without allocating (device tensors in
+    and out; see include/vdbc.h for who needs it and its limits)."""
+    d = make_dense(vol)
+    p = EncodeParams(float(ratio), int(metric), int(payload), 8, 0)
+    _check(lib().vdbc_select_bricks_noalloc(ctypes.byref(d), ctypes.byref(p), _ptr(background_bits_out)[0],
+                                            _ptr(active_out)[0], _ptr(counts_out)[0], _stream(stream)))
 
 
 def vdbc_philox(ctr, key) -> np.ndarray:

@@ -974,3 +974,121 @@ extern "C" void vdbc_grid_free(vdbc_grid* g)
     if (g->stats) cudaFree(g->stats);
     delete g;
 }
+
+// ---------------------------------------------------------------- brick selection without allocation
+// Some callers cannot allocate device memory while they run: a renderer
+// embedded in a host application that owns the whole device-memory budget
+// and forbids allocation after start-up, or a frame loop where cudaMalloc /
+// cudaFree would stall on their implicit device synchronization.  For them,
+// vdbc_select_bricks_noalloc runs the selection phase of vdbc_encode (the
+// histogram for B, brick ranges, scores, choice of the bricks to activate)
+// with its scratch in the fixed array below, so the call allocates nothing.
+// The array is part of this library's device image: every GPU that loads the
+// library holds it (about 1.6 MiB) until the process exits.
+namespace vdbc {
+namespace {
+
+constexpr long long kNoAllocMaxBricks = 65536;
+
+struct NoAllocScratch {
+    unsigned long long hist[65536];          // histogram of one level of B's bit pattern
+    unsigned long long fkey[kNoAllocMaxBricks];
+    uint32_t lo_key[kNoAllocMaxBricks];
+    uint32_t hi_key[kNoAllocMaxBricks];
+    uint8_t empty[kNoAllocMaxBricks];
+    uint32_t bsel[2];
+    int nonfinite;
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// device address of g_noalloc_scratch, looked up once per device (with that
+// device current) and cached; host code must not use the symbol itself
+vdbc_status noalloc_scratch(NoAllocScratch** out)
+{
+    constexpr int kMaxDevices = 64;
+    static NoAllocScratch* cache[kMaxDevices] = {nullptr};
+    int dev = 0;
+    VDBC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(VDBC_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    if (!cache[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(scratch)");
+        cache[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    *out = cache[dev];
+    return VDBC_OK;
+}
+
+__global__ void k_noalloc_finish(const uint32_t* __restrict__ bsel, const int* __restrict__ nonfinite,
+                                 uint32_t* __restrict__ b_out, long long* __restrict__ counts_out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        b_out[0] = bsel[1];
+        counts_out[2] = nonfinite[0];
+    }
+}
+
+}  // namespace
+}  // namespace vdbc
+
+// Same results as the selection inside vdbc_encode, written to the caller's
+// device buffers; enqueued on `stream`, nothing waits and nothing is
+// allocated.  The first call on a device looks up the scratch address (make
+// it before any stream capture).  All calls share one scratch array, so calls
+// whose work overlaps on the GPU (different streams, or threads without an
+// ordering) race: serialize them.
+extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vdbc_encode_params* params,
+                                                  uint32_t* background_bits_out, uint8_t* active_out,
+                                                  int64_t* counts_out, void* stream)
+{
+    clear_error();
+    if (!in || !params || !in->data || !background_bits_out || !active_out || !counts_out)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: null argument");
+    if (!in->on_device)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: the volume must be in device memory");
+    for (int a = 0; a < 3; ++a)
+        if (in->dims[a] < 1 || in->dims[a] > kMaxDim)
+            return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: dims[%d]=%d outside 1..%d", a,
+                             in->dims[a], kMaxDim);
+    const double ratio = params->ratio;
+    if (!(ratio >= 1.0) || !std::isfinite(ratio))
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: ratio must be a finite value >= 1");
+    const int metric = params->metric == 0 ? VDBC_F2 : params->metric;
+    if (metric < VDBC_F1 || metric > VDBC_F3)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: unknown metric %d", metric);
+    const int payload = params->payload;
+    if (payload < VDBC_FP32 || payload > VDBC_FP8)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: unknown payload %d", payload);
+    Dims d;
+    d.nx = in->dims[0]; d.ny = in->dims[1]; d.nz = in->dims[2];
+    d.bx = (d.nx + 31) / 32; d.by = (d.ny + 31) / 32; d.bz = (d.nz + 31) / 32;
+    const long long nb = (long long)d.bx * d.by * d.bz;
+    if (nb > kNoAllocMaxBricks)
+        return set_error(VDBC_ERR_INVALID_ARG,
+                         "vdbc_select_bricks_noalloc: %lld bricks of 32^3 exceed the fixed scratch limit of %lld",
+                         nb, kNoAllocMaxBricks);
+    NoAllocScratch* sc = nullptr;
+    VDBC_TRY(noalloc_scratch(&sc));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double nbud = std::floor((double)nb * 131072.0 / (ratio * (double)brick_bytes(payload)));
+    const long long budget = nbud > (double)nb ? nb : (long long)nbud;
+    // the scratch keeps the previous call's contents: clear what accumulates
+    VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
+    VDBC_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
+    KLAUNCH(k_pass1<<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->hist,
+                                                          &sc->nonfinite));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 0));
+    VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
+    KLAUNCH(k_pass2<<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel, sc->hist));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 1));
+    KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(sc->lo_key, sc->hi_key, (int)nb, sc->bsel, metric, sc->fkey,
+                                                     sc->empty));
+    KLAUNCH(k_select<<<1, 1024, 0, s>>>(sc->fkey, sc->empty, (int)nb, budget, active_out,
+                                        reinterpret_cast<long long*>(counts_out)));
+    KLAUNCH(k_noalloc_finish<<<1, 32, 0, s>>>(sc->bsel, &sc->nonfinite, background_bits_out,
+                                              reinterpret_cast<long long*>(counts_out)));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
