@@ -69,6 +69,10 @@ __global__ void __launch_bounds__(kPassThreads) k_pass1(const float* __restrict_
     const bool valid = lane < ex;
     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     const int rows = ey * ez;
+    // rows whose lanes all share one key (constant regions, the background)
+    // add to a per-warp run instead of hitting the same bin with atomics
+    uint32_t run_key = 0xffffffffu;
+    unsigned long long run_cnt = 0;
     constexpr int U = 4;   // rows in flight per warp
     for (int r0 = warp * U; r0 < rows; r0 += (kPassThreads / 32) * U) {
         uint32_t u[U];
@@ -91,10 +95,21 @@ __global__ void __launch_bounds__(kPassThreads) k_pass1(const float* __restrict_
                 kmin = min(kmin, k);
                 kmax = max(kmax, k);
                 unsigned peers = __match_any_sync(vmask, w >> 16);
-                if (lane == __ffs(peers) - 1) atomicAdd(hist + (w >> 16), (unsigned long long)__popc(peers));
+                if (peers == vmask) {                       // warp-uniform
+                    if ((w >> 16) == run_key) {
+                        run_cnt += (unsigned long long)__popc(vmask);
+                    } else {
+                        if (run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
+                        run_key = w >> 16;
+                        run_cnt = (unsigned long long)__popc(vmask);
+                    }
+                } else if (lane == __ffs(peers) - 1) {
+                    atomicAdd(hist + (w >> 16), (unsigned long long)__popc(peers));
+                }
             }
         }
     }
+    if (valid && run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
     if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
@@ -154,20 +169,45 @@ __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict_
     const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool valid = lane < ex;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     const int rows = ey * ez;
-    for (int row = warp; row < rows; row += kPassThreads / 32) {
-        uint32_t w = 0;
-        if (valid) {
-            int y = row % ey, z = row / ey;
-            w = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+    uint32_t run_key = 0xffffffffu;          // per-warp run of one key, as in pass 1
+    unsigned long long run_cnt = 0;
+    constexpr int U = 4;
+    for (int r0 = warp * U; r0 < rows; r0 += (kPassThreads / 32) * U) {
+        uint32_t u[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            int row = r0 + q;
+            u[q] = 0;
+            if (valid && row < rows) {
+                int y = row % ey, z = row / ey;
+                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+            }
         }
-        bool in = valid && (w >> 16) == H;
-        unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) {
-            unsigned peers = __match_any_sync(m, w & 0xffffu);
-            if (lane == __ffs(peers) - 1) atomicAdd(hist + (w & 0xffffu), (unsigned long long)__popc(peers));
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (r0 + q >= rows) break;               // warp-uniform
+            uint32_t w = u[q];
+            bool in = valid && (w >> 16) == H;
+            unsigned m = __ballot_sync(0xffffffffu, in);       // warp-uniform
+            if (m == 0u) continue;
+            unsigned peers = in ? __match_any_sync(m, w & 0xffffu) : 0u;   // only the lanes of m call it
+            bool uniform = __all_sync(0xffffffffu, !valid || peers == vmask) && m == vmask;
+            if (uniform) {                                      // one key in the whole row
+                if ((w & 0xffffu) == run_key) {
+                    run_cnt += (unsigned long long)__popc(vmask);
+                } else {
+                    if (run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
+                    run_key = w & 0xffffu;
+                    run_cnt = (unsigned long long)__popc(vmask);
+                }
+            } else if (in && lane == __ffs(peers) - 1) {
+                atomicAdd(hist + (w & 0xffffu), (unsigned long long)__popc(peers));
+            }
         }
     }
+    if (valid && run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
 }
 
 // ---------------------------------------------------------------- scores (Eq. f1-f3)
