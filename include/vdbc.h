@@ -258,6 +258,56 @@ vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vdbc_encode_p
                                        uint32_t* background_bits_out, uint8_t* active_out,
                                        int64_t* counts_out, void* stream);
 
+/* ---------------- many volumes in one launch (a project extension) ------ */
+/* one render job of a batch: a grid, its own camera, medium (PT), spp per
+ * frame and seed; rgba_out (device, width*height*4 floats) receives the
+ * running mean over the frames rendered so far */
+typedef struct {
+    const vdbc_grid* grid;
+    vdbc_camera camera;
+    vdbc_medium medium;
+    int32_t spp;
+    int32_t reserved;
+    uint64_t seed;
+    float* rgba_out;
+} vdbc_job;
+
+/* launch shape of the batched path tracer, chosen by the autotuner */
+typedef struct {
+    int32_t threads;       /* threads per block: 128 or 256 */
+    int32_t chunk;         /* paths a warp takes from the work counter at once (>= 32) */
+    int32_t coarse;        /* 1: cross empty 8^3 blocks of macrocells in one DDA step */
+    int32_t reserved;
+    float   frame_ms;      /* the tuner's measurement of one frame with this shape */
+} vdbc_tuning;
+
+typedef struct vdbc_batch vdbc_batch;
+
+/*
+ * vdbc_batch_create -- prepare a batch of up to 64 path-tracing jobs on
+ * grids of any size and payload, rendered together by ONE persistent launch
+ * per frame (Section 4's tracker; the paper renders one volume at a time).
+ * With autotune != 0 the launch shape is chosen by timing one frame per
+ * candidate (cached per GPU and batch layout in this process, and in the file
+ * named by VDBC_TUNE_CACHE when set).  The per-frame work (work-counter reset,
+ * persistent tracker, per-pixel accumulation) is then captured in a CUDA
+ * graph on `stream`.  Grids must outlive the batch.  Errors: INVALID_ARG
+ * (n outside 1..64, a null grid or output, EA media, bad spp/camera/medium);
+ * OOM; CUDA.
+ */
+vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_t autotune, void* stream,
+                              vdbc_batch** out);
+/* renders `frames` more progressive frames of every job (frame f uses sample
+ * ids [f*spp, (f+1)*spp), so F frames equal one render with F*spp samples)
+ * by replaying the captured graph; does not wait */
+vdbc_status vdbc_batch_render_frames(vdbc_batch* batch, int32_t frames, void* stream);
+/* restarts the accumulation at frame 0 */
+vdbc_status vdbc_batch_reset(vdbc_batch* batch, void* stream);
+vdbc_status vdbc_batch_get_tuning(const vdbc_batch* batch, vdbc_tuning* tuning);
+/* counters of the last frame; waits for `stream` */
+vdbc_status vdbc_batch_stats_get(const vdbc_batch* batch, void* stream, vdbc_render_stats* stats);
+void        vdbc_batch_free(vdbc_batch* batch);
+
 /* vdbc_philox -- n outputs of the device Philox4x32-10 (the generator every
  * render draws from), for checking it against its published definition.
  * ctr: 4*n counters, key: 2 words, out: 4*n words; all host arrays. */

@@ -76,6 +76,16 @@ class Medium(ctypes.Structure):
                 ("sun_dir", ctypes.c_float * 3), ("sun_rad", ctypes.c_float * 3), ("env_rad", ctypes.c_float * 3)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("camera", Camera), ("medium", Medium), ("spp", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rgba_out", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("chunk", ctypes.c_int32), ("coarse", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("frame_ms", ctypes.c_float)]
+
+
 class RenderStats(ctypes.Structure):
     _fields_ = [("lookups", ctypes.c_uint64), ("paths", ctypes.c_uint64), ("error_flags", ctypes.c_uint64),
                 ("events", ctypes.c_uint64 * 6)]
@@ -106,6 +116,13 @@ SIGNATURES = {
     "vdbc_philox": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
     "vdbc_select_bricks_noalloc": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.POINTER(EncodeParams), _vp, _vp,
                                                   _vp, _vp]),
+    "vdbc_batch_create": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_int32, ctypes.c_int32, _vp,
+                                         ctypes.POINTER(_vp)]),
+    "vdbc_batch_render_frames": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "vdbc_batch_reset": (ctypes.c_int, [_vp, _vp]),
+    "vdbc_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
+    "vdbc_batch_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
+    "vdbc_batch_free": (None, [_vp]),
     "vdbc_kernel_launches": (ctypes.c_uint64, []),
     "vdbc_last_error": (ctypes.c_char_p, []),
     "vdbc_version": (ctypes.c_char_p, []),
@@ -321,6 +338,65 @@ def vdbc_volume_render_stats_get(volume: Volume, stream=None) -> RenderStats:
     s = RenderStats()
     _check(lib().vdbc_volume_render_stats_get(volume.handle, _stream(stream), ctypes.byref(s)))
     return s
+
+
+class Batch:
+    """Owning wrapper of a vdbc_batch*; keeps its grids and outputs alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib().vdbc_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_job(grid: Grid, camera: Camera, medium: Medium, spp, seed, out) -> Job:
+    j = Job()
+    j.grid = grid.handle
+    j.camera = camera
+    j.medium = medium
+    j.spp = int(spp)
+    j.seed = int(seed)
+    j.rgba_out = _ptr(out)[0]
+    return j
+
+
+def vdbc_batch_create(jobs, autotune=True, stream=None, keep=()) -> Batch:
+    """jobs: a list of Job structs (see make_job); `keep` holds Python objects
+    (grids, output tensors) that must outlive the batch."""
+    arr = (Job * len(jobs))(*jobs)
+    h = ctypes.c_void_p()
+    _check(lib().vdbc_batch_create(arr, len(jobs), int(bool(autotune)), _stream(stream), ctypes.byref(h)))
+    return Batch(h.value, (list(keep), jobs))
+
+
+def vdbc_batch_render_frames(batch: Batch, frames=1, stream=None):
+    _check(lib().vdbc_batch_render_frames(batch.handle, int(frames), _stream(stream)))
+
+
+def vdbc_batch_reset(batch: Batch, stream=None):
+    _check(lib().vdbc_batch_reset(batch.handle, _stream(stream)))
+
+
+def vdbc_batch_get_tuning(batch: Batch) -> Tuning:
+    t = Tuning()
+    _check(lib().vdbc_batch_get_tuning(batch.handle, ctypes.byref(t)))
+    return t
+
+
+def vdbc_batch_stats_get(batch: Batch, stream=None) -> RenderStats:
+    st = RenderStats()
+    _check(lib().vdbc_batch_stats_get(batch.handle, _stream(stream), ctypes.byref(st)))
+    return st
 
 
 def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, counts_out, metric=F2, payload=FP32,

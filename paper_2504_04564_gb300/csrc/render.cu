@@ -21,8 +21,13 @@
 // per free flight: u0 = optical depth, u1 = accept, u2/u3 = phase function.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "vdbc_host.h"
 
@@ -324,38 +329,69 @@ __device__ __forceinline__ bool next_cell(Track& tr, const Majorants& m, const M
     return false;
 }
 
-// gbits: nwords fine occupancy words followed by ncwords coarse words; the
-// parts that fit in `smem_words` are staged in shared memory (coarse first)
+// Constants of one render job as the tracker sees them.
+struct JobView {
+    Majorants m;
+    CamDev cam;
+    MedDev med;
+    const uint32_t* bits;      // occupancy bit per macrocell (majorant > 0)
+    const uint32_t* cbits;     // occupancy bit per kCoarse^3 block of macrocells
+    int cx_n, cy_n;            // coarse grid size along x and y
+    float4* path_out;          // spp x npix path radiances of the frame
+    int npix, spp, tiles_x;
+    uint32_t k0, k1;           // Philox key = the seed
+    uint32_t sample_base;      // sample id of the frame's first sample (progressive frames)
+    unsigned long long item_begin, items;   // this job's range of the work counter
+};
+
+// one job: constants in kernel parameters, the grid's payload fixed at compile time
 template <class S>
-#ifndef VDBC_PT_MIN_BLOCKS
-#define VDBC_PT_MIN_BLOCKS 2
-#endif
-__global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
-    k_pt(S smp, Majorants m, CamDev cam, MedDev med, int spp, uint32_t k0, uint32_t k1,
-         const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
-         float4* __restrict__ path_out, DevStats* __restrict__ st, unsigned long long nitems, int tiles_x, int chunk)
-{
-    extern __shared__ uint32_t s_bits[];
-    const uint32_t* cbits = gbits + nwords;
-    const uint32_t* bits = gbits;
-    if (ncwords <= smem_words) {
-        for (int i = threadIdx.x; i < ncwords; i += blockDim.x) s_bits[i] = gbits[nwords + i];
-        cbits = s_bits;
-        if (ncwords + nwords <= smem_words) {
-            for (int i = threadIdx.x; i < nwords; i += blockDim.x) s_bits[ncwords + i] = gbits[i];
-            bits = s_bits + ncwords;
-        }
+struct SingleSource {
+    static constexpr bool kMulti = false;
+    const JobView& j;
+    const S& smp;
+    const uint32_t* b;
+    const uint32_t* cb;
+    __device__ __forceinline__ int find(unsigned long long) const { return 0; }
+    __device__ __forceinline__ const JobView& job(int) const { return j; }
+    __device__ __forceinline__ const uint32_t* bits(int) const { return b; }
+    __device__ __forceinline__ const uint32_t* cbits(int) const { return cb; }
+    __device__ __forceinline__ float sample(int, float x, float y, float z, Accessor& a) const { return smp(x, y, z, a); }
+};
+
+// many jobs: their constants and grids staged in shared memory; each lane
+// decodes its job's payload type at run time
+struct BatchSource {
+    static constexpr bool kMulti = true;
+    const JobView* jobs;
+    const GridView* grids;
+    int n;
+    __device__ __forceinline__ int find(unsigned long long item) const
+    {
+        int j = 0;
+        while (j + 1 < n && item >= jobs[j + 1].item_begin) ++j;
+        return j;
     }
-    __syncthreads();
-    const int cx_n = (m.mx + kCoarse - 1) / kCoarse, cy_n = (m.my + kCoarse - 1) / kCoarse;
+    __device__ __forceinline__ const JobView& job(int i) const { return jobs[i]; }
+    __device__ __forceinline__ const uint32_t* bits(int i) const { return jobs[i].bits; }
+    __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
+    __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
+    {
+        return vdb_trilinear<-1>(grids[i], x, y, z, a);
+    }
+};
+
+// The tracker loop shared by the single-job and the batch kernels.
+template <class Src>
+__device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
+                                        int chunk)
+{
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int npix = cam.w * cam.h;
-    const int dda_guard = m.mx + m.my + m.mz + 8;
     Walk w{};
     unsigned long long paths = 0;
 
-    int mode = kNeed;
+    int mode = kNeed, jb = 0;
     uint32_t pixel = 0, sample = 0, call = 0, lcall = 0;
     int bounce = 0;
     float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), nd = d, L = f3(0.f, 0.f, 0.f);
@@ -387,36 +423,41 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
                 if (item >= nitems) {
                     mode = kDone;
                 } else {
-                    // item -> (sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
-                    unsigned long long per = nitems / (unsigned long long)spp;
-                    sample = (uint32_t)(item / per);
-                    uint32_t q = (uint32_t)(item % per), tile = q >> 5, in = q & 31;
-                    int px = (int)(tile % tiles_x) * 8 + (int)(in & 7);
-                    int py = (int)(tile / tiles_x) * 4 + (int)(in >> 3);
-                    if (px < cam.w && py < cam.h) {
+                    // item -> (job, sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
+                    jb = src.find(item);
+                    const JobView& F = src.job(jb);
+                    unsigned long long local = item - F.item_begin;
+                    unsigned long long per = F.items / (unsigned long long)F.spp;
+                    sample = (uint32_t)(local / per);
+                    uint32_t q = (uint32_t)(local % per), tile = q >> 5, in = q & 31;
+                    int px = (int)(tile % F.tiles_x) * 8 + (int)(in & 7);
+                    int py = (int)(tile / F.tiles_x) * 4 + (int)(in >> 3);
+                    if (px < F.cam.w && py < F.cam.h) {
                         VDBC_EVENT(w, 5);
-                        pixel = (uint32_t)(py * cam.w + px);
-                        Rng rng{pixel, sample, k0, k1};
+                        pixel = (uint32_t)(py * F.cam.w + px);
+                        if (src.kMulti) acc.reset();   // another job may use another grid
+                        Rng rng{pixel, F.sample_base + sample, F.k0, F.k1};
                         call = 0;
                         lcall = 0;
                         U4 r = rng.draw(call++, 0);
-                        camera_ray(cam, px, py, u01(r.x), u01(r.y), o, d);
+                        camera_ray(F.cam, px, py, u01(r.x), u01(r.y), o, d);
                         L = f3(0.f, 0.f, 0.f);
                         beta = 1.0f;
                         bounce = 0;
                         float tin, tout;
-                        if (!clip_box(m, o, d, tin, tout)) {
-                            path_out[(size_t)sample * npix + pixel] = make_float4(med.env_rad.x, med.env_rad.y,
-                                                                                 med.env_rad.z, 1.0f);
+                        if (!clip_box(F.m, o, d, tin, tout)) {
+                            F.path_out[(size_t)sample * F.npix + pixel] = make_float4(F.med.env_rad.x, F.med.env_rad.y,
+                                                                                     F.med.env_rad.z, 1.0f);
                             ++paths;
                         } else {
-                            tr.dda.init(m, o, d, tin, tout);
+                            tr.dda.init(F.m, o, d, tin, tout);
                             tau = -1.0f;   // every ray starts a new free flight
                             VDBC_EVENT(w, 4);
-                            guard = dda_guard;
+                            guard = F.m.mx + F.m.my + F.m.mz + 8;
                             steps_in_cell = 0;
                             mode = kDelta;
-                            if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kDelta;   // leaves at once
+                            if (!next_cell(tr, F.m, F.med, o, src.bits(jb), src.cbits(jb), F.cx_n, F.cy_n, guard, w))
+                                mode = -kDelta;   // leaves at once
                         }
                     }
                 }
@@ -425,13 +466,19 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
             else pool_next += n;
         }
         if (__all_sync(0xffffffffu, mode == kDone)) break;
+        const JobView& J = src.job(jb);
+        const Majorants& m = J.m;
+        const MedDev& med = J.med;
+        const uint32_t* bits = src.bits(jb);
+        const uint32_t* cbits = src.cbits(jb);
+        const int cx_n = J.cx_n, cy_n = J.cy_n;
 
         // ---- one free flight per lane: draw tau, spend it over the cells, and
         // where it runs out evaluate the density (delta: accept or not;
         // ratio: attenuate)
         if (mode == kDelta || mode == kRatio) {
             if (tau < 0.0f) {
-                Rng rng{pixel, sample, k0, k1};
+                Rng rng{pixel, J.sample_base + sample, J.k0, J.k1};
                 U4 r = (mode == kDelta) ? rng.draw(call++, 0) : rng.draw(lcall++, 1);
                 VDBC_EVENT(w, 3);
                 tau = -logf(1.0f - u01(r.x));
@@ -462,7 +509,7 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
                 tr.tcur = t;
                 tau = -1.0f;
                 float3 x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
-                float sigma = __fmul_rn(med.sigma_scale, smp(x.x, x.y, x.z, acc));
+                float sigma = __fmul_rn(med.sigma_scale, src.sample(jb, x.x, x.y, x.z, acc));
                 ++w.lookups;
                 if (mode == kRatio) {
                     T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
@@ -488,7 +535,7 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
                         tr.dda.init(m, o, d, tin, tout);
                         tau = -1.0f;   // every ray starts a new free flight
                         VDBC_EVENT(w, 4);
-                        guard = dda_guard;
+                        guard = m.mx + m.my + m.mz + 8;
                         steps_in_cell = 0;
                         if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kRatio;
                     } else {
@@ -518,7 +565,7 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
                         tr.dda.init(m, o, d, tin, tout);
                         tau = -1.0f;   // every ray starts a new free flight
                         VDBC_EVENT(w, 4);
-                        guard = dda_guard;
+                        guard = m.mx + m.my + m.mz + 8;
                         steps_in_cell = 0;
                         mode = kDelta;
                         if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kDelta;
@@ -530,13 +577,61 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
                 }
             }
             if (finished) {
-                path_out[(size_t)sample * npix + pixel] = make_float4(L.x, L.y, L.z, 1.0f);
+                J.path_out[(size_t)sample * J.npix + pixel] = make_float4(L.x, L.y, L.z, 1.0f);
                 ++paths;
                 mode = kNeed;
             }
         }
     }
     flush_stats(st, w, paths);
+}
+
+#ifndef VDBC_PT_MIN_BLOCKS
+#define VDBC_PT_MIN_BLOCKS 2
+#endif
+
+// gbits: nwords fine occupancy words followed by ncwords coarse words; the
+// parts that fit in `smem_words` are staged in shared memory (coarse first)
+template <class S>
+__global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
+    k_pt(S smp, JobView job, const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
+         DevStats* __restrict__ st, int chunk)
+{
+    extern __shared__ uint32_t s_bits[];
+    const uint32_t* cbits = gbits + nwords;
+    const uint32_t* bits = gbits;
+    if (ncwords <= smem_words) {
+        for (int i = threadIdx.x; i < ncwords; i += blockDim.x) s_bits[i] = gbits[nwords + i];
+        cbits = s_bits;
+        if (ncwords + nwords <= smem_words) {
+            for (int i = threadIdx.x; i < nwords; i += blockDim.x) s_bits[ncwords + i] = gbits[i];
+            bits = s_bits + ncwords;
+        }
+    }
+    __syncthreads();
+    SingleSource<S> src{job, smp, bits, cbits};
+    pt_loop(src, job.items, st, chunk);
+}
+
+// all jobs of a batch in one persistent launch; frame[0] numbers the
+// progressive frame, so frame f renders sample ids [f*spp, (f+1)*spp)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 512 / kThreads)
+    k_pt_batch(const JobView* __restrict__ jobs, const GridView* __restrict__ grids, int n,
+               unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk)
+{
+    extern __shared__ unsigned char s_raw[];
+    JobView* sj = reinterpret_cast<JobView*>(s_raw);
+    GridView* sg = reinterpret_cast<GridView*>(s_raw + sizeof(JobView) * n);
+    const int f = frame[0];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sj[i] = jobs[i];
+        sj[i].sample_base = (uint32_t)f * (uint32_t)sj[i].spp;
+        sg[i] = grids[i];
+    }
+    __syncthreads();
+    BatchSource src{sj, sg, n};
+    pt_loop(src, nitems, st, chunk);
 }
 
 // average of the spp path radiances of each pixel, in sample order
@@ -551,6 +646,31 @@ __global__ void k_pt_reduce(const float4* __restrict__ path_out, int npix, int s
     }
     float inv = 1.0f / (float)spp;
     out[p] = make_float4(r * inv, g * inv, b * inv, 1.0f);
+}
+
+// batch accumulation: per job (blockIdx.y) and pixel, add this frame's spp
+// path radiances (in sample order) to the running sum and write the mean
+__global__ void k_batch_reduce(const JobView* __restrict__ jobs, float4* const* __restrict__ sums,
+                               float* const* __restrict__ outs, const int* __restrict__ frame)
+{
+    const JobView& J = jobs[blockIdx.y];
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= J.npix) return;
+    float r = 0.f, g = 0.f, b = 0.f;
+    for (int s = 0; s < J.spp; ++s) {
+        float4 v = J.path_out[(size_t)s * J.npix + p];
+        r += v.x; g += v.y; b += v.z;
+    }
+    float4 acc = sums[blockIdx.y][p];
+    acc.x += r; acc.y += g; acc.z += b;
+    sums[blockIdx.y][p] = acc;
+    float inv = 1.0f / ((float)(frame[0] + 1) * (float)J.spp);
+    reinterpret_cast<float4*>(outs[blockIdx.y])[p] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, 1.0f);
+}
+
+__global__ void k_batch_next_frame(int* frame)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) frame[0] += 1;
 }
 
 // coarse occupancy: a bit per kCoarse^3 block of macrocells, set if any
@@ -755,10 +875,32 @@ int work_chunk()
 }
 constexpr size_t kSmemBitsMax = 96 * 1024;
 
+// the job's constants for the tracker (bits are filled in by the caller)
+JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int spp, uint64_t seed,
+                 float4* path_out)
+{
+    JobView j;
+    std::memset(&j, 0, sizeof(j));
+    j.m = mj;
+    j.cam = cam;
+    j.med = med;
+    j.cx_n = (mj.mx + kCoarse - 1) / kCoarse;
+    j.cy_n = (mj.my + kCoarse - 1) / kCoarse;
+    j.path_out = path_out;
+    j.npix = cam.w * cam.h;
+    j.spp = spp;
+    j.tiles_x = (cam.w + 7) / 8;
+    j.k0 = (uint32_t)seed;
+    j.k1 = (uint32_t)(seed >> 32);
+    j.sample_base = 0;
+    j.item_begin = 0;
+    j.items = (unsigned long long)spp * (unsigned long long)j.tiles_x * (unsigned long long)((cam.h + 3) / 4) * 32ull;
+    return j;
+}
+
 template <class S>
-vdbc_status launch_pt(const S& smp, const Majorants& mj, const CamDev& cam, const MedDev& med, int spp,
-                      uint64_t seed, const uint32_t* bits, int nwords, int ncwords, float4* path_out,
-                      DevStats* stats, unsigned long long nitems, int tiles_x, int chunk, cudaStream_t s)
+vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, int nwords, int ncwords,
+                      DevStats* stats, int chunk, cudaStream_t s)
 {
     int smem_words = std::min<int>(nwords + ncwords, (int)(kSmemBitsMax / 4));
     if (smem_words < ncwords) smem_words = 0;
@@ -768,11 +910,10 @@ vdbc_status launch_pt(const S& smp, const Majorants& mj, const CamDev& cam, cons
     int per_sm = 0;
     VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    long long want = (nitems + kPtThreads - 1) / kPtThreads;
+    long long want = (long long)((job.items + kPtThreads - 1) / kPtThreads);
     long long blocks = std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
-    KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, mj, cam, med, spp, (uint32_t)seed,
-                                                            (uint32_t)(seed >> 32), bits, nwords, ncwords,
-                                                            smem_words, path_out, stats, nitems, tiles_x, chunk));
+    KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, job, bits, nwords, ncwords, smem_words, stats,
+                                                            chunk));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
@@ -792,8 +933,6 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     int nwords = (int)((ncell + 31) / 32);
     int cxn = (mj.mx + kCoarse - 1) / kCoarse, cyn = (mj.my + kCoarse - 1) / kCoarse, czn = (mj.mz + kCoarse - 1) / kCoarse;
     int ncwords = (cxn * cyn * czn + 31) / 32;
-    int tiles_x = (cam.w + 7) / 8, tiles_y = (cam.h + 3) / 4;
-    unsigned long long nitems = (unsigned long long)spp * tiles_x * tiles_y * 32;
     uint32_t* bits = nullptr;
     float4* path_out = nullptr;
     VDBC_TRY(dev_alloc(reinterpret_cast<void**>(&bits), (size_t)(nwords + ncwords) * 4, s));
@@ -806,8 +945,8 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     } else {
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
-    st = launch_pt<S>(smp, mj, cam, med, spp, seed, bits, nwords, ncwords, path_out, stats, nitems, tiles_x,
-                      work_chunk(), s);
+    JobView job = make_job(mj, cam, med, spp, seed, path_out);
+    st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, work_chunk(), s);
     if (st == VDBC_OK) {
         KLAUNCH(k_pt_reduce<<<blocks_for(npix, 256), 256, 0, s>>>(path_out, (int)npix, spp, out));
         cudaError_t e = cudaGetLastError();
@@ -1027,4 +1166,396 @@ extern "C" vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void
     out->error_flags = h.error_flags;
     for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
     return VDBC_OK;
+}
+
+// ---------------------------------------------------------------- batches
+namespace vdbc {
+namespace {
+
+struct TuneKey {
+    std::string text;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, vdbc_tuning> g_tune_cache;
+
+std::string gpu_name()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    return p.name;
+}
+
+bool tune_file_lookup(const std::string& key, vdbc_tuning* t)
+{
+    const char* path = std::getenv("VDBC_TUNE_CACHE");
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[900];
+        vdbc_tuning v{};
+        if (std::sscanf(line, "%899s %d %d %d %f", k, &v.threads, &v.chunk, &v.coarse, &v.frame_ms) == 5 &&
+            key == k) {
+            *t = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_file_store(const std::string& key, const vdbc_tuning& t)
+{
+    const char* path = std::getenv("VDBC_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), t.threads, t.chunk, t.coarse, t.frame_ms);
+    std::fclose(f);
+}
+
+}  // namespace
+}  // namespace vdbc
+
+struct vdbc_batch {
+    int n = 0;
+    std::vector<vdbc_job> jobs;
+    vdbc::JobView* d_jobs = nullptr;        // device job table (bits point at the chosen variant)
+    vdbc::GridView* d_grids = nullptr;
+    std::vector<vdbc::JobView> h_jobs;
+    std::vector<uint32_t*> bits_on, bits_off;   // per job: fine + coarse words, coarse skipping on / off
+    std::vector<int> nwords;
+    float4* path_out = nullptr;
+    float4* sums = nullptr;
+    float4** d_sums = nullptr;
+    float** d_outs = nullptr;
+    int* d_frame = nullptr;
+    vdbc::DevStats* stats = nullptr;
+    unsigned long long nitems = 0;
+    size_t max_npix = 0;
+    vdbc_tuning tuning{256, 256, 1, 0, 0.0f};
+    unsigned blocks128 = 0, blocks256 = 0;        // launch configuration per block size
+    size_t smem128 = 0, smem256 = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace vdbc {
+namespace {
+
+vdbc_status batch_alloc(vdbc_batch* b, void** p, size_t bytes)
+{
+    if (fault_injected("oom")) return set_error(VDBC_ERR_OOM, "device allocation of %zu bytes refused (VDBC_FAULT=oom)", bytes);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return cuda_status(e, "vdbc_batch_create alloc"); }
+    b->allocs.push_back(*p);
+    return VDBC_OK;
+}
+
+// points every job's cbits at the coarse words with skipping on or off and uploads the table
+vdbc_status batch_select_bits(vdbc_batch* b, bool coarse, cudaStream_t s)
+{
+    for (int i = 0; i < b->n; ++i) {
+        uint32_t* base = coarse ? b->bits_on[i] : b->bits_off[i];
+        b->h_jobs[i].bits = base;
+        b->h_jobs[i].cbits = base + b->nwords[i];
+    }
+    VDBC_CUDA(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(JobView) * b->n, cudaMemcpyHostToDevice, s));
+    return VDBC_OK;
+}
+
+// grid size and shared memory of the batched tracker for a block size; called
+// before any capture (it sets a function attribute and queries occupancy)
+template <int kThreads>
+vdbc_status batch_config(const vdbc_batch* b, unsigned* blocks, size_t* smem)
+{
+    *smem = (sizeof(JobView) + sizeof(GridView)) * (size_t)b->n;
+    auto kern = k_pt_batch<kThreads>;
+    if (*smem > 48 * 1024)
+        VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+    int per_sm = 0;
+    VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, *smem));
+    if (per_sm < 1) per_sm = 1;
+    long long want = (long long)((b->nitems + kThreads - 1) / kThreads);
+    *blocks = (unsigned)std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
+    return VDBC_OK;
+}
+
+template <int kThreads>
+vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, cudaStream_t s)
+{
+    unsigned& blocks = kThreads == 128 ? b->blocks128 : b->blocks256;
+    size_t& smem = kThreads == 128 ? b->smem128 : b->smem256;
+    if (blocks == 0) VDBC_TRY(batch_config<kThreads>(b, &blocks, &smem));
+    KLAUNCH(k_pt_batch<kThreads><<<blocks, kThreads, smem, s>>>(b->d_jobs, b->d_grids, b->n, b->nitems, b->d_frame,
+                                                                b->stats, chunk));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
+
+// the work of one frame: counters, tracker, accumulation, next frame number
+vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s)
+{
+    VDBC_CUDA(cudaMemsetAsync(b->stats, 0, sizeof(DevStats), s));
+    if (t.threads == 128) VDBC_TRY(batch_launch_pt<128>(b, t.chunk, s));
+    else VDBC_TRY(batch_launch_pt<256>(b, t.chunk, s));
+    if (accumulate) {
+        dim3 grid((unsigned)((b->max_npix + 255) / 256), (unsigned)b->n);
+        KLAUNCH(k_batch_reduce<<<grid, 256, 0, s>>>(b->d_jobs, b->d_sums, b->d_outs, b->d_frame));
+        KLAUNCH(k_batch_next_frame<<<1, 32, 0, s>>>(b->d_frame));
+        VDBC_CUDA(cudaGetLastError());
+    }
+    return VDBC_OK;
+}
+
+std::string batch_key(const vdbc_batch* b)
+{
+    // GPU and the layout that decides the work: grid sizes, payloads, macrocells, images, spp
+    unsigned long long h = 0xcbf29ce484222325ull;
+    auto mix = [&](long long v) { h ^= (unsigned long long)v; h *= 0x100000001b3ull; };
+    for (const vdbc_job& j : b->jobs) {
+        for (int a = 0; a < 3; ++a) mix(j.grid->info.dims[a]);
+        mix(j.grid->info.payload); mix(j.grid->info.macrocell); mix(j.grid->info.n_leaves);
+        mix(j.camera.width); mix(j.camera.height); mix(j.spp); mix(j.medium.max_bounces);
+    }
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), "%016llx", h);
+    std::string name = gpu_name();
+    for (char& c : name) if (c == ' ') c = '_';
+    return name + "|" + buf;
+}
+
+// times one frame for each candidate shape and keeps the fastest
+vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
+{
+    const std::string key = batch_key(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { b->tuning = it->second; return VDBC_OK; }
+    }
+    vdbc_tuning cached;
+    if (tune_file_lookup(key, &cached)) {
+        b->tuning = cached;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = cached;
+        return VDBC_OK;
+    }
+    const int threads[] = {128, 256};
+    const int chunks[] = {64, 256, 1024};
+    const int coarses[] = {1, 0};
+    cudaEvent_t e0, e1;
+    VDBC_CUDA(cudaEventCreate(&e0));
+    VDBC_CUDA(cudaEventCreate(&e1));
+    vdbc_tuning best{256, 256, 1, 0, 1e30f};
+    vdbc_status st = VDBC_OK;
+    for (int co : coarses) {
+        st = batch_select_bits(b, co != 0, s);
+        if (st != VDBC_OK) break;
+        for (int th : threads)
+            for (int ch : chunks) {
+                vdbc_tuning t{th, ch, co, 0, 0.0f};
+                st = batch_frame(b, t, false, s);           // warm-up
+                if (st == VDBC_OK && cudaEventRecord(e0, s) != cudaSuccess) st = set_error(VDBC_ERR_CUDA, "tune event");
+                if (st == VDBC_OK) st = batch_frame(b, t, false, s);
+                if (st == VDBC_OK && cudaEventRecord(e1, s) != cudaSuccess) st = set_error(VDBC_ERR_CUDA, "tune event");
+                if (st == VDBC_OK) st = wait_stream(s);
+                if (st != VDBC_OK) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t.frame_ms = ms;
+                if (ms < best.frame_ms) best = t;
+            }
+        if (st != VDBC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != VDBC_OK) return st;
+    b->tuning = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    tune_file_store(key, best);
+    return VDBC_OK;
+}
+
+// captures one frame on a private stream (capture cannot use the legacy
+// default stream); the graph is launched later into the caller's stream
+vdbc_status batch_capture(vdbc_batch* b, cudaStream_t s)
+{
+    VDBC_TRY(batch_select_bits(b, b->tuning.coarse != 0, s));
+    if (b->tuning.threads == 128) VDBC_TRY(batch_config<128>(b, &b->blocks128, &b->smem128));
+    else VDBC_TRY(batch_config<256>(b, &b->blocks256, &b->smem256));
+    VDBC_TRY(wait_stream(s));
+    cudaStream_t cs = nullptr;
+    VDBC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_status(e, "cudaStreamBeginCapture"); }
+    vdbc_status st = batch_frame(b, b->tuning, true, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st != VDBC_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+    b->graph = g;
+    VDBC_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    return VDBC_OK;
+}
+
+}  // namespace
+}  // namespace vdbc
+
+extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_t autotune, void* stream,
+                                         vdbc_batch** out)
+{
+    clear_error();
+    if (!jobs || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_create: null argument");
+    *out = nullptr;
+    if (n < 1 || n > 64) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_create: %d jobs outside 1..64", n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    vdbc_batch* b = new vdbc_batch();
+    auto fail = [&](vdbc_status st) { vdbc_batch_free(b); return st; };
+    b->n = n;
+    b->jobs.assign(jobs, jobs + n);
+    b->h_jobs.resize(n);
+    b->bits_on.resize(n);
+    b->bits_off.resize(n);
+    b->nwords.resize(n);
+    std::vector<GridView> grids(n);
+    std::vector<float4*> sum_ptrs(n);
+    std::vector<float*> outs(n);
+    unsigned long long items = 0;
+    size_t path_floats4 = 0, sum_floats4 = 0;
+    for (int i = 0; i < n; ++i) {
+        const vdbc_job& j = jobs[i];
+        if (!j.grid || !j.rgba_out) return fail(set_error(VDBC_ERR_INVALID_ARG, "job %d: null grid or output", i));
+        vdbc_status st = check_camera(&j.camera);
+        if (st != VDBC_OK) return fail(st);
+        if (j.medium.mode != VDBC_MODE_PT) return fail(set_error(VDBC_ERR_INVALID_ARG, "job %d: batches path trace", i));
+        MedHost mh;
+        st = make_med(&j.medium, j.grid->info.dims, j.spp, s, mh);
+        if (st != VDBC_OK) return fail(st);
+        const GridView& g = j.grid->view;
+        Majorants mj{g.mcmax, g.mc, g.mx, g.my, g.mz, g.nx, g.ny, g.nz};
+        CamDev cam = make_cam(&j.camera, j.grid->info.dims);
+        JobView jv = make_job(mj, cam, mh.dev, j.spp, j.seed, nullptr);
+        jv.item_begin = items;
+        items += jv.items;
+        path_floats4 += (size_t)j.spp * jv.npix;
+        sum_floats4 += (size_t)jv.npix;
+        b->max_npix = std::max<size_t>(b->max_npix, (size_t)jv.npix);
+        b->h_jobs[i] = jv;
+        grids[i] = g;
+        outs[i] = j.rgba_out;
+    }
+    b->nitems = items;
+    vdbc_status st = batch_alloc(b, reinterpret_cast<void**>(&b->path_out), path_floats4 * sizeof(float4));
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->sums), sum_floats4 * sizeof(float4));
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_jobs), sizeof(JobView) * n);
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_grids), sizeof(GridView) * n);
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_sums), sizeof(float4*) * n);
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_outs), sizeof(float*) * n);
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_frame), sizeof(int));
+    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->stats), sizeof(DevStats));
+    if (st != VDBC_OK) return fail(st);
+    size_t po = 0, so = 0;
+    for (int i = 0; i < n; ++i) {
+        JobView& jv = b->h_jobs[i];
+        jv.path_out = b->path_out + po;
+        po += (size_t)jv.spp * jv.npix;
+        sum_ptrs[i] = b->sums + so;
+        so += (size_t)jv.npix;
+        // occupancy bits, once with coarse skipping and once without
+        const Majorants& mj = jv.m;
+        long long ncell = (long long)mj.mx * mj.my * mj.mz;
+        int nwords = (int)((ncell + 31) / 32);
+        int czn = (mj.mz + kCoarse - 1) / kCoarse;
+        int ncwords = (jv.cx_n * jv.cy_n * czn + 31) / 32;
+        b->nwords[i] = nwords;
+        st = batch_alloc(b, reinterpret_cast<void**>(&b->bits_on[i]), (size_t)(nwords + ncwords) * 4);
+        if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->bits_off[i]), (size_t)(nwords + ncwords) * 4);
+        if (st != VDBC_OK) return fail(st);
+        KLAUNCH(k_occupancy<<<blocks_for(ncell, 256), 256, 0, s>>>(mj.mcmax, ncell, jv.med.sigma_scale, b->bits_on[i]));
+        KLAUNCH(k_coarse_occupancy<<<blocks_for((long long)jv.cx_n * jv.cy_n * czn, 256), 256, 0, s>>>(
+            b->bits_on[i], mj.mx, mj.my, mj.mz, b->bits_on[i] + nwords, jv.cx_n, jv.cy_n, czn));
+        cudaError_t e = cudaMemcpyAsync(b->bits_off[i], b->bits_on[i], (size_t)nwords * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->bits_off[i] + nwords, 0xff, (size_t)ncwords * 4, s);
+        if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create bits"));
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_grids, grids.data(), sizeof(GridView) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_sums, sum_ptrs.data(), sizeof(float4*) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_outs, outs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_frame, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sums, 0, sum_floats4 * sizeof(float4), s);
+    if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create upload"));
+    st = batch_select_bits(b, true, s);
+    if (st == VDBC_OK) st = wait_stream(s);      // host vectors above must outlive their copies
+    if (st == VDBC_OK && autotune) st = batch_autotune(b, s);
+    if (st == VDBC_OK) st = vdbc_batch_reset(b, stream);
+    if (st == VDBC_OK) st = batch_capture(b, s);
+    if (st != VDBC_OK) return fail(st);
+    *out = b;
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_batch_render_frames(vdbc_batch* b, int32_t frames, void* stream)
+{
+    clear_error();
+    if (!b || !b->exec || frames < 0) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_render_frames: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int f = 0; f < frames; ++f) {
+        count_launch(b->n > 0 ? 3 : 0);      // tracker, reduce, frame counter
+        VDBC_CUDA(cudaGraphLaunch(b->exec, s));
+    }
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_batch_reset(vdbc_batch* b, void* stream)
+{
+    clear_error();
+    if (!b) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_reset: null batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t npix = 0;
+    for (const JobView& j : b->h_jobs) npix += (size_t)j.npix;
+    VDBC_CUDA(cudaMemsetAsync(b->d_frame, 0, sizeof(int), s));
+    VDBC_CUDA(cudaMemsetAsync(b->sums, 0, npix * sizeof(float4), s));
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_batch_get_tuning(const vdbc_batch* b, vdbc_tuning* t)
+{
+    clear_error();
+    if (!b || !t) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_get_tuning: null argument");
+    *t = b->tuning;
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_batch_stats_get(const vdbc_batch* b, void* stream, vdbc_render_stats* out)
+{
+    clear_error();
+    if (!b || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_stats_get: null argument");
+    VDBC_TRY(wait_stream(static_cast<cudaStream_t>(stream)));
+    DevStats h;
+    VDBC_CUDA(cudaMemcpy(&h, b->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    out->lookups = h.lookups;
+    out->paths = h.paths;
+    out->error_flags = h.error_flags;
+    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    return VDBC_OK;
+}
+
+extern "C" void vdbc_batch_free(vdbc_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
 }

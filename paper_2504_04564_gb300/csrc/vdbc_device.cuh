@@ -138,39 +138,45 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 
 // trilinear reconstruction at index-space position p, clamp to edge; every
 // call descends the tree (through the accessor's cached leaf) and decodes the
-// eight voxels; P is the payload type of the grid
+// eight voxels; P is the payload type of the grid (-1: read at run time)
+template <int P>
+__device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, float py, float pz, Accessor& acc)
+{
+    float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+    float tx = px - fx, ty = py - fy, tz = pz - fz;
+    int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
+    int x0 = min(max(i0, 0), g.nx - 1), x1 = min(max(i0 + 1, 0), g.nx - 1);
+    int y0 = min(max(j0, 0), g.ny - 1), y1 = min(max(j0 + 1, 0), g.ny - 1);
+    int z0 = min(max(k0, 0), g.nz - 1), z1 = min(max(k0 + 1, 0), g.nz - 1);
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if ((x0 >> 3) == (x1 >> 3) && (y0 >> 3) == (y1 >> 3) && (z0 >> 3) == (z1 >> 3)) {
+        uint32_t e = acc.leaf(g, x0 >> 3, y0 >> 3, z0 >> 3);
+        if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
+        int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
+        int az = (z0 & 7) << 6, bz = (z1 & 7) << 6;
+        float2 sm = acc.sm;
+        v000 = leaf_value_t<P>(g, e, az | ay | ax, sm); v100 = leaf_value_t<P>(g, e, az | ay | bx, sm);
+        v010 = leaf_value_t<P>(g, e, az | by | ax, sm); v110 = leaf_value_t<P>(g, e, az | by | bx, sm);
+        v001 = leaf_value_t<P>(g, e, bz | ay | ax, sm); v101 = leaf_value_t<P>(g, e, bz | ay | bx, sm);
+        v011 = leaf_value_t<P>(g, e, bz | by | ax, sm); v111 = leaf_value_t<P>(g, e, bz | by | bx, sm);
+    } else {
+        v000 = voxel_t<P>(g, acc, x0, y0, z0); v100 = voxel_t<P>(g, acc, x1, y0, z0);
+        v010 = voxel_t<P>(g, acc, x0, y1, z0); v110 = voxel_t<P>(g, acc, x1, y1, z0);
+        v001 = voxel_t<P>(g, acc, x0, y0, z1); v101 = voxel_t<P>(g, acc, x1, y0, z1);
+        v011 = voxel_t<P>(g, acc, x0, y1, z1); v111 = voxel_t<P>(g, acc, x1, y1, z1);
+    }
+    float c00 = lerpf(v000, v100, tx), c10 = lerpf(v010, v110, tx);
+    float c01 = lerpf(v001, v101, tx), c11 = lerpf(v011, v111, tx);
+    float c0 = lerpf(c00, c10, ty), c1 = lerpf(c01, c11, ty);
+    return lerpf(c0, c1, tz);
+}
+
 template <int P>
 struct VdbSamplerT {
     GridView g;
     __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor& acc) const
     {
-        float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
-        float tx = px - fx, ty = py - fy, tz = pz - fz;
-        int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
-        int x0 = min(max(i0, 0), g.nx - 1), x1 = min(max(i0 + 1, 0), g.nx - 1);
-        int y0 = min(max(j0, 0), g.ny - 1), y1 = min(max(j0 + 1, 0), g.ny - 1);
-        int z0 = min(max(k0, 0), g.nz - 1), z1 = min(max(k0 + 1, 0), g.nz - 1);
-        float v000, v100, v010, v110, v001, v101, v011, v111;
-        if ((x0 >> 3) == (x1 >> 3) && (y0 >> 3) == (y1 >> 3) && (z0 >> 3) == (z1 >> 3)) {
-            uint32_t e = acc.leaf(g, x0 >> 3, y0 >> 3, z0 >> 3);
-            if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
-            int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
-            int az = (z0 & 7) << 6, bz = (z1 & 7) << 6;
-            float2 sm = acc.sm;
-            v000 = leaf_value_t<P>(g, e, az | ay | ax, sm); v100 = leaf_value_t<P>(g, e, az | ay | bx, sm);
-            v010 = leaf_value_t<P>(g, e, az | by | ax, sm); v110 = leaf_value_t<P>(g, e, az | by | bx, sm);
-            v001 = leaf_value_t<P>(g, e, bz | ay | ax, sm); v101 = leaf_value_t<P>(g, e, bz | ay | bx, sm);
-            v011 = leaf_value_t<P>(g, e, bz | by | ax, sm); v111 = leaf_value_t<P>(g, e, bz | by | bx, sm);
-        } else {
-            v000 = voxel_t<P>(g, acc, x0, y0, z0); v100 = voxel_t<P>(g, acc, x1, y0, z0);
-            v010 = voxel_t<P>(g, acc, x0, y1, z0); v110 = voxel_t<P>(g, acc, x1, y1, z0);
-            v001 = voxel_t<P>(g, acc, x0, y0, z1); v101 = voxel_t<P>(g, acc, x1, y0, z1);
-            v011 = voxel_t<P>(g, acc, x0, y1, z1); v111 = voxel_t<P>(g, acc, x1, y1, z1);
-        }
-        float c00 = lerpf(v000, v100, tx), c10 = lerpf(v010, v110, tx);
-        float c01 = lerpf(v001, v101, tx), c11 = lerpf(v011, v111, tx);
-        float c0 = lerpf(c00, c10, ty), c1 = lerpf(c01, c11, ty);
-        return lerpf(c0, c1, tz);
+        return vdb_trilinear<P>(g, px, py, pz, acc);
     }
 };
 
