@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="vdbc", choices=["vdbc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-volume batched section")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="the ncu capture case: the same workload at a 512x512 image, two renders")
@@ -296,6 +297,8 @@ def run_vdbc(args):
         e2e = {"value": round(world * paths_per_step * args.steps / e2e_s / 1e6, 3), "unit": "Mpaths/s",
                "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16)}
 
+    batch = None if args.no_batch else run_batch_section(v, volgen, scenes, dev, stream, args)
+
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
@@ -320,6 +323,7 @@ def run_vdbc(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,
+        "batch": batch,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -328,6 +332,67 @@ def run_vdbc(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_batch_section(v, volgen, scenes, dev, stream, args):
+    """The batched form: 32 volumes of uneven size (FP16/FP8 leaves, rates 1:4..1:20,
+    images 256^2..1024^2, 4..32 spp) in one persistent launch per frame from a
+    captured CUDA graph, against rendering the same jobs one by one."""
+    import torch
+
+    specs = scenes.batch_jobs()
+    grids, imgs, jobs = [], [], []
+    payload_bytes = 0
+    for sp in specs:
+        vol = volgen.generate_torch(volgen.make_params(sp["kind"], sp["dims"], sp["seed"]), dev)
+        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"], stream=stream)
+        del vol
+        payload_bytes += int(g.info.payload_bytes)
+        cam = v.make_camera(*scenes.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
+        med = v.make_medium(v.MODE_PT, **sp["medium"])
+        img = torch.empty((sp["height"], sp["width"], 4), dtype=torch.float32, device=dev)
+        grids.append(g)
+        imgs.append(img)
+        jobs.append((v.make_job(g, cam, med, sp["spp"], sp["seed"], img), cam, med))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = v.vdbc_batch_create([j[0] for j in jobs], autotune=True, stream=stream, keep=(grids, imgs))
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    tuning = v.vdbc_batch_get_tuning(b)
+    paths = sum(sp["width"] * sp["height"] * sp["spp"] for sp in specs)
+    frames = max(2, min(args.steps, 3))
+    v.vdbc_batch_render_frames(b, 1, stream=stream)        # warm-up frame
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    v.vdbc_batch_render_frames(b, frames, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / frames
+    st = v.vdbc_batch_stats_get(b, stream=stream)
+    # the plain form: one vdbc_render per job, same samples
+    for (job, cam, med), sp, img in zip(jobs[:1], specs[:1], imgs[:1]):
+        v.vdbc_render(grids[0], cam, med, sp["spp"], sp["seed"], img, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (job, cam, med), sp, img, g in zip(jobs, specs, imgs, grids):
+        v.vdbc_render(g, cam, med, sp["spp"], sp["seed"], img, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    b.close()
+    for g in grids:
+        g.close()
+    return {"jobs": len(specs), "paths_per_frame": paths, "frame_ms": round(batch_ms, 3),
+            "mpaths_per_s": round(paths / (batch_ms * 1e-3) / 1e6, 3),
+            "one_by_one_ms": round(plain_ms, 3),
+            "one_by_one_mpaths_per_s": round(paths / (plain_ms * 1e-3) / 1e6, 3),
+            "speedup_vs_one_by_one": round(plain_ms / batch_ms, 4),
+            "payload_bytes": payload_bytes, "lookups_per_frame": int(st.lookups),
+            "tuning": {"threads": tuning.threads, "chunk": tuning.chunk, "coarse": tuning.coarse},
+            "create_s_incl_autotune": round(create_s, 3),
+            "workload": "32 blob+fBm volumes, edges 64..384, rates 1:4..1:20, FP16/FP8, 256^2..1024^2, 4..32 spp"}
 
 
 class CpuOracle:

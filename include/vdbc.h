@@ -278,7 +278,7 @@ typedef struct {
     int32_t chunk;         /* paths a warp takes from the work counter at once (>= 32) */
     int32_t coarse;        /* 1: cross empty 8^3 blocks of macrocells in one DDA step */
     int32_t reserved;
-    float   frame_ms;      /* the tuner's measurement of one frame with this shape */
+    float   frame_ms;      /* the tuner's time for every 8th path of a frame with this shape */
 } vdbc_tuning;
 
 typedef struct vdbc_batch vdbc_batch;
@@ -287,8 +287,8 @@ typedef struct vdbc_batch vdbc_batch;
  * vdbc_batch_create -- prepare a batch of up to 64 path-tracing jobs on
  * grids of any size and payload, rendered together by ONE persistent launch
  * per frame (Section 4's tracker; the paper renders one volume at a time).
- * With autotune != 0 the launch shape is chosen by timing one frame per
- * candidate (cached per GPU and batch layout in this process, and in the file
+ * With autotune != 0 the launch shape is chosen by timing every 8th path of a
+ * frame per candidate (cached per GPU and batch layout in this process, and in the file
  * named by VDBC_TUNE_CACHE when set).  The per-frame work (work-counter reset,
  * persistent tracker, per-pixel accumulation) is then captured in a CUDA
  * graph on `stream`.  Grids must outlive the batch.  Errors: INVALID_ARG

@@ -27,6 +27,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "vdbc_host.h"
@@ -352,7 +353,7 @@ struct SingleSource {
     const S& smp;
     const uint32_t* b;
     const uint32_t* cb;
-    __device__ __forceinline__ int find(unsigned long long) const { return 0; }
+    __device__ __forceinline__ int find(unsigned long long, int) const { return 0; }
     __device__ __forceinline__ const JobView& job(int) const { return j; }
     __device__ __forceinline__ const uint32_t* bits(int) const { return b; }
     __device__ __forceinline__ const uint32_t* cbits(int) const { return cb; }
@@ -366,9 +367,10 @@ struct BatchSource {
     const JobView* jobs;
     const GridView* grids;
     int n;
-    __device__ __forceinline__ int find(unsigned long long item) const
+    // a lane's items only grow, so the search starts at its current job
+    __device__ __forceinline__ int find(unsigned long long item, int from) const
     {
-        int j = 0;
+        int j = from;
         while (j + 1 < n && item >= jobs[j + 1].item_begin) ++j;
         return j;
     }
@@ -377,14 +379,19 @@ struct BatchSource {
     __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
     __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
     {
-        return vdb_trilinear<-1>(grids[i], x, y, z, a);
+        const GridView& g = grids[i];
+        // one dispatch per lookup on the job's payload, not one per voxel
+        if (g.payload == 1) return vdb_trilinear<1>(g, x, y, z, a);
+        if (g.payload == 2) return vdb_trilinear<2>(g, x, y, z, a);
+        return vdb_trilinear<0>(g, x, y, z, a);
     }
 };
 
 // The tracker loop shared by the single-job and the batch kernels.
+// stride > 1 renders every stride-th path only (the autotuner's sample of a frame)
 template <class Src>
 __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
-                                        int chunk)
+                                        int chunk, unsigned stride)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -419,12 +426,12 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             }
             if (mode == kNeed) {
                 const unsigned long long r = (unsigned long long)__popc(need & lt_mask);
-                unsigned long long item = r < avail ? pool_next + r : fresh + (r - avail);
+                unsigned long long item = (r < avail ? pool_next + r : fresh + (r - avail)) * stride;
                 if (item >= nitems) {
                     mode = kDone;
                 } else {
                     // item -> (job, sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
-                    jb = src.find(item);
+                    jb = src.find(item, jb);
                     const JobView& F = src.job(jb);
                     unsigned long long local = item - F.item_begin;
                     unsigned long long per = F.items / (unsigned long long)F.spp;
@@ -467,8 +474,10 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         }
         if (__all_sync(0xffffffffu, mode == kDone)) break;
         const JobView& J = src.job(jb);
-        const Majorants& m = J.m;
-        const MedDev& med = J.med;
+        // batch: copies in registers (the job table is in shared memory and the
+        // DDA walk reads these per cell); one job: references to kernel parameters
+        typename std::conditional<Src::kMulti, const Majorants, const Majorants&>::type m = J.m;
+        typename std::conditional<Src::kMulti, const MedDev, const MedDev&>::type med = J.med;
         const uint32_t* bits = src.bits(jb);
         const uint32_t* cbits = src.cbits(jb);
         const int cx_n = J.cx_n, cy_n = J.cy_n;
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
     }
     __syncthreads();
     SingleSource<S> src{job, smp, bits, cbits};
-    pt_loop(src, job.items, st, chunk);
+    pt_loop(src, job.items, st, chunk, 1u);
 }
 
 // all jobs of a batch in one persistent launch; frame[0] numbers the
@@ -618,7 +627,8 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 512 / kThreads)
     k_pt_batch(const JobView* __restrict__ jobs, const GridView* __restrict__ grids, int n,
-               unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk)
+               unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk,
+               unsigned stride)
 {
     extern __shared__ unsigned char s_raw[];
     JobView* sj = reinterpret_cast<JobView*>(s_raw);
@@ -631,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads)
     }
     __syncthreads();
     BatchSource src{sj, sg, n};
-    pt_loop(src, nitems, st, chunk);
+    pt_loop(src, nitems, st, chunk, stride);
 }
 
 // average of the spp path radiances of each pixel, in sample order
@@ -1288,23 +1298,23 @@ vdbc_status batch_config(const vdbc_batch* b, unsigned* blocks, size_t* smem)
 }
 
 template <int kThreads>
-vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, cudaStream_t s)
+vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStream_t s)
 {
     unsigned& blocks = kThreads == 128 ? b->blocks128 : b->blocks256;
     size_t& smem = kThreads == 128 ? b->smem128 : b->smem256;
     if (blocks == 0) VDBC_TRY(batch_config<kThreads>(b, &blocks, &smem));
     KLAUNCH(k_pt_batch<kThreads><<<blocks, kThreads, smem, s>>>(b->d_jobs, b->d_grids, b->n, b->nitems, b->d_frame,
-                                                                b->stats, chunk));
+                                                                b->stats, chunk, stride));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
 
 // the work of one frame: counters, tracker, accumulation, next frame number
-vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s)
+vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s, unsigned stride = 1)
 {
     VDBC_CUDA(cudaMemsetAsync(b->stats, 0, sizeof(DevStats), s));
-    if (t.threads == 128) VDBC_TRY(batch_launch_pt<128>(b, t.chunk, s));
-    else VDBC_TRY(batch_launch_pt<256>(b, t.chunk, s));
+    if (t.threads == 128) VDBC_TRY(batch_launch_pt<128>(b, t.chunk, stride, s));
+    else VDBC_TRY(batch_launch_pt<256>(b, t.chunk, stride, s));
     if (accumulate) {
         dim3 grid((unsigned)((b->max_npix + 255) / 256), (unsigned)b->n);
         KLAUNCH(k_batch_reduce<<<grid, 256, 0, s>>>(b->d_jobs, b->d_sums, b->d_outs, b->d_frame));
@@ -1331,7 +1341,9 @@ std::string batch_key(const vdbc_batch* b)
     return name + "|" + buf;
 }
 
-// times one frame for each candidate shape and keeps the fastest
+constexpr unsigned kTuneStride = 8;
+
+// times (a sample of) one frame for each candidate shape and keeps the fastest
 vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
 {
     const std::string key = batch_key(b);
@@ -1361,9 +1373,10 @@ vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
         for (int th : threads)
             for (int ch : chunks) {
                 vdbc_tuning t{th, ch, co, 0, 0.0f};
-                st = batch_frame(b, t, false, s);           // warm-up
+                // every kTuneStride-th path of a frame: a sample spread over all jobs
+                st = batch_frame(b, t, false, s, kTuneStride);           // warm-up
                 if (st == VDBC_OK && cudaEventRecord(e0, s) != cudaSuccess) st = set_error(VDBC_ERR_CUDA, "tune event");
-                if (st == VDBC_OK) st = batch_frame(b, t, false, s);
+                if (st == VDBC_OK) st = batch_frame(b, t, false, s, kTuneStride);
                 if (st == VDBC_OK && cudaEventRecord(e1, s) != cudaSuccess) st = set_error(VDBC_ERR_CUDA, "tune event");
                 if (st == VDBC_OK) st = wait_stream(s);
                 if (st != VDBC_OK) break;

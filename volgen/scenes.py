@@ -49,3 +49,22 @@ TURBULENCE_512 = dict(kind="turbulence", dims=(512, 512, 512), seed=0, ratio=10.
                       spp=16, medium=pt_medium_args(), macrocell=16)
 # the 64^3 blobs volume at 1:4, EA, 128^2, step 0.5, ortho +z
 BLOBS_64_EA = dict(kind="blobs", dims=(64, 64, 64), seed=0, ratio=4.0, width=128, height=128, step=0.5)
+
+
+# the batch: 32 blob+fBm volumes of uneven size (edges uniform in 64..384), each
+# at a rate from {1:4, 1:6, 1:10, 1:20} with FP16 or FP8 leaves, its own
+# pinhole camera (square image, edge uniform in 256..1024) and 4..32 spp
+def batch_jobs(n=32, seed=0):
+    rng = np.random.default_rng(10_000 + seed)
+    jobs = []
+    for i in range(n):
+        dims = tuple(int(x) for x in rng.integers(64, 385, size=3))
+        ratio = float(rng.choice([4.0, 6.0, 10.0, 20.0]))
+        payload = int(rng.choice([1, 2]))              # FP16 or FP8 (E4M3)
+        edge = int(rng.integers(256, 1025))
+        spp = int(rng.integers(4, 33))
+        theta = float(rng.uniform(0.0, 2.0 * math.pi))
+        direction = (math.cos(theta), 0.45, math.sin(theta))
+        jobs.append(dict(kind="blobs", dims=dims, seed=i, ratio=ratio, payload=payload, width=edge, height=edge,
+                         spp=spp, direction=direction, medium=pt_medium_args(density_scale=30.0)))
+    return jobs
