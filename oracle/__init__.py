@@ -122,9 +122,15 @@ def lib():
 
 def _bind_mlp(L):
     vp = ctypes.c_void_p
+    L.or_mlp_num_params.restype = ctypes.c_int
     L.or_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
     L.or_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
     L.or_mlp_loss_grad.restype = ctypes.c_double
+    L.or_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.or_round_bf16.argtypes = [ctypes.c_float]
+    L.or_round_bf16.restype = ctypes.c_float
+    L.or_mlp_forward_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
 
 
 def _p(a):
@@ -389,3 +395,56 @@ def psnr(a, b) -> float:
     """PSNR with peak 1 (the convention that reproduces the paper's MSE/PSNR table)."""
     m = mse(a, b)
     return float("inf") if m == 0 else 10.0 * np.log10(1.0 / m)
+
+
+# ---------------------------------------------------------------- learned leaf decoder
+MLP_IN, MLP_HID, MLP_LATENT = 19, 32, 16
+
+
+def mlp_num_params() -> int:
+    return int(lib().or_mlp_num_params())
+
+
+def mlp_forward(params, inputs) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, MLP_IN)
+    out = np.zeros(x.shape[0])
+    lib().or_mlp_forward(_p(p), _p(x), x.shape[0], _p(out))
+    return out
+
+
+def mlp_forward_bf16(params, inputs) -> np.ndarray:
+    """The forward pass at the tensor-core path's precision (bf16 operands and activations)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, MLP_IN)
+    out = np.zeros(x.shape[0])
+    lib().or_mlp_forward_bf16(_p(p), _p(x), x.shape[0], _p(out))
+    return out
+
+
+def round_bf16(x: float) -> float:
+    return float(lib().or_round_bf16(x))
+
+
+def mlp_loss_grad(params, inputs, targets):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, MLP_IN)
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    gp = np.zeros_like(p)
+    gx = np.zeros_like(x)
+    loss = lib().or_mlp_loss_grad(_p(p), _p(x), _p(t), x.shape[0], _p(gp), _p(gx))
+    return float(loss), gp, gx
+
+
+def adam_step(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on float64 arrays params, m, v."""
+    g = np.ascontiguousarray(grads, dtype=np.float64)
+    lib().or_adam_step(_p(params), _p(g), _p(m), _p(v), params.size, step, lr, beta1, beta2, eps)
+
+
+def leaf_inputs(latent, n=None):
+    """The 512 network inputs of one leaf (x fastest): (i, j, k) / 7 and the latent."""
+    z = np.asarray(latent, dtype=np.float64).reshape(MLP_LATENT)
+    idx = np.arange(512)
+    uvw = np.stack([(idx & 7) / 7.0, ((idx >> 3) & 7) / 7.0, (idx >> 6) / 7.0], axis=1)
+    return np.concatenate([uvw, np.broadcast_to(z, (512, MLP_LATENT))], axis=1)

@@ -105,6 +105,16 @@ void   or_render_pixels(const float* d, const int64_t dims[3], const float* cell
                         uint64_t seed, const int64_t* pixels, int64_t npix,
                         double* out_rgba);
 
+/* ---------------- learned leaf decoder (a project extension) ------------ */
+int    or_mlp_num_params(void);
+void   or_mlp_forward(const double* params, const double* inputs, int64_t n, double* out);
+double or_mlp_loss_grad(const double* params, const double* inputs, const double* targets, int64_t n,
+                        double* grad_params, double* grad_inputs);
+void   or_adam_step(double* params, const double* grads, double* m, double* v, int64_t n, int64_t step,
+                    double lr, double beta1, double beta2, double eps);
+float  or_round_bf16(float x);
+void   or_mlp_forward_bf16(const double* params, const double* inputs, int64_t n, double* out);
+
 #ifdef __cplusplus
 }
 #endif

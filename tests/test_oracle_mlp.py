@@ -1,0 +1,125 @@
+"""Pins of the oracle's learned leaf decoder (a project extension: parity
+against the paper is unpinned).  The backward pass is pinned to the forward
+by central finite differences, the forward to networks built by hand whose
+output is known in closed form, and Adam to the closed form of its first
+step."""
+import numpy as np
+import pytest
+
+
+def layout(orc):
+    n_in, h = orc.MLP_IN, orc.MLP_HID
+    sizes = [h * n_in, h, h * h, h, h, 1]
+    offs = np.cumsum([0] + sizes)
+    return dict(W1=(offs[0], (h, n_in)), b1=(offs[1], (h,)), W2=(offs[2], (h, h)), b2=(offs[3], (h,)),
+                w3=(offs[4], (h,)), b3=(offs[5], (1,)))
+
+
+def view(p, lay, name):
+    o, shape = lay[name]
+    return p[o:o + int(np.prod(shape))].reshape(shape)
+
+
+def test_parameter_count(orc):
+    assert orc.mlp_num_params() == 32 * 19 + 32 + 32 * 32 + 32 + 32 + 1 == 1729
+
+
+def test_forward_closed_form_networks(orc):
+    lay = layout(orc)
+    p = np.zeros(orc.mlp_num_params())
+    # zero weights: the output is the last bias
+    view(p, lay, "b3")[0] = 0.37
+    x = np.random.default_rng(0).random((10, 19))
+    assert np.allclose(orc.mlp_forward(p, x), 0.37, atol=0, rtol=0)
+    # y = relu(2 u - 1) + 3 z_4 (z_4 >= 0) through explicit weights
+    W1, b1, W2, w3 = view(p, lay, "W1"), view(p, lay, "b1"), view(p, lay, "W2"), view(p, lay, "w3")
+    W1[0, 0], b1[0] = 2.0, -1.0
+    W1[1, 3 + 4] = 3.0
+    W2[0, 0] = 1.0
+    W2[1, 1] = 1.0
+    w3[0], w3[1] = 1.0, 1.0
+    view(p, lay, "b3")[0] = 0.0
+    want = np.maximum(2 * x[:, 0] - 1, 0) + 3 * x[:, 7]
+    assert np.allclose(orc.mlp_forward(p, x), want, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_gradients_match_finite_differences(orc, seed):
+    rng = np.random.default_rng(seed)
+    n = 7
+    p = rng.normal(0, 0.4, orc.mlp_num_params())
+    x = rng.random((n, 19))
+    t = rng.random(n)
+    loss, gp, gx = orc.mlp_loss_grad(p, x, t)
+    h = 1e-6
+    idx = rng.choice(p.size, 60, replace=False)
+    for i in idx:
+        q = p.copy(); q[i] += h
+        lp = orc.mlp_loss_grad(q, x, t)[0]
+        q[i] -= 2 * h
+        lm = orc.mlp_loss_grad(q, x, t)[0]
+        assert abs((lp - lm) / (2 * h) - gp[i]) <= 1e-6 * max(1.0, abs(gp[i]))
+    for s in range(n):
+        for k in (0, 2, 3, 10, 18):
+            y = x.copy(); y[s, k] += h
+            lp = orc.mlp_loss_grad(p, y, t)[0]
+            y[s, k] -= 2 * h
+            lm = orc.mlp_loss_grad(p, y, t)[0]
+            assert abs((lp - lm) / (2 * h) - gx[s, k]) <= 1e-6 * max(1.0, abs(gx[s, k]))
+    # and the loss is the mean squared error of the forward pass
+    assert abs(loss - np.mean((orc.mlp_forward(p, x) - t) ** 2)) < 1e-14
+
+
+def test_adam_first_step_closed_form(orc):
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    p = p0.copy(); m = np.zeros(50); v = np.zeros(50)
+    orc.adam_step(p, g, m, v, 1, lr=0.01)
+    # step 1: m_hat = g, v_hat = g^2, so the update is lr * g / (|g| + eps)
+    assert np.allclose(p, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_training_fits_a_smooth_leaf(orc):
+    """Gradient descent with the oracle's own pieces fits one smooth leaf:
+    the loss falls by more than 10x (a sanity check of the whole loop)."""
+    rng = np.random.default_rng(4)
+    p = rng.normal(0, 0.3, orc.mlp_num_params())
+    z = rng.normal(0, 0.1, 16)
+    x = orc.leaf_inputs(z)
+    t = 0.5 + 0.3 * np.sin(3 * x[:, 0]) * x[:, 1]
+    m = np.zeros_like(p); v = np.zeros_like(p)
+    l0 = orc.mlp_loss_grad(p, x, t)[0]
+    for step in range(1, 301):
+        loss, gp, gx = orc.mlp_loss_grad(p, x, t)
+        orc.adam_step(p, gp, m, v, step, lr=3e-3)
+    assert loss < l0 / 10
+
+
+def test_bf16_rounding_matches_torch(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.normal(size=20000), rng.normal(size=2000) * 1e-30, [0.0, 1.0, 1.0 / 7, 3.0 / 7]])
+    xs = xs.astype(np.float32)
+    want = torch.from_numpy(xs).to(torch.bfloat16).to(torch.float32).numpy()
+    got = np.array([orc.round_bf16(float(x)) for x in xs], dtype=np.float32)
+    assert np.array_equal(got, want)
+
+
+def test_bf16_forward_close_to_full_precision(orc):
+    """The bf16 forward differs from the FP64 one by the rounding of its
+    operands only: a few bf16 ulps on a well-scaled network."""
+    rng = np.random.default_rng(6)
+    p = rng.normal(0, 0.3, orc.mlp_num_params())
+    x = rng.random((200, 19))
+    a = orc.mlp_forward(p, x)
+    b = orc.mlp_forward_bf16(p, x)
+    assert np.abs(a - b).max() < 0.05 * max(1.0, np.abs(a).max())
+    # exact on inputs and weights that bf16 represents, when no activation needs rounding
+    q = np.zeros_like(p)
+    q[0] = 1.0              # W1[0,0]
+    q[32 * 19 + 32] = 1.0   # W2[0,0]
+    q[32 * 19 + 32 + 32 * 32 + 32] = 2.0  # w3[0]
+    xx = np.zeros((3, 19)); xx[:, 0] = [0.5, 0.25, 0.75]
+    assert np.array_equal(orc.mlp_forward_bf16(q, xx), 2.0 * xx[:, 0])
