@@ -58,8 +58,10 @@ enum { VDBC_F1 = 1,  /* closest:  min(|lo-B|, |hi-B|)  */
        VDBC_F3 = 3   /* median:   |(lo+hi)/2 - B|      */ };
 
 /* leaf payload: FP32 as in the paper; FP16 / FP8 (E4M3) with a per-leaf
- * FP32 scale and offset are a project extension (not in the paper) */
-enum { VDBC_FP32 = 0, VDBC_FP16 = 1, VDBC_FP8 = 2 };
+ * FP32 scale and offset are a project extension (not in the paper), as is
+ * VDBC_LEARNED: leaves decoded by a small shared network from a per-leaf
+ * FP16 latent, with FP16 leaves as the fallback (vdbc_learn) */
+enum { VDBC_FP32 = 0, VDBC_FP16 = 1, VDBC_FP8 = 2, VDBC_LEARNED = 3 };
 
 enum { VDBC_CAM_ORTHO = 0, VDBC_CAM_PINHOLE = 1 };
 enum { VDBC_MODE_EA = 0,   /* emission-absorption ray marching (fixed step) */
@@ -98,7 +100,8 @@ typedef struct {
     int64_t  budget;           /* N = floor(n_bricks * 131072 / (ratio * brick payload bytes)) */
     int64_t  n_active;         /* bricks activated = min(budget, n_nonempty) */
     int64_t  n_upper, n_lower, n_leaves, n_tiles;
-    uint64_t payload_bytes;    /* leaf values plus per-leaf scale/offset */
+    int64_t  n_neural;         /* learned grids: leaves decoded by the network (n_leaves = fallbacks) */
+    uint64_t payload_bytes;    /* leaf values plus per-leaf scale/offset (and latents + network) */
     uint64_t node_bytes;       /* root, upper and lower tables plus tile values */
     uint64_t total_bytes;      /* everything the grid holds on the device, incl. majorants */
 } vdbc_grid_info;
@@ -307,6 +310,71 @@ vdbc_status vdbc_batch_get_tuning(const vdbc_batch* batch, vdbc_tuning* tuning);
 /* counters of the last frame; waits for `stream` */
 vdbc_status vdbc_batch_stats_get(const vdbc_batch* batch, void* stream, vdbc_render_stats* stats);
 void        vdbc_batch_free(vdbc_batch* batch);
+
+/* ---------------- learned leaf codec (a project extension) -------------- */
+/*
+ * The paper's Section 2.3 mentions network-decoded leaves (NeuralVDB) only as
+ * related work, too slow there for real-time rendering.  Here a leaf may be
+ * "neural": it stores a 16-value FP16 latent z and its (scale, offset), and
+ * voxel (i, j, k) of the leaf decodes to
+ *     offset + scale * clamp(y, 0, 1),
+ *     y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3,  x = (i/7, j/7, k/7, z),
+ * one network (19 -> 32 -> 32 -> 1, 1729 FP32 parameters in the order W1
+ * (32x19 row major), b1, W2 (32x32), b2, w3, b3) shared by all leaves.
+ * Rendering evaluates it on the tensor cores with bf16 inputs, weights and
+ * hidden activations and FP32 accumulation, at each of the 8 trilinear
+ * corners that falls in a neural leaf; a leaf that the network cannot
+ * represent within the error bound keeps a raw FP16 payload instead.
+ */
+typedef struct {
+    int32_t  steps;             /* Adam steps (0: keep the initial network and latents) */
+    int32_t  samples_per_leaf;  /* S: voxels drawn per leaf per step, 16, 32, 64 or 128 */
+    float    lr;                /* Adam step size of the network (beta1 0.9, beta2 0.999, eps 1e-8) */
+    float    lr_latent;         /* Adam step size of the latents */
+    float    max_error;         /* a leaf whose largest |decoded - source| exceeds this is a raw candidate */
+    int32_t  reserved;
+    uint64_t max_bytes;         /* size limit of the whole learned grid (0: none); raw candidates beyond
+                                   it stay neural, the largest errors (then the lowest leaf numbers) kept raw */
+    uint64_t seed;              /* Philox key of the initialisation and of the voxel draws */
+    const float*   init_params;   /* device, 1729 floats, or NULL: weights uniform in +-sqrt(6/fan_in)
+                                     (counter (i, 0, 0, 0x494E4954)), biases 0, b3 = 1/2 */
+    const float*   init_latents;  /* device, 16 floats per leaf POSITION (lk*nly + lj)*nlx + li with
+                                     nl = ceil(dims/8), or NULL: zeros */
+    const uint8_t* force;         /* device, one byte per leaf position: 0 by error, 1 neural, 2 raw; or NULL */
+} vdbc_learn_params;
+
+/*
+ * vdbc_learn -- fit the network and one latent per leaf of `src` (any
+ * non-learned payload) to the leaves' values normalised by their
+ * (scale, offset), and build the learned grid *out (free with
+ * vdbc_grid_free; payload VDBC_LEARNED, n_leaves = raw leaves, n_neural =
+ * neural leaves).  Training minimises the mean squared error of y against
+ * (v - offset) / scale with Adam over `steps` steps; step t (from 0) uses,
+ * for every leaf not forced raw, voxel s*(512/S) + (r mod 512/S) for
+ * s = 0..S-1, r the first word of Philox4x32-10 at counter
+ * (leaf position, t, s, 0x4C454146) and key `seed`; the latents' gradient
+ * is the sum over the leaf's samples.  Tree tables, tiles and the
+ * background are those of `src`.  loss_out (host, `steps` doubles, or
+ * NULL) receives the loss of each step.  Waits for `stream`.
+ * Errors: INVALID_ARG (null, a learned source, steps outside 0..1e6, S not
+ * 16/32/64/128, non-positive learning rates, negative max_error); OOM; CUDA.
+ */
+vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params* params, void* stream, vdbc_grid** out,
+                       double* loss_out);
+
+/*
+ * vdbc_learn_loss_grad -- the training kernels on explicit samples: loss =
+ * mean over the n rows of (y - target)^2, grad_params (1729) its gradient,
+ * grad_inputs (n x 19, or NULL) the gradient with respect to each input row.
+ * params, inputs (n x 19 row major), targets, grad_* are device arrays; loss
+ * a host double (or NULL).  FP32 arithmetic, sums in a fixed order.  Waits
+ * for `stream`.  Errors: INVALID_ARG (null arrays, n outside 1..2^31); CUDA.
+ */
+vdbc_status vdbc_learn_loss_grad(const float* params, const float* inputs, const float* targets, int64_t n,
+                                 double* loss, float* grad_params, float* grad_inputs, void* stream);
+
+/* the 1729 FP32 parameters of a learned grid's network (host array) */
+vdbc_status vdbc_learn_get_params(const vdbc_grid* grid, float* host_params);
 
 /* vdbc_philox -- n outputs of the device Philox4x32-10 (the generator every
  * render draws from), for checking it against its published definition.

@@ -131,6 +131,9 @@ def _bind_mlp(L):
     L.or_round_bf16.argtypes = [ctypes.c_float]
     L.or_round_bf16.restype = ctypes.c_float
     L.or_mlp_forward_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.or_learned_leaf.argtypes = [vp, vp, vp, vp]
+    L.or_tree_leaf.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp]
+    L.or_tree_leaf.restype = ctypes.c_int
 
 
 def _p(a):
@@ -240,6 +243,11 @@ class Tree:
 
     def value(self, i, j, k) -> float:
         return float(lib().or_tree_value(self.h, i, j, k))
+
+    def leaf(self, li, lj, lk):
+        """The 512 values of the leaf node at leaf position (li, lj, lk), or None for a tile."""
+        out = np.zeros(512, dtype=np.float32)
+        return out if lib().or_tree_leaf(self.h, li, lj, lk, _p(out)) else None
 
     def counts(self) -> dict:
         out = np.zeros(6, dtype=np.int64)
@@ -448,3 +456,49 @@ def leaf_inputs(latent, n=None):
     idx = np.arange(512)
     uvw = np.stack([(idx & 7) / 7.0, ((idx >> 3) & 7) / 7.0, (idx >> 6) / 7.0], axis=1)
     return np.concatenate([uvw, np.broadcast_to(z, (512, MLP_LATENT))], axis=1)
+
+
+def learned_leaf(params, latent, src):
+    """Decoded values of a neural leaf whose source values are `src` (512)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    z = np.ascontiguousarray(latent, dtype=np.float32).reshape(MLP_LATENT)
+    v = np.ascontiguousarray(src, dtype=np.float32).reshape(512)
+    out = np.zeros(512, dtype=np.float32)
+    lib().or_learned_leaf(_p(p), _p(z), _p(v), _p(out))
+    return out
+
+
+def learned_decode(vol, active, b_bits, params, latents, force):
+    """Dense decode of the learned grid built from the FP32 grid of
+    (vol, active, b_bits): the leaf at position p = (lk*nly + lj)*nlx + li is
+    neural when force[p] == 1 (latent latents[p]), raw FP16 when force[p] == 2;
+    tiles and the background as in the FP32 grid.  Returns (dense, kinds)
+    with kinds[p] = 0 tile, 1 neural, 2 raw."""
+    v = np.ascontiguousarray(vol, dtype=np.float32)
+    nz, ny, nx = v.shape
+    nl = ((nx + 7) // 8, (ny + 7) // 8, (nz + 7) // 8)
+    out = decode_dense(v, active, b_bits, FP32)
+    tree = Tree(v, active, b_bits, FP32)
+    kinds = np.zeros(nl[0] * nl[1] * nl[2], dtype=np.uint8)
+    lat = np.asarray(latents, dtype=np.float32).reshape(-1, MLP_LATENT)
+    for lk in range(nl[2]):
+        for lj in range(nl[1]):
+            for li in range(nl[0]):
+                pidx = (lk * nl[1] + lj) * nl[0] + li
+                src = tree.leaf(li, lj, lk)
+                if src is None:
+                    continue
+                if force[pidx] == 2:
+                    dec, _, _ = quantize_leaf(src, FP16)
+                    kinds[pidx] = 2
+                elif force[pidx] == 1:
+                    dec = learned_leaf(params, lat[pidx], src)
+                    kinds[pidx] = 1
+                else:
+                    raise ValueError("learned_decode needs force 1 or 2 at every leaf")
+                blk = dec.reshape(8, 8, 8)
+                z0, y0, x0 = lk * 8, lj * 8, li * 8
+                ez, ey, ex = min(8, nz - z0), min(8, ny - y0), min(8, nx - x0)
+                out[z0:z0 + ez, y0:y0 + ey, x0:x0 + ex] = blk[:ez, :ey, :ex]
+    tree.close()
+    return out, kinds

@@ -398,6 +398,24 @@ float or_tree_value(const or_tree* t, int64_t i, int64_t j, int64_t k)
     return f->v[((k & 7) * 8 + (j & 7)) * 8 + (i & 7)];
 }
 
+/* the 512 values of the leaf node at leaf position (li, lj, lk) (voxel
+ * (8li + a, 8lj + b, 8lk + c) at a + 8b + 64c, including voxels past the
+ * volume's edge); 0 (and out untouched) where that position is a tile */
+int or_tree_leaf(const or_tree* t, int64_t li, int64_t lj, int64_t lk, float out[512])
+{
+    int64_t i = li * 8, j = lj * 8, k = lk * 8;
+    const or_entry* r = &t->root[((k >> 12) * t->nroot[1] + (j >> 12)) * t->nroot[0] + (i >> 12)];
+    if (!r->is_child) return 0;
+    const or_upper* u = (const or_upper*)r->child;
+    const or_entry* ue = &u->e[(((k >> 7) & 31) * 32 + ((j >> 7) & 31)) * 32 + ((i >> 7) & 31)];
+    if (!ue->is_child) return 0;
+    const or_lower* l = (const or_lower*)ue->child;
+    const or_entry* le = &l->e[(((k >> 3) & 15) * 16 + ((j >> 3) & 15)) * 16 + ((i >> 3) & 15)];
+    if (!le->is_child) return 0;
+    memcpy(out, ((const or_leaf*)le->child)->v, sizeof(float) * 512);
+    return 1;
+}
+
 /* out = {root entries, upper nodes, lower nodes, leaves, lower-level tiles
  *        that are not the background, upper-level tiles that are not the background} */
 void or_tree_counts(const or_tree* t, int64_t out[6])

@@ -58,6 +58,7 @@ or_tree* or_tree_build(const float* v, const int64_t dims[3], const uint8_t* act
                        uint32_t b_bits, int payload);
 float    or_tree_value(const or_tree* t, int64_t i, int64_t j, int64_t k);
 void     or_tree_counts(const or_tree* t, int64_t out[6]);
+int      or_tree_leaf(const or_tree* t, int64_t li, int64_t lj, int64_t lk, float out[512]);
 void     or_tree_free(or_tree* t);
 
 /* ---------------- renderer: Section 4 plus the project's extensions ----- */
@@ -114,6 +115,7 @@ void   or_adam_step(double* params, const double* grads, double* m, double* v, i
                     double lr, double beta1, double beta2, double eps);
 float  or_round_bf16(float x);
 void   or_mlp_forward_bf16(const double* params, const double* inputs, int64_t n, double* out);
+void   or_learned_leaf(const double* params, const float latent[16], const float src[512], float out[512]);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ LIB_PATH = _build.LIB
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_FORMAT, ERR_TIMEOUT, ERR_DEVICE_FLAG, ERR_UNSUPPORTED = range(8)
 F1, F2, F3 = 1, 2, 3
-FP32, FP16, FP8 = 0, 1, 2
+FP32, FP16, FP8, LEARNED = 0, 1, 2, 3
 CAM_ORTHO, CAM_PINHOLE = 0, 1
 MODE_EA, MODE_PT = 0, 1
 FILTER_TEXTURE, FILTER_LINEAR = 0, 1
@@ -52,7 +52,7 @@ class GridInfo(ctypes.Structure):
                 ("ratio", ctypes.c_double), ("n_bricks", ctypes.c_int64), ("n_nonempty", ctypes.c_int64),
                 ("budget", ctypes.c_int64), ("n_active", ctypes.c_int64), ("n_upper", ctypes.c_int64),
                 ("n_lower", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
-                ("payload_bytes", ctypes.c_uint64), ("node_bytes", ctypes.c_uint64),
+                ("n_neural", ctypes.c_int64), ("payload_bytes", ctypes.c_uint64), ("node_bytes", ctypes.c_uint64),
                 ("total_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -91,6 +91,15 @@ class RenderStats(ctypes.Structure):
                 ("events", ctypes.c_uint64 * 6)]
 
 
+class LearnParams(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("samples_per_leaf", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("lr_latent", ctypes.c_float), ("max_error", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("max_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("init_params", ctypes.c_void_p),
+                ("init_latents", ctypes.c_void_p), ("force", ctypes.c_void_p)]
+
+
+MLP_PARAMS = 1729   # 19 -> 32 -> 32 -> 1: W1, b1, W2, b2, w3, b3
+
 _lib = None
 
 # name -> (restype, argtypes); the exported surface of include/vdbc.h
@@ -123,6 +132,9 @@ SIGNATURES = {
     "vdbc_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     "vdbc_batch_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
     "vdbc_batch_free": (None, [_vp]),
+    "vdbc_learn": (ctypes.c_int, [_vp, ctypes.POINTER(LearnParams), _vp, ctypes.POINTER(_vp), _vp]),
+    "vdbc_learn_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
+    "vdbc_learn_get_params": (ctypes.c_int, [_vp, _vp]),
     "vdbc_kernel_launches": (ctypes.c_uint64, []),
     "vdbc_last_error": (ctypes.c_char_p, []),
     "vdbc_version": (ctypes.c_char_p, []),
@@ -407,6 +419,37 @@ def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, coun
     p = EncodeParams(float(ratio), int(metric), int(payload), 8, 0)
     _check(lib().vdbc_select_bricks_noalloc(ctypes.byref(d), ctypes.byref(p), _ptr(background_bits_out)[0],
                                             _ptr(active_out)[0], _ptr(counts_out)[0], _stream(stream)))
+
+
+def vdbc_learn(grid: Grid, steps=200, samples_per_leaf=64, lr=1e-3, lr_latent=1e-2, max_error=0.0, max_bytes=0,
+               seed=0, init_params=None, init_latents=None, force=None, stream=None):
+    """Learned grid from `grid` (see include/vdbc.h).  init_params (1729),
+    init_latents (per leaf position x 16) and force (per leaf position,
+    uint8) are device tensors or None.  Returns (Grid, per-step losses)."""
+    p = LearnParams(int(steps), int(samples_per_leaf), float(lr), float(lr_latent), float(max_error), 0,
+                    int(max_bytes), int(seed), _ptr(init_params)[0] if init_params is not None else None,
+                    _ptr(init_latents)[0] if init_latents is not None else None,
+                    _ptr(force)[0] if force is not None else None)
+    out = _vp()
+    losses = np.zeros(max(int(steps), 1), dtype=np.float64)
+    _check(lib().vdbc_learn(grid.handle, ctypes.byref(p), _stream(stream), ctypes.byref(out), losses.ctypes.data))
+    return Grid(out.value), losses[:int(steps)]
+
+
+def vdbc_learn_loss_grad(params, inputs, targets, grad_params, grad_inputs=None, stream=None) -> float:
+    """Loss and gradients of the training kernels on explicit samples (device tensors)."""
+    n = int(targets.numel())
+    loss = ctypes.c_double(0.0)
+    _check(lib().vdbc_learn_loss_grad(_ptr(params)[0], _ptr(inputs)[0], _ptr(targets)[0], n, ctypes.byref(loss),
+                                      _ptr(grad_params)[0],
+                                      _ptr(grad_inputs)[0] if grad_inputs is not None else None, _stream(stream)))
+    return loss.value
+
+
+def vdbc_learn_get_params(grid: Grid) -> np.ndarray:
+    out = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(lib().vdbc_learn_get_params(grid.handle, out.ctypes.data))
+    return out
 
 
 def vdbc_philox(ctr, key) -> np.ndarray:

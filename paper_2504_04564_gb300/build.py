@@ -16,11 +16,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvdbc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["encode.cu", "render.cu", "util.cu"]
+SOURCES = ["encode.cu", "render.cu", "util.cu", "learn.cu"]
 # render.cu fuses multiply-adds only where the source says so (__fmaf_rn), so
 # every sampler instantiation of the tracker computes the same bits
 PER_FILE_FLAGS = {"render.cu": ["--fmad=false"]}
-HEADERS = ["vdbc_device.cuh", "vdbc_host.h"]
+HEADERS = ["vdbc_device.cuh", "vdbc_host.h", "learn.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -697,7 +697,10 @@ static int64_t brick_bytes(int payload)
     return 32768 * 4;
 }
 
-static int payload_elem(int payload) { return payload == VDBC_FP32 ? 4 : (payload == VDBC_FP16 ? 2 : 1); }
+static int payload_elem(int payload)
+{
+    return payload == VDBC_FP32 ? 4 : (payload == VDBC_FP8 ? 1 : 2);   // learned fallbacks are FP16
+}
 
 void bind_view(vdbc_grid* g)
 {
@@ -719,10 +722,14 @@ void bind_view(vdbc_grid* g)
     v.meta = reinterpret_cast<const float2*>(base + g->off_meta);
     v.mcmin = reinterpret_cast<const float*>(base + g->off_mcmin);
     v.mcmax = reinterpret_cast<const float*>(base + g->off_mcmax);
+    v.latents = reinterpret_cast<const __half*>(base + g->off_latents);
+    v.nmeta = reinterpret_cast<const float2*>(base + g->off_nmeta);
+    v.mlp_frag = reinterpret_cast<const uint2*>(base + g->off_frag);
+    v.mlp_bias = reinterpret_cast<const float*>(base + g->off_bias);
 }
 
 // offsets of every table inside the one linear block, from the counts in g->info
-static void layout(vdbc_grid* g)
+void layout(vdbc_grid* g)
 {
     vdbc_grid_info& in = g->info;
     long long rx = (in.dims[0] + 4095) / 4096, ry = (in.dims[1] + 4095) / 4096, rz = (in.dims[2] + 4095) / 4096;
@@ -737,23 +744,54 @@ static void layout(vdbc_grid* g)
     g->off_meta = off;   off = align256(off + (in.payload != VDBC_FP32 ? (size_t)in.n_leaves * 8 : 0));
     g->off_mcmin = off;  off = align256(off + (size_t)ncell * 4);
     g->off_mcmax = off;  off = align256(off + (size_t)ncell * 4);
+    const bool learned = in.payload == VDBC_LEARNED;
+    const size_t nn = learned ? (size_t)in.n_neural : 0;
+    g->off_latents = off; off = align256(off + nn * 16 * 2);
+    g->off_nmeta = off;   off = align256(off + nn * 8);
+    g->off_frag = off;    off = align256(off + (learned ? (size_t)18 * 32 * 8 : 0));
+    g->off_bias = off;    off = align256(off + (learned ? (size_t)65 * 4 : 0));
+    g->off_params = off;  off = align256(off + (learned ? (size_t)1729 * 4 : 0));
     g->block_bytes = off;
     in.payload_bytes = (uint64_t)in.n_leaves * kLeafN * payload_elem(in.payload) +
-                       (in.payload != VDBC_FP32 ? (uint64_t)in.n_leaves * 8 : 0);
+                       (in.payload != VDBC_FP32 ? (uint64_t)in.n_leaves * 8 : 0) +
+                       (learned ? (uint64_t)nn * (32 + 8) + 18 * 32 * 8 + 65 * 4 : 0);
     in.node_bytes = (uint64_t)(rx * ry * rz) * 4 + (uint64_t)in.n_upper * kUpperN * 4 +
                     (uint64_t)in.n_lower * kLowerN * 4 + (uint64_t)in.n_tiles * 4;
     in.total_bytes = off;
 }
 
-vdbc_status build_macrocells(vdbc_grid* g, cudaStream_t s)
+vdbc_status macrocells_of_view(const GridView& v, float* mcmin, float* mcmax, cudaStream_t s)
 {
-    const GridView& v = g->view;
     long long ncell = (long long)v.mx * v.my * v.mz;
-    char* base = static_cast<char*>(g->block);
-    KLAUNCH(k_macrocells<<<grid1d(ncell * 32, 256), 256, 0, s>>>(v, reinterpret_cast<float*>(base + g->off_mcmin),
-                                                          reinterpret_cast<float*>(base + g->off_mcmax), ncell));
+    KLAUNCH(k_macrocells<<<grid1d(ncell * 32, 256), 256, 0, s>>>(v, mcmin, mcmax, ncell));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
+}
+
+vdbc_status build_macrocells(vdbc_grid* g, cudaStream_t s)
+{
+    if (g->info.payload == VDBC_LEARNED) return build_learned_macrocells(g, s);
+    char* base = static_cast<char*>(g->block);
+    return macrocells_of_view(g->view, reinterpret_cast<float*>(base + g->off_mcmin),
+                              reinterpret_cast<float*>(base + g->off_mcmax), s);
+}
+
+void decode_view(const GridView& v, float* out, long long n, cudaStream_t s)
+{
+    KLAUNCH(k_decode<<<grid1d(std::min<long long>(n, 152LL * 2048), 256), 256, 0, s>>>(v, out, n));
+}
+
+long long scan_tmp_words(long long n) { return scan_blocks(n) + 1; }
+
+void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* tmp, uint32_t* total_dev, cudaStream_t s)
+{
+    scan_exclusive(in, out, n, tmp, total_dev, s);
+}
+
+void select_largest(const unsigned long long* key, const uint8_t* skip, int n, long long budget, uint8_t* chosen,
+                    long long* counts, cudaStream_t s)
+{
+    KLAUNCH(k_select<<<1, 1024, 0, s>>>(key, skip, n, budget, chosen, counts));
 }
 
 }  // namespace vdbc
@@ -968,8 +1006,19 @@ extern "C" vdbc_status vdbc_grid_decode(const vdbc_grid* g, float* out, int32_t 
         VDBC_TRY(dev_alloc(&tmp, (size_t)n * 4, s));
         dst = static_cast<float*>(tmp);
     }
-    KLAUNCH(k_decode<<<grid1d(std::min<long long>(n, 152LL * 2048), 256), 256, 0, s>>>(g->view, dst, n));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (g->info.payload == VDBC_LEARNED) {
+        // neural leaves go through the network once, into a temporary FP32 view
+        Materialized m;
+        vdbc_status st = materialize_learned(g, s, &m);
+        if (st == VDBC_OK) decode_view(m.view, dst, n, s);
+        e = cudaGetLastError();
+        m.release(s);
+        if (st != VDBC_OK) { if (tmp) dev_free(tmp, s); return st; }
+    } else {
+        decode_view(g->view, dst, n, s);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, dst, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) { if (tmp) dev_free(tmp, s); return cuda_status(e, "vdbc_grid_decode"); }
     if (!out_on_device) {

@@ -1,0 +1,252 @@
+// learn.cuh -- the learned leaf decoder's network on the tensor cores.
+//
+// Network (a project extension; the paper's Section 2.3 only mentions
+// NeuralVDB as related work): x = (u, v, w, z_0..z_15) with (u, v, w) the
+// voxel's position in its 8^3 leaf divided by 7 and z the leaf's latent;
+// h1 = relu(W1 x + b1) (32), h2 = relu(W2 h1 + b2) (32), y = w3 . h2 + b3.
+// A neural leaf decodes to offset + scale * clamp(y, 0, 1).
+//
+// Evaluation is warp-cooperative: 16 input rows (bf16, padded to 32
+// columns) go through three layers of mma.sync.m16n8k16 (bf16 in, fp32
+// accumulate): layer 1 = 2 k-steps x 4 n-tiles, layer 2 = 2 x 4, layer 3 =
+// 2 x 1.  The accumulator fragments of two adjacent n-tiles are exactly the
+// A fragment of the next layer's 16-wide k-step, so activations stay in
+// registers (bias + relu + bf16 rounding on the way).  Weights are stored as
+// per-lane B fragments (18 fragments x 32 lanes x 2 words).
+//
+// A row is 64 bytes = four 16-byte chunks; chunk c of row r sits at chunk
+// slot c ^ ((r >> 1) & 3), which makes both the row stores and the fragment
+// loads free of shared-memory bank conflicts.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "vdbc_device.cuh"
+
+namespace vdbc {
+
+constexpr int kMlpIn = 19, kMlpHid = 32, kMlpLatent = 16;
+constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;   // 1729
+constexpr int kMlpFrags = 18;          // B fragments: layer 1 (0..7), layer 2 (8..15), layer 3 (16..17)
+constexpr int kMlpBias = 2 * kMlpHid + 1;
+
+// offsets of the parameter blocks in the FP32 parameter vector
+constexpr int kOffW1 = 0, kOffB1 = kMlpHid * kMlpIn, kOffW2 = kOffB1 + kMlpHid, kOffB2 = kOffW2 + kMlpHid * kMlpHid,
+              kOffW3 = kOffB2 + kMlpHid, kOffB3 = kOffW3 + kMlpHid;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);      // .x (low half) = lo
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint2 b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// word w of row r in a 16-row tile (16 words per row, swizzled chunks)
+__device__ __forceinline__ int tile_word(int r, int w) { return r * 16 + ((((w >> 2) ^ (r >> 1)) & 3) << 2) + (w & 3); }
+
+// y for the 16 rows of `rows` (16 x 16 words in shared memory, swizzled);
+// all 32 lanes of the warp must call it together.  out[r] is written by the
+// lanes with (lane & 3) == 0.
+__device__ __forceinline__ void mlp_tile(const uint32_t* rows, const uint2* __restrict__ frag,
+                                         const float* __restrict__ bias, float* out)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t a[2][4];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        a[s][0] = rows[tile_word(g, s * 8 + t)];
+        a[s][1] = rows[tile_word(g + 8, s * 8 + t)];
+        a[s][2] = rows[tile_word(g, s * 8 + 4 + t)];
+        a[s][3] = rows[tile_word(g + 8, s * 8 + 4 + t)];
+    }
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+        float c[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) mma_bf16_16816(c[j], a[s], __ldg(frag + (layer * 8 + s * 4 + j) * 32 + lane));
+        }
+        const float* b = bias + layer * kMlpHid;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float b0 = __ldg(b + 8 * j + 2 * t), b1 = __ldg(b + 8 * j + 2 * t + 1);
+            c[j][0] = fmaxf(__fadd_rn(c[j][0], b0), 0.0f);
+            c[j][1] = fmaxf(__fadd_rn(c[j][1], b1), 0.0f);
+            c[j][2] = fmaxf(__fadd_rn(c[j][2], b0), 0.0f);
+            c[j][3] = fmaxf(__fadd_rn(c[j][3], b1), 0.0f);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            a[s][0] = pack_bf16(c[2 * s][0], c[2 * s][1]);
+            a[s][1] = pack_bf16(c[2 * s][2], c[2 * s][3]);
+            a[s][2] = pack_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
+            a[s][3] = pack_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
+        }
+    }
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) mma_bf16_16816(d, a[s], __ldg(frag + (16 + s) * 32 + lane));
+    if (t == 0) {
+        const float b3 = __ldg(bias + 2 * kMlpHid);
+        out[g] = __fadd_rn(d[0], b3);
+        out[g + 8] = __fadd_rn(d[2], b3);
+    }
+}
+
+// row r of a tile: (i, j, k) / 7 of voxel n of the leaf, then the leaf's FP16
+// latent, all rounded to bf16 and zero padded to 32 columns
+__device__ __forceinline__ void mlp_row(uint32_t* rows, int r, int n, const __half* __restrict__ latent)
+{
+    const uint4* lp = reinterpret_cast<const uint4*>(latent);
+    uint4 q0 = __ldg(lp), q1 = __ldg(lp + 1);
+    const __half* z0 = reinterpret_cast<const __half*>(&q0);
+    const __half* z1 = reinterpret_cast<const __half*>(&q1);
+    float z[kMlpLatent];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { z[q] = __half2float(z0[q]); z[8 + q] = __half2float(z1[q]); }
+    const float u = __fdiv_rn((float)(n & 7), 7.0f), v = __fdiv_rn((float)((n >> 3) & 7), 7.0f),
+                w = __fdiv_rn((float)(n >> 6), 7.0f);
+    uint4 c0 = make_uint4(pack_bf16(u, v), pack_bf16(w, z[0]), pack_bf16(z[1], z[2]), pack_bf16(z[3], z[4]));
+    uint4 c1 = make_uint4(pack_bf16(z[5], z[6]), pack_bf16(z[7], z[8]), pack_bf16(z[9], z[10]), pack_bf16(z[11], z[12]));
+    uint4 c2 = make_uint4(pack_bf16(z[13], z[14]), pack_bf16(z[15], 0.0f), 0u, 0u);
+    uint4* rp = reinterpret_cast<uint4*>(rows) + r * 4;
+    const int sw = (r >> 1) & 3;
+    rp[0 ^ sw] = c0;
+    rp[1 ^ sw] = c1;
+    rp[2 ^ sw] = c2;
+    rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// B fragment f (0..17) of lane `lane` from the FP32 parameters, bf16-rounded:
+// layer 1 (f = s*4 + j): W1[8j+g][16s+2t(+1)], W1[8j+g][16s+8+2t(+1)], zero past column 18;
+// layer 2 (f = 8 + s*4 + j): the same of W2; layer 3 (f = 16 + s): w3 in output column 0 only
+__device__ __forceinline__ uint2 mlp_frag(const float* __restrict__ p, int f, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    const float* W;
+    int ncol, row, s;
+    if (f < 8) { W = p + kOffW1; ncol = kMlpIn; s = f >> 2; row = 8 * (f & 3) + g; }
+    else if (f < 16) { W = p + kOffW2; ncol = kMlpHid; s = (f - 8) >> 2; row = 8 * ((f - 8) & 3) + g; }
+    else { W = p + kOffW3; ncol = kMlpHid; s = f - 16; row = g == 0 ? 0 : -1; }
+    float e[4];
+    const int k0 = 16 * s + 2 * t;
+    const int ks[4] = {k0, k0 + 1, k0 + 8, k0 + 9};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = (row >= 0 && ks[q] < ncol) ? W[row * ncol + ks[q]] : 0.0f;
+    return make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
+}
+
+// Trilinear lookups in a learned grid.  Tiles and raw FP16 leaves decode as
+// in a plain grid; a corner in a neural leaf becomes one row of a shared
+// 16-row tile, and the warp pushes its tiles through the network together.
+// collective() must be called by all 32 lanes of a warp at once (lanes
+// without a lookup pass look = false); at most kMaxWarps warps per block.
+struct LearnedSampler {
+    static constexpr bool kCollective = true;
+    static constexpr int kMaxWarps = 8;
+    GridView g;
+
+    // leaf-level entry through the accessor's cache; (scale, offset) of the
+    // leaf from meta (raw) or nmeta (neural)
+    __device__ __forceinline__ uint32_t leaf(Accessor& a, int li, int lj, int lk) const
+    {
+        if (li != a.li || lj != a.lj || lk != a.lk) {
+            a.li = li; a.lj = lj; a.lk = lk;
+            a.entry = descend_to_leaf(g, li, lj, lk);
+            if (!(a.entry & kTile))
+                a.sm = (a.entry & kNeural) ? __ldg(g.nmeta + (a.entry & ~kNeural)) : __ldg(g.meta + a.entry);
+        }
+        return a.entry;
+    }
+
+    __device__ __forceinline__ float collective(bool look, float px, float py, float pz, Accessor& acc) const
+    {
+        __shared__ __align__(16) uint32_t s_rows[kMaxWarps][256];
+        __shared__ float s_out[kMaxWarps][16];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        float v[8];
+        uint32_t nmask = 0;
+        float tx = 0.f, ty = 0.f, tz = 0.f;
+        int xs[2] = {0, 0}, ys[2] = {0, 0}, zs[2] = {0, 0};
+        if (look) {
+            const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+            tx = px - fx; ty = py - fy; tz = pz - fz;
+            const int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
+            xs[0] = min(max(i0, 0), g.nx - 1); xs[1] = min(max(i0 + 1, 0), g.nx - 1);
+            ys[0] = min(max(j0, 0), g.ny - 1); ys[1] = min(max(j0 + 1, 0), g.ny - 1);
+            zs[0] = min(max(k0, 0), g.nz - 1); zs[1] = min(max(k0 + 1, 0), g.nz - 1);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
+                const uint32_t e = leaf(acc, x >> 3, y >> 3, z >> 3);
+                if (e & kTile) {
+                    v[c] = __ldg(g.tiles + (e & ~kTile));
+                } else if (e & kNeural) {
+                    v[c] = __uint_as_float(e & ~kNeural);      // the rank, until the network answers
+                    nmask |= 1u << c;
+                } else {
+                    v[c] = leaf_value_t<1>(g, e, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7), acc.sm);
+                }
+            }
+        }
+        // rows of the warp's neural corners: this lane's are [base, base + cnt)
+        const int cnt = __popc(nmask);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int base = incl - cnt;
+        uint32_t* rows = s_rows[wid];
+        float* outs = s_out[wid];
+        for (int t0 = 0; t0 < total; t0 += 16) {
+            int q = base;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (nmask & (1u << c)) {
+                    if (q >= t0 && q < t0 + 16) {
+                        const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
+                        mlp_row(rows, q - t0, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7),
+                                g.latents + (size_t)__float_as_uint(v[c]) * kMlpLatent);
+                    }
+                    ++q;
+                }
+            }
+            __syncwarp();
+            mlp_tile(rows, g.mlp_frag, g.mlp_bias, outs);   // rows past `total` are stale and unread
+            __syncwarp();
+            q = base;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (nmask & (1u << c)) {
+                    if (q >= t0 && q < t0 + 16) {
+                        const float2 m = __ldg(g.nmeta + __float_as_uint(v[c]));
+                        v[c] = __fmaf_rn(m.x, fminf(fmaxf(outs[q - t0], 0.0f), 1.0f), m.y);
+                    }
+                    ++q;
+                }
+            }
+            __syncwarp();
+        }
+        if (!look) return 0.0f;
+        const float c00 = lerpf(v[0], v[1], tx), c10 = lerpf(v[2], v[3], tx);
+        const float c01 = lerpf(v[4], v[5], tx), c11 = lerpf(v[6], v[7], tx);
+        const float c0 = lerpf(c00, c10, ty), c1 = lerpf(c01, c11, ty);
+        return lerpf(c0, c1, tz);
+    }
+};
+
+}  // namespace vdbc

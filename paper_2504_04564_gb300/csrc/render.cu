@@ -30,6 +30,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "learn.cuh"
 #include "vdbc_host.h"
 
 namespace vdbc {
@@ -349,6 +350,7 @@ struct JobView {
 template <class S>
 struct SingleSource {
     static constexpr bool kMulti = false;
+    static constexpr bool kCollective = S::kCollective;
     const JobView& j;
     const S& smp;
     const uint32_t* b;
@@ -358,12 +360,17 @@ struct SingleSource {
     __device__ __forceinline__ const uint32_t* bits(int) const { return b; }
     __device__ __forceinline__ const uint32_t* cbits(int) const { return cb; }
     __device__ __forceinline__ float sample(int, float x, float y, float z, Accessor& a) const { return smp(x, y, z, a); }
+    __device__ __forceinline__ float collective(bool look, float x, float y, float z, Accessor& a) const
+    {
+        return smp.collective(look, x, y, z, a);
+    }
 };
 
 // many jobs: their constants and grids staged in shared memory; each lane
 // decodes its job's payload type at run time
 struct BatchSource {
     static constexpr bool kMulti = true;
+    static constexpr bool kCollective = false;
     const JobView* jobs;
     const GridView* grids;
     int n;
@@ -485,6 +492,8 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         // ---- one free flight per lane: draw tau, spend it over the cells, and
         // where it runs out evaluate the density (delta: accept or not;
         // ratio: attenuate)
+        bool look = false;
+        float3 x = f3(0.f, 0.f, 0.f);
         if (mode == kDelta || mode == kRatio) {
             if (tau < 0.0f) {
                 Rng rng{pixel, J.sample_base + sample, J.k0, J.k1};
@@ -517,39 +526,50 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 float t = __fadd_rn(tr.tcur, __fdiv_rn(tau, tr.mj));
                 tr.tcur = t;
                 tau = -1.0f;
-                float3 x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
-                float sigma = __fmul_rn(med.sigma_scale, src.sample(jb, x.x, x.y, x.z, acc));
-                ++w.lookups;
-                if (mode == kRatio) {
-                    T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
-                } else if (__fmul_rn(ua, tr.mj) < sigma) {
-                    // real collision: scatter, then trace the light ray from here
-                    beta *= med.albedo;
-                    ph = hg_eval(dot3(d, med.sun_dir), med.g);
-                    float mu = hg_sample_mu(med.g, ub);
-                    float st_ = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
-                    float sphi, cphi;
-                    sincospif(2.0f * uc, &sphi, &cphi);
-                    float3 b1, b2;
-                    onb(d, b1, b2);
-                    nd = norm3(f3(st_ * cphi * b1.x + st_ * sphi * b2.x + mu * d.x,
-                                  st_ * cphi * b1.y + st_ * sphi * b2.y + mu * d.y,
-                                  st_ * cphi * b1.z + st_ * sphi * b2.z + mu * d.z));
-                    o = x;
-                    d = med.sun_dir;
-                    T = 1.0f;
-                    float tin, tout;
-                    mode = kRatio;
-                    if (clip_box(m, o, d, tin, tout)) {
-                        tr.dda.init(m, o, d, tin, tout);
-                        tau = -1.0f;   // every ray starts a new free flight
-                        VDBC_EVENT(w, 4);
-                        guard = m.mx + m.my + m.mz + 8;
-                        steps_in_cell = 0;
-                        if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kRatio;
-                    } else {
-                        mode = -kRatio;
-                    }
+                x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
+                look = true;
+            }
+        }
+        // ---- the density lookup: per lane, or for a learned grid by the whole
+        // warp at once (its network runs on warp-wide tiles)
+        float dens = 0.0f;
+        if constexpr (Src::kCollective) {
+            __syncwarp();
+            dens = src.collective(look, x.x, x.y, x.z, acc);
+        }
+        if (look) {
+            if constexpr (!Src::kCollective) dens = src.sample(jb, x.x, x.y, x.z, acc);
+            float sigma = __fmul_rn(med.sigma_scale, dens);
+            ++w.lookups;
+            if (mode == kRatio) {
+                T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
+            } else if (__fmul_rn(ua, tr.mj) < sigma) {
+                // real collision: scatter, then trace the light ray from here
+                beta *= med.albedo;
+                ph = hg_eval(dot3(d, med.sun_dir), med.g);
+                float mu = hg_sample_mu(med.g, ub);
+                float st_ = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+                float sphi, cphi;
+                sincospif(2.0f * uc, &sphi, &cphi);
+                float3 b1, b2;
+                onb(d, b1, b2);
+                nd = norm3(f3(st_ * cphi * b1.x + st_ * sphi * b2.x + mu * d.x,
+                              st_ * cphi * b1.y + st_ * sphi * b2.y + mu * d.y,
+                              st_ * cphi * b1.z + st_ * sphi * b2.z + mu * d.z));
+                o = x;
+                d = med.sun_dir;
+                T = 1.0f;
+                float tin, tout;
+                mode = kRatio;
+                if (clip_box(m, o, d, tin, tout)) {
+                    tr.dda.init(m, o, d, tin, tout);
+                    tau = -1.0f;   // every ray starts a new free flight
+                    VDBC_EVENT(w, 4);
+                    guard = m.mx + m.my + m.mz + 8;
+                    steps_in_cell = 0;
+                    if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kRatio;
+                } else {
+                    mode = -kRatio;
                 }
             }
         }
@@ -759,6 +779,60 @@ __global__ void __launch_bounds__(128) k_ea(S smp, Majorants m, CamDev cam, MedD
     flush_stats(st, w, paths);
 }
 
+// the same marcher for samplers whose lookups are warp-collective: every lane
+// stays in the loop until the whole warp is done and calls the lookup each
+// step (look = false once its own ray has ended)
+template <class S>
+__global__ void __launch_bounds__(128) k_ea_collective(S smp, Majorants m, CamDev cam, MedDev med,
+                                                       float4* __restrict__ out, DevStats* __restrict__ st)
+{
+    extern __shared__ float4 s_tf[];
+    for (int i = threadIdx.x; i < med.tf_n; i += blockDim.x) s_tf[i] = med.tf[i];
+    __syncthreads();
+    const int npix = cam.w * cam.h;
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    Walk w{};
+    unsigned long long paths = 0;
+    Accessor acc;
+    acc.reset();
+    float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
+    float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.0f, tin = 0.f, tout = 0.f;
+    bool active = false;
+    long long kmax = 0;
+    const float dt = med.step;
+    const float tfm = (float)(med.tf_n - 1);
+    if (pix < npix) {
+        camera_ray(cam, pix % cam.w, pix / cam.w, 0.5f, 0.5f, o, d);
+        active = clip_box(m, o, d, tin, tout);
+        if (active) kmax = (long long)((tout - tin) / dt) + 2;
+    }
+    for (long long k = 0;; ++k) {
+        float t = tin + ((float)k + 0.5f) * dt;
+        if (active && (k >= kmax || t >= tout)) active = false;
+        if (!__any_sync(0xffffffffu, active)) break;
+        float s = smp.collective(active, o.x + t * d.x, o.y + t * d.y, o.z + t * d.z, acc);
+        if (active) {
+            ++w.lookups;
+            s = fminf(fmaxf(s, 0.0f), 1.0f);
+            float x = s * tfm;
+            int i0 = min((int)floorf(x), med.tf_n - 2);
+            float f = x - (float)i0;
+            float4 a = s_tf[i0], b = s_tf[i0 + 1];
+            float r = lerpf(a.x, b.x, f), gg = lerpf(a.y, b.y, f), bb = lerpf(a.z, b.z, f), al = lerpf(a.w, b.w, f);
+            float alpha = 1.0f - expf(-al * dt);
+            float ta = T * alpha;
+            cr += ta * r; cg += ta * gg; cb += ta * bb;
+            T *= 1.0f - alpha;
+            if (T < 1e-6f) active = false;
+        }
+    }
+    if (pix < npix) {
+        out[pix] = make_float4(cr, cg, cb, 1.0f - T);
+        paths = 1;
+    }
+    flush_stats(st, w, paths);
+}
+
 unsigned blocks_for(long long n, int t) { return (unsigned)std::max<long long>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -935,7 +1009,11 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     long long npix = (long long)cam.w * cam.h;
     VDBC_CUDA(cudaMemsetAsync(stats, 0, sizeof(DevStats), s));
     if (med.mode == VDBC_MODE_EA) {
-        KLAUNCH(k_ea<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out, stats));
+        if constexpr (S::kCollective)
+            KLAUNCH(k_ea_collective<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out,
+                                                                                                stats));
+        else
+            KLAUNCH(k_ea<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out, stats));
         VDBC_CUDA(cudaGetLastError());
         return VDBC_OK;
     }
@@ -1042,6 +1120,9 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
     if (!grid) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_render: grid is null");
     const GridView& g = grid->view;
     Majorants mj{g.mcmax, g.mc, g.mx, g.my, g.mz, g.nx, g.ny, g.nz};
+    if (g.payload == VDBC_LEARNED)
+        return render_common(LearnedSampler{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
+                             out_on_device, stream);
     if (g.payload == VDBC_FP16)
         return render_common(VdbSamplerT<1>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                              out_on_device, stream);
@@ -1449,6 +1530,8 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     for (int i = 0; i < n; ++i) {
         const vdbc_job& j = jobs[i];
         if (!j.grid || !j.rgba_out) return fail(set_error(VDBC_ERR_INVALID_ARG, "job %d: null grid or output", i));
+        if (j.grid->info.payload == VDBC_LEARNED)
+            return fail(set_error(VDBC_ERR_UNSUPPORTED, "job %d: learned grids render through vdbc_render", i));
         vdbc_status st = check_camera(&j.camera);
         if (st != VDBC_OK) return fail(st);
         if (j.medium.mode != VDBC_MODE_PT) return fail(set_error(VDBC_ERR_INVALID_ARG, "job %d: batches path trace", i));

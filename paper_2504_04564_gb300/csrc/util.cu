@@ -136,12 +136,12 @@ extern "C" vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], u
 }
 
 // ---------------------------------------------------------------- save / load
-// File: 64-byte header {magic "VDBCGRD1", version, header bytes, info bytes,
-// block bytes, offsets[8], FNV-1a 64 of info+active+block}, then the
+// File: header {magic "VDBCGRD1", version, info bytes, activation bytes,
+// block bytes, table offsets[16], FNV-1a 64 of info+active+block}, then the
 // vdbc_grid_info struct, the activation flags and the linear block.
 namespace {
 constexpr char kMagic[8] = {'V', 'D', 'B', 'C', 'G', 'R', 'D', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 struct FileHeader {
     char magic[8];
@@ -149,7 +149,7 @@ struct FileHeader {
     uint32_t info_bytes;
     uint64_t active_bytes;
     uint64_t block_bytes;
-    uint64_t offsets[8];
+    uint64_t offsets[16];
     uint64_t checksum;
 };
 
@@ -173,9 +173,10 @@ extern "C" vdbc_status vdbc_grid_save(const vdbc_grid* g, const char* path)
     h.info_bytes = sizeof(vdbc_grid_info);
     h.active_bytes = g->active.size();
     h.block_bytes = g->block_bytes;
-    size_t offs[8] = {g->off_root, g->off_upper, g->off_lower, g->off_tiles, g->off_leaves, g->off_meta,
-                      g->off_mcmin, g->off_mcmax};
-    for (int i = 0; i < 8; ++i) h.offsets[i] = offs[i];
+    size_t offs[13] = {g->off_root, g->off_upper, g->off_lower, g->off_tiles, g->off_leaves, g->off_meta,
+                       g->off_mcmin, g->off_mcmax, g->off_latents, g->off_nmeta, g->off_frag, g->off_bias,
+                       g->off_params};
+    for (int i = 0; i < 13; ++i) h.offsets[i] = offs[i];
     uint64_t c = 0xcbf29ce484222325ull;
     c = fnv1a(c, &g->info, sizeof(vdbc_grid_info));
     c = fnv1a(c, g->active.data(), g->active.size());
@@ -225,9 +226,9 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
     for (int a = 0; a < 3; ++a)
         if (info.dims[a] < 1 || info.dims[a] > kMaxDim) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad dims");
     if ((long long)active.size() != info.n_bricks || info.macrocell < 1 || info.macrocell > 64 ||
-        info.payload < VDBC_FP32 || info.payload > VDBC_FP8)
+        info.payload < VDBC_FP32 || info.payload > VDBC_LEARNED)
         return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: inconsistent header");
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 16; ++i)
         if (h.offsets[i] > h.block_bytes || (h.offsets[i] & 255)) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad offsets");
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -238,6 +239,8 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
     g->off_root = h.offsets[0]; g->off_upper = h.offsets[1]; g->off_lower = h.offsets[2];
     g->off_tiles = h.offsets[3]; g->off_leaves = h.offsets[4]; g->off_meta = h.offsets[5];
     g->off_mcmin = h.offsets[6]; g->off_mcmax = h.offsets[7];
+    g->off_latents = h.offsets[8]; g->off_nmeta = h.offsets[9]; g->off_frag = h.offsets[10];
+    g->off_bias = h.offsets[11]; g->off_params = h.offsets[12];
     cudaGetDevice(&g->device);
     vdbc_status st = dev_alloc(&g->block, g->block_bytes, s);
     if (st == VDBC_OK) st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);

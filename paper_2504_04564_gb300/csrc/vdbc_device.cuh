@@ -9,6 +9,8 @@
 //   leaves payload[n_leaves * 512]  8^3 values, x fastest (f32, f16 or e4m3)
 //   meta   float2[n_leaves]         (scale, offset) of quantized leaves
 //   mcmin, mcmax f32[n_macrocells]  min/max of the decoded grid per macrocell
+//   learned grids add: latents f16[n_neural * 16], nmeta float2[n_neural],
+//   the network's B fragments u32x2[18 * 32], biases f32[65], params f32[1729]
 // An entry of root/upper/lower is a child index (bit 31 clear) or a tile
 // (bit 31 set, low bits index `tiles`).  This is the {5,4,3} tree of Section
 // 2.3 with the root made a dense table because the input is a bounded
@@ -41,7 +43,16 @@ struct GridView {
     const float2* meta;
     const float* mcmin;
     const float* mcmax;
+    // learned grids (payload 3): latents and (scale, offset) of neural leaves,
+    // network as B fragments and biases; `leaves`/`meta` hold the FP16 fallbacks
+    const __half* latents;
+    const float2* nmeta;
+    const uint2* mlp_frag;
+    const float* mlp_bias;
 };
+
+constexpr uint32_t kNeural = 0x40000000u;   // lower entry of a neural leaf (with bit 31 clear)
+constexpr int kLearned = 3;
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., SC'11: 10 rounds of two 32x32 multiplies, key bumped by the
@@ -104,7 +115,9 @@ __device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, i
 }
 
 // per-thread cached accessor: remembers the last leaf-level entry (Section
-// 3.2.2: NanoVDB's accessors cache the path of the last lookup)
+// 3.2.2: NanoVDB's accessors cache the path of the last lookup).  leaf() is
+// for FP32/FP16/FP8 grids; learned grids resolve entries through
+// LearnedSampler::leaf, which knows the neural entries.
 struct Accessor {
     int li, lj, lk;
     uint32_t entry;
@@ -173,6 +186,7 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
 
 template <int P>
 struct VdbSamplerT {
+    static constexpr bool kCollective = false;
     GridView g;
     __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor& acc) const
     {
@@ -182,6 +196,7 @@ struct VdbSamplerT {
 
 // plain form, linear device array, the same software trilinear
 struct LinearSampler {
+    static constexpr bool kCollective = false;
     const float* d;
     int nx, ny, nz;
     __device__ __forceinline__ float at(int i, int j, int k) const
@@ -205,6 +220,7 @@ struct LinearSampler {
 // plain form, 3D CUDA texture with hardware trilinear and clamp addressing
 // (unnormalized coordinates: texel centres sit at i + 1/2)
 struct TexSampler {
+    static constexpr bool kCollective = false;
     cudaTextureObject_t tex;
     __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor&) const
     {

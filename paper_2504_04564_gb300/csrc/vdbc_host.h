@@ -69,6 +69,7 @@ struct vdbc_grid {
     size_t block_bytes = 0;
     size_t off_root = 0, off_upper = 0, off_lower = 0, off_tiles = 0, off_leaves = 0, off_meta = 0,
            off_mcmin = 0, off_mcmax = 0;
+    size_t off_latents = 0, off_nmeta = 0, off_frag = 0, off_bias = 0, off_params = 0;   // learned grids
     std::vector<uint8_t> active;     // host copy of the activation flags (one per brick)
     vdbc::GridView view{};
     vdbc::DevStats* stats = nullptr; // device counters of the last render
@@ -90,7 +91,36 @@ struct vdbc_volume {
 namespace vdbc {
 // fills g.view from the offsets and the block pointer
 void bind_view(vdbc_grid* g);
-// builds the macrocell min/max of a grid (encode and load call it)
+// offsets of every table in the block from the counts in g->info
+void layout(vdbc_grid* g);
+// builds the macrocell min/max of a grid (encode, learn and load call it)
 vdbc_status build_macrocells(vdbc_grid* g, cudaStream_t s);
+vdbc_status macrocells_of_view(const GridView& v, float* mcmin, float* mcmax, cudaStream_t s);
+// k_decode over an explicit view (FP32/FP16/FP8 payloads)
+void decode_view(const GridView& v, float* out, long long n, cudaStream_t s);
 size_t align256(size_t x);
+// exclusive scan of n u32 values (total to total_dev[0]); tmp holds scan_tmp_words(n) words
+long long scan_tmp_words(long long n);
+void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* tmp, uint32_t* total_dev, cudaStream_t s);
+// chosen[i] = 1 for the `budget` largest keys among i with !skip[i], ties to
+// the lower index (one CTA); counts = {#candidates, #chosen}
+void select_largest(const unsigned long long* key, const uint8_t* skip, int n, long long budget, uint8_t* chosen,
+                    long long* counts, cudaStream_t s);
+
+// A learned grid seen as a plain FP32 grid: its lower table with neural
+// entries renumbered after the raw leaves, and every leaf decoded (raw FP16
+// leaves by their scale/offset, neural leaves through the network).
+struct Materialized {
+    void* lower = nullptr;
+    void* leaves = nullptr;
+    GridView view{};
+    void release(cudaStream_t s)
+    {
+        if (lower) dev_free(lower, s);
+        if (leaves) dev_free(leaves, s);
+        lower = leaves = nullptr;
+    }
+};
+vdbc_status materialize_learned(const vdbc_grid* g, cudaStream_t s, Materialized* out);
+vdbc_status build_learned_macrocells(vdbc_grid* g, cudaStream_t s);
 }  // namespace vdbc

@@ -1,0 +1,279 @@
+"""The learned leaf codec on the GPU (a project extension; the paper's
+Section 2.3 names network-decoded leaves as related work only).
+
+Checked here: the FP32 training kernels' loss and gradients against the FP64
+oracle; one whole training step (Philox draws, targets, gradients, Adam)
+against the oracle replaying it; learned grids decoded on the tensor cores
+against the oracle's bf16-precision decode; renders of learned grids against
+the plain-form render of their decoded values (bit-exact) and against the
+FP64 oracle; save/load; and what the trained network gains over the method
+without it at equal memory.
+
+Tolerances.  Training: FP32 sums of at most a few thousand terms against
+FP64, relative error of a sum below n * 2^-24 of the sum of magnitudes, so
+1e-4 of the largest gradient entry.  Decode: both sides round the operands
+and the hidden activations to bf16, but the tensor cores accumulate in FP32
+and the oracle exactly; an activation whose FP32 sum lands on the other side
+of a bf16 rounding boundary would move y by about |w| * 2^-8 * |h| (1e-3 of
+the leaf's range), so that is the bound for single voxels, with the mean
+held to 1e-6 of the range (measured on a GB300: 98.6 % of the neural voxels
+bit-exact, the largest difference 8e-8 of the range).  Path tracing: mean
+abs 1e-4 per channel, as for the other payloads.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PT_MEAN_ABS = 1e-4
+DRAW_TAG = 0x4C454146
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import oracle
+    import paper_2504_04564_gb300 as v
+    import volgen
+    from volgen import scenes
+    return dict(torch=torch, v=v, orc=oracle, vg=volgen, sc=scenes, dev=torch.device("cuda:0"))
+
+
+def he_params(orc, rng, scale=1.0):
+    """Seeded weights uniform in +-sqrt(6/fan_in), biases small."""
+    n_in, h = orc.MLP_IN, orc.MLP_HID
+    parts = [rng.uniform(-1, 1, h * n_in) * math.sqrt(6 / n_in), rng.uniform(-0.1, 0.1, h),
+             rng.uniform(-1, 1, h * h) * math.sqrt(6 / h), rng.uniform(-0.1, 0.1, h),
+             rng.uniform(-1, 1, h) * math.sqrt(6 / h), [0.5]]
+    return (np.concatenate(parts) * scale).astype(np.float32)
+
+
+def leaf_grid(dims):
+    return ((dims[0] + 7) // 8, (dims[1] + 7) // 8, (dims[2] + 7) // 8)
+
+
+def source(env, kind, dims, seed, ratio):
+    torch, v, orc, vg = env["torch"], env["v"], env["orc"], env["vg"]
+    host = vg.generate_host(vg.make_params(kind, dims, seed))
+    grid = v.vdbc_encode(torch.from_numpy(host).to(env["dev"]), ratio)
+    e = orc.encode(host, ratio)
+    return host, grid, e
+
+
+def decode(env, grid, dims):
+    torch, v = env["torch"], env["v"]
+    out = torch.empty(dims[2], dims[1], dims[0], dtype=torch.float32, device=env["dev"])
+    v.vdbc_grid_decode(grid, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def psnr(a, b):
+    peak = float(b.max() - b.min())
+    mse = float(np.mean((a.astype(np.float64) - b.astype(np.float64)) ** 2))
+    return 10 * math.log10(peak * peak / max(mse, 1e-30))
+
+
+# ------------------------------------------------------------------ training kernels
+@pytest.mark.parametrize("n", [1, 129, 1000])
+def test_loss_grad_matches_oracle(env, n):
+    torch, v, orc = env["torch"], env["v"], env["orc"]
+    rng = np.random.default_rng(n)
+    p = he_params(orc, rng)
+    x = rng.random((n, 19)).astype(np.float32)
+    t = rng.random(n).astype(np.float32)
+    dev = env["dev"]
+    gp = torch.zeros(orc.mlp_num_params(), device=dev)
+    gx = torch.zeros(n, 19, device=dev)
+    loss = v.vdbc_learn_loss_grad(torch.from_numpy(p).to(dev), torch.from_numpy(x).to(dev),
+                                  torch.from_numpy(t).to(dev), gp, gx)
+    rl, rp, rx = orc.mlp_loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - rl) <= 1e-5 * rl
+    gp, gx = gp.cpu().numpy(), gx.cpu().numpy()
+    assert np.max(np.abs(gp - rp)) <= 1e-4 * np.max(np.abs(rp))
+    assert np.max(np.abs(gx - rx)) <= 1e-4 * np.max(np.abs(rx))
+
+
+def test_one_training_step_matches_oracle(env):
+    """Step 0 replayed on the CPU: the same Philox draws pick the voxels, the
+    targets are (v - offset) / scale in FP32, the oracle's FP64 gradient and
+    Adam step give the parameters after the step."""
+    torch, v, orc = env["torch"], env["v"], env["orc"]
+    dims, S, seed, lr, lr_lat = (40, 36, 44), 16, 7, 1e-3, 1e-2
+    host, grid, e = source(env, "blobs", dims, 0, 1.0)
+    nl = leaf_grid(dims)
+    rng = np.random.default_rng(11)
+    p0 = he_params(orc, rng)
+    lat = (rng.random((nl[0] * nl[1] * nl[2], 16)) * 0.2 - 0.1).astype(np.float32)
+    dev = env["dev"]
+    learned, losses = v.vdbc_learn(grid, steps=1, samples_per_leaf=S, lr=lr, lr_latent=lr_lat, seed=seed,
+                                   init_params=torch.from_numpy(p0).to(dev),
+                                   init_latents=torch.from_numpy(lat).to(dev))
+    p1 = v.vdbc_learn_get_params(learned)
+    tree = orc.Tree(host, e["active"], e["background_bits"])
+    X, T = [], []
+    stratum = 512 // S
+    for lk in range(nl[2]):
+        for lj in range(nl[1]):
+            for li in range(nl[0]):
+                src = tree.leaf(li, lj, lk)
+                if src is None:
+                    continue
+                pos = (lk * nl[1] + lj) * nl[0] + li
+                _, scale, offset = orc.quantize_leaf(src, orc.FP16)
+                for s in range(S):
+                    r = orc.philox([pos, 0, s, DRAW_TAG], [seed & 0xFFFFFFFF, seed >> 32])
+                    nv = s * stratum + int(r[0] & (stratum - 1))
+                    tgt = np.float32(np.float32(src[nv] - np.float32(offset)) / np.float32(scale))
+                    uvw = [np.float32(k / 7.0) for k in (nv & 7, (nv >> 3) & 7, nv >> 6)]
+                    X.append(np.concatenate([uvw, lat[pos]]).astype(np.float64))
+                    T.append(float(tgt))
+    X, T = np.array(X), np.array(T)
+    assert len(T) == S * tree.counts()["leaves"]
+    rl, rg, _ = orc.mlp_loss_grad(p0.astype(np.float64), X, T)
+    assert abs(losses[0] - rl) <= 1e-5 * rl
+    ref = p0.astype(np.float64)
+    m, vv = np.zeros_like(ref), np.zeros_like(ref)
+    orc.adam_step(ref, rg, m, vv, 1, lr=lr)
+    big = np.abs(rg) > 1e-3 * np.abs(rg).max()
+    assert big.sum() > 500
+    assert np.max(np.abs(p1[big] - ref[big])) <= 1e-2 * lr
+    assert np.max(np.abs(p1 - ref)) <= 2.0 * lr
+
+
+# ------------------------------------------------------------------ decode and render
+def learned_fixture(env, dims=(40, 36, 44), ratio=2.0, neural_frac=0.7, seed=3):
+    torch, v, orc = env["torch"], env["v"], env["orc"]
+    host, grid, e = source(env, "blobs", dims, seed, ratio)
+    nl = leaf_grid(dims)
+    npos = nl[0] * nl[1] * nl[2]
+    rng = np.random.default_rng(seed)
+    p = he_params(orc, rng)
+    lat = (rng.random((npos, 16)) * 2 - 1).astype(np.float32)
+    force = np.where(rng.random(npos) < neural_frac, 1, 2).astype(np.uint8)
+    dev = env["dev"]
+    learned, _ = v.vdbc_learn(grid, steps=0, init_params=torch.from_numpy(p).to(dev),
+                              init_latents=torch.from_numpy(lat).to(dev), force=torch.from_numpy(force).to(dev))
+    want, kinds = orc.learned_decode(host, e["active"], e["background_bits"], p.astype(np.float64), lat, force)
+    return host, grid, learned, want, kinds
+
+
+def test_learned_decode_matches_oracle(env):
+    v = env["v"]
+    dims = (40, 36, 44)
+    host, grid, learned, want, kinds = learned_fixture(env, dims)
+    info = learned.info
+    assert info.payload == v.LEARNED
+    assert info.n_neural == int((kinds == 1).sum()) and info.n_leaves == int((kinds == 2).sum())
+    assert info.n_neural > 20 and info.n_leaves > 5
+    got = decode(env, learned, dims)
+    nl = leaf_grid(dims)
+    kv = np.repeat(np.repeat(np.repeat(kinds.reshape(nl[2], nl[1], nl[0]), 8, 0), 8, 1), 8, 2)
+    kv = kv[:dims[2], :dims[1], :dims[0]]
+    plain = kv != 1
+    assert np.array_equal(got[plain].view(np.uint32), want[plain].view(np.uint32))
+    rng_ = float(host.max() - host.min())
+    d = np.abs(got[~plain].astype(np.float64) - want[~plain])
+    print("\nneural voxels %d: max |diff| %.3g, mean %.3g, exact %.4f (of the value range)"
+          % (d.size, d.max() / rng_, d.mean() / rng_, float(np.mean(d == 0))))
+    assert d.max() <= 1e-3 * rng_
+    assert d.mean() <= 1e-6 * rng_
+
+
+def test_learned_grid_save_load(env, tmp_path):
+    v = env["v"]
+    dims = (40, 36, 44)
+    _, _, learned, _, _ = learned_fixture(env, dims, seed=4)
+    path = str(tmp_path / "learned.vdbc")
+    v.vdbc_grid_save(learned, path)
+    back = v.vdbc_grid_load(path)
+    assert back.info.n_neural == learned.info.n_neural
+    assert np.array_equal(decode(env, back, dims).view(np.uint32), decode(env, learned, dims).view(np.uint32))
+    assert np.array_equal(v.vdbc_learn_get_params(back), v.vdbc_learn_get_params(learned))
+
+
+@pytest.mark.parametrize("mode", ["pt", "ea"])
+def test_learned_render_equals_dense_render_of_its_decode(env, mode):
+    """The collective lookups decode every neural corner exactly as the decode
+    entry point does, so a learned-grid render equals the linear plain-form
+    render of the decoded grid bit for bit."""
+    torch, v, sc = env["torch"], env["v"], env["sc"]
+    dims = (40, 36, 44)
+    _, _, learned, _, _ = learned_fixture(env, dims, seed=5)
+    dec = torch.from_numpy(decode(env, learned, dims)).to(env["dev"])
+    vol = v.vdbc_volume_create(dec, v.FILTER_LINEAR)
+    cam = v.make_camera(*sc.pinhole_orbit(dims, 36, 28))
+    if mode == "pt":
+        med = v.make_medium(v.MODE_PT, **sc.pt_medium_args(density_scale=40.0))
+        spp = 8
+    else:
+        med = v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf(), step=0.5)
+        spp = 1
+    a = torch.zeros(28, 36, 4, device=env["dev"])
+    b = torch.zeros(28, 36, 4, device=env["dev"])
+    v.vdbc_render(learned, cam, med, spp, 3, a)
+    v.vdbc_render_dense(vol, cam, med, spp, 3, b)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert v.vdbc_render_stats_get(learned).lookups > 0
+
+
+def test_learned_render_matches_oracle(env):
+    torch, v, orc, sc = env["torch"], env["v"], env["orc"], env["sc"]
+    dims = (40, 36, 44)
+    _, _, learned, want, _ = learned_fixture(env, dims, seed=6)
+    cam_args = sc.pinhole_orbit(dims, 32, 24)
+    kw = sc.pt_medium_args(density_scale=40.0)
+    out = torch.zeros(24, 32, 4, device=env["dev"])
+    v.vdbc_render(learned, v.make_camera(*cam_args), v.make_medium(v.MODE_PT, **kw), 8, 9, out)
+    torch.cuda.synchronize()
+    mx = orc.macrocell_minmax(want, 8)[1]
+    ref = orc.render_image(want, mx, orc.make_camera(*cam_args), orc.make_medium(1, macrocell=8, **kw), 8, 9,
+                           threads=8)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got[..., :3] - ref[..., :3]).mean(axis=(0, 1)) <= PT_MEAN_ABS)
+
+
+def test_learn_argument_errors(env):
+    torch, v = env["torch"], env["v"]
+    _, grid, _ = source(env, "blobs", (24, 24, 24), 0, 2.0)
+    with pytest.raises(v.VdbcError):
+        v.vdbc_learn(grid, samples_per_leaf=20)
+    with pytest.raises(v.VdbcError):
+        v.vdbc_learn(grid, steps=5, lr=0.0)
+    learned, _ = v.vdbc_learn(grid, steps=0)
+    with pytest.raises(v.VdbcError):
+        v.vdbc_learn(learned, steps=0)
+    out = torch.zeros(8, 8, 4, device=env["dev"])
+    cam = v.make_camera(v.CAM_PINHOLE, 8, 8, (60, 60, 60), (12, 12, 12), (0, 1, 0), 40)
+    med = v.make_medium(v.MODE_PT, density_scale=5.0)
+    with pytest.raises(v.VdbcError):
+        v.vdbc_batch_create([v.make_job(learned, cam, med, 1, 0, out)], autotune=False)
+
+
+# ------------------------------------------------------------------ what the network gains
+def test_trained_network_beats_vdb_at_equal_memory(env):
+    """A 96^3 turbulent medium: the method without the network (FP32 VDB at
+    1:10) against a learned grid no larger than it, built from every
+    non-empty brick; and the same learned grid untrained."""
+    v = env["v"]
+    dims = (96, 96, 96)
+    host, full, _ = source(env, "turbulence", dims, 2, 1.0)
+    _, vdb10, _ = source(env, "turbulence", dims, 2, 10.0)
+    budget = int(vdb10.info.total_bytes)
+    learned, losses = v.vdbc_learn(full, steps=400, samples_per_leaf=64, lr=2e-3, lr_latent=2e-2,
+                                   max_bytes=budget, seed=1)
+    untrained, _ = v.vdbc_learn(full, steps=0, max_bytes=budget, seed=1)
+    assert learned.info.total_bytes <= budget and untrained.info.total_bytes <= budget
+    assert losses[-1] < 0.2 * losses[0]
+    p_vdb = psnr(decode(env, vdb10, dims), host)
+    p_learned = psnr(decode(env, learned, dims), host)
+    p_untrained = psnr(decode(env, untrained, dims), host)
+    print("\nequal memory (%d B): VDB 1:10 %.2f dB, learned %.2f dB (%d neural, %d raw), untrained %.2f dB"
+          % (budget, p_vdb, p_learned, learned.info.n_neural, learned.info.n_leaves, p_untrained))
+    assert p_learned >= p_vdb + 3.0
+    assert p_learned >= p_untrained + 3.0

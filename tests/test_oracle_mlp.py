@@ -123,3 +123,90 @@ def test_bf16_forward_close_to_full_precision(orc):
     q[32 * 19 + 32 + 32 * 32 + 32] = 2.0  # w3[0]
     xx = np.zeros((3, 19)); xx[:, 0] = [0.5, 0.25, 0.75]
     assert np.array_equal(orc.mlp_forward_bf16(q, xx), 2.0 * xx[:, 0])
+
+
+def _u_network(orc):
+    """y = u (the voxel's x position in its leaf / 7) through explicit weights."""
+    lay = layout(orc)
+    p = np.zeros(orc.mlp_num_params())
+    view(p, lay, "W1")[0, 0] = 1.0
+    view(p, lay, "W2")[0, 0] = 1.0
+    view(p, lay, "w3")[0] = 1.0
+    return p, lay
+
+
+def test_learned_leaf_closed_forms(orc):
+    rng = np.random.default_rng(3)
+    src = rng.random(512).astype(np.float32) * 5 - 1
+    _, scale, offset = orc.quantize_leaf(src, orc.FP16)
+    assert scale == np.float32(src.max()) - np.float32(src.min()) and offset == src.min()
+    lay = layout(orc)
+    z = rng.random(16).astype(np.float32)
+    # constant networks: y = b3, clamped to [0, 1]
+    for b3, want in ((0.25, 0.25), (2.0, 1.0), (-1.0, 0.0)):
+        p = np.zeros(orc.mlp_num_params())
+        view(p, lay, "b3")[0] = b3
+        out = orc.learned_leaf(p, z, src)
+        assert np.all(out == np.float32(np.float64(offset) + np.float64(scale) * want))
+    # y = u: bf16 rounding of i/7 shows in the output, the latent does not
+    p, _ = _u_network(orc)
+    out = orc.learned_leaf(p, z, src)
+    i = np.arange(512) & 7
+    u_bf16 = np.array([orc.round_bf16(np.float32(k / 7.0)) for k in range(8)])
+    want = (np.float64(offset) + np.float64(scale) * u_bf16[i]).astype(np.float32)
+    assert np.array_equal(out, want)
+    assert not np.array_equal(u_bf16, np.arange(8) / 7.0)     # the rounding is visible
+
+
+def test_learned_leaf_latent_is_fp16_then_bf16(orc):
+    # y = z_0 through the network: the latent is stored in FP16, then enters as bf16
+    lay = layout(orc)
+    p = np.zeros(orc.mlp_num_params())
+    view(p, lay, "W1")[0, 3] = 1.0
+    view(p, lay, "W2")[0, 0] = 1.0
+    view(p, lay, "w3")[0] = 1.0
+    src = np.linspace(0, 1, 512, dtype=np.float32)
+    z = np.zeros(16, dtype=np.float32)
+    z[0] = np.float32(0.3337)
+    out = orc.learned_leaf(p, z, src)
+    want = orc.round_bf16(orc.round_fp16(z[0]))
+    assert np.all(out == np.float32(want))       # offset 0, scale 1
+
+
+def test_tree_leaf_matches_decode(orc, vg):
+    vol = vg.generate_host(vg.make_params("blobs", (40, 36, 44), 0))
+    enc = orc.encode(vol, 4.0)
+    tree = orc.Tree(vol, enc["active"], enc["background_bits"])
+    dec = orc.decode_dense(vol, enc["active"], enc["background_bits"])
+    B = np.uint32(enc["background_bits"]).view(np.float32)
+    nz, ny, nx = vol.shape
+    n = 0
+    for lk in range((nz + 7) // 8):
+        for lj in range((ny + 7) // 8):
+            for li in range((nx + 7) // 8):
+                leaf = tree.leaf(li, lj, lk)
+                blk = dec[lk * 8:lk * 8 + 8, lj * 8:lj * 8 + 8, li * 8:li * 8 + 8]
+                if leaf is None:
+                    # a tile: the decoded region is constant
+                    assert np.all(blk.view(np.uint32) == blk.reshape(-1)[0].view(np.uint32))
+                    continue
+                n += 1
+                cube = leaf.reshape(8, 8, 8)
+                ez, ey, ex = blk.shape
+                assert np.array_equal(cube[:ez, :ey, :ex].view(np.uint32), blk.view(np.uint32))
+                outside = np.ones((8, 8, 8), bool)
+                outside[:ez, :ey, :ex] = False
+                assert np.all(cube[outside] == B)
+    assert n == tree.counts()["leaves"] and n > 0
+
+
+def test_learned_decode_all_raw_is_the_fp16_grid(orc, vg):
+    vol = vg.generate_host(vg.make_params("blobs", (40, 36, 44), 1))
+    enc = orc.encode(vol, 2.0)
+    nl = 5 * 5 * 6
+    force = np.full(nl, 2, np.uint8)
+    out, kinds = orc.learned_decode(vol, enc["active"], enc["background_bits"], np.zeros(orc.mlp_num_params()),
+                                    np.zeros((nl, 16), np.float32), force)
+    want = orc.decode_dense(vol, enc["active"], enc["background_bits"], orc.FP16)
+    assert np.array_equal(out.view(np.uint32), want.view(np.uint32))
+    assert int((kinds == 2).sum()) == orc.Tree(vol, enc["active"], enc["background_bits"]).counts()["leaves"]
