@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-volume batched section")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-decoder section")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="the ncu capture case: the same workload at a 512x512 image, two renders")
@@ -298,6 +299,7 @@ def run_vdbc(args):
                "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16)}
 
     batch = None if args.no_batch else run_batch_section(v, volgen, scenes, dev, stream, args)
+    learned = None if args.no_learned else run_learned_section(v, volgen, scenes, dev, stream)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
@@ -324,6 +326,7 @@ def run_vdbc(args):
         "clocks": clk,
         "e2e": e2e,
         "batch": batch,
+        "learned": learned,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -393,6 +396,84 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
             "tuning": {"threads": tuning.threads, "chunk": tuning.chunk, "coarse": tuning.coarse},
             "create_s_incl_autotune": round(create_s, 3),
             "workload": "32 blob+fBm volumes, edges 64..384, rates 1:4..1:20, FP16/FP8, 256^2..1024^2, 4..32 spp"}
+
+
+def run_learned_section(v, volgen, scenes, dev, stream):
+    """The learned leaf decoder on the 994 x 676 x 1225 cloud: a learned grid
+    built from every non-empty brick and held to the bytes of VDB FP32 at 1:10,
+    against VDB FP32 and FP16 at 1:10 (equal bytes by the rate's definition);
+    volume PSNR against the input, and each at 1920 x 1080 x 32 spp against
+    the dense-texture render (image PSNR, Mpaths/s)."""
+    import math
+
+    import torch
+
+    w = scenes.CLOUD_994
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev)
+    torch.cuda.synchronize()
+    peak = float(vol.max() - vol.min())
+
+    def vpsnr(g):
+        out = torch.empty_like(vol)
+        v.vdbc_grid_decode(g, out, stream=stream)
+        torch.cuda.synchronize()
+        mse = float(((out.double() - vol.double()) ** 2).mean())
+        return round(10 * math.log10(peak * peak / max(mse, 1e-30)), 3)
+
+    full = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"], stream=stream)
+    vdb32 = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
+    vdb16 = v.vdbc_encode(vol, w["ratio"], payload=v.FP16, macrocell=w["macrocell"], stream=stream)
+    budget = int(vdb32.info.total_bytes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    learned, losses = v.vdbc_learn(full, max_bytes=budget, stream=stream, **w["learn"])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], w["width"], w["height"]))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, w["macrocell"], stream=stream)
+    img = torch.empty((w["height"], w["width"], 4), dtype=torch.float32, device=dev)
+    paths = w["width"] * w["height"] * w["spp"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_render(target, is_dense=False):
+        fn = v.vdbc_render_dense if is_dense else v.vdbc_render
+        fn(target, cam, med, w["spp"], 1, img, stream=stream)      # warm-up
+        e0.record(stream)
+        fn(target, cam, med, w["spp"], 1, img, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = (v.vdbc_volume_render_stats_get if is_dense else v.vdbc_render_stats_get)(target, stream=stream)
+        return e0.elapsed_time(e1), img.clone(), int(st.lookups)
+
+    ref_ms, ref, ref_lk = timed_render(dense, True)
+
+    def entry(g, name):
+        ms, im, lk = timed_render(g)
+        mse = float(((im[..., :3].double() - ref[..., :3].double()) ** 2).mean())
+        info = g.info
+        return {"total_bytes": int(info.total_bytes), "volume_psnr_db": vpsnr(g),
+                "image_psnr_vs_dense_db": round(10 * math.log10(1.0 / max(mse, 1e-30)), 3),
+                "render_ms": round(ms, 3), "mpaths_per_s": round(paths / (ms * 1e-3) / 1e6, 3),
+                "lookups": lk}
+
+    res = {"workload": "cloud994x676x1225_learned_vs_vdb_r10_pt1920x1080_32spp",
+           "zero_fraction": round(float((vol == 0).float().mean()), 4),
+           "byte_budget": budget,
+           "dense_texture": {"render_ms": round(ref_ms, 3), "mpaths_per_s": round(paths / (ref_ms * 1e-3) / 1e6, 3),
+                             "lookups": ref_lk},
+           "vdb_fp32_r10": entry(vdb32, "vdb32"), "vdb_fp16_r10": entry(vdb16, "vdb16")}
+    le = entry(learned, "learned")
+    le.update({"n_neural": int(learned.info.n_neural), "n_raw": int(learned.info.n_leaves),
+               "train_s": round(train_s, 3), "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+               "training": dict(w["learn"]), "source_leaves": int(full.info.n_leaves)})
+    res["learned"] = le
+    for g in (full, vdb32, vdb16, learned):
+        g.close()
+    dense.close()
+    del vol
+    torch.cuda.empty_cache()
+    return res
 
 
 class CpuOracle:
