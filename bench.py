@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-volume batched section")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-decoder section")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--profile-learned", action="store_true",
+                    help="ncu capture case of the learned codec: 50 training steps and two 512^2 x 16 spp "
+                         "renders of a learned 512^3 medium")
     ap.add_argument("--profile-case", action="store_true",
                     help="the ncu capture case: the same workload at a 512x512 image, two renders")
     return ap.parse_args()
@@ -584,9 +587,40 @@ def run_profile_case():
                       "paths": int(st.paths)}))
 
 
+def run_profile_learned():
+    """The capture case of the learned codec: the 512^3 medium's every
+    non-empty brick turned into a learned grid held to the bytes of VDB 1:10
+    (50 training steps, 64 samples per leaf), rendered twice at 512x512 x 16 spp."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2504_04564_gb300 as v
+    import volgen
+    from volgen import scenes
+
+    w = scenes.TURBULENCE_512
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 512, 512))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
+    full = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"])
+    budget = int(v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"]).info.total_bytes)
+    g, losses = v.vdbc_learn(full, steps=50, samples_per_leaf=64, lr=2e-3, lr_latent=2e-2, max_bytes=budget, seed=1)
+    img = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        v.vdbc_render(g, cam, med, w["spp"], 2024, img)
+    torch.cuda.synchronize()
+    st = v.vdbc_render_stats_get(g)
+    print(json.dumps({"profile_case": "turbulence512_learned_pt512sq_16spp", "lookups": int(st.lookups),
+                      "paths": int(st.paths), "n_neural": int(g.info.n_neural), "n_raw": int(g.info.n_leaves),
+                      "loss_last": float(losses[-1])}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_case:
+    if a.profile_learned:
+        run_profile_learned()
+    elif a.profile_case:
         run_profile_case()
     elif a.impl == "reference":
         run_reference(a)
