@@ -65,6 +65,19 @@ def dist_env():
     return rank, world, local
 
 
+def replica_throughput(total_ms, paths_per_step, steps, world, device=None):
+    """Whole-job throughput of N independent replicas: the timed region is the
+    max over ranks (one all-reduce of the timing, no data-path collective) and
+    the value counts every rank's paths.  Returns (max_ms, Mpaths/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * paths_per_step * steps / (total_ms * 1e-3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -234,13 +247,8 @@ def run_vdbc(args):
     info = grids[-1].info
     for g in grids:
         g.close()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = replica_throughput(total_ms, paths_per_step, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * paths_per_step * args.steps / (total_ms * 1e-3) / 1e6
     render_ms = sum(ren_ms) / len(ren_ms)
     lookups = int(stats.lookups)
     vdb_img = img.clone()
