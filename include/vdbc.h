@@ -65,7 +65,8 @@ enum { VDBC_FP32 = 0, VDBC_FP16 = 1, VDBC_FP8 = 2, VDBC_LEARNED = 3 };
 
 enum { VDBC_CAM_ORTHO = 0, VDBC_CAM_PINHOLE = 1 };
 enum { VDBC_MODE_EA = 0,   /* emission-absorption ray marching (fixed step) */
-       VDBC_MODE_PT = 1    /* delta tracking, ratio-tracked light, scattering */ };
+       VDBC_MODE_PT = 1,   /* delta tracking, ratio-tracked light, scattering */
+       VDBC_MODE_ISO = 2   /* implicit ISO surface, normals as colour (Section 5's ZFP comparison) */ };
 enum { VDBC_FILTER_TEXTURE = 0,  /* plain form: 3D CUDA texture, hardware trilinear */
        VDBC_FILTER_LINEAR = 1    /* plain form: linear device array, software trilinear */ };
 
@@ -118,16 +119,16 @@ typedef struct {
 } vdbc_camera;
 
 typedef struct {
-    int32_t mode;              /* VDBC_MODE_EA or VDBC_MODE_PT */
+    int32_t mode;              /* VDBC_MODE_EA, VDBC_MODE_PT or VDBC_MODE_ISO */
     int32_t tf_n;              /* EA: number of RGBA entries of the transfer function, 2..2048 */
     const float* tf_rgba;      /* EA: host pointer to tf_n RGBA float entries; alpha is
                                   the extinction per voxel length */
-    float   step;              /* EA: step in voxels (> 0) */
+    float   step;              /* EA, ISO: step in voxels (> 0) */
     float   density_scale;     /* PT: extinction per world unit at density 1 */
     float   albedo;            /* PT: single-scattering albedo in [0,1] */
     float   g;                 /* PT: Henyey-Greenstein asymmetry in (-1,1) */
     int32_t max_bounces;       /* PT: scattering events per path, 1..4096 */
-    int32_t reserved;
+    float   iso;               /* ISO: the surface value (finite) */
     float   sun_dir[3];        /* PT: unit direction toward the directional light */
     float   sun_rad[3];        /* PT: its irradiance (RGB) */
     float   env_rad[3];        /* PT: constant environment radiance (RGB) */
@@ -200,6 +201,15 @@ void        vdbc_grid_free(vdbc_grid* grid);
  *   mode PT: spp paths per pixel, Philox counter (pixel, sample, call,
  *            stream) keyed by seed; light from a directional source by ratio
  *            tracking plus a constant environment.
+ *   mode ISO: the implicit ISO-surface marcher the paper uses for its ZFP
+ *            comparison (Section 5, fig:zfp-comparison-iso), which it names
+ *            without details: one ray per pixel centre, samples t_k = t_in +
+ *            (k + 1/2) step; the first change of (f >= iso) between
+ *            consecutive samples is halved 12 times and shaded with its
+ *            normal n = -grad f / |grad f| (central differences, 1/2 voxel)
+ *            as rgb = (n + 1) / 2, alpha 1; rays without one give 0.
+ *            Macrocells whose [min, max] excludes iso are crossed without
+ *            lookups (the result is the plain march's); spp must be 1.
  *   rgba_out width*height*4 floats (RGBA per pixel, row 0 at the top),
  *            device pointer if out_on_device else host (the call then waits).
  * Errors: INVALID_ARG; OOM; CUDA; TIMEOUT; DEVICE_FLAG.

@@ -26,7 +26,7 @@ SOURCES = ["philox.c", "encode.c", "render.c", "mlp.c"]
 F1, F2, F3 = 1, 2, 3
 FP32, FP16, FP8 = 0, 1, 2
 CAM_ORTHO, CAM_PINHOLE = 0, 1
-MODE_EA, MODE_PT = 0, 1
+MODE_EA, MODE_PT, MODE_ISO = 0, 1, 2
 
 c_i64p = ctypes.POINTER(ctypes.c_int64)
 
@@ -58,7 +58,7 @@ class Medium(ctypes.Structure):
                 ("density_scale", ctypes.c_double), ("albedo", ctypes.c_double),
                 ("g", ctypes.c_double), ("max_bounces", ctypes.c_int32),
                 ("macrocell", ctypes.c_int32), ("sun_dir", ctypes.c_double * 3),
-                ("sun_rad", ctypes.c_double * 3), ("env_rad", ctypes.c_double * 3)]
+                ("sun_rad", ctypes.c_double * 3), ("env_rad", ctypes.c_double * 3), ("iso", ctypes.c_double)]
 
 
 _lib = None
@@ -278,7 +278,7 @@ def make_camera(kind, width, height, eye, look, up, fovy_or_height) -> Camera:
 
 
 def make_medium(mode, tf=None, step=0.5, density_scale=1.0, albedo=0.9, g=0.0, max_bounces=1,
-                macrocell=8, sun_dir=(0, 0, 1), sun_rad=(0, 0, 0), env_rad=(0, 0, 0)):
+                macrocell=8, sun_dir=(0, 0, 1), sun_rad=(0, 0, 0), env_rad=(0, 0, 0), iso=0.5):
     m = Medium()
     m.mode = int(mode)
     keep = None
@@ -288,6 +288,7 @@ def make_medium(mode, tf=None, step=0.5, density_scale=1.0, albedo=0.9, g=0.0, m
         m.tf_rgba = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     m.step, m.density_scale, m.albedo, m.g = float(step), float(density_scale), float(albedo), float(g)
     m.max_bounces, m.macrocell = int(max_bounces), int(macrocell)
+    m.iso = float(iso)
     for a in range(3):
         m.sun_dir[a], m.sun_rad[a], m.env_rad[a] = float(sun_dir[a]), float(sun_rad[a]), float(env_rad[a])
     m._keep = keep

@@ -63,7 +63,8 @@ void     or_tree_free(or_tree* t);
 
 /* ---------------- renderer: Section 4 plus the project's extensions ----- */
 enum { OR_CAM_ORTHO = 0, OR_CAM_PINHOLE = 1 };
-enum { OR_MODE_EA = 0, OR_MODE_PT = 1 };
+enum { OR_MODE_EA = 0, OR_MODE_PT = 1, OR_MODE_ISO = 2 };
+enum { OR_ISO_BISECT = 12 };
 
 typedef struct {
     int32_t kind;
@@ -82,6 +83,7 @@ typedef struct {
     int32_t max_bounces;
     int32_t macrocell;        /* macrocell edge in voxels */
     double  sun_dir[3], sun_rad[3], env_rad[3];
+    double  iso;              /* ISO: the surface value */
 } or_medium;
 
 double or_trilinear(const float* d, const int64_t dims[3], const double p[3]);

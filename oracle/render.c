@@ -283,6 +283,55 @@ static void ea_pixel(const float* d, const int64_t dims[3], const or_camera* cam
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
 }
 
+/* ---- implicit ISO surface (the ray marcher of Section 5's ZFP comparison,
+ * Fig. fig:zfp-comparison-iso; the paper names it only) ---------------------
+ * The samples are those of the EA marcher, t_k = t_in + (k + 1/2) step; the
+ * surface is the first change of inside = (f >= iso) between consecutive
+ * samples, located by OR_ISO_BISECT halvings of that step, and shaded with
+ * its normal n = -grad f / |grad f| (central differences, h = 1/2 voxel) as
+ * rgb = (n + 1) / 2, alpha 1.  A ray without a change gives (0, 0, 0, 0). */
+static void iso_pixel(const float* d, const int64_t dims[3], const or_camera* cam,
+                      const or_medium* m, int64_t px, int64_t py, double out[4])
+{
+    double o[3], dir[3], tin, tout;
+    or_camera_ray(cam, dims, px, py, 0.5, 0.5, o, dir);
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    if (!or_clip_box(dims, o, dir, &tin, &tout)) return;
+    double dt = m->step, t_prev = 0.0;
+    int prev = -1;
+    for (int64_t k = 0;; ++k) {
+        double t = tin + ((double)k + 0.5) * dt;
+        if (t >= tout) return;
+        double p[3] = {o[0] + t * dir[0], o[1] + t * dir[1], o[2] + t * dir[2]};
+        int in = or_trilinear(d, dims, p) >= m->iso;
+        if (prev >= 0 && in != prev) {
+            double a = t_prev, b = t;     /* inside(a) = prev, inside(b) = in */
+            for (int j = 0; j < OR_ISO_BISECT; ++j) {
+                double mid = 0.5 * (a + b);
+                double q[3] = {o[0] + mid * dir[0], o[1] + mid * dir[1], o[2] + mid * dir[2]};
+                if ((or_trilinear(d, dims, q) >= m->iso) == prev) a = mid; else b = mid;
+            }
+            double th = 0.5 * (a + b);
+            double h[3] = {o[0] + th * dir[0], o[1] + th * dir[1], o[2] + th * dir[2]};
+            double g[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                double pp[3] = {h[0], h[1], h[2]}, pm[3] = {h[0], h[1], h[2]};
+                pp[ax] += 0.5;
+                pm[ax] -= 0.5;
+                g[ax] = or_trilinear(d, dims, pp) - or_trilinear(d, dims, pm);
+            }
+            double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            double n[3];
+            for (int ax = 0; ax < 3; ++ax) n[ax] = gl > 0.0 ? -g[ax] / gl : -dir[ax];
+            for (int c = 0; c < 3; ++c) out[c] = 0.5 * (n[c] + 1.0);
+            out[3] = 1.0;
+            return;
+        }
+        prev = in;
+        t_prev = t;
+    }
+}
+
 /* ---- tracking ----------------------------------------------------------- */
 typedef struct {
     const float* d;
@@ -460,6 +509,10 @@ void or_render_pixels(const float* d, const int64_t dims[3], const float* cell_m
         double* out = out_rgba + 4 * n;
         if (m->mode == OR_MODE_EA) {
             ea_pixel(d, dims, cam, m, px, py, out);
+            continue;
+        }
+        if (m->mode == OR_MODE_ISO) {
+            iso_pixel(d, dims, cam, m, px, py, out);
             continue;
         }
         double acc[3] = {0, 0, 0};

@@ -24,7 +24,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_FORMAT, ERR_TIMEOUT, ERR_DEVICE_FLAG
 F1, F2, F3 = 1, 2, 3
 FP32, FP16, FP8, LEARNED = 0, 1, 2, 3
 CAM_ORTHO, CAM_PINHOLE = 0, 1
-MODE_EA, MODE_PT = 0, 1
+MODE_EA, MODE_PT, MODE_ISO = 0, 1, 2
 FILTER_TEXTURE, FILTER_LINEAR = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "FORMAT", 5: "TIMEOUT",
@@ -72,7 +72,7 @@ class Camera(ctypes.Structure):
 class Medium(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tf_n", ctypes.c_int32), ("tf_rgba", ctypes.c_void_p),
                 ("step", ctypes.c_float), ("density_scale", ctypes.c_float), ("albedo", ctypes.c_float),
-                ("g", ctypes.c_float), ("max_bounces", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("g", ctypes.c_float), ("max_bounces", ctypes.c_int32), ("iso", ctypes.c_float),
                 ("sun_dir", ctypes.c_float * 3), ("sun_rad", ctypes.c_float * 3), ("env_rad", ctypes.c_float * 3)]
 
 
@@ -216,7 +216,7 @@ def make_camera(kind, width, height, eye, look, up, fovy_or_height) -> Camera:
 
 
 def make_medium(mode, tf=None, step=0.5, density_scale=1.0, albedo=0.9, g=0.0, max_bounces=1,
-                sun_dir=(0, 0, 1), sun_rad=(0, 0, 0), env_rad=(0, 0, 0)) -> Medium:
+                sun_dir=(0, 0, 1), sun_rad=(0, 0, 0), env_rad=(0, 0, 0), iso=0.5) -> Medium:
     m = Medium()
     m.mode = int(mode)
     m._tf = None
@@ -226,6 +226,7 @@ def make_medium(mode, tf=None, step=0.5, density_scale=1.0, albedo=0.9, g=0.0, m
         m.tf_rgba = m._tf.ctypes.data
     m.step, m.density_scale, m.albedo, m.g = float(step), float(density_scale), float(albedo), float(g)
     m.max_bounces = int(max_bounces)
+    m.iso = float(iso)
     for a in range(3):
         m.sun_dir[a], m.sun_rad[a], m.env_rad[a] = float(sun_dir[a]), float(sun_rad[a]), float(env_rad[a])
     return m

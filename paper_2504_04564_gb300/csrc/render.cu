@@ -52,6 +52,7 @@ struct MedDev {
     float albedo, g;
     int max_bounces;
     float3 sun_dir, sun_rad, env_rad;
+    float iso;
 };
 
 struct Majorants {
@@ -59,6 +60,7 @@ struct Majorants {
     int mc;
     int mx, my, mz;
     int nx, ny, nz;
+    const float* mcmin;   // read by the ISO marcher's interval test only
 };
 
 // coarse occupancy level over kCoarse^3 macrocells: a ray crosses an empty
@@ -833,6 +835,138 @@ __global__ void __launch_bounds__(128) k_ea_collective(S smp, Majorants m, CamDe
     flush_stats(st, w, paths);
 }
 
+// ---------------------------------------------------------------- ISO surface
+// The implicit ISO-surface marcher the paper uses for its ZFP comparison
+// (Section 5), which it names without details.  Samples t_k = t_in + (k + 1/2)
+// step as the EA marcher, inside = (f >= iso); the first change of inside
+// between consecutive samples is halved kIsoBisect times and shaded with its
+// normal n = -grad f / |grad f| (central differences, 1/2 voxel) as
+// rgb = (n + 1) / 2, alpha 1.  Interval skipping: in a macrocell whose dilated
+// [min, max] (which bounds the trilinear field over the cell) excludes iso,
+// every sample has a known inside, so the march crosses the cell without a
+// lookup and lands on the sample before its exit; the result is the plain
+// march's.  Each loop iteration makes at most one lookup per lane, at one
+// program point, so a warp-collective sampler works unchanged.
+constexpr int kIsoBisect = 12;
+enum { kIsoMarch = 0, kIsoHalve = 1, kIsoNormal = 2, kIsoDone = 3 };
+
+// inside of every point of macrocell `id`: 1, 0, or -1 when iso is inside its range
+__device__ __forceinline__ int iso_known(const Majorants& m, int id, float iso)
+{
+    if (__ldg(m.mcmin + id) >= iso) return 1;
+    if (__ldg(m.mcmax + id) < iso) return 0;
+    return -1;
+}
+
+template <class S>
+__global__ void __launch_bounds__(128) k_iso(S smp, Majorants m, CamDev cam, MedDev med, float4* __restrict__ out,
+                                             DevStats* __restrict__ st)
+{
+    const int npix = cam.w * cam.h;
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    Walk w{};
+    Accessor acc;
+    acc.reset();
+    float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
+    float tin = 0.f, tout = 0.f;
+    int phase = kIsoDone;
+    if (pix < npix) {
+        camera_ray(cam, pix % cam.w, pix / cam.w, 0.5f, 0.5f, o, d);
+        if (clip_box(m, o, d, tin, tout)) phase = kIsoMarch;
+    }
+    const float dt = med.step, iso = med.iso;
+    const long long kmax = phase == kIsoMarch ? (long long)((tout - tin) / dt) + 2 : 0;
+    Dda dda;
+    int cell_id = 0, known = -1;
+    float texit = 0.f;
+    bool have_cell = false;
+    if (phase == kIsoMarch) {
+        dda.init(m, o, d, tin, tout);
+        have_cell = dda.cell(m, cell_id, texit);
+        if (have_cell) known = iso_known(m, cell_id, iso);
+    }
+    int guard = m.mx + m.my + m.mz + 8;      // DDA cells a ray may cross
+    long long k = 0;
+    int prev = -1, halvings = 0, q = 0;
+    float t = 0.f, t_prev = 0.f, a = 0.f, b = 0.f, th = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    float4 color = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (;;) {
+        bool look = false;
+        float3 p = o;
+        if (phase == kIsoMarch) {
+            for (;;) {
+                if (k >= kmax) { phase = kIsoDone; break; }
+                t = tin + ((float)k + 0.5f) * dt;
+                if (t >= tout) { phase = kIsoDone; break; }
+                while (have_cell && t >= texit) {
+                    if (--guard < 0) { w.flags |= kErrDdaSteps; have_cell = false; break; }
+                    dda.advance(m, o, texit);
+                    have_cell = dda.cell(m, cell_id, texit);
+                    if (have_cell) known = iso_known(m, cell_id, iso);
+                }
+                if (!have_cell) known = -1;      // past the cell grid by rounding: look the sample up
+                if (known < 0) {
+                    look = true;
+                    p = f3(o.x + t * d.x, o.y + t * d.y, o.z + t * d.z);
+                    break;
+                }
+                if (prev >= 0 && known != prev) { a = t_prev; b = t; halvings = 0; phase = kIsoHalve; break; }
+                // the cell's later samples share this inside: go on from the last one before its exit
+                prev = known;
+                t_prev = t;
+                long long kn = (long long)floorf((texit - tin) / dt - 0.5f);
+                if (kn > k + 1) {
+                    k = kn;
+                    t_prev = tin + ((float)(kn - 1) + 0.5f) * dt;
+                } else {
+                    ++k;
+                }
+            }
+        }
+        if (phase == kIsoHalve) {
+            const float mid = 0.5f * (a + b);
+            p = f3(o.x + mid * d.x, o.y + mid * d.y, o.z + mid * d.z);
+            look = true;
+        } else if (phase == kIsoNormal) {
+            p = f3(o.x + th * d.x, o.y + th * d.y, o.z + th * d.z);
+            const float h = (q & 1) ? -0.5f : 0.5f;
+            if (q < 2) p.x += h; else if (q < 4) p.y += h; else p.z += h;
+            look = true;
+        }
+        float f = 0.0f;
+        if constexpr (S::kCollective) {
+            __syncwarp();
+            f = smp.collective(look, p.x, p.y, p.z, acc);
+        } else {
+            if (look) f = smp(p.x, p.y, p.z, acc);
+        }
+        if (look) {
+            ++w.lookups;
+            const int in = f >= iso ? 1 : 0;
+            if (phase == kIsoMarch) {
+                if (prev >= 0 && in != prev) { a = t_prev; b = t; halvings = 0; phase = kIsoHalve; }
+                else { prev = in; t_prev = t; ++k; }
+            } else if (phase == kIsoHalve) {
+                const float mid = 0.5f * (a + b);
+                if (in == prev) a = mid; else b = mid;
+                if (++halvings == kIsoBisect) { th = 0.5f * (a + b); q = 0; phase = kIsoNormal; }
+            } else {
+                const float sg = (q & 1) ? -f : f;
+                if (q < 2) gx += sg; else if (q < 4) gy += sg; else gz += sg;
+                if (++q == 6) {
+                    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+                    float3 n = gl > 0.0f ? f3(-gx / gl, -gy / gl, -gz / gl) : f3(-d.x, -d.y, -d.z);
+                    color = make_float4(0.5f * (n.x + 1.0f), 0.5f * (n.y + 1.0f), 0.5f * (n.z + 1.0f), 1.0f);
+                    phase = kIsoDone;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, phase == kIsoDone)) break;
+    }
+    if (pix < npix) out[pix] = color;
+    flush_stats(st, w, pix < npix ? 1ull : 0ull);
+}
+
 unsigned blocks_for(long long n, int t) { return (unsigned)std::max<long long>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -923,6 +1057,12 @@ vdbc_status make_med(const vdbc_medium* m, const int dims[3], int spp, cudaStrea
         d.sun_dir = make_float3((float)(m->sun_dir[0] / sl), (float)(m->sun_dir[1] / sl), (float)(m->sun_dir[2] / sl));
         d.sun_rad = make_float3(m->sun_rad[0], m->sun_rad[1], m->sun_rad[2]);
         d.env_rad = make_float3(m->env_rad[0], m->env_rad[1], m->env_rad[2]);
+    } else if (m->mode == VDBC_MODE_ISO) {
+        if (!(m->step > 0.0f)) return set_error(VDBC_ERR_INVALID_ARG, "ISO step must be > 0");
+        if (!std::isfinite(m->iso)) return set_error(VDBC_ERR_INVALID_ARG, "ISO value must be finite");
+        if (spp != 1) return set_error(VDBC_ERR_INVALID_ARG, "ISO renders 1 sample per pixel");
+        d.step = m->step;
+        d.iso = m->iso;
     } else {
         return set_error(VDBC_ERR_INVALID_ARG, "medium mode %d unknown", m->mode);
     }
@@ -1008,6 +1148,12 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
 {
     long long npix = (long long)cam.w * cam.h;
     VDBC_CUDA(cudaMemsetAsync(stats, 0, sizeof(DevStats), s));
+    if (med.mode == VDBC_MODE_ISO) {
+        if (!mj.mcmin) return set_error(VDBC_ERR_INVALID_ARG, "ISO needs the macrocell minima");
+        KLAUNCH(k_iso<S><<<blocks_for(npix, 128), 128, 0, s>>>(smp, mj, cam, med, out, stats));
+        VDBC_CUDA(cudaGetLastError());
+        return VDBC_OK;
+    }
     if (med.mode == VDBC_MODE_EA) {
         if constexpr (S::kCollective)
             KLAUNCH(k_ea_collective<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out,
@@ -1119,7 +1265,7 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
     clear_error();
     if (!grid) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_render: grid is null");
     const GridView& g = grid->view;
-    Majorants mj{g.mcmax, g.mc, g.mx, g.my, g.mz, g.nx, g.ny, g.nz};
+    Majorants mj{g.mcmax, g.mc, g.mx, g.my, g.mz, g.nx, g.ny, g.nz, g.mcmin};
     if (g.payload == VDBC_LEARNED)
         return render_common(LearnedSampler{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                              out_on_device, stream);
@@ -1236,7 +1382,7 @@ extern "C" vdbc_status vdbc_render_dense(const vdbc_volume* vol, const vdbc_came
     clear_error();
     if (!vol) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_render_dense: volume is null");
     Majorants mj{vol->mcmax, vol->macrocell, vol->mcdims[0], vol->mcdims[1], vol->mcdims[2],
-                 vol->dims[0], vol->dims[1], vol->dims[2]};
+                 vol->dims[0], vol->dims[1], vol->dims[2], vol->mcmin};
     if (vol->filter == VDBC_FILTER_LINEAR) {
         LinearSampler smp{vol->linear, vol->dims[0], vol->dims[1], vol->dims[2]};
         return render_common(smp, mj, vol->dims, vol->stats, camera, medium, spp, seed, rgba_out, out_on_device, stream);

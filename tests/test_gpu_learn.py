@@ -196,7 +196,7 @@ def test_learned_grid_save_load(env, tmp_path):
     assert np.array_equal(v.vdbc_learn_get_params(back), v.vdbc_learn_get_params(learned))
 
 
-@pytest.mark.parametrize("mode", ["pt", "ea"])
+@pytest.mark.parametrize("mode", ["pt", "ea", "iso"])
 def test_learned_render_equals_dense_render_of_its_decode(env, mode):
     """The collective lookups decode every neural corner exactly as the decode
     entry point does, so a learned-grid render equals the linear plain-form
@@ -210,8 +210,11 @@ def test_learned_render_equals_dense_render_of_its_decode(env, mode):
     if mode == "pt":
         med = v.make_medium(v.MODE_PT, **sc.pt_medium_args(density_scale=40.0))
         spp = 8
-    else:
+    elif mode == "ea":
         med = v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf(), step=0.5)
+        spp = 1
+    else:
+        med = v.make_medium(v.MODE_ISO, step=0.5, iso=0.3)
         spp = 1
     a = torch.zeros(28, 36, 4, device=env["dev"])
     b = torch.zeros(28, 36, 4, device=env["dev"])

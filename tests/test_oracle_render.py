@@ -295,3 +295,90 @@ def test_image_independent_of_macrocell_size(orc, vg):
     b = orc.render_image(vol, mG, cam, medG, 64, 11, threads=4)[..., 0]
     diff = (a - b).ravel()
     assert abs(diff.mean()) < 4 * diff.std() / math.sqrt(diff.size)
+
+
+# ------------------------------------------------------------------ ISO surface marcher
+def _iso_image(orc, vol, cam_args, iso=0.5, step=0.5):
+    cam = orc.make_camera(*cam_args)
+    med = orc.make_medium(orc.MODE_ISO, step=step, iso=iso)
+    return orc.render_image(np.ascontiguousarray(vol, np.float32), None, cam, med, 1, 0)
+
+
+def _ortho(dims, w, h):
+    from volgen import scenes
+    return scenes.ortho_plus_z(dims, w, h)
+
+
+@pytest.mark.parametrize("grad", [(0.0, 0.0, 1.0), (1.0, 2.0, 3.0), (-2.0, 0.5, 1.5)])
+def test_iso_linear_field_normals_are_exact(orc, grad):
+    """Trilinear reconstruction of a linear field is the field, so the
+    iso-surface is a plane and every hit pixel shows -grad/|grad|."""
+    dims = (24, 20, 28)
+    z, y, x = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    g = np.asarray(grad)
+    vol = (g[0] * x + g[1] * y + g[2] * z) / 40.0 + 0.5 - (g[0] * 11.5 + g[1] * 9.5 + g[2] * 13.5) / 40.0
+    img = _iso_image(orc, vol, _ortho(dims, 20, 18))
+    n = -g / np.linalg.norm(g)
+    hit = img[..., 3] == 1.0
+    assert hit.mean() > 0.5
+    want = 0.5 * (n + 1.0)
+    # away from the clamped border the central differences see the plane exactly
+    core = img[4:-4, 4:-4]
+    core_hit = core[..., 3] == 1.0
+    assert core_hit.any()
+    assert np.allclose(core[core_hit][:, :3], want, atol=1e-9)
+    assert np.all(img[~hit] == 0.0)
+
+
+def test_iso_constant_fields_miss(orc):
+    dims = (16, 16, 16)
+    for value in (0.2, 0.9):    # all outside, and all inside: no change along any ray
+        img = _iso_image(orc, np.full(dims[::-1], value, np.float32), _ortho(dims, 12, 12))
+        assert np.all(img == 0.0)
+
+
+def test_iso_takes_the_first_of_two_slabs(orc):
+    """Two slabs along z; +z rays meet the near face of the first one, whose
+    normal is -z; a ray reversed along -z meets the far slab's back face."""
+    dims = (16, 16, 48)
+    vol = np.zeros(dims[::-1], np.float32)
+    vol[10:18] = 1.0
+    vol[30:40] = 1.0
+    img = _iso_image(orc, vol, _ortho(dims, 10, 10))
+    assert np.all(img[..., 3] == 1.0)
+    assert np.allclose(img[..., :3], [0.5, 0.5, 0.0], atol=1e-12)
+    from volgen import scenes
+    ex, ey, ez = scenes.world_extent(dims)
+    back = (0, 10, 10, (0.5 * ex, 0.5 * ey, ez + 1.0), (0.5 * ex, 0.5 * ey, ez), (0, 1, 0), ey)
+    img = _iso_image(orc, vol, back)
+    assert np.allclose(img[..., :3], [0.5, 0.5, 1.0], atol=1e-12)
+
+
+def test_iso_sphere_matches_the_analytic_surface(orc):
+    """f = clamp(1 - |p - c| / R): the 0.5 surface is the sphere of radius R/2;
+    the shaded normal of each hit pixel follows the analytic intersection."""
+    dims = (48, 48, 48)
+    c, R = np.array([23.5, 23.5, 23.5]), 36.0
+    z, y, x = np.meshgrid(np.arange(48), np.arange(48), np.arange(48), indexing="ij")
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    vol = np.clip(1.0 - r / R, 0.0, 1.0).astype(np.float32)
+    cam_args = _ortho(dims, 24, 24)
+    img = _iso_image(orc, vol, cam_args, step=0.25)
+    cam = orc.make_camera(*cam_args)
+    rs = R / 2
+    checked = 0
+    for py in range(24):
+        for px in range(24):
+            o, d = orc.camera_ray(cam, dims, px, py)
+            oc = o - c
+            b = np.dot(oc, d)
+            disc = b * b - (np.dot(oc, oc) - rs * rs)
+            if disc < 4.0:          # grazing rays: leave them out
+                assert img[py, px, 3] == 0.0 or disc > 0
+                continue
+            t = -b - np.sqrt(disc)
+            n = (o + t * d - c) / rs
+            assert img[py, px, 3] == 1.0
+            assert np.max(np.abs(img[py, px, :3] - 0.5 * (n + 1))) < 0.03
+            checked += 1
+    assert checked > 100
