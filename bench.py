@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-volume batched section")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-decoder section")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--study", choices=["worstcase", "metrics", "hdda", "fullscale"],
+                    help="one of the studies beside the benchmark (one JSON line each): lossless dense-noise "
+                         "sizes 32^3..2048^3 vs the texture; f1/f2/f3 x rate volume PSNR; hierarchical vs "
+                         "uniform DDA; the 1987x1351x2449 cloud at five rates")
     ap.add_argument("--profile-learned", action="store_true",
                     help="ncu capture case of the learned codec: 50 training steps and two 512^2 x 16 spp "
                          "renders of a learned 512^3 medium")
@@ -624,9 +628,179 @@ def run_profile_learned():
                       "loss_last": float(losses[-1])}))
 
 
+def _study_env():
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2504_04564_gb300 as v
+    import volgen
+    from volgen import scenes
+    return torch, v, volgen, scenes
+
+
+def _timed_render(torch, v, target, cam, med, spp, img, dense=False, reps=1):
+    fn = v.vdbc_render_dense if dense else v.vdbc_render
+    fn(target, cam, med, spp, 1, img)                      # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn(target, cam, med, spp, 1, img)
+    e1.record()
+    torch.cuda.synchronize()
+    st = (v.vdbc_volume_render_stats_get if dense else v.vdbc_render_stats_get)(target)
+    return e0.elapsed_time(e1) / reps, int(st.lookups)
+
+
+def study_worstcase():
+    """The paper's worst case (tab:worstcase): dense noise in (0, 1] that leaves
+    no brick empty, encoded losslessly (1:1) at 32^3..2048^3; grid bytes
+    against the dense bytes, and path-tracing throughput of the grid against
+    the dense texture (1024^2 x 4 spp, the benchmark's medium and macrocells)."""
+    torch, v, volgen, scenes = _study_env()
+    rows = []
+    for n in (32, 64, 128, 256, 512, 1024, 2048):
+        dims = (n, n, n)
+        vol = volgen.generate_torch(volgen.make_params("noise", dims, 7))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = v.vdbc_encode(vol, 1.0, macrocell=scenes.TURBULENCE_512["macrocell"])
+        torch.cuda.synchronize()
+        enc_ms = (time.perf_counter() - t0) * 1e3
+        dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, scenes.TURBULENCE_512["macrocell"])
+        cam = v.make_camera(*scenes.pinhole_orbit(dims, 1024, 1024))
+        med = v.make_medium(v.MODE_PT, **scenes.pt_medium_args())
+        img = torch.empty((1024, 1024, 4), dtype=torch.float32, device="cuda")
+        paths = 1024 * 1024 * 4
+        ms_g, lk_g = _timed_render(torch, v, g, cam, med, 4, img)
+        ms_d, lk_d = _timed_render(torch, v, dense, cam, med, 4, img, dense=True)
+        info = g.info
+        dense_bytes = n * n * n * 4
+        rows.append({"n": n, "dense_bytes": dense_bytes, "grid_bytes": int(info.total_bytes),
+                     "overhead_pct": round(100.0 * (int(info.total_bytes) / dense_bytes - 1.0), 2),
+                     "n_leaves": int(info.n_leaves), "n_tiles": int(info.n_tiles), "encode_ms": round(enc_ms, 2),
+                     "grid_mpaths_per_s": round(paths / (ms_g * 1e-3) / 1e6, 2),
+                     "texture_mpaths_per_s": round(paths / (ms_d * 1e-3) / 1e6, 2),
+                     "grid_over_texture": round(ms_d / ms_g, 4), "lookups_grid": lk_g, "lookups_texture": lk_d})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        g.close()
+        dense.close()
+        del vol
+        torch.cuda.empty_cache()
+    return {"study": "worstcase_dense_noise_lossless",
+            "render": "pt 1024x1024x4spp, density 20/unit, %d^3 cells" % scenes.TURBULENCE_512["macrocell"],
+            "rows": rows}
+
+
+def study_metrics():
+    """f1/f2/f3 x rate (Fig. fig:distance): volume PSNR (peak 1) of the decoded
+    grid against the input, on the 512^3 medium and the 994x676x1225 cloud."""
+    torch, v, volgen, scenes = _study_env()
+    out = {"study": "metric_rate_psnr", "rates": [1.0, 1.33, 2.0, 4.0, 6.0, 10.0, 20.0, 50.0], "volumes": {}}
+    for name, kind, dims in (("turbulence512", "turbulence", (512, 512, 512)), ("cloud994", "cloud", (994, 676, 1225))):
+        vol = volgen.generate_torch(volgen.make_params(kind, dims, 0))
+        dec = torch.empty_like(vol)
+        res = {}
+        for metric in (v.F1, v.F2, v.F3):
+            curve = []
+            for r in out["rates"]:
+                g = v.vdbc_encode(vol, r, metric=metric)
+                v.vdbc_grid_decode(g, dec)
+                mse = float(((dec.double() - vol.double()) ** 2).mean())
+                curve.append(round(10 * math.log10(1.0 / mse), 3) if mse > 0 else None)
+                g.close()
+            res["f%d" % metric] = curve
+        out["volumes"][name] = res
+        del vol, dec
+        torch.cuda.empty_cache()
+    return out
+
+
+def study_hdda():
+    """Hierarchical against uniform DDA (Section 4 found diminishing returns):
+    the benchmark's frame with the coarse level (8^3 blocks of macrocells; at
+    16^3 cells a block is a lower node's 128^3 voxels) on and off, per
+    macrocell size.  (The renderer turns the level on for cells of at most 8
+    voxels; the study forces both settings.)"""
+    torch, v, volgen, scenes = _study_env()
+    w = scenes.TURBULENCE_512
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], w["width"], w["height"]))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    img = torch.empty((w["height"], w["width"], 4), dtype=torch.float32, device="cuda")
+    paths = w["width"] * w["height"] * w["spp"]
+    rows = []
+    for mc in (8, 16, 32, 48, 64):
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=mc)
+        for coarse in ("1", "0"):
+            os.environ["VDBC_PT_COARSE"] = coarse
+            ms, lk = _timed_render(torch, v, g, cam, med, w["spp"], img, reps=3)
+            rows.append({"macrocell": mc, "hierarchical": coarse == "1", "render_ms": round(ms, 3),
+                         "mpaths_per_s": round(paths / (ms * 1e-3) / 1e6, 2), "lookups": lk})
+        g.close()
+    os.environ.pop("VDBC_PT_COARSE", None)
+    return {"study": "hierarchical_vs_uniform_dda", "workload": WORKLOAD, "rows": rows}
+
+
+def study_fullscale():
+    """The 1987 x 1351 x 2449 cloud (26.3 GB) at 1:20, 1:10, 1:6, 1:5 and 1:4,
+    1920x1080 x 64 spp, up to 32 bounces, against the dense texture: Mpaths/s,
+    lookups/s, algorithmic lookup GB/s as a fraction of the measured HBM
+    bandwidth, volume PSNR and image PSNR against the texture render."""
+    torch, v, volgen, scenes = _study_env()
+    dims = (1987, 1351, 2449)
+    vol = volgen.generate_torch(volgen.make_params("cloud", dims, 0))
+    torch.cuda.synchronize()
+    W, H, spp = 1920, 1080, 64
+    cam = v.make_camera(*scenes.pinhole_orbit(dims, W, H))
+    med = v.make_medium(v.MODE_PT, **scenes.pt_medium_args(albedo=0.95, g=0.8, max_bounces=32))
+    img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    paths = W * H * spp
+    peak, _ = measured_peaks()
+    mc = scenes.CLOUD_994["macrocell"]
+    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, mc)
+    ms_d, lk_d = _timed_render(torch, v, dense, cam, med, spp, img, dense=True)
+    ref = img.clone()
+    dense.close()
+    rows = []
+    dec = None
+    for r in (20.0, 10.0, 6.0, 5.0, 4.0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = v.vdbc_encode(vol, r, macrocell=mc)
+        torch.cuda.synchronize()
+        enc_ms = (time.perf_counter() - t0) * 1e3
+        ms, lk = _timed_render(torch, v, g, cam, med, spp, img)
+        mse_i = float(((img[..., :3].double() - ref[..., :3].double()) ** 2).mean())
+        if dec is None:
+            dec = torch.empty_like(vol)
+        v.vdbc_grid_decode(g, dec)
+        mse_v = float(((dec.double() - vol.double()) ** 2).mean())
+        gbs = lk * 32 / (ms * 1e-3) / 1e9
+        info = g.info
+        rows.append({"rate": r, "payload_bytes": int(info.payload_bytes), "total_bytes": int(info.total_bytes),
+                     "encode_ms": round(enc_ms, 1), "render_ms": round(ms, 2),
+                     "mpaths_per_s": round(paths / (ms * 1e-3) / 1e6, 2), "glookups_per_s": round(lk / ms / 1e6, 3),
+                     "lookup_gbs": round(gbs, 1), "lookup_gbs_frac_of_measured_hbm": round(gbs / peak, 4),
+                     "volume_psnr_db": round(10 * math.log10(1.0 / max(mse_v, 1e-30)), 3),
+                     "image_psnr_vs_texture_db": round(10 * math.log10(1.0 / max(mse_i, 1e-30)), 3)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        g.close()
+    return {"study": "fullscale_cloud1987x1351x2449", "render": "pt 1920x1080x64spp, albedo 0.95, g 0.8, 32 bounces",
+            "texture": {"render_ms": round(ms_d, 2), "mpaths_per_s": round(paths / (ms_d * 1e-3) / 1e6, 2),
+                        "lookups": lk_d},
+            "zero_fraction": round(float((vol == 0).float().mean()), 4), "rows": rows}
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_learned:
+    if a.study:
+        import math
+        res = {"worstcase": study_worstcase, "metrics": study_metrics, "hdda": study_hdda,
+               "fullscale": study_fullscale}[a.study]()
+        print(json.dumps(res), flush=True)
+    elif a.profile_learned:
         run_profile_learned()
     elif a.profile_case:
         run_profile_case()
