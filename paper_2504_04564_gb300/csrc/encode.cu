@@ -25,6 +25,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "vdbc_host.h"
 
@@ -49,75 +51,64 @@ __device__ __forceinline__ void brick_coords(const Dims& d, int b, int& bx, int&
 // ---------------------------------------------------------------- pass 1
 constexpr int kPassThreads = 256;
 
-__global__ void __launch_bounds__(kPassThreads) k_pass1(const float* __restrict__ v, Dims d,
-                                                        uint32_t* __restrict__ lo_key,
-                                                        uint32_t* __restrict__ hi_key,
-                                                        unsigned long long* __restrict__ hist,
-                                                        int* __restrict__ nonfinite)
+// One block per 32^3 brick: the brick's min/max keys, and its counts of the
+// upper 16 bits added to the global level-1 histogram.  The counts are first
+// gathered in a block-private histogram of 16-bit bins in shared memory, two
+// bins per word (a brick has 32768 voxels, so a bin cannot overflow into its
+// neighbour); the lanes of a row that share a key add once (match_any), and
+// only the non-zero bins reach the global histogram.
+constexpr int kPass1Threads = 1024;
+constexpr size_t kPass1Smem = 32768 * sizeof(uint32_t);
+
+__global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict__ v, Dims d,
+                                                         uint32_t* __restrict__ lo_key,
+                                                         uint32_t* __restrict__ hi_key,
+                                                         unsigned long long* __restrict__ hist,
+                                                         int* __restrict__ nonfinite)
 {
-    __shared__ uint32_t s_min[kPassThreads / 32], s_max[kPassThreads / 32];
+    extern __shared__ uint32_t s_hist[];
+    __shared__ uint32_t s_min[kPass1Threads / 32], s_max[kPass1Threads / 32];
     __shared__ int s_bad;
+    for (int i = threadIdx.x; i < 32768; i += kPass1Threads) s_hist[i] = 0u;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
     const int b = blockIdx.x;
     int bx, by, bz;
     brick_coords(d, b, bx, by, bz);
     const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
     const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_bad = 0;
     uint32_t kmin = 0xffffffffu, kmax = 0u;
     bool bad = false;
     const bool valid = lane < ex;
     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     const int rows = ey * ez;
-    // rows whose lanes all share one key (constant regions, the background)
-    // add to a per-warp run instead of hitting the same bin with atomics
-    uint32_t run_key = 0xffffffffu;
-    unsigned long long run_cnt = 0;
-    constexpr int U = 4;   // rows in flight per warp
-    for (int r0 = warp * U; r0 < rows; r0 += (kPassThreads / 32) * U) {
-        uint32_t u[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            int row = r0 + q;
-            u[q] = 0;
-            if (valid && row < rows) {
-                int y = row % ey, z = row / ey;
-                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            if (r0 + q >= rows) break;               // warp-uniform
-            if (valid) {
-                uint32_t w = u[q];
-                bad |= ((w & 0x7f800000u) == 0x7f800000u);
-                uint32_t k = okey(w);
-                kmin = min(kmin, k);
-                kmax = max(kmax, k);
-                unsigned peers = __match_any_sync(vmask, w >> 16);
-                if (peers == vmask) {                       // warp-uniform
-                    if ((w >> 16) == run_key) {
-                        run_cnt += (unsigned long long)__popc(vmask);
-                    } else {
-                        if (run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
-                        run_key = w >> 16;
-                        run_cnt = (unsigned long long)__popc(vmask);
-                    }
-                } else if (lane == __ffs(peers) - 1) {
-                    atomicAdd(hist + (w >> 16), (unsigned long long)__popc(peers));
-                }
-            }
+    for (int row = warp; row < rows; row += kPass1Threads / 32) {
+        if (valid) {
+            const int y = row % ey, z = row / ey;
+            const uint32_t w = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+            bad |= ((w & 0x7f800000u) == 0x7f800000u);
+            const uint32_t k = okey(w);
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+            const uint32_t key = w >> 16;
+            const unsigned peers = __match_any_sync(vmask, key);
+            if (lane == __ffs(peers) - 1) atomicAdd(s_hist + (key >> 1), (uint32_t)__popc(peers) << ((key & 1u) * 16));
         }
     }
-    if (valid && run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
     if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
     if (lane == 0) { s_min[warp] = kmin; s_max[warp] = kmax; }
     __syncthreads();
+    for (int i = threadIdx.x; i < 32768; i += kPass1Threads) {
+        const uint32_t c = s_hist[i];
+        if (c & 0xffffu) atomicAdd(hist + 2 * i, (unsigned long long)(c & 0xffffu));
+        if (c >> 16) atomicAdd(hist + 2 * i + 1, (unsigned long long)(c >> 16));
+    }
     if (threadIdx.x == 0) {
         uint32_t a = s_min[0], c = s_max[0];
-        for (int w = 1; w < kPassThreads / 32; ++w) { a = min(a, s_min[w]); c = max(c, s_max[w]); }
+        for (int w = 1; w < kPass1Threads / 32; ++w) { a = min(a, s_min[w]); c = max(c, s_max[w]); }
         lo_key[b] = a;
         hi_key[b] = c;
         if (s_bad) atomicOr(nonfinite, 1);
@@ -622,12 +613,32 @@ __global__ void k_fill_leaves(const float* __restrict__ v, Dims d, const int* __
 
 // ---------------------------------------------------------------- macrocells
 // min/max of the decoded grid over each macrocell's voxels dilated by one
-// voxel (Section 4: the majorant ranges); one warp per macrocell
-__global__ void k_macrocells(GridView g, float* __restrict__ mcmin, float* __restrict__ mcmax, long long ncell)
+// voxel (Section 4: the majorant ranges); kGroup threads per macrocell (a warp
+// for small cells, a whole block for large ones)
+template <int kGroup>
+__device__ __forceinline__ bool group_all(bool p, int* s_flag)
 {
-    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (c >= ncell) return;
+    if constexpr (kGroup == 32) {
+        return __all_sync(0xffffffffu, p);
+    } else {
+        __syncthreads();
+        if (threadIdx.x == 0) *s_flag = 1;
+        __syncthreads();
+        if (!p) *s_flag = 0;
+        __syncthreads();
+        return *s_flag != 0;
+    }
+}
+
+template <int kGroup>
+__global__ void __launch_bounds__(kGroup == 32 ? 256 : kGroup)
+    k_macrocells(GridView g, float* __restrict__ mcmin, float* __restrict__ mcmax, long long ncell)
+{
+    __shared__ int s_flag;
+    __shared__ float s_lo[kGroup / 32], s_hi[kGroup / 32];
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    int lane = threadIdx.x % kGroup;
+    if (kGroup == 32 && c >= ncell) return;     // a whole warp; block groups have one cell per block
     int cx = (int)(c % g.mx), cy = (int)((c / g.mx) % g.my), cz = (int)(c / ((long long)g.mx * g.my));
     int x0 = max(cx * g.mc - 1, 0), x1 = min(cx * g.mc + g.mc, g.nx - 1);
     int y0 = max(cy * g.mc - 1, 0), y1 = min(cy * g.mc + g.mc, g.ny - 1);
@@ -637,7 +648,7 @@ __global__ void k_macrocells(GridView g, float* __restrict__ mcmin, float* __res
     int nl = (lx1 - lx0 + 1) * (ly1 - ly0 + 1) * (lz1 - lz0 + 1);
     float vmin = INFINITY, vmax = -INFINITY;
     bool all_tiles = true;
-    for (int q = lane; q < nl; q += 32) {
+    for (int q = lane; q < nl; q += kGroup) {
         int a = lx0 + q % (lx1 - lx0 + 1);
         int b = ly0 + (q / (lx1 - lx0 + 1)) % (ly1 - ly0 + 1);
         int e = lz0 + q / ((lx1 - lx0 + 1) * (ly1 - ly0 + 1));
@@ -650,12 +661,12 @@ __global__ void k_macrocells(GridView g, float* __restrict__ mcmin, float* __res
             all_tiles = false;
         }
     }
-    if (!__all_sync(0xffffffffu, all_tiles)) {
+    if (!group_all<kGroup>(all_tiles, &s_flag)) {
         Accessor acc;
         acc.reset();
         int ex = x1 - x0 + 1, ey = y1 - y0 + 1, ez = z1 - z0 + 1;
         int n = ex * ey * ez;
-        for (int q = lane; q < n; q += 32) {
+        for (int q = lane; q < n; q += kGroup) {
             int x = x0 + q % ex, y = y0 + (q / ex) % ey, z = z0 + q / (ex * ey);
             float val = voxel(g, acc, x, y, z);
             vmin = fminf(vmin, val);
@@ -665,6 +676,13 @@ __global__ void k_macrocells(GridView g, float* __restrict__ mcmin, float* __res
     for (int o = 16; o > 0; o >>= 1) {
         vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if constexpr (kGroup > 32) {
+        if ((threadIdx.x & 31) == 0) { s_lo[threadIdx.x >> 5] = vmin; s_hi[threadIdx.x >> 5] = vmax; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kGroup / 32; ++w) { vmin = fminf(vmin, s_lo[w]); vmax = fmaxf(vmax, s_hi[w]); }
+        }
     }
     if (lane == 0) { mcmin[c] = vmin; mcmax[c] = vmax; }
 }
@@ -678,6 +696,20 @@ __global__ void k_decode(GridView g, float* __restrict__ out, long long n)
         acc.reset();
         out[i] = voxel(g, acc, x, y, z);
     }
+}
+
+// k_pass1's 128 KB of shared memory needs an opt-in, once per device
+vdbc_status pass1_setup()
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    VDBC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return VDBC_OK;
+    VDBC_CUDA(cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+    done.push_back(dev);
+    return VDBC_OK;
 }
 
 unsigned grid1d(long long n, int threads)
@@ -763,7 +795,11 @@ void layout(vdbc_grid* g)
 vdbc_status macrocells_of_view(const GridView& v, float* mcmin, float* mcmax, cudaStream_t s)
 {
     long long ncell = (long long)v.mx * v.my * v.mz;
-    KLAUNCH(k_macrocells<<<grid1d(ncell * 32, 256), 256, 0, s>>>(v, mcmin, mcmax, ncell));
+    const long long dil = (long long)(v.mc + 2) * (v.mc + 2) * (v.mc + 2);
+    if (dil > 4096)
+        KLAUNCH(k_macrocells<256><<<(unsigned)ncell, 256, 0, s>>>(v, mcmin, mcmax, ncell));
+    else
+        KLAUNCH(k_macrocells<32><<<grid1d(ncell * 32, 256), 256, 0, s>>>(v, mcmin, mcmax, ncell));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
@@ -875,7 +911,8 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     // phase 1: histogram -> B (two levels), brick ranges
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
     VDBC_CUDA(cudaMemsetAsync(nonfinite, 0, 4, s));
-    KLAUNCH(k_pass1<<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, hist, nonfinite));
+    VDBC_TRY(pass1_setup());
+    KLAUNCH(k_pass1<<<nb, kPass1Threads, kPass1Smem, s>>>(vol, d, lo_key, hi_key, hist, nonfinite));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0));
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
     KLAUNCH(k_pass2<<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
@@ -1166,7 +1203,8 @@ extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vd
     // the scratch keeps the previous call's contents: clear what accumulates
     VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
     VDBC_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
-    KLAUNCH(k_pass1<<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->hist,
+    VDBC_TRY(pass1_setup());
+    KLAUNCH(k_pass1<<<(unsigned)nb, kPass1Threads, kPass1Smem, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->hist,
                                                           &sc->nonfinite));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 0));
     VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
