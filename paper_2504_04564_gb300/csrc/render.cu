@@ -414,6 +414,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
     float beta = 1.0f, T = 1.0f, ph = 0.0f;
     float tau = -1.0f, ua = 0.0f, ub = 0.0f, uc = 0.0f;   // current free flight: optical depth left, u1..u3
     int steps_in_cell = 0, guard = 0;
+    bool start = false;   // a ray to start before the next free flight
     unsigned long long pool_next = 0, pool_end = 0;   // this warp's share of the work counter
     Track tr;
     Accessor acc;
@@ -460,21 +461,8 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                         L = f3(0.f, 0.f, 0.f);
                         beta = 1.0f;
                         bounce = 0;
-                        float tin, tout;
-                        if (!clip_box(F.m, o, d, tin, tout)) {
-                            F.path_out[(size_t)sample * F.npix + pixel] = make_float4(F.med.env_rad.x, F.med.env_rad.y,
-                                                                                     F.med.env_rad.z, 1.0f);
-                            ++paths;
-                        } else {
-                            tr.dda.init(F.m, o, d, tin, tout);
-                            tau = -1.0f;   // every ray starts a new free flight
-                            VDBC_EVENT(w, 4);
-                            guard = F.m.mx + F.m.my + F.m.mz + 8;
-                            steps_in_cell = 0;
-                            mode = kDelta;
-                            if (!next_cell(tr, F.m, F.med, o, src.bits(jb), src.cbits(jb), F.cx_n, F.cy_n, guard, w))
-                                mode = -kDelta;   // leaves at once
-                        }
+                        mode = kDelta;
+                        start = true;
                     }
                 }
             }
@@ -490,6 +478,23 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         const uint32_t* bits = src.bits(jb);
         const uint32_t* cbits = src.cbits(jb);
         const int cx_n = J.cx_n, cy_n = J.cy_n;
+
+        // ---- the lane's pending ray (camera ray, light ray or next bounce):
+        // box clip and first occupied cell, from one place in the code
+        if (start) {
+            start = false;
+            float tin, tout;
+            if (clip_box(m, o, d, tin, tout)) {
+                tr.dda.init(m, o, d, tin, tout);
+                tau = -1.0f;   // every ray starts a new free flight
+                VDBC_EVENT(w, 4);
+                guard = m.mx + m.my + m.mz + 8;
+                steps_in_cell = 0;
+                if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -mode;   // leaves at once
+            } else {
+                mode = -mode;
+            }
+        }
 
         // ---- one free flight per lane: draw tau, spend it over the cells, and
         // where it runs out evaluate the density (delta: accept or not;
@@ -561,18 +566,8 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 o = x;
                 d = med.sun_dir;
                 T = 1.0f;
-                float tin, tout;
                 mode = kRatio;
-                if (clip_box(m, o, d, tin, tout)) {
-                    tr.dda.init(m, o, d, tin, tout);
-                    tau = -1.0f;   // every ray starts a new free flight
-                    VDBC_EVENT(w, 4);
-                    guard = m.mx + m.my + m.mz + 8;
-                    steps_in_cell = 0;
-                    if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kRatio;
-                } else {
-                    mode = -kRatio;
-                }
+                start = true;
             }
         }
         // ---- a ray ended (negative mode): escape, or the light ray's contribution
@@ -587,24 +582,9 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 if (++bounce >= med.max_bounces) {
                     finished = true;
                 } else {
-                    d = nd;
-                    float tin, tout;
-                    if (!clip_box(m, o, d, tin, tout)) {
-                        L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
-                        finished = true;
-                    } else {
-                        tr.dda.init(m, o, d, tin, tout);
-                        tau = -1.0f;   // every ray starts a new free flight
-                        VDBC_EVENT(w, 4);
-                        guard = m.mx + m.my + m.mz + 8;
-                        steps_in_cell = 0;
-                        mode = kDelta;
-                        if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -kDelta;
-                        if (mode == -kDelta) {
-                            L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
-                            finished = true;
-                        }
-                    }
+                    d = nd;          // the next bounce starts at the top of the next iteration
+                    mode = kDelta;
+                    start = true;
                 }
             }
             if (finished) {
