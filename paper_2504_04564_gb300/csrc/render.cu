@@ -304,6 +304,9 @@ struct Track {
 // coarse bit is clear are crossed in one step; inside an occupied block,
 // cells whose own bit is clear (majorant <= 0) are passed without loading
 // their majorant.
+// kUseCoarse: test the coarse level before the cell (compiled out where the
+// coarse level is off, which also frees the registers skip_block needs)
+template <bool kUseCoarse>
 __device__ __forceinline__ bool next_cell(Track& tr, const Majorants& m, const MedDev& med, float3 o,
                                           const uint32_t* bits, const uint32_t* cbits, int cx_n, int cy_n,
                                           int& guard, Walk& w)
@@ -313,11 +316,13 @@ __device__ __forceinline__ bool next_cell(Track& tr, const Majorants& m, const M
     while (tr.dda.cell(m, id, texit)) {
         VDBC_EVENT(w, 1);
         if (--guard < 0) return false;
-        int cid = ((tr.dda.cz / kCoarse) * cy_n + tr.dda.cy / kCoarse) * cx_n + tr.dda.cx / kCoarse;
-        if (!((cbits[cid >> 5] >> (cid & 31)) & 1u)) {
-            VDBC_EVENT(w, 2);
-            if (!tr.dda.skip_block(m, o)) return false;
-            continue;
+        if constexpr (kUseCoarse) {
+            int cid = ((tr.dda.cz / kCoarse) * cy_n + tr.dda.cy / kCoarse) * cx_n + tr.dda.cx / kCoarse;
+            if (!((cbits[cid >> 5] >> (cid & 31)) & 1u)) {
+                VDBC_EVENT(w, 2);
+                if (!tr.dda.skip_block(m, o)) return false;
+                continue;
+            }
         }
         if (((bits[id >> 5] >> (id & 31)) & 1u) && texit > tr.dda.t) {
             float mj = __fmul_rn(med.sigma_scale, __ldg(m.mcmax + id));
@@ -398,7 +403,7 @@ struct BatchSource {
 
 // The tracker loop shared by the single-job and the batch kernels.
 // stride > 1 renders every stride-th path only (the autotuner's sample of a frame)
-template <class Src>
+template <bool kUseCoarse, class Src>
 __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
                                         int chunk, unsigned stride)
 {
@@ -490,7 +495,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 VDBC_EVENT(w, 4);
                 guard = m.mx + m.my + m.mz + 8;
                 steps_in_cell = 0;
-                if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -mode;   // leaves at once
+                if (!next_cell<kUseCoarse>(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) mode = -mode;   // leaves at once
             } else {
                 mode = -mode;
             }
@@ -518,7 +523,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 tau = __fsub_rn(tau, reach);
                 tr.dda.advance(m, o, tr.texit);
                 steps_in_cell = 0;
-                if (!next_cell(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) {
+                if (!next_cell<kUseCoarse>(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w)) {
                     if (guard < 0) w.flags |= kErrDdaSteps;
                     ended = true;
                     break;
@@ -597,14 +602,24 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
     flush_stats(st, w, paths);
 }
 
+// resident 256-thread blocks per SM the tracker is compiled for: 4 (64
+// registers) measured fastest for the plain samplers without the coarse level
+// (36.4 ms against 40.1 at 2, 44.0 at 3, 37.1 at 5 on the 512^3 medium with
+// 48^3 cells); with the coarse level (8^3 cells) 2 is faster (130.9 against
+// 153.6 ms), and the learned sampler keeps 2 (its tile code needs the registers)
 #ifndef VDBC_PT_MIN_BLOCKS
-#define VDBC_PT_MIN_BLOCKS 2
+#define VDBC_PT_MIN_BLOCKS 4
 #endif
+template <class S, bool kUseCoarse>
+constexpr int pt_min_blocks()
+{
+    return (S::kCollective || kUseCoarse) ? 2 : VDBC_PT_MIN_BLOCKS;
+}
 
 // gbits: nwords fine occupancy words followed by ncwords coarse words; the
 // parts that fit in `smem_words` are staged in shared memory (coarse first)
-template <class S>
-__global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
+template <class S, bool kUseCoarse>
+__global__ void __launch_bounds__(256, (pt_min_blocks<S, kUseCoarse>()))
     k_pt(S smp, JobView job, const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
          DevStats* __restrict__ st, int chunk)
 {
@@ -621,7 +636,7 @@ __global__ void __launch_bounds__(256, VDBC_PT_MIN_BLOCKS)
     }
     __syncthreads();
     SingleSource<S> src{job, smp, bits, cbits};
-    pt_loop(src, job.items, st, chunk, 1u);
+    pt_loop<kUseCoarse>(src, job.items, st, chunk, 1u);
 }
 
 // all jobs of a batch in one persistent launch; frame[0] numbers the
@@ -643,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads)
     }
     __syncthreads();
     BatchSource src{sj, sg, n};
-    pt_loop(src, nitems, st, chunk, stride);
+    pt_loop<true>(src, nitems, st, chunk, stride);   // the tuner decides per frame whether cbits skip anything
 }
 
 // average of the spp path radiances of each pixel, in sample order
@@ -1076,11 +1091,19 @@ bool coarse_skipping(int mc)
 }
 
 // items a warp takes from the work counter at once (>= 32); VDBC_PT_CHUNK overrides
-int work_chunk()
+// items a warp takes from the work counter at once: 256, or less for small
+// frames so that every resident warp gets at least four chunks (a 256^2 x 4 spp
+// frame would otherwise busy a fifth of the warps); VDBC_PT_CHUNK overrides
+int work_chunk(unsigned long long items, long long resident_warps)
 {
+    if (const char* e = std::getenv("VDBC_PT_CHUNK")) {
+        int c = std::atoi(e);
+        return c < 32 ? 32 : c;
+    }
     int c = 256;
-    if (const char* e = std::getenv("VDBC_PT_CHUNK")) c = std::atoi(e);
-    return c < 32 ? 32 : c;
+    while (c > 32 && (unsigned long long)c * 4ull * (unsigned long long)std::max<long long>(resident_warps, 1) > items)
+        c >>= 1;
+    return c;
 }
 constexpr size_t kSmemBitsMax = 96 * 1024;
 
@@ -1107,24 +1130,35 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     return j;
 }
 
-template <class S>
-vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, int nwords, int ncwords,
-                      DevStats* stats, int chunk, cudaStream_t s)
+template <class S, bool kUseCoarse>
+vdbc_status launch_pt_t(const S& smp, const JobView& job, const uint32_t* bits, int nwords, int ncwords,
+                        DevStats* stats, int chunk, cudaStream_t s)
 {
     int smem_words = std::min<int>(nwords + ncwords, (int)(kSmemBitsMax / 4));
     if (smem_words < ncwords) smem_words = 0;
     size_t smem = (size_t)smem_words * 4;
-    auto kern = k_pt<S>;
+    auto kern = k_pt<S, kUseCoarse>;
     if (smem > 48 * 1024) VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
     if (per_sm < 1) per_sm = 1;
     long long want = (long long)((job.items + kPtThreads - 1) / kPtThreads);
     long long blocks = std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
+    if (chunk <= 0) chunk = work_chunk(job.items, blocks * (kPtThreads / 32));
     KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, job, bits, nwords, ncwords, smem_words, stats,
                                                             chunk));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
+}
+
+template <class S>
+vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, int nwords, int ncwords,
+                      DevStats* stats, int chunk, bool coarse, cudaStream_t s)
+{
+    if constexpr (!S::kCollective) {
+        if (coarse) return launch_pt_t<S, true>(smp, job, bits, nwords, ncwords, stats, chunk, s);
+    }
+    return launch_pt_t<S, false>(smp, job, bits, nwords, ncwords, stats, chunk, s);
 }
 
 template <class S>
@@ -1158,14 +1192,15 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     vdbc_status st = dev_alloc(reinterpret_cast<void**>(&path_out), (size_t)spp * npix * sizeof(float4), s);
     if (st != VDBC_OK) { dev_free(bits, s); return st; }
     KLAUNCH(k_occupancy<<<blocks_for(ncell, 256), 256, 0, s>>>(mj.mcmax, ncell, med.sigma_scale, bits));
-    if (coarse_skipping(mj.mc)) {
+    const bool coarse = !S::kCollective && coarse_skipping(mj.mc);
+    if (coarse) {
         KLAUNCH(k_coarse_occupancy<<<blocks_for((long long)cxn * cyn * czn, 256), 256, 0, s>>>(
             bits, mj.mx, mj.my, mj.mz, bits + nwords, cxn, cyn, czn));
     } else {
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
     JobView job = make_job(mj, cam, med, spp, seed, path_out);
-    st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, work_chunk(), s);
+    st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, 0, coarse, s);
     if (st == VDBC_OK) {
         KLAUNCH(k_pt_reduce<<<blocks_for(npix, 256), 256, 0, s>>>(path_out, (int)npix, spp, out));
         cudaError_t e = cudaGetLastError();
