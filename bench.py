@@ -389,7 +389,9 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / frames
     st = v.vdbc_batch_stats_get(b, stream=stream)
-    # the plain form: one vdbc_render per job, same samples
+    # the plain form: one vdbc_render per job, same samples, with the coarse
+    # DDA level the tuner chose for the batch
+    os.environ["VDBC_PT_COARSE"] = str(int(tuning.coarse))
     for (job, cam, med), sp, img in zip(jobs[:1], specs[:1], imgs[:1]):
         v.vdbc_render(grids[0], cam, med, sp["spp"], sp["seed"], img, stream=stream)
     torch.cuda.synchronize()
@@ -399,6 +401,7 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1)
+    os.environ.pop("VDBC_PT_COARSE", None)
     b.close()
     for g in grids:
         g.close()

@@ -641,8 +641,8 @@ __global__ void __launch_bounds__(256, (pt_min_blocks<S, kUseCoarse>()))
 
 // all jobs of a batch in one persistent launch; frame[0] numbers the
 // progressive frame, so frame f renders sample ids [f*spp, (f+1)*spp)
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 512 / kThreads)
+template <int kThreads, bool kUseCoarse>
+__global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads)
     k_pt_batch(const JobView* __restrict__ jobs, const GridView* __restrict__ grids, int n,
                unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk,
                unsigned stride)
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads)
     }
     __syncthreads();
     BatchSource src{sj, sg, n};
-    pt_loop<true>(src, nitems, st, chunk, stride);   // the tuner decides per frame whether cbits skip anything
+    pt_loop<kUseCoarse>(src, nitems, st, chunk, stride);
 }
 
 // average of the spp path radiances of each pixel, in sample order
@@ -1496,8 +1496,8 @@ struct vdbc_batch {
     unsigned long long nitems = 0;
     size_t max_npix = 0;
     vdbc_tuning tuning{256, 256, 1, 0, 0.0f};
-    unsigned blocks128 = 0, blocks256 = 0;        // launch configuration per block size
-    size_t smem128 = 0, smem256 = 0;
+    unsigned blocks[2][2] = {{0, 0}, {0, 0}};     // launch configuration per [256 threads][coarse level]
+    size_t smem[2][2] = {{0, 0}, {0, 0}};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> allocs;
@@ -1529,11 +1529,13 @@ vdbc_status batch_select_bits(vdbc_batch* b, bool coarse, cudaStream_t s)
 
 // grid size and shared memory of the batched tracker for a block size; called
 // before any capture (it sets a function attribute and queries occupancy)
-template <int kThreads>
-vdbc_status batch_config(const vdbc_batch* b, unsigned* blocks, size_t* smem)
+template <int kThreads, bool kUseCoarse>
+vdbc_status batch_config(vdbc_batch* b)
 {
+    unsigned* blocks = &b->blocks[kThreads == 256][kUseCoarse];
+    size_t* smem = &b->smem[kThreads == 256][kUseCoarse];
     *smem = (sizeof(JobView) + sizeof(GridView)) * (size_t)b->n;
-    auto kern = k_pt_batch<kThreads>;
+    auto kern = k_pt_batch<kThreads, kUseCoarse>;
     if (*smem > 48 * 1024)
         VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
     int per_sm = 0;
@@ -1544,14 +1546,14 @@ vdbc_status batch_config(const vdbc_batch* b, unsigned* blocks, size_t* smem)
     return VDBC_OK;
 }
 
-template <int kThreads>
+template <int kThreads, bool kUseCoarse>
 vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStream_t s)
 {
-    unsigned& blocks = kThreads == 128 ? b->blocks128 : b->blocks256;
-    size_t& smem = kThreads == 128 ? b->smem128 : b->smem256;
-    if (blocks == 0) VDBC_TRY(batch_config<kThreads>(b, &blocks, &smem));
-    KLAUNCH(k_pt_batch<kThreads><<<blocks, kThreads, smem, s>>>(b->d_jobs, b->d_grids, b->n, b->nitems, b->d_frame,
-                                                                b->stats, chunk, stride));
+    const unsigned& blocks = b->blocks[kThreads == 256][kUseCoarse];
+    const size_t& smem = b->smem[kThreads == 256][kUseCoarse];
+    if (blocks == 0) VDBC_TRY((batch_config<kThreads, kUseCoarse>(b)));
+    KLAUNCH((k_pt_batch<kThreads, kUseCoarse><<<blocks, kThreads, smem, s>>>(b->d_jobs, b->d_grids, b->n, b->nitems,
+                                                                            b->d_frame, b->stats, chunk, stride)));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
@@ -1560,8 +1562,13 @@ vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStrea
 vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s, unsigned stride = 1)
 {
     VDBC_CUDA(cudaMemsetAsync(b->stats, 0, sizeof(DevStats), s));
-    if (t.threads == 128) VDBC_TRY(batch_launch_pt<128>(b, t.chunk, stride, s));
-    else VDBC_TRY(batch_launch_pt<256>(b, t.chunk, stride, s));
+    if (t.threads == 128) {
+        if (t.coarse) VDBC_TRY((batch_launch_pt<128, true>(b, t.chunk, stride, s)));
+        else VDBC_TRY((batch_launch_pt<128, false>(b, t.chunk, stride, s)));
+    } else {
+        if (t.coarse) VDBC_TRY((batch_launch_pt<256, true>(b, t.chunk, stride, s)));
+        else VDBC_TRY((batch_launch_pt<256, false>(b, t.chunk, stride, s)));
+    }
     if (accumulate) {
         dim3 grid((unsigned)((b->max_npix + 255) / 256), (unsigned)b->n);
         KLAUNCH(k_batch_reduce<<<grid, 256, 0, s>>>(b->d_jobs, b->d_sums, b->d_outs, b->d_frame));
@@ -1651,8 +1658,9 @@ vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
 vdbc_status batch_capture(vdbc_batch* b, cudaStream_t s)
 {
     VDBC_TRY(batch_select_bits(b, b->tuning.coarse != 0, s));
-    if (b->tuning.threads == 128) VDBC_TRY(batch_config<128>(b, &b->blocks128, &b->smem128));
-    else VDBC_TRY(batch_config<256>(b, &b->blocks256, &b->smem256));
+    const bool c = b->tuning.coarse != 0;
+    if (b->tuning.threads == 128) VDBC_TRY(c ? (batch_config<128, true>(b)) : (batch_config<128, false>(b)));
+    else VDBC_TRY(c ? (batch_config<256, true>(b)) : (batch_config<256, false>(b)));
     VDBC_TRY(wait_stream(s));
     cudaStream_t cs = nullptr;
     VDBC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
