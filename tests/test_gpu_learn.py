@@ -280,3 +280,25 @@ def test_trained_network_beats_vdb_at_equal_memory(env):
           % (budget, p_vdb, p_learned, learned.info.n_neural, learned.info.n_leaves, p_untrained))
     assert p_learned >= p_vdb + 3.0
     assert p_learned >= p_untrained + 3.0
+
+
+def test_learn_degenerate_grids(env):
+    """A grid with no leaves (a constant volume: everything pruned to tiles)
+    learns nothing and renders as before; a byte budget below the all-neural
+    size keeps every leaf neural."""
+    torch, v, sc = env["torch"], env["v"], env["sc"]
+    dims = (24, 20, 28)
+    const = torch.full((28, 20, 24), 0.25, device=env["dev"])
+    grid = v.vdbc_encode(const, 1.0)
+    assert grid.info.n_leaves == 0
+    learned, losses = v.vdbc_learn(grid, steps=3)
+    assert learned.info.n_neural == 0 and learned.info.n_leaves == 0
+    assert np.all(losses == 0.0)
+    assert np.array_equal(decode(env, learned, dims), np.full((28, 20, 24), 0.25, np.float32))
+    out = torch.zeros(6, 7, 4, device=env["dev"])
+    v.vdbc_render(learned, v.make_camera(*sc.pinhole_orbit(dims, 7, 6)), v.make_medium(v.MODE_PT, density_scale=5.0,
+                                                                                        sun_dir=(0, 0, 1)), 2, 0, out)
+    torch.cuda.synchronize()
+    _, src, _ = source(env, "blobs", (40, 36, 44), 1, 1.0)
+    tiny, _ = v.vdbc_learn(src, steps=0, max_bytes=1)
+    assert tiny.info.n_leaves == 0 and tiny.info.n_neural == src.info.n_leaves
