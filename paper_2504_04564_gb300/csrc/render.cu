@@ -1078,16 +1078,15 @@ int sm_count()
 
 constexpr int kPtThreads = 256;
 
-// Crossing empty kCoarse^3 blocks of macrocells in one DDA step pays where
-// cells are small (8^3: 77 against 99 ms on the 512^3 medium); from 16^3 up its
-// extra per-cell test costs more than it saves (16^3: 61.7 against 57.2 ms), so
-// it is on for macrocells of at most 8 voxels.  VDBC_PT_COARSE=0/1 overrides.
-bool coarse_skipping(int mc)
+// The coarse level (empty kCoarse^3 blocks of macrocells crossed in one DDA
+// step) is a compile-time variant of the tracker.  With the level compiled out
+// the tracker fits 4 blocks per SM, and the uniform grid wins at every measured
+// cell size on the 512^3 medium (8^3: 74.5 against 90.2 ms; 48^3: 30.1 against
+// 47.9 ms), so it is off unless VDBC_PT_COARSE=1 (the batch tuner tries both).
+bool coarse_skipping(int)
 {
     const char* e = std::getenv("VDBC_PT_COARSE");
-    if (e && e[0] == '0') return false;
-    if (e && e[0] == '1') return true;
-    return mc <= 8;
+    return e && e[0] == '1';
 }
 
 // items a warp takes from the work counter at once (>= 32); VDBC_PT_CHUNK overrides
