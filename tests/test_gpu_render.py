@@ -258,3 +258,24 @@ def test_full_size_turbulence_sampled_pixels(env):
                             w["spp"], 2024, pix, threads=8)
     err = np.abs(img[pix, :3] - ref[:, :3]).mean(axis=0)
     assert np.all(err <= PT_MEAN_ABS), err
+
+
+def test_pt_coarse_level_changes_no_image(env, monkeypatch):
+    """The coarse DDA level (opt-in, VDBC_PT_COARSE=1) crosses empty 8^3 blocks
+    of macrocells in one step, landing where cell-by-cell stepping lands: the
+    images are bit-identical with and without it, and match the oracle."""
+    torch, v, orc, vg, sc = env["torch"], env["v"], env["orc"], env["vg"], env["sc"]
+    dims = (128, 112, 120)
+    host = vg.generate_host(vg.make_params("blobs", dims, 6))
+    grid = v.vdbc_encode(torch.from_numpy(host).to(env["dev"]), 4.0, macrocell=4)
+    cam = sc.pinhole_orbit(dims, 48, 40)
+    med = v.make_medium(v.MODE_PT, **sc.pt_medium_args(density_scale=30.0))
+    monkeypatch.setenv("VDBC_PT_COARSE", "1")
+    on = gpu_image(env, grid, cam, med, 8, 3)
+    monkeypatch.setenv("VDBC_PT_COARSE", "0")
+    off = gpu_image(env, grid, cam, med, 8, 3)
+    assert np.array_equal(on, off)
+    e = orc.encode(host, 4.0)
+    D = orc.decode_dense(host, e["active"], e["background_bits"])
+    ref = oracle_image(env, D, cam, 1, 8, 3, macrocell=4, **sc.pt_medium_args(density_scale=30.0))
+    assert np.all(np.abs(on[..., :3] - ref[..., :3]).mean(axis=(0, 1)) <= PT_MEAN_ABS)
