@@ -60,7 +60,7 @@ enum { VDBC_F1 = 1,  /* closest:  min(|lo-B|, |hi-B|)  */
 /* leaf payload: FP32 as in the paper; FP16 / FP8 (E4M3) with a per-leaf
  * FP32 scale and offset are a project extension (not in the paper), as is
  * VDBC_LEARNED: leaves decoded by a small shared network from a per-leaf
- * FP16 latent, with FP16 leaves as the fallback (vdbc_learn) */
+ * bf16 latent, with FP16 leaves as the fallback (vdbc_learn) */
 enum { VDBC_FP32 = 0, VDBC_FP16 = 1, VDBC_FP8 = 2, VDBC_LEARNED = 3 };
 
 enum { VDBC_CAM_ORTHO = 0, VDBC_CAM_PINHOLE = 1 };
@@ -325,7 +325,7 @@ void        vdbc_batch_free(vdbc_batch* batch);
 /*
  * The paper's Section 2.3 mentions network-decoded leaves (NeuralVDB) only as
  * related work, too slow there for real-time rendering.  Here a leaf may be
- * "neural": it stores a 16-value FP16 latent z and its (scale, offset), and
+ * "neural": it stores a 16-value bf16 latent z and its (scale, offset), and
  * voxel (i, j, k) of the leaf decodes to
  *     offset + scale * clamp(y, 0, 1),
  *     y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3,  x = (i/7, j/7, k/7, z),

@@ -160,7 +160,8 @@ void or_mlp_forward_bf16(const double* params, const double* inputs, int64_t n, 
 
 /* A neural leaf: the leaf's (scale, offset) are those of its FP16 payload
  * (range and minimum of the source values, or_quantize_leaf), its latent is
- * stored in FP16, and voxel n = a + 8b + 64c decodes to
+ * stored in bfloat16 (the precision the network reads it in, so one rounding
+ * of the trained FP32 value), and voxel n = a + 8b + 64c decodes to
  * offset + scale * clamp(y, 0, 1) with y the network at (a/7, b/7, c/7, z)
  * evaluated in the tensor cores' precision (or_mlp_forward_bf16); the FP32
  * result is the rounding of that exact value. */
@@ -173,7 +174,7 @@ void or_learned_leaf(const double* params, const float latent[16], const float s
         x[n * IN + 0] = (double)(float)((double)(n & 7) / 7.0);
         x[n * IN + 1] = (double)(float)((double)((n >> 3) & 7) / 7.0);
         x[n * IN + 2] = (double)(float)((double)(n >> 6) / 7.0);
-        for (int c = 0; c < 16; ++c) x[n * IN + 3 + c] = (double)or_round_fp16(latent[c]);
+        for (int c = 0; c < 16; ++c) x[n * IN + 3 + c] = (double)latent[c];   /* rounded to bf16 in the forward */
     }
     or_mlp_forward_bf16(params, x, 512, y);
     for (int n = 0; n < 512; ++n) {

@@ -754,7 +754,7 @@ void bind_view(vdbc_grid* g)
     v.meta = reinterpret_cast<const float2*>(base + g->off_meta);
     v.mcmin = reinterpret_cast<const float*>(base + g->off_mcmin);
     v.mcmax = reinterpret_cast<const float*>(base + g->off_mcmax);
-    v.latents = reinterpret_cast<const __half*>(base + g->off_latents);
+    v.latents = reinterpret_cast<const uint32_t*>(base + g->off_latents);
     v.nmeta = reinterpret_cast<const float2*>(base + g->off_nmeta);
     v.mlp_frag = reinterpret_cast<const uint2*>(base + g->off_frag);
     v.mlp_bias = reinterpret_cast<const float*>(base + g->off_bias);

@@ -13,7 +13,7 @@
 //  3. every leaf is decoded through the tensor-core network, the render's own
 //     arithmetic, and its largest error against the source is measured;
 //  4. leaves over the error bound keep a raw FP16 payload (the worst first,
-//     as far as the byte budget allows); the others keep only an FP16 latent;
+//     as far as the byte budget allows); the others keep only a bf16 latent;
 //  5. the learned grid is assembled (tree tables copied, leaf entries
 //     renumbered: raw leaves by rank, neural leaves as kNeural | rank) and
 //     its macrocell ranges are taken from the decoded values.
@@ -489,10 +489,11 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     }
 }
 
-__global__ void k_to_half(const float* __restrict__ a, __half* __restrict__ b, long long n)
+// latents to their stored form: bf16 pairs, (z_2k, z_2k+1) in word k
+__global__ void k_to_bf16(const float* __restrict__ a, uint32_t* __restrict__ b, long long nwords)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = __float2half_rn(a[i]);
+    if (i < nwords) b[i] = pack_bf16(a[2 * i], a[2 * i + 1]);
 }
 
 // the network's B fragments and biases from the FP32 parameters
@@ -509,11 +510,11 @@ __global__ void k_pack_net(const float* __restrict__ params, uint2* __restrict__
 
 // ---------------------------------------------------------------- decode through the network
 // one warp per neural leaf, two 16-row tiles per pass: leaf id -> latent
-// lat[id * 16], (scale, offset) meta[id]; decoded = offset + scale * clamp(y, 0, 1).
+// lat[id * 8] (bf16 pairs), (scale, offset) meta[id]; decoded = offset + scale * clamp(y, 0, 1).
 // out (if given) receives the 512 decoded values at out[(out_base + id) * 512];
 // err (if given) the largest |decoded - cmp| with cmp the source leaf `id`.
 constexpr int kDecWarps = 8;
-__global__ void __launch_bounds__(kDecWarps * 32) k_neural_decode(const __half* __restrict__ lat,
+__global__ void __launch_bounds__(kDecWarps * 32) k_neural_decode(const uint32_t* __restrict__ lat,
                                                                  const float2* __restrict__ meta, long long count,
                                                                  const uint32_t* __restrict__ only,
                                                                  const uint2* __restrict__ frag,
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_neural_decode(const __half* 
     const long long id = (long long)blockIdx.x * kDecWarps + wid;
     if (id >= count) return;                     // warp-uniform
     if (only && !only[id]) return;               // warp-uniform
-    const __half* z = lat + id * kMlpLatent;
+    const uint32_t* z = lat + id * (kMlpLatent / 2);
     const float2 m = __ldg(meta + id);
     const float2 csm = (err && cmp.payload != 0) ? __ldg(cmp.meta + id) : make_float2(0.f, 0.f);
     const int r = lane & 15, half = lane >> 4;
@@ -607,15 +608,15 @@ __global__ void k_fill_raw(GridView src, const float2* __restrict__ lmeta, const
     }
 }
 
-__global__ void k_fill_neural(const __half* __restrict__ lat, const float2* __restrict__ lmeta,
+__global__ void k_fill_neural(const uint32_t* __restrict__ lat, const float2* __restrict__ lmeta,
                               const uint32_t* __restrict__ neural, const uint32_t* __restrict__ neural_rank,
-                              long long nleaves, __half* __restrict__ latents, float2* __restrict__ nmeta)
+                              long long nleaves, uint32_t* __restrict__ latents, float2* __restrict__ nmeta)
 {
     long long leaf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (leaf >= nleaves || !neural[leaf]) return;
     const size_t r = neural_rank[leaf];
-    const uint4* a = reinterpret_cast<const uint4*>(lat + leaf * kMlpLatent);
-    uint4* b = reinterpret_cast<uint4*>(latents + r * kMlpLatent);
+    const uint4* a = reinterpret_cast<const uint4*>(lat + leaf * (kMlpLatent / 2));
+    uint4* b = reinterpret_cast<uint4*>(latents + r * (kMlpLatent / 2));
     b[0] = a[0];
     b[1] = a[1];
     nmeta[r] = lmeta[leaf];
@@ -846,15 +847,15 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
         for (int t = 0; t < lp->steps; ++t) loss_out[t] = 0.0;
     }
 
-    // ---- 3. FP16 latents, network tables, per-leaf error through the tensor cores
-    __half* lath = nullptr;
+    // ---- 3. bf16 latents, network tables, per-leaf error through the tensor cores
+    uint32_t* lath = nullptr;
     uint2* frag = nullptr;
     float *bias = nullptr, *err = nullptr;
-    VDBC_TRY(pool.get(&lath, std::max<long long>(nl, 1) * kMlpLatent));
+    VDBC_TRY(pool.get(&lath, std::max<long long>(nl, 1) * (kMlpLatent / 2)));
     VDBC_TRY(pool.get(&frag, kMlpFrags * 32));
     VDBC_TRY(pool.get(&bias, kMlpBias));
     VDBC_TRY(pool.get(&err, std::max<long long>(nl, 1)));
-    if (nl > 0) KLAUNCH(k_to_half<<<blocks(nl * kMlpLatent, 256), 256, 0, s>>>(lat, lath, nl * kMlpLatent));
+    if (nl > 0) KLAUNCH(k_to_bf16<<<blocks(nl * (kMlpLatent / 2), 256), 256, 0, s>>>(lat, lath, nl * (kMlpLatent / 2)));
     KLAUNCH(k_pack_net<<<blocks(kMlpFrags * 32, 256), 256, 0, s>>>(params, frag, bias));
     VDBC_CUDA(cudaMemsetAsync(err, 0, (size_t)std::max<long long>(nl, 1) * 4, s));
     if (nl > 0)
@@ -936,7 +937,7 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
                                                                reinterpret_cast<__half*>(b + g->off_leaves),
                                                                reinterpret_cast<float2*>(b + g->off_meta)));
         KLAUNCH(k_fill_neural<<<blocks(nl, 256), 256, 0, s>>>(lath, lmeta, neural, neural_rank, nl,
-                                                              reinterpret_cast<__half*>(b + g->off_latents),
+                                                              reinterpret_cast<uint32_t*>(b + g->off_latents),
                                                               reinterpret_cast<float2*>(b + g->off_nmeta)));
     }
     e = cudaGetLastError();

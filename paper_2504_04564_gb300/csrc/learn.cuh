@@ -4,10 +4,13 @@
 // NeuralVDB as related work): x = (u, v, w, z_0..z_15) with (u, v, w) the
 // voxel's position in its 8^3 leaf divided by 7 and z the leaf's latent;
 // h1 = relu(W1 x + b1) (32), h2 = relu(W2 h1 + b2) (32), y = w3 . h2 + b3.
-// A neural leaf decodes to offset + scale * clamp(y, 0, 1).
+// A neural leaf decodes to offset + scale * clamp(y, 0, 1); its latent is
+// stored in bf16, the precision the tensor cores read.
 //
 // Evaluation is warp-cooperative: 16 input rows (bf16, padded to 32
-// columns) go through three layers of mma.sync.m16n8k16 (bf16 in, fp32
+// columns; in a row the latent comes first, z_0..z_15, then u, v, w, so that
+// the leaf's stored bf16 latent is copied into the row as it is) go through
+// three layers of mma.sync.m16n8k16 (bf16 in, fp32
 // accumulate): layer 1 = 2 k-steps x 4 n-tiles, layer 2 = 2 x 4, layer 3 =
 // 2 x 1.  The accumulator fragments of two adjacent n-tiles are exactly the
 // A fragment of the next layer's 16-wide k-step, so activations stay in
@@ -104,46 +107,46 @@ __device__ __forceinline__ void mlp_tile(const uint32_t* rows, const uint2* __re
     }
 }
 
-// row r of a tile: (i, j, k) / 7 of voxel n of the leaf, then the leaf's FP16
-// latent, all rounded to bf16 and zero padded to 32 columns
-__device__ __forceinline__ void mlp_row(uint32_t* rows, int r, int n, const __half* __restrict__ latent)
+// row r of a tile for voxel n of a leaf: the leaf's latent (8 words of bf16
+// pairs, copied), then (i, j, k) / 7 rounded to bf16, zero padded to 32 columns
+__device__ __forceinline__ void mlp_row(uint32_t* rows, int r, int n, const uint32_t* __restrict__ latent)
 {
     const uint4* lp = reinterpret_cast<const uint4*>(latent);
-    uint4 q0 = __ldg(lp), q1 = __ldg(lp + 1);
-    const __half* z0 = reinterpret_cast<const __half*>(&q0);
-    const __half* z1 = reinterpret_cast<const __half*>(&q1);
-    float z[kMlpLatent];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) { z[q] = __half2float(z0[q]); z[8 + q] = __half2float(z1[q]); }
+    const uint4 q0 = __ldg(lp), q1 = __ldg(lp + 1);
     const float u = __fdiv_rn((float)(n & 7), 7.0f), v = __fdiv_rn((float)((n >> 3) & 7), 7.0f),
                 w = __fdiv_rn((float)(n >> 6), 7.0f);
-    uint4 c0 = make_uint4(pack_bf16(u, v), pack_bf16(w, z[0]), pack_bf16(z[1], z[2]), pack_bf16(z[3], z[4]));
-    uint4 c1 = make_uint4(pack_bf16(z[5], z[6]), pack_bf16(z[7], z[8]), pack_bf16(z[9], z[10]), pack_bf16(z[11], z[12]));
-    uint4 c2 = make_uint4(pack_bf16(z[13], z[14]), pack_bf16(z[15], 0.0f), 0u, 0u);
     uint4* rp = reinterpret_cast<uint4*>(rows) + r * 4;
     const int sw = (r >> 1) & 3;
-    rp[0 ^ sw] = c0;
-    rp[1 ^ sw] = c1;
-    rp[2 ^ sw] = c2;
+    rp[0 ^ sw] = q0;
+    rp[1 ^ sw] = q1;
+    rp[2 ^ sw] = make_uint4(pack_bf16(u, v), pack_bf16(w, 0.0f), 0u, 0u);
     rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// the parameter column of W1 that row column k of a tile multiplies (-1: none)
+__device__ __forceinline__ int w1_column(int k) { return k < kMlpLatent ? 3 + k : (k < kMlpIn ? k - kMlpLatent : -1); }
+
 // B fragment f (0..17) of lane `lane` from the FP32 parameters, bf16-rounded:
-// layer 1 (f = s*4 + j): W1[8j+g][16s+2t(+1)], W1[8j+g][16s+8+2t(+1)], zero past column 18;
-// layer 2 (f = 8 + s*4 + j): the same of W2; layer 3 (f = 16 + s): w3 in output column 0 only
+// layer 1 (f = s*4 + j): W1[8j+g][c(16s+2t(+1))], W1[8j+g][c(16s+8+2t(+1))] with c the row
+// column's parameter column (w1_column), zero where there is none;
+// layer 2 (f = 8 + s*4 + j): W2[8j+g][16s+2t(+1)], ...; layer 3 (f = 16 + s): w3 in output column 0 only
 __device__ __forceinline__ uint2 mlp_frag(const float* __restrict__ p, int f, int lane)
 {
     const int g = lane >> 2, t = lane & 3;
-    const float* W;
-    int ncol, row, s;
-    if (f < 8) { W = p + kOffW1; ncol = kMlpIn; s = f >> 2; row = 8 * (f & 3) + g; }
-    else if (f < 16) { W = p + kOffW2; ncol = kMlpHid; s = (f - 8) >> 2; row = 8 * ((f - 8) & 3) + g; }
-    else { W = p + kOffW3; ncol = kMlpHid; s = f - 16; row = g == 0 ? 0 : -1; }
-    float e[4];
-    const int k0 = 16 * s + 2 * t;
+    const int k0 = 16 * ((f < 8 ? f : (f < 16 ? f - 8 : f - 16)) >> (f < 16 ? 2 : 0)) + 2 * t;
     const int ks[4] = {k0, k0 + 1, k0 + 8, k0 + 9};
+    float e[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) e[q] = (row >= 0 && ks[q] < ncol) ? W[row * ncol + ks[q]] : 0.0f;
+    for (int q = 0; q < 4; ++q) {
+        if (f < 8) {
+            const int c = w1_column(ks[q]);
+            e[q] = c >= 0 ? p[kOffW1 + (8 * (f & 3) + g) * kMlpIn + c] : 0.0f;
+        } else if (f < 16) {
+            e[q] = p[kOffW2 + (8 * ((f - 8) & 3) + g) * kMlpHid + ks[q]];
+        } else {
+            e[q] = g == 0 ? p[kOffW3 + ks[q]] : 0.0f;
+        }
+    }
     return make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
 }
 
@@ -220,7 +223,7 @@ struct LearnedSampler {
                     if (q >= t0 && q < t0 + 16) {
                         const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
                         mlp_row(rows, q - t0, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7),
-                                g.latents + (size_t)__float_as_uint(v[c]) * kMlpLatent);
+                                g.latents + (size_t)__float_as_uint(v[c]) * (kMlpLatent / 2));
                     }
                     ++q;
                 }

@@ -9,7 +9,7 @@
 //   leaves payload[n_leaves * 512]  8^3 values, x fastest (f32, f16 or e4m3)
 //   meta   float2[n_leaves]         (scale, offset) of quantized leaves
 //   mcmin, mcmax f32[n_macrocells]  min/max of the decoded grid per macrocell
-//   learned grids add: latents f16[n_neural * 16], nmeta float2[n_neural],
+//   learned grids add: latents bf16[n_neural * 16], nmeta float2[n_neural],
 //   the network's B fragments u32x2[18 * 32], biases f32[65], params f32[1729]
 // An entry of root/upper/lower is a child index (bit 31 clear) or a tile
 // (bit 31 set, low bits index `tiles`).  This is the {5,4,3} tree of Section
@@ -43,9 +43,10 @@ struct GridView {
     const float2* meta;
     const float* mcmin;
     const float* mcmax;
-    // learned grids (payload 3): latents and (scale, offset) of neural leaves,
-    // network as B fragments and biases; `leaves`/`meta` hold the FP16 fallbacks
-    const __half* latents;
+    // learned grids (payload 3): latents (8 words per neural leaf: its 16
+    // values as bf16 pairs) and (scale, offset) of neural leaves, network as B
+    // fragments and biases; `leaves`/`meta` hold the FP16 fallbacks
+    const uint32_t* latents;
     const float2* nmeta;
     const uint2* mlp_frag;
     const float* mlp_bias;

@@ -158,8 +158,10 @@ def test_learned_leaf_closed_forms(orc):
     assert not np.array_equal(u_bf16, np.arange(8) / 7.0)     # the rounding is visible
 
 
-def test_learned_leaf_latent_is_fp16_then_bf16(orc):
-    # y = z_0 through the network: the latent is stored in FP16, then enters as bf16
+def test_learned_leaf_latent_is_rounded_once_to_bf16(orc):
+    # y = z_0 through the network: the latent is stored in bf16, one rounding of
+    # its FP32 value.  z_0 = 1/2 + 2^-9 + 2^-13 rounds up to 1/2 + 2^-8 in bf16,
+    # while a detour through FP16 would land on the bf16 midpoint and tie to 1/2.
     lay = layout(orc)
     p = np.zeros(orc.mlp_num_params())
     view(p, lay, "W1")[0, 3] = 1.0
@@ -167,10 +169,11 @@ def test_learned_leaf_latent_is_fp16_then_bf16(orc):
     view(p, lay, "w3")[0] = 1.0
     src = np.linspace(0, 1, 512, dtype=np.float32)
     z = np.zeros(16, dtype=np.float32)
-    z[0] = np.float32(0.3337)
+    z[0] = np.float32(0.5 + 2.0 ** -9 + 2.0 ** -13)
     out = orc.learned_leaf(p, z, src)
-    want = orc.round_bf16(orc.round_fp16(z[0]))
-    assert np.all(out == np.float32(want))       # offset 0, scale 1
+    assert orc.round_bf16(z[0]) == 0.5 + 2.0 ** -8
+    assert orc.round_bf16(orc.round_fp16(z[0])) == 0.5
+    assert np.all(out == np.float32(0.5 + 2.0 ** -8))       # offset 0, scale 1
 
 
 def test_tree_leaf_matches_decode(orc, vg):
