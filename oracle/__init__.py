@@ -132,6 +132,8 @@ def _bind_mlp(L):
     L.or_round_bf16.restype = ctypes.c_float
     L.or_mlp_forward_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
     L.or_learned_leaf.argtypes = [vp, vp, vp, vp]
+    L.or_mlp_loss_grad_bf16.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    L.or_mlp_loss_grad_bf16.restype = ctypes.c_double
     L.or_tree_leaf.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp]
     L.or_tree_leaf.restype = ctypes.c_int
 
@@ -442,6 +444,17 @@ def mlp_loss_grad(params, inputs, targets):
     gp = np.zeros_like(p)
     gx = np.zeros_like(x)
     loss = lib().or_mlp_loss_grad(_p(p), _p(x), _p(t), x.shape[0], _p(gp), _p(gx))
+    return float(loss), gp, gx
+
+
+def mlp_loss_grad_bf16(params, inputs, targets):
+    """Loss and gradients at the tensor cores' precision (see or_mlp_loss_grad_bf16)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, MLP_IN)
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    gp = np.zeros_like(p)
+    gx = np.zeros_like(x)
+    loss = lib().or_mlp_loss_grad_bf16(_p(p), _p(x), _p(t), x.shape[0], _p(gp), _p(gx))
     return float(loss), gp, gx
 
 

@@ -182,3 +182,81 @@ void or_learned_leaf(const double* params, const float latent[16], const float s
         out[n] = (float)((double)offset + (double)scale * yc);
     }
 }
+
+/* The training gradient at the tensor cores' precision: the loss of the bf16
+ * forward above (inputs, weights and hidden activations rounded to bf16, w3
+ * and h2 rounded to bf16 in the output sum), differentiated with the backward
+ * operands that feed a multiply also rounded to bf16: dh2 = relu'(a2) dy
+ * bf(w3) and dh1 = relu'(a1) (bf(W2)^T bf(dh2)); weight gradients
+ * gW2 = sum bf(dh2) bf(h1)^T, gW1 = sum bf(dh1) bf(x)^T, gw3 = sum dy bf(h2);
+ * bias gradients from the unrounded dh1, dh2, dy; input gradients
+ * bf(W1)^T bf(dh1).  Sums exact (FP64); FP32 values rounded where the GPU
+ * holds them in FP32 (pre-activations, dy, dh2, dh1). */
+double or_mlp_loss_grad_bf16(const double* params, const double* inputs, const double* targets, int64_t n,
+                             double* grad_params, double* grad_inputs)
+{
+    const double* W1 = params;
+    const double* b1 = W1 + HID * IN;
+    const double* W2 = b1 + HID;
+    const double* b2 = W2 + HID * HID;
+    const double* w3 = b2 + HID;
+    const double* b3 = w3 + HID;
+    double* gW1 = grad_params;
+    double* gb1 = gW1 + HID * IN;
+    double* gW2 = gb1 + HID;
+    double* gb2 = gW2 + HID * HID;
+    double* gw3 = gb2 + HID;
+    double* gb3 = gw3 + HID;
+    memset(grad_params, 0, sizeof(double) * NPAR);
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double* x = inputs + s * IN;
+        double xb[IN], a1[HID], h1b[HID], a2[HID], h2b[HID];
+        for (int k = 0; k < IN; ++k) xb[k] = bf(x[k]);
+        for (int i = 0; i < HID; ++i) {
+            double a = 0.0;
+            for (int k = 0; k < IN; ++k) a += bf(W1[i * IN + k]) * xb[k];
+            a1[i] = (double)(float)((double)(float)a + (double)(float)b1[i]);
+            h1b[i] = bf(a1[i] > 0.0 ? a1[i] : 0.0);
+        }
+        for (int i = 0; i < HID; ++i) {
+            double a = 0.0;
+            for (int k = 0; k < HID; ++k) a += bf(W2[i * HID + k]) * h1b[k];
+            a2[i] = (double)(float)((double)(float)a + (double)(float)b2[i]);
+            h2b[i] = bf(a2[i] > 0.0 ? a2[i] : 0.0);
+        }
+        double o = 0.0;
+        for (int k = 0; k < HID; ++k) o += bf(w3[k]) * h2b[k];
+        double y = (double)(float)((double)(float)o + (double)(float)b3[0]);
+        double e = y - targets[s];
+        loss += e * e;
+        double dy = (double)(float)(2.0 * e / (double)n);
+        double dh2[HID], dh1[HID];
+        gb3[0] += dy;
+        for (int k = 0; k < HID; ++k) {
+            gw3[k] += dy * h2b[k];
+            dh2[k] = a2[k] > 0.0 ? (double)(float)(dy * bf(w3[k])) : 0.0;
+        }
+        for (int i = 0; i < HID; ++i) {
+            gb2[i] += dh2[i];
+            for (int k = 0; k < HID; ++k) gW2[i * HID + k] += bf(dh2[i]) * h1b[k];
+        }
+        for (int k = 0; k < HID; ++k) {
+            double a = 0.0;
+            for (int i = 0; i < HID; ++i) a += bf(W2[i * HID + k]) * bf(dh2[i]);
+            dh1[k] = a1[k] > 0.0 ? (double)(float)a : 0.0;
+        }
+        for (int i = 0; i < HID; ++i) {
+            gb1[i] += dh1[i];
+            for (int k = 0; k < IN; ++k) gW1[i * IN + k] += bf(dh1[i]) * xb[k];
+        }
+        if (grad_inputs) {
+            for (int k = 0; k < IN; ++k) {
+                double a = 0.0;
+                for (int i = 0; i < HID; ++i) a += bf(W1[i * IN + k]) * bf(dh1[i]);
+                grad_inputs[s * IN + k] = a;
+            }
+        }
+    }
+    return loss / (double)n;
+}

@@ -118,6 +118,8 @@ void   or_adam_step(double* params, const double* grads, double* m, double* v, i
 float  or_round_bf16(float x);
 void   or_mlp_forward_bf16(const double* params, const double* inputs, int64_t n, double* out);
 void   or_learned_leaf(const double* params, const float latent[16], const float src[512], float out[512]);
+double or_mlp_loss_grad_bf16(const double* params, const double* inputs, const double* targets, int64_t n,
+                             double* grad_params, double* grad_inputs);
 
 #ifdef __cplusplus
 }

@@ -213,3 +213,64 @@ def test_learned_decode_all_raw_is_the_fp16_grid(orc, vg):
     want = orc.decode_dense(vol, enc["active"], enc["background_bits"], orc.FP16)
     assert np.array_equal(out.view(np.uint32), want.view(np.uint32))
     assert int((kinds == 2).sum()) == orc.Tree(vol, enc["active"], enc["background_bits"]).counts()["leaves"]
+
+
+def _representable_case(orc, rng):
+    """A network, inputs and targets on which every value the bf16 gradient
+    rounds is already a bf16 number: sparse weights of +-1/2, +-1, inputs in
+    {0, 1/2, 1}, and targets that put the errors at +-1/4 or +-1/2."""
+    lay = layout(orc)
+    p = np.zeros(orc.mlp_num_params())
+    W1, b1, W2, b2 = view(p, lay, "W1"), view(p, lay, "b1"), view(p, lay, "W2"), view(p, lay, "b2")
+    w3, b3 = view(p, lay, "w3"), view(p, lay, "b3")
+    vals = np.array([-1.0, -0.5, 0.5, 1.0])
+    for i in range(32):
+        for k in rng.choice(19, 3, replace=False):
+            W1[i, k] = rng.choice(vals)
+        for k in rng.choice(32, 3, replace=False):
+            W2[i, k] = rng.choice(vals)
+    b1[:] = rng.choice([-0.25, 0.0, 0.25, 0.5], 32)
+    b2[:] = rng.choice([-0.25, 0.0, 0.25], 32)
+    w3[:] = rng.choice(vals, 32)
+    b3[0] = 0.25
+    x = rng.choice([0.0, 0.5, 1.0], (4, 19))
+    y = orc.mlp_forward(p, x)
+    t = y - rng.choice([-0.5, -0.25, 0.25, 0.5], 4)
+    return p, x, t
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bf16_gradient_is_exact_on_representable_networks(orc, seed):
+    p, x, t = _representable_case(orc, np.random.default_rng(seed))
+    l0, g0, gx0 = orc.mlp_loss_grad(p, x, t)
+    l1, g1, gx1 = orc.mlp_loss_grad_bf16(p, x, t)
+    assert l1 == l0
+    assert np.array_equal(g1, g0) and np.array_equal(gx1, gx0)
+    assert np.abs(g0).max() > 0
+
+
+def test_bf16_gradient_loss_is_the_bf16_forward_mse(orc):
+    rng = np.random.default_rng(5)
+    p = rng.normal(0, 0.4, orc.mlp_num_params())
+    x = rng.random((40, 19))
+    t = rng.random(40)
+    loss, _, _ = orc.mlp_loss_grad_bf16(p, x, t)
+    y = orc.mlp_forward_bf16(p, x)
+    assert loss == pytest.approx(np.mean((y - t) ** 2), rel=1e-6)
+
+
+def test_bf16_gradient_close_to_exact_gradient(orc):
+    """bf16 operands move the gradient by about 2^-8 relative: a transposed
+    weight, a wrong mask or a dropped term would move it by order one."""
+    rng = np.random.default_rng(6)
+    p = rng.normal(0, 0.4, orc.mlp_num_params())
+    x = rng.random((200, 19))
+    t = rng.random(200)
+    _, g0, gx0 = orc.mlp_loss_grad(p, x, t)
+    _, g1, gx1 = orc.mlp_loss_grad_bf16(p, x, t)
+    assert np.abs(g1 - g0).max() <= 2e-2 * np.abs(g0).max()
+    # a single sample's input gradient can move further where bf16 operands flip
+    # the sign of a pre-activation near zero (its ReLU mask); most samples do not
+    far = np.abs(gx1 - gx0).max(axis=1) > 2e-2 * np.abs(gx0).max()
+    assert far.mean() <= 0.1
+    assert np.abs(g1 - g0).max() > 0          # the rounding is there
