@@ -359,7 +359,8 @@ typedef struct {
  * (scale, offset), and build the learned grid *out (free with
  * vdbc_grid_free; payload VDBC_LEARNED, n_leaves = raw leaves, n_neural =
  * neural leaves).  Training minimises the mean squared error of y against
- * (v - offset) / scale with Adam over `steps` steps; step t (from 0) uses,
+ * (v - offset) / scale with Adam over `steps` steps (the gradient as in
+ * vdbc_learn_loss_grad); step t (from 0) uses,
  * for every leaf not forced raw, voxel s*(512/S) + (r mod 512/S) for
  * s = 0..S-1, r the first word of Philox4x32-10 at counter
  * (leaf position, t, s, 0x4C454146) and key `seed`; the latents' gradient
@@ -377,8 +378,10 @@ vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params* params, vo
  * mean over the n rows of (y - target)^2, grad_params (1729) its gradient,
  * grad_inputs (n x 19, or NULL) the gradient with respect to each input row.
  * params, inputs (n x 19 row major), targets, grad_* are device arrays; loss
- * a host double (or NULL).  FP32 arithmetic, sums in a fixed order.  Waits
- * for `stream`.  Errors: INVALID_ARG (null arrays, n outside 1..2^31); CUDA.
+ * a host double (or NULL).  Tensor-core arithmetic at the network's own
+ * precision: y as the render evaluates it, the backward operands (dh2, dh1,
+ * h1, x, weights) rounded to bf16, FP32 sums in a fixed order.  Waits for
+ * `stream`.  Errors: INVALID_ARG (null arrays, n outside 1..2^31); CUDA.
  */
 vdbc_status vdbc_learn_loss_grad(const float* params, const float* inputs, const float* targets, int64_t n,
                                  double* loss, float* grad_params, float* grad_inputs, void* stream);

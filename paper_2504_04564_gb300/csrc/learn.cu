@@ -9,7 +9,8 @@
 //     fitted jointly to the leaves' normalised values (mean squared error,
 //     Adam).  Each step draws S voxels of every leaf, one uniformly from each
 //     stratum of 512 / S consecutive voxels; the forward and backward passes
-//     run in FP32 on the CUDA cores (k_mlp_grad);
+//     run on the tensor cores in the precision the network is evaluated in
+//     (bf16 operands, FP32 accumulation; k_mlp_grad);
 //  3. every leaf is decoded through the tensor-core network, the render's own
 //     arithmetic, and its largest error against the source is measured;
 //  4. leaves over the error bound keep a raw FP16 payload (the worst first,
@@ -28,15 +29,10 @@
 namespace vdbc {
 namespace {
 
-constexpr int kTrainThreads = 128;     // samples per tile = threads of k_mlp_grad
-constexpr int kXs = 20;                // row stride of the inputs in shared memory
-constexpr int kHs = 36;                // row stride of activations / their gradients (16-byte rows)
 constexpr int kPart = 1792;            // one block's partial gradient (>= kMlpParams)
 constexpr uint32_t kDrawTag = 0x4C454146u;   // fourth counter word of the voxel draws
 constexpr uint32_t kInitTag = 0x494E4954u;   // fourth counter word of the weight initialisation
 constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kEps = 1e-8f;
-constexpr size_t kTrainSmem =
-    (size_t)(32 * kXs + 32 + 1024 + 32 + 32 + 4 + kTrainThreads * kXs + 4 * kTrainThreads * kHs + kTrainThreads) * 4;
 
 __device__ __forceinline__ uint32_t okey(uint32_t b) { return (b & 0x80000000u) ? ~b : (b | 0x80000000u); }
 __device__ __forceinline__ uint32_t okey_inv(uint32_t k) { return (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k; }
@@ -138,29 +134,94 @@ __global__ void k_init_params(float* __restrict__ p, uint32_t k0, uint32_t k1)
 }
 
 // ---------------------------------------------------------------- training
-__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d)
-{
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
-}
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// ---------------------------------------------------------------- training on the tensor cores
+// One warp trains on tiles of 16 samples with mma.sync.m16n8k16 (bf16 in,
+// FP32 accumulate), at the precision the network is evaluated in:
+//   forward   a1 = W1 x + b1, h1 = relu(a1), a2 = W2 bf(h1) + b2, h2 = relu(a2),
+//             y = b3 + bf(w3) . bf(h2)   (x, W1, W2 as bf16; FP32 sums)
+//   backward  dy = 2 (y - t) / n, dh2 = relu'(a2) dy bf(w3),
+//             dh1 = relu'(a1) (bf(W2)^T bf(dh2)), dx = bf(W1)^T bf(dh1)
+//   weights   gW2 = sum_m bf(dh2) bf(h1)^T and gW1 = sum_m bf(dh1) bf(x)^T as MMAs
+//             over the tile's samples (A and B read transposed from shared
+//             memory by ldmatrix.trans); gb1, gb2, gw3, gb3 in FP32.
+// Weight gradients accumulate in registers over all of a warp's tiles; the
+// block adds its warps in order and writes one partial (k_sum_parts adds the
+// blocks in order), so a run is bit-reproducible on a device.
+constexpr int kTcWarps = 4;
+constexpr int kTileWords = 256;                  // 16 rows x 16 words (bf16 pairs), swizzled
+constexpr int kNetFrags = 30;                    // fwd W1 (8), fwd W2 (8), bwd W2 (8), bwd W1 (6)
+constexpr size_t kTcSmem = (size_t)kNetFrags * 32 * 8 + 4 * (2 * kMlpHid + kMlpHid + 4) +
+                           (size_t)kTcWarps * (4 * kTileWords * 4 + 16 * 4) + (size_t)kTcWarps * kPart * 4;
 
-// samples given explicitly: n rows of 19 inputs and their targets
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const uint32_t* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// the 16-byte chunk c of row r of a swizzled tile
+__device__ __forceinline__ const uint32_t* tile_chunk(const uint32_t* tile, int r, int c)
+{
+    return tile + r * 16 + (((c ^ (r >> 1)) & 3) << 2);
+}
+
+__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// backward B fragments: bf(W2) as B[i][k] (f = s*4 + j: i = 16s.., k = 8j + g),
+// bf(W1) as B[i][c] over the row columns c (f = s*3 + j: c = 8j + g, zero past 18)
+__device__ __forceinline__ uint2 bwd_frag(const float* __restrict__ p, int f, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    float e[4];
+    if (f < 8) {
+        const int s = f >> 2, j = f & 3, k = 8 * j + g;
+        const int is[4] = {16 * s + 2 * t, 16 * s + 2 * t + 1, 16 * s + 2 * t + 8, 16 * s + 2 * t + 9};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = p[kOffW2 + is[q] * kMlpHid + k];
+    } else {
+        const int ff = f - 8, s = ff / 3, j = ff % 3, c = w1_column(8 * j + g);
+        const int is[4] = {16 * s + 2 * t, 16 * s + 2 * t + 1, 16 * s + 2 * t + 8, 16 * s + 2 * t + 9};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = c >= 0 ? p[kOffW1 + is[q] * kMlpIn + c] : 0.0f;
+    }
+    return make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
+}
+
+// samples given explicitly: n rows of 19 inputs (u, v, w, z) and their targets;
+// a tile is 16 consecutive samples
 struct ExplicitSamples {
     static constexpr bool kLeaf = false;
     const float* X;
     const float* T;
-    __device__ __forceinline__ float get(long long q, float* row) const
+    long long n;
+    // lane (r = lane >> 1, h = lane & 1) writes half of row r of the tile (the
+    // latent columns for h = 0, the position columns for h = 1); returns the
+    // row's target to the h = 1 lane
+    __device__ __forceinline__ float row(long long tile, int r, int h, uint32_t* xt) const
     {
-        const float* p = X + q * kMlpIn;
+        const long long q = tile * 16 + r;
+        uint4* rp = reinterpret_cast<uint4*>(xt) + r * 4;
+        const int sw = (r >> 1) & 3;
+        const bool ok = q < n;
+        const float* x = X + q * kMlpIn;
+        if (h == 0) {
+            uint32_t w[8];
 #pragma unroll
-        for (int c = 0; c < 5; ++c)
-            st4(row + 4 * c, __ldg(p + 4 * c), __ldg(p + 4 * c + 1), __ldg(p + 4 * c + 2),
-                4 * c + 3 < kMlpIn ? __ldg(p + 4 * c + 3) : 0.0f);
-        return __ldg(T + q);
+            for (int k = 0; k < 8; ++k) w[k] = ok ? pack_bf16(__ldg(x + 3 + 2 * k), __ldg(x + 4 + 2 * k)) : 0u;
+            rp[0 ^ sw] = make_uint4(w[0], w[1], w[2], w[3]);
+            rp[1 ^ sw] = make_uint4(w[4], w[5], w[6], w[7]);
+            return 0.0f;
+        }
+        rp[2 ^ sw] = make_uint4(ok ? pack_bf16(__ldg(x), __ldg(x + 1)) : 0u, ok ? pack_bf16(__ldg(x + 2), 0.0f) : 0u, 0u, 0u);
+        rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+        return ok ? __ldg(T + q) : 0.0f;
     }
 };
 
-// samples drawn from the leaves: sample q = s-th voxel of training leaf q / S
+// samples drawn from the leaves: sample s of training leaf a is voxel
+// s*(512/S) + (r mod 512/S) of it; a warp's task is one leaf (S/16 tiles)
 struct LeafSamples {
     static constexpr bool kLeaf = true;
     GridView src;
@@ -170,291 +231,341 @@ struct LeafSamples {
     const float* lat;          // leaf -> FP32 latent (16)
     int lg_s;                  // log2 S
     uint32_t step, k0, k1;
-    __device__ __forceinline__ float get(long long q, float* row) const
+    __device__ __forceinline__ float row(uint32_t leaf, int s, int r, int h, uint32_t* xt) const
     {
-        const uint32_t leaf = __ldg(list + (q >> lg_s));
-        const int s = (int)(q & ((1 << lg_s) - 1));
+        uint4* rp = reinterpret_cast<uint4*>(xt) + r * 4;
+        const int sw = (r >> 1) & 3;
+        if (h == 0) {
+            const float4* L = reinterpret_cast<const float4*>(lat + (size_t)leaf * kMlpLatent);
+            const float4 z0 = __ldg(L), z1 = __ldg(L + 1), z2 = __ldg(L + 2), z3 = __ldg(L + 3);
+            rp[0 ^ sw] = make_uint4(pack_bf16(z0.x, z0.y), pack_bf16(z0.z, z0.w), pack_bf16(z1.x, z1.y), pack_bf16(z1.z, z1.w));
+            rp[1 ^ sw] = make_uint4(pack_bf16(z2.x, z2.y), pack_bf16(z2.z, z2.w), pack_bf16(z3.x, z3.y), pack_bf16(z3.z, z3.w));
+            return 0.0f;
+        }
         const int stratum = kLeafN >> lg_s;
-        U4 r = philox4x32_10(__ldg(pos + leaf), step, (uint32_t)s, kDrawTag, k0, k1);
-        const int n = s * stratum + (int)(r.x & (uint32_t)(stratum - 1));
+        const U4 rr = philox4x32_10(__ldg(pos + leaf), step, (uint32_t)s, kDrawTag, k0, k1);
+        const int nv = s * stratum + (int)(rr.x & (uint32_t)(stratum - 1));
         const float2 sm = src.payload != 0 ? __ldg(src.meta + leaf) : make_float2(0.f, 0.f);
-        const float v = leaf_value_t<-1>(src, leaf, n, sm);
+        const float v = leaf_value_t<-1>(src, leaf, nv, sm);
         const float2 lm = __ldg(lmeta + leaf);
-        const float4* L = reinterpret_cast<const float4*>(lat + (size_t)leaf * kMlpLatent);
-        const float4 z0 = __ldg(L), z1 = __ldg(L + 1), z2 = __ldg(L + 2), z3 = __ldg(L + 3);
-        st4(row, __fdiv_rn((float)(n & 7), 7.0f), __fdiv_rn((float)((n >> 3) & 7), 7.0f),
-            __fdiv_rn((float)(n >> 6), 7.0f), z0.x);
-        st4(row + 4, z0.y, z0.z, z0.w, z1.x);
-        st4(row + 8, z1.y, z1.z, z1.w, z2.x);
-        st4(row + 12, z2.y, z2.z, z2.w, z3.x);
-        st4(row + 16, z3.y, z3.z, z3.w, 0.0f);
+        const float u = __fdiv_rn((float)(nv & 7), 7.0f), vv = __fdiv_rn((float)((nv >> 3) & 7), 7.0f),
+                    w = __fdiv_rn((float)(nv >> 6), 7.0f);
+        rp[2 ^ sw] = make_uint4(pack_bf16(u, vv), pack_bf16(w, 0.0f), 0u, 0u);
+        rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
         return lm.x != 0.0f ? __fdiv_rn(__fsub_rn(v, lm.y), lm.x) : 0.0f;
     }
 };
 
-// Forward and backward of kTrainThreads samples per tile, one sample per
-// thread; the weight gradients are reduced over the tile in shared memory by
-// thread-owned groups of four entries, in a fixed order, and each block
-// writes one partial gradient (summed by k_sum_parts, again in fixed order),
-// so a run is bit-reproducible on a given device.  Explicit samples write
-// their input gradients to gx[q * 19 + k]; leaf samples sum the latent part
-// over each leaf's S samples (S divides the tile) into gx[leaf * 16 + c].
+// a warp's gradient accumulators (per lane)
+struct TcAcc {
+    float gw2[2][4][4];    // gW2 [m-tile of i][n-tile of k][frag]
+    float gw1[2][3][4];    // gW1 [m-tile of i][n-tile of row column][frag]
+    float gb1[4][2], gb2[4][2], gw3[4][2];   // columns 8j + 2t (+1), summed over this lane's rows
+    float gb3;
+    double loss;
+};
+
+// one tile through the network and back: xt holds the 16 input rows, tg the
+// targets of the lane's rows g and g + 8, val their validity; adds to acc,
+// returns the latent-column input gradients of rows g and g + 8 in dz
+// (columns 8j + 2t (+1), j = 0, 1) and, when `full`, the position columns in dx3
+template <bool kFull>
+__device__ __forceinline__ void tc_tile(const uint32_t* xt, uint32_t* h1t, uint32_t* dh2t, uint32_t* dh1t,
+                                        const uint2* fr, const float* b1s, const float* b2s, const float* w3s,
+                                        float b3, float tg0, float tg1, bool val0, bool val1, float inv_n, TcAcc& A,
+                                        float dz[2][4], float dx3[4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t a[2][4];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        a[s][0] = xt[tile_word(g, s * 8 + t)];
+        a[s][1] = xt[tile_word(g + 8, s * 8 + t)];
+        a[s][2] = xt[tile_word(g, s * 8 + 4 + t)];
+        a[s][3] = xt[tile_word(g + 8, s * 8 + 4 + t)];
+    }
+    // layer 1
+    float c[4][4];
+    unsigned m1 = 0, m2 = 0;           // relu' masks, bit j*4 + q
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) mma_bf16_16816(c[j], a[s], fr[(s * 4 + j) * 32 + lane]);
+        const float bb0 = b1s[8 * j + 2 * t], bb1 = b1s[8 * j + 2 * t + 1];
+        c[j][0] = __fadd_rn(c[j][0], bb0); c[j][1] = __fadd_rn(c[j][1], bb1);
+        c[j][2] = __fadd_rn(c[j][2], bb0); c[j][3] = __fadd_rn(c[j][3], bb1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c[j][q] > 0.0f) m1 |= 1u << (j * 4 + q); else c[j][q] = 0.0f;
+        }
+        h1t[tile_word(g, 4 * j + t)] = pack_bf16(c[j][0], c[j][1]);
+        h1t[tile_word(g + 8, 4 * j + t)] = pack_bf16(c[j][2], c[j][3]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        a[s][0] = pack_bf16(c[2 * s][0], c[2 * s][1]);
+        a[s][1] = pack_bf16(c[2 * s][2], c[2 * s][3]);
+        a[s][2] = pack_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
+        a[s][3] = pack_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
+    }
+    // layer 2 and the output
+    float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) mma_bf16_16816(c[j], a[s], fr[(8 + s * 4 + j) * 32 + lane]);
+        const float bb0 = b2s[8 * j + 2 * t], bb1 = b2s[8 * j + 2 * t + 1];
+        c[j][0] = __fadd_rn(c[j][0], bb0); c[j][1] = __fadd_rn(c[j][1], bb1);
+        c[j][2] = __fadd_rn(c[j][2], bb0); c[j][3] = __fadd_rn(c[j][3], bb1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c[j][q] > 0.0f) { m2 |= 1u << (j * 4 + q); c[j][q] = bfr(c[j][q]); } else c[j][q] = 0.0f;
+        }
+        const float w0 = w3s[8 * j + 2 * t], w1 = w3s[8 * j + 2 * t + 1];
+        y0 = fmaf(w0, c[j][0], y0); y0 = fmaf(w1, c[j][1], y0);
+        y1 = fmaf(w0, c[j][2], y1); y1 = fmaf(w1, c[j][3], y1);
+    }
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 1); y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 1); y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+    const float e0 = val0 ? __fadd_rn(y0, b3) - tg0 : 0.0f, e1 = val1 ? __fadd_rn(y1, b3) - tg1 : 0.0f;
+    if (t == 0) A.loss += (double)e0 * e0 + (double)e1 * e1;
+    const float dy0 = 2.0f * e0 * inv_n, dy1 = 2.0f * e1 * inv_n;
+    if (t == 0) A.gb3 += dy0 + dy1;
+    // dh2 = relu'(a2) dy bf(w3); gw3 += dy bf(h2); gb2 += dh2
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float w0 = w3s[8 * j + 2 * t], w1 = w3s[8 * j + 2 * t + 1];
+        A.gw3[j][0] += dy0 * c[j][0] + dy1 * c[j][2];
+        A.gw3[j][1] += dy0 * c[j][1] + dy1 * c[j][3];
+        c[j][0] = (m2 >> (j * 4 + 0)) & 1u ? dy0 * w0 : 0.0f;
+        c[j][1] = (m2 >> (j * 4 + 1)) & 1u ? dy0 * w1 : 0.0f;
+        c[j][2] = (m2 >> (j * 4 + 2)) & 1u ? dy1 * w0 : 0.0f;
+        c[j][3] = (m2 >> (j * 4 + 3)) & 1u ? dy1 * w1 : 0.0f;
+        A.gb2[j][0] += c[j][0] + c[j][2];
+        A.gb2[j][1] += c[j][1] + c[j][3];
+        dh2t[tile_word(g, 4 * j + t)] = pack_bf16(c[j][0], c[j][1]);
+        dh2t[tile_word(g + 8, 4 * j + t)] = pack_bf16(c[j][2], c[j][3]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        a[s][0] = pack_bf16(c[2 * s][0], c[2 * s][1]);
+        a[s][1] = pack_bf16(c[2 * s][2], c[2 * s][3]);
+        a[s][2] = pack_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
+        a[s][3] = pack_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
+    }
+    // dh1 = relu'(a1) (bf(W2)^T bf(dh2)); gb1 += dh1
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) mma_bf16_16816(c[j], a[s], fr[(16 + s * 4 + j) * 32 + lane]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (!((m1 >> (j * 4 + q)) & 1u)) c[j][q] = 0.0f;
+        A.gb1[j][0] += c[j][0] + c[j][2];
+        A.gb1[j][1] += c[j][1] + c[j][3];
+        dh1t[tile_word(g, 4 * j + t)] = pack_bf16(c[j][0], c[j][1]);
+        dh1t[tile_word(g + 8, 4 * j + t)] = pack_bf16(c[j][2], c[j][3]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        a[s][0] = pack_bf16(c[2 * s][0], c[2 * s][1]);
+        a[s][1] = pack_bf16(c[2 * s][2], c[2 * s][3]);
+        a[s][2] = pack_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
+        a[s][3] = pack_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
+    }
+    // dx = bf(W1)^T bf(dh1): latent columns (n-tiles 0, 1), position columns (n-tile 2)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        dz[j][0] = dz[j][1] = dz[j][2] = dz[j][3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) mma_bf16_16816(dz[j], a[s], fr[(24 + s * 3 + j) * 32 + lane]);
+    }
+    if constexpr (kFull) {
+        dx3[0] = dx3[1] = dx3[2] = dx3[3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) mma_bf16_16816(dx3, a[s], fr[(24 + s * 3 + 2) * 32 + lane]);
+    }
+    __syncwarp();
+    // weight gradients over the tile's samples
+    const int q = lane >> 3, r = lane & 7;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+        uint32_t at2[4], at1[4];
+        ldsm_x4_trans(at2, tile_chunk(dh2t, ((q >> 1) << 3) + r, 2 * mi + (q & 1)));
+        ldsm_x4_trans(at1, tile_chunk(dh1t, ((q >> 1) << 3) + r, 2 * mi + (q & 1)));
+#pragma unroll
+        for (int nj = 0; nj < 4; nj += 2) {
+            uint32_t bh[4], bx[4];
+            ldsm_x4_trans(bh, tile_chunk(h1t, ((q & 1) << 3) + r, nj + (q >> 1)));
+            ldsm_x4_trans(bx, tile_chunk(xt, ((q & 1) << 3) + r, nj + (q >> 1)));
+            mma_bf16_16816(A.gw2[mi][nj], at2, make_uint2(bh[0], bh[1]));
+            mma_bf16_16816(A.gw2[mi][nj + 1], at2, make_uint2(bh[2], bh[3]));
+            mma_bf16_16816(A.gw1[mi][nj], at1, make_uint2(bx[0], bx[1]));
+            if (nj + 1 < 3) mma_bf16_16816(A.gw1[mi][nj + 1], at1, make_uint2(bx[2], bx[3]));
+        }
+    }
+    __syncwarp();
+}
+
 template <class Src>
-__global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(Src src, long long n, float inv_n,
+__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_grad(Src src, long long ntasks, float inv_n,
                                                             const float* __restrict__ params, float* __restrict__ part,
                                                             double* __restrict__ loss_part, float* __restrict__ gx)
 {
     extern __shared__ float4 s_f4[];
-    float* W1s = reinterpret_cast<float*>(s_f4);     // [32][20]
-    float* b1s = W1s + 32 * kXs;
-    float* W2s = b1s + 32;                           // [32][32]
-    float* b2s = W2s + 1024;
-    float* w3s = b2s + 32;
-    float* b3s = w3s + 32;                           // [4]
-    float* X = b3s + 4;                              // [128][20]
-    float* H1 = X + kTrainThreads * kXs;             // [128][36] each
-    float* H2 = H1 + kTrainThreads * kHs;
-    float* DH1 = H2 + kTrainThreads * kHs;
-    float* DH2 = DH1 + kTrainThreads * kHs;
-    float* DY = DH2 + kTrainThreads * kHs;           // [128]
-    const int tid = threadIdx.x;
-    for (int e = tid; e < 32 * kXs; e += blockDim.x) {
-        int i = e / kXs, k = e % kXs;
-        W1s[e] = k < kMlpIn ? params[kOffW1 + i * kMlpIn + k] : 0.0f;
+    uint2* fr = reinterpret_cast<uint2*>(s_f4);                       // [30][32]
+    float* b1s = reinterpret_cast<float*>(fr + kNetFrags * 32);
+    float* b2s = b1s + kMlpHid;
+    float* w3s = b2s + kMlpHid;                                       // bf16-rounded w3
+    float* b3s = w3s + kMlpHid;                                       // [4]
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(b3s + 4);           // [warps][4 tiles]
+    float* tgs = reinterpret_cast<float*>(tiles + kTcWarps * 4 * kTileWords);   // [warps][16]
+    float* red = tgs + kTcWarps * 16;                                 // [warps][kPart]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < kNetFrags * 32; i += blockDim.x) {
+        const int f = i >> 5, l = i & 31;
+        fr[i] = f < 16 ? mlp_frag(params, f, l) : bwd_frag(params, f - 16, l);
     }
-    for (int e = tid; e < 1024; e += blockDim.x) W2s[e] = params[kOffW2 + e];
-    for (int e = tid; e < 32; e += blockDim.x) {
-        b1s[e] = params[kOffB1 + e];
-        b2s[e] = params[kOffB2 + e];
-        w3s[e] = params[kOffW3 + e];
+    for (int i = tid; i < kMlpHid; i += blockDim.x) {
+        b1s[i] = params[kOffB1 + i];
+        b2s[i] = params[kOffB2 + i];
+        w3s[i] = bfr(params[kOffW3 + i]);
     }
-    if (tid < 4) b3s[tid] = tid == 0 ? params[kOffB3] : 0.0f;
+    if (tid == 0) b3s[0] = params[kOffB3];
     __syncthreads();
-
-    // owned gradient groups: W1 groups tid, tid+128 (< 160: row g/5, columns
-    // 4(g%5)..+3), W2 groups tid, tid+128 (row g/8, columns 4(g%8)..+3), and
-    // vector group tid (< 25: b1, b2, w3 in fours, then b3)
-    float4 aw1[2], aw2[2], av;
-    aw1[0] = aw1[1] = aw2[0] = aw2[1] = av = make_float4(0.f, 0.f, 0.f, 0.f);
-    double lacc = 0.0;
-    const long long ntiles = (n + kTrainThreads - 1) / kTrainThreads;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long q = tile * kTrainThreads + tid;
-        const bool valid = q < n;
-        // forward, one layer's vector live at a time: each layer's output
-        // goes to this thread's row in shared memory, four values at a time
-        float* xr = X + tid * kXs;
-        float* h1r = H1 + tid * kHs;
-        float* h2r = H2 + tid * kHs;
-        float tg = 0.0f;
-        if (valid) {
-            tg = src.get(q, xr);
-        } else {
+    const float b3 = b3s[0];
+    uint32_t* xt = tiles + wid * 4 * kTileWords;
+    uint32_t* h1t = xt + kTileWords;
+    uint32_t* dh2t = h1t + kTileWords;
+    uint32_t* dh1t = dh2t + kTileWords;
+    float* tg = tgs + wid * 16;
+    TcAcc A;
 #pragma unroll
-            for (int c = 0; c < 5; ++c) st4(xr + 4 * c, 0.f, 0.f, 0.f, 0.f);
-        }
-        float dx[kXs];
-        {
-            float x[kXs];
+    for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                float4 v = ld4(xr + 4 * c);
-                x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
-            }
+        for (int nj = 0; nj < 4; ++nj)
 #pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
-                float hv[4];
+            for (int k = 0; k < 4; ++k) { A.gw2[mi][nj][k] = 0.0f; if (nj < 3) A.gw1[mi][nj][k] = 0.0f; }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = 4 * i4 + j;
-                    float a = b1s[i];
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) {
-                        float4 ww = ld4(W1s + i * kXs + 4 * c);
-                        a = fmaf(ww.x, x[4 * c], a); a = fmaf(ww.y, x[4 * c + 1], a);
-                        a = fmaf(ww.z, x[4 * c + 2], a); a = fmaf(ww.w, x[4 * c + 3], a);
-                    }
-                    hv[j] = a > 0.0f ? a : 0.0f;
-                }
-                st4(h1r + 4 * i4, hv[0], hv[1], hv[2], hv[3]);
-            }
-        }
-        float dy;
-        asm volatile("" ::: "memory");
-        {
-            float h1[kMlpHid];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float4 v = ld4(h1r + 4 * c);
-                h1[4 * c] = v.x; h1[4 * c + 1] = v.y; h1[4 * c + 2] = v.z; h1[4 * c + 3] = v.w;
-            }
-            float y = b3s[0];
-#pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
-                float hv[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = 4 * i4 + j;
-                    float a = b2s[i];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        float4 ww = ld4(W2s + i * 32 + 4 * c);
-                        a = fmaf(ww.x, h1[4 * c], a); a = fmaf(ww.y, h1[4 * c + 1], a);
-                        a = fmaf(ww.z, h1[4 * c + 2], a); a = fmaf(ww.w, h1[4 * c + 3], a);
-                    }
-                    hv[j] = a > 0.0f ? a : 0.0f;
-                }
-                y = fmaf(w3s[4 * i4], hv[0], y); y = fmaf(w3s[4 * i4 + 1], hv[1], y);
-                y = fmaf(w3s[4 * i4 + 2], hv[2], y); y = fmaf(w3s[4 * i4 + 3], hv[3], y);
-                st4(h2r + 4 * i4, hv[0], hv[1], hv[2], hv[3]);
-            }
-            const float e = valid ? y - tg : 0.0f;
-            lacc += (double)e * (double)e;
-            dy = 2.0f * e * inv_n;
-        }
-        // backward: dh2 = relu'(h2) dy w3, dh1 = relu'(h1) W2^T dh2, dx = W1^T dh1.
-        // The compiler barrier makes the backward pass re-read the weights from
-        // shared memory instead of keeping the forward pass's 1.6k values live.
-        asm volatile("" ::: "memory");
-        {
-            float dh1[kMlpHid];
-#pragma unroll
-            for (int k = 0; k < kMlpHid; ++k) dh1[k] = 0.0f;
-#pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
-                const float4 hv = ld4(h2r + 4 * i4);
-                const float d[4] = {hv.x > 0.0f ? dy * w3s[4 * i4] : 0.0f, hv.y > 0.0f ? dy * w3s[4 * i4 + 1] : 0.0f,
-                                    hv.z > 0.0f ? dy * w3s[4 * i4 + 2] : 0.0f, hv.w > 0.0f ? dy * w3s[4 * i4 + 3] : 0.0f};
-                st4(DH2 + tid * kHs + 4 * i4, d[0], d[1], d[2], d[3]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        float4 ww = ld4(W2s + (4 * i4 + j) * 32 + 4 * c);
-                        dh1[4 * c] = fmaf(ww.x, d[j], dh1[4 * c]); dh1[4 * c + 1] = fmaf(ww.y, d[j], dh1[4 * c + 1]);
-                        dh1[4 * c + 2] = fmaf(ww.z, d[j], dh1[4 * c + 2]); dh1[4 * c + 3] = fmaf(ww.w, d[j], dh1[4 * c + 3]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float4 hv = ld4(h1r + 4 * c);
-                dh1[4 * c] = hv.x > 0.0f ? dh1[4 * c] : 0.0f; dh1[4 * c + 1] = hv.y > 0.0f ? dh1[4 * c + 1] : 0.0f;
-                dh1[4 * c + 2] = hv.z > 0.0f ? dh1[4 * c + 2] : 0.0f; dh1[4 * c + 3] = hv.w > 0.0f ? dh1[4 * c + 3] : 0.0f;
-                st4(DH1 + tid * kHs + 4 * c, dh1[4 * c], dh1[4 * c + 1], dh1[4 * c + 2], dh1[4 * c + 3]);
-            }
-#pragma unroll
-            for (int k = 0; k < kXs; ++k) dx[k] = 0.0f;
-            asm volatile("" ::: "memory");
-#pragma unroll
-            for (int i = 0; i < kMlpHid; ++i) {
-#pragma unroll
-                for (int c = 0; c < 5; ++c) {
-                    float4 ww = ld4(W1s + i * kXs + 4 * c);
-                    dx[4 * c] = fmaf(ww.x, dh1[i], dx[4 * c]); dx[4 * c + 1] = fmaf(ww.y, dh1[i], dx[4 * c + 1]);
-                    dx[4 * c + 2] = fmaf(ww.z, dh1[i], dx[4 * c + 2]); dx[4 * c + 3] = fmaf(ww.w, dh1[i], dx[4 * c + 3]);
-                }
-            }
-        }
-        DY[tid] = dy;
-        __syncthreads();
-        // weight gradients of the tile, samples in order
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int g1 = tid + h * kTrainThreads;
-            if (g1 < 160) {
-                const int i = g1 / 5, c = g1 % 5;
-                float4 a = aw1[h];
-                for (int s = 0; s < kTrainThreads; ++s) {
-                    const float d = DH1[s * kHs + i];
-                    const float4 xv = *reinterpret_cast<const float4*>(X + s * kXs + 4 * c);
-                    a.x = fmaf(d, xv.x, a.x); a.y = fmaf(d, xv.y, a.y); a.z = fmaf(d, xv.z, a.z); a.w = fmaf(d, xv.w, a.w);
-                }
-                aw1[h] = a;
-            }
-            const int g2 = tid + h * kTrainThreads;
-            {
-                const int i = g2 >> 3, c = g2 & 7;
-                float4 a = aw2[h];
-                for (int s = 0; s < kTrainThreads; ++s) {
-                    const float d = DH2[s * kHs + i];
-                    const float4 hv = *reinterpret_cast<const float4*>(H1 + s * kHs + 4 * c);
-                    a.x = fmaf(d, hv.x, a.x); a.y = fmaf(d, hv.y, a.y); a.z = fmaf(d, hv.z, a.z); a.w = fmaf(d, hv.w, a.w);
-                }
-                aw2[h] = a;
-            }
-        }
-        if (tid < 25) {
-            float4 a = av;
-            for (int s = 0; s < kTrainThreads; ++s) {
-                float4 v;
-                if (tid < 8) v = *reinterpret_cast<const float4*>(DH1 + s * kHs + 4 * tid);
-                else if (tid < 16) v = *reinterpret_cast<const float4*>(DH2 + s * kHs + 4 * (tid - 8));
-                else if (tid < 24) {
-                    const float d = DY[s];
-                    float4 hv = *reinterpret_cast<const float4*>(H2 + s * kHs + 4 * (tid - 16));
-                    v = make_float4(d * hv.x, d * hv.y, d * hv.z, d * hv.w);
-                } else {
-                    v = make_float4(DY[s], 0.f, 0.f, 0.f);
-                }
-                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
-            }
-            av = a;
-        }
-        __syncthreads();
+    for (int j = 0; j < 4; ++j) { A.gb1[j][0] = A.gb1[j][1] = A.gb2[j][0] = A.gb2[j][1] = A.gw3[j][0] = A.gw3[j][1] = 0.0f; }
+    A.gb3 = 0.0f;
+    A.loss = 0.0;
+    const int g = lane >> 2, t = lane & 3, rr = lane >> 1, hh = lane & 1;
+    const long long gw = (long long)blockIdx.x * kTcWarps + wid, nw = (long long)gridDim.x * kTcWarps;
+    for (long long task = gw; task < ntasks; task += nw) {
         if constexpr (Src::kLeaf) {
-            // latent gradient of each leaf of the tile: the sum over its S samples
-            float* DX = H2;
+            // a leaf: S / 16 tiles; its latent gradient sums over all of them
+            const uint32_t leaf = __ldg(src.list + task);
+            const int S = 1 << src.lg_s;
+            float zs[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+            for (int s0 = 0; s0 < S; s0 += 16) {
+                const float trow = src.row(leaf, s0 + rr, rr, hh, xt);
+                if (hh) tg[rr] = trow;
+                __syncwarp();
+                float dz[2][4], dx3[4];
+                tc_tile<false>(xt, h1t, dh2t, dh1t, fr, b1s, b2s, w3s, b3, tg[g], tg[g + 8], true, true, inv_n, A,
+                               dz, dx3);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) st4(DX + tid * kHs + 4 * c, dx[3 + 4 * c], dx[4 + 4 * c], dx[5 + 4 * c], dx[6 + 4 * c]);
-            __syncthreads();
-            const int S = 1 << src.lg_s, per = kTrainThreads >> src.lg_s;
-            if (tid < per * kMlpLatent) {
-                const int a = tid >> 4, c = tid & 15;
-                const long long first = tile * kTrainThreads + (long long)a * S;
-                if (first < n) {
-                    float sum = 0.0f;
-                    for (int s = 0; s < S; ++s) sum += DX[(a * S + s) * kHs + c];
-                    gx[(size_t)__ldg(src.list + (first >> src.lg_s)) * kMlpLatent + c] = sum;
+                for (int j = 0; j < 2; ++j) { zs[j][0] += dz[j][0] + dz[j][2]; zs[j][1] += dz[j][1] + dz[j][3]; }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) zs[j][k] += __shfl_xor_sync(0xffffffffu, zs[j][k], o);
+            if (g == 0) {
+                float* out = gx + (size_t)leaf * kMlpLatent;
+                out[2 * t] = zs[0][0]; out[2 * t + 1] = zs[0][1];
+                out[8 + 2 * t] = zs[1][0]; out[8 + 2 * t + 1] = zs[1][1];
+            }
+        } else {
+            const float trow = src.row(task, rr, hh, xt);
+            if (hh) tg[rr] = trow;
+            __syncwarp();
+            const long long q0 = task * 16 + g, q1 = q0 + 8;
+            float dz[2][4], dx3[4];
+            tc_tile<true>(xt, h1t, dh2t, dh1t, fr, b1s, b2s, w3s, b3, tg[g], tg[g + 8], q0 < src.n, q1 < src.n, inv_n, A,
+                          dz, dx3);
+            if (gx) {
+                // row column c = 8j + 2t (+1): latent z_c (j < 2) or position c - 16 (j = 2)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float* v = j < 2 ? dz[j] : dx3;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int col = w1_column(8 * j + 2 * t + k);
+                        if (col < 0) continue;
+                        if (q0 < src.n) gx[q0 * kMlpIn + col] = v[k];
+                        if (q1 < src.n) gx[q1 * kMlpIn + col] = v[2 + k];
+                    }
                 }
             }
-            __syncthreads();
-        } else {
-            if (valid && gx) {
+        }
+    }
+    // the warp's gradient to shared memory in parameter order, then the warps in order
+    float* R = red + wid * kPart;
 #pragma unroll
-                for (int k = 0; k < kMlpIn; ++k) gx[q * kMlpIn + k] = dx[k];
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) {
+            const int i0 = 16 * mi + g, k0 = 8 * nj + 2 * t;
+            R[kOffW2 + i0 * kMlpHid + k0] = A.gw2[mi][nj][0];
+            R[kOffW2 + i0 * kMlpHid + k0 + 1] = A.gw2[mi][nj][1];
+            R[kOffW2 + (i0 + 8) * kMlpHid + k0] = A.gw2[mi][nj][2];
+            R[kOffW2 + (i0 + 8) * kMlpHid + k0 + 1] = A.gw2[mi][nj][3];
+            if (nj < 3) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int col = w1_column(8 * nj + 2 * t + k);
+                    if (col < 0) continue;
+                    R[kOffW1 + i0 * kMlpIn + col] = A.gw1[mi][nj][k];
+                    R[kOffW1 + (i0 + 8) * kMlpIn + col] = A.gw1[mi][nj][2 + k];
+                }
             }
         }
-    }
-    // this block's partial gradient, in parameter order
-    float* P = part + (size_t)blockIdx.x * kPart;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int g1 = tid + h * kTrainThreads;
-        if (g1 < 160) {
-            const int i = g1 / 5, c = g1 % 5;
-            const float v[4] = {aw1[h].x, aw1[h].y, aw1[h].z, aw1[h].w};
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (4 * c + j < kMlpIn) P[kOffW1 + i * kMlpIn + 4 * c + j] = v[j];
+        for (int k = 0; k < 2; ++k) {
+            float v1 = A.gb1[j][k], v2 = A.gb2[j][k], v3 = A.gw3[j][k];
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+            }
+            if (g == 0) {
+                R[kOffB1 + 8 * j + 2 * t + k] = v1;
+                R[kOffB2 + 8 * j + 2 * t + k] = v2;
+                R[kOffW3 + 8 * j + 2 * t + k] = v3;
+            }
         }
-        const int g2 = tid + h * kTrainThreads;
-        const int i = g2 >> 3, c = g2 & 7;
-        st4(P + kOffW2 + i * 32 + 4 * c, aw2[h].x, aw2[h].y, aw2[h].z, aw2[h].w);
+    float gb3 = A.gb3;
+    double ls = A.loss;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
+        ls += __shfl_xor_sync(0xffffffffu, ls, o);
     }
-    if (tid < 8) st4(P + kOffB1 + 4 * tid, av.x, av.y, av.z, av.w);
-    else if (tid < 16) st4(P + kOffB2 + 4 * (tid - 8), av.x, av.y, av.z, av.w);
-    else if (tid < 24) st4(P + kOffW3 + 4 * (tid - 16), av.x, av.y, av.z, av.w);
-    else if (tid == 24) P[kOffB3] = av.x;
-    // loss partial: warp sums, then the warps in order
-    __shared__ double s_loss[kTrainThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
-    if ((tid & 31) == 0) s_loss[tid >> 5] = lacc;
+    if (lane == 0) R[kOffB3] = gb3;
+    __shared__ double s_loss[kTcWarps];
+    if (lane == 0) s_loss[wid] = ls;
     __syncthreads();
+    float* P = part + (size_t)blockIdx.x * kPart;
+    for (int e = tid; e < kMlpParams; e += blockDim.x) {
+        float v = red[e];
+#pragma unroll
+        for (int w = 1; w < kTcWarps; ++w) v += red[w * kPart + e];
+        P[e] = v;
+    }
     if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kTrainThreads / 32; ++w) t += s_loss[w];
-        loss_part[blockIdx.x] = t;
+        double l = 0.0;
+        for (int w = 0; w < kTcWarps; ++w) l += s_loss[w];
+        loss_part[blockIdx.x] = l;
     }
 }
 
@@ -673,30 +784,34 @@ struct Pool {
 
 // gradient of the loss over n explicit or drawn samples into grad (and the
 // loss, if asked); part / loss_part hold grid partials
+// gradient of the loss over n samples (ntasks warp tasks) into grad, and the
+// loss if asked; part / loss_part hold the grid's partials
 template <class Src>
-vdbc_status run_grad(const Src& src, long long n, const float* params, float* part, double* loss_part, int grid,
-                     float* grad, double* loss, float* gx, cudaStream_t s)
+vdbc_status run_grad(const Src& src, long long ntasks, long long n, const float* params, float* part,
+                     double* loss_part, int grid, float* grad, double* loss, float* gx, cudaStream_t s)
 {
     auto kern = k_mlp_grad<Src>;
-    VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
-    KLAUNCH(kern<<<grid, kTrainThreads, kTrainSmem, s>>>(src, n, (float)(1.0 / (double)n), params, part, loss_part, gx));
+    VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+    KLAUNCH(kern<<<grid, kTcWarps * 32, kTcSmem, s>>>(src, ntasks, (float)(1.0 / (double)n), params, part, loss_part,
+                                                      gx));
     KLAUNCH(k_sum_parts<<<blocks(kMlpParams, 256), 256, 0, s>>>(part, grid, grad, loss_part, 1.0 / (double)n, loss));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
 
-int grad_grid(long long n)
+// blocks of the training kernel for ntasks warp tasks: at most one wave
+int grad_grid(long long ntasks)
 {
     static int per_sm = -1;
     if (per_sm < 0) {
         auto kern = k_mlp_grad<LeafSamples>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTrainThreads, kTrainSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcWarps * 32, kTcSmem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
-    long long tiles = (n + kTrainThreads - 1) / kTrainThreads;
-    return (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count_dev() * per_sm));
+    long long need = (ntasks + kTcWarps - 1) / kTcWarps;
+    return (int)std::max<long long>(1, std::min<long long>(need, (long long)sm_count_dev() * per_sm));
 }
 
 }  // namespace
@@ -826,14 +941,14 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     }
     const long long nsamp = (long long)n_train << lg_s;
     if (lp->steps > 0 && nsamp > 0) {
-        const int grid = grad_grid(nsamp);
+        const int grid = grad_grid((long long)n_train);
         VDBC_TRY(pool.get(&part, (size_t)grid * kPart));
         VDBC_TRY(pool.get(&loss_part, grid));
         VDBC_TRY(pool.get(&loss_hist, lp->steps));
         LeafSamples ls{src->view, list, pos, lmeta, lat, lg_s, 0u, k0, k1};
         for (int t = 0; t < lp->steps; ++t) {
             ls.step = (uint32_t)t;
-            VDBC_TRY(run_grad(ls, nsamp, params, part, loss_part, grid, grad, loss_hist + t, glat, s));
+            VDBC_TRY(run_grad(ls, (long long)n_train, nsamp, params, part, loss_part, grid, grad, loss_hist + t, glat, s));
             const float c1 = (float)(1.0 - std::pow((double)kBeta1, (double)(t + 1)));
             const float c2 = (float)(1.0 - std::pow((double)kBeta2, (double)(t + 1)));
             KLAUNCH(k_adam<<<blocks(kMlpParams, 256), 256, 0, s>>>(params, grad, pm, pv, kMlpParams, lp->lr, c1, c2));
@@ -962,14 +1077,15 @@ extern "C" vdbc_status vdbc_learn_loss_grad(const float* params, const float* in
     if (n < 1 || n > ((int64_t)1 << 31)) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn_loss_grad: n %lld outside 1..2^31", (long long)n);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pool pool(s);
-    const int grid = grad_grid(n);
+    const long long ntiles = (n + 15) / 16;
+    const int grid = grad_grid(ntiles);
     float* part = nullptr;
     double *loss_part = nullptr, *dloss = nullptr;
     VDBC_TRY(pool.get(&part, (size_t)grid * kPart));
     VDBC_TRY(pool.get(&loss_part, grid));
     VDBC_TRY(pool.get(&dloss, 1));
-    ExplicitSamples es{inputs, targets};
-    VDBC_TRY(run_grad(es, n, params, part, loss_part, grid, grad_params, dloss, grad_inputs, s));
+    ExplicitSamples es{inputs, targets, (long long)n};
+    VDBC_TRY(run_grad(es, ntiles, (long long)n, params, part, loss_part, grid, grad_params, dloss, grad_inputs, s));
     double h = 0.0;
     VDBC_CUDA(cudaMemcpyAsync(&h, dloss, 8, cudaMemcpyDeviceToHost, s));
     VDBC_TRY(wait_stream(s));

@@ -1,17 +1,21 @@
 """The learned leaf codec on the GPU (a project extension; the paper's
 Section 2.3 names network-decoded leaves as related work only).
 
-Checked here: the FP32 training kernels' loss and gradients against the FP64
-oracle; one whole training step (Philox draws, targets, gradients, Adam)
-against the oracle replaying it; learned grids decoded on the tensor cores
+Checked here: the tensor-core training kernels' loss and gradients against
+the oracle's gradient at the same precision (bf16 operands, exact sums); one
+whole training step (Philox draws, targets, gradients, Adam) against the
+oracle replaying it; learned grids decoded on the tensor cores
 against the oracle's bf16-precision decode; renders of learned grids against
 the plain-form render of their decoded values (bit-exact) and against the
 FP64 oracle; save/load; and what the trained network gains over the method
 without it at equal memory.
 
-Tolerances.  Training: FP32 sums of at most a few thousand terms against
-FP64, relative error of a sum below n * 2^-24 of the sum of magnitudes, so
-1e-4 of the largest gradient entry.  Decode: both sides round the operands
+Tolerances.  Training: the kernels round the same operands to bf16 as the
+oracle and sum in FP32 (the oracle exactly); a sum of up to a few thousand
+terms is within n * 2^-24 of the sum of magnitudes, and an FP32 value that
+lands on the other side of a bf16 rounding boundary moves one sample's
+backward operand by 2^-8, so parameter gradients agree to 2e-3 of the
+largest entry and per-sample input gradients on 99 % of the samples.  Decode: both sides round the operands
 and the hidden activations to bf16, but the tensor cores accumulate in FP32
 and the oracle exactly; an activation whose FP32 sum lands on the other side
 of a bf16 rounding boundary would move y by about |w| * 2^-8 * |h| (1e-3 of
@@ -91,11 +95,12 @@ def test_loss_grad_matches_oracle(env, n):
     gx = torch.zeros(n, 19, device=dev)
     loss = v.vdbc_learn_loss_grad(torch.from_numpy(p).to(dev), torch.from_numpy(x).to(dev),
                                   torch.from_numpy(t).to(dev), gp, gx)
-    rl, rp, rx = orc.mlp_loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    rl, rp, rx = orc.mlp_loss_grad_bf16(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
     assert abs(loss - rl) <= 1e-5 * rl
     gp, gx = gp.cpu().numpy(), gx.cpu().numpy()
-    assert np.max(np.abs(gp - rp)) <= 1e-4 * np.max(np.abs(rp))
-    assert np.max(np.abs(gx - rx)) <= 1e-4 * np.max(np.abs(rx))
+    assert np.max(np.abs(gp - rp)) <= 2e-3 * np.max(np.abs(rp))
+    far = np.abs(gx - rx).max(axis=1) > 2e-3 * np.max(np.abs(rx))
+    assert far.mean() <= 0.01 + 1.0 / n
 
 
 def test_one_training_step_matches_oracle(env):
@@ -134,7 +139,7 @@ def test_one_training_step_matches_oracle(env):
                     T.append(float(tgt))
     X, T = np.array(X), np.array(T)
     assert len(T) == S * tree.counts()["leaves"]
-    rl, rg, _ = orc.mlp_loss_grad(p0.astype(np.float64), X, T)
+    rl, rg, _ = orc.mlp_loss_grad_bf16(p0.astype(np.float64), X, T)
     assert abs(losses[0] - rl) <= 1e-5 * rl
     ref = p0.astype(np.float64)
     m, vv = np.zeros_like(ref), np.zeros_like(ref)
