@@ -145,10 +145,18 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the tracker's sources with comments and
+    blank lines removed: the code the ncu counters were taken on."""
+    import re
+
     h = hashlib.sha256()
     for f in ("render.cu", "vdbc_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2504_04564_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2504_04564_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,18 +3,24 @@
 //
 //   k_ea  emission-absorption marching, fixed step, front to back; one
 //         thread per pixel (the project's sci-vis mode)
+//   k_iso the implicit ISO-surface marcher (Section 5's ZFP comparison), with
+//         interval skipping over the macrocell ranges
 //   k_pt  Monte Carlo path tracing: 3D-DDA over the macrocell majorant grid
-//         (with a coarse occupancy level that crosses empty 8^3 blocks of
-//         macrocells in one step), Woodcock (delta) tracking with one optical
-//         depth per free flight carried across the non-empty cells (the
-//         free-path sampling of Szirmay-Kalos et al. 2011 that Section 4 cites),
-//         Henyey-Greenstein scattering, the directional light's transmittance
-//         by ratio tracking, a constant environment on escape.  Persistent
-//         lanes each carry one path and fetch the next when it ends; path
-//         radiance is averaged per pixel in sample order by k_pt_reduce.
-// Both are templated on the sampler: VdbSamplerT<payload> (tree descent + leaf
-// decode + trilinear, every lookup), LinearSampler (dense array, the same
-// software trilinear) and TexSampler (3D CUDA texture, hardware trilinear).
+//         (optionally with a coarse occupancy level that crosses empty 8^3
+//         blocks of macrocells in one step, a compile-time variant), Woodcock
+//         (delta) tracking with one optical depth per free flight carried
+//         across the non-empty cells (the free-path sampling of Szirmay-Kalos
+//         et al. 2011 that Section 4 cites), Henyey-Greenstein scattering, the
+//         directional light's transmittance by ratio tracking, a constant
+//         environment on escape.  Persistent lanes each carry one path and
+//         fetch the next when it ends; path radiance is averaged per pixel in
+//         sample order by k_pt_reduce.  k_pt_batch runs the same loop over
+//         many jobs (grids, cameras, media) in one launch.
+// All are templated on the sampler: VdbSamplerT<payload> (tree descent + leaf
+// decode + trilinear, every lookup), LearnedSampler (the same, with neural
+// leaves decoded by the network in warp-wide tensor-core tiles), LinearSampler
+// (dense array, the same software trilinear) and TexSampler (3D CUDA texture,
+// hardware trilinear).
 //
 // Random numbers: Philox4x32-10, counter (pixel, sample, call, stream), key =
 // seed; stream 0 for the camera and the walk, 1 for the light rays; one call
