@@ -83,17 +83,33 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
     const bool valid = lane < ex;
     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     const int rows = ey * ez;
-    for (int row = warp; row < rows; row += kPass1Threads / 32) {
-        if (valid) {
-            const int y = row % ey, z = row / ey;
-            const uint32_t w = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
-            bad |= ((w & 0x7f800000u) == 0x7f800000u);
-            const uint32_t k = okey(w);
-            kmin = min(kmin, k);
-            kmax = max(kmax, k);
-            const uint32_t key = w >> 16;
-            const unsigned peers = __match_any_sync(vmask, key);
-            if (lane == __ffs(peers) - 1) atomicAdd(s_hist + (key >> 1), (uint32_t)__popc(peers) << ((key & 1u) * 16));
+    // four rows' loads in flight per warp before any of them is used
+    constexpr int U = 4, kWarps = kPass1Threads / 32;
+    for (int r0 = warp; r0 < rows; r0 += kWarps * U) {
+        uint32_t u[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int row = r0 + q * kWarps;
+            u[q] = 0u;
+            if (valid && row < rows) {
+                const int y = row % ey, z = row / ey;
+                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (r0 + q * kWarps >= rows) break;       // warp-uniform
+            if (valid) {
+                const uint32_t w = u[q];
+                bad |= ((w & 0x7f800000u) == 0x7f800000u);
+                const uint32_t k = okey(w);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+                const uint32_t key = w >> 16;
+                const unsigned peers = __match_any_sync(vmask, key);
+                if (lane == __ffs(peers) - 1)
+                    atomicAdd(s_hist + (key >> 1), (uint32_t)__popc(peers) << ((key & 1u) * 16));
+            }
         }
     }
     kmin = __reduce_min_sync(0xffffffffu, kmin);
@@ -687,6 +703,51 @@ __global__ void __launch_bounds__(kGroup == 32 ? 256 : kGroup)
     if (lane == 0) { mcmin[c] = vmin; mcmax[c] = vmax; }
 }
 
+// Macrocell ranges of an FP32 grid straight from the input: the decoded grid
+// is V in the activated bricks and at the two corner voxels and B elsewhere
+// (its definition), so no tree descent is needed; one block per macrocell,
+// the input read only where a brick is active.  Same values, same ranges as
+// k_macrocells on the tree.
+__global__ void __launch_bounds__(256) k_macrocells_input(const float* __restrict__ v, Dims d,
+                                                          const uint8_t* __restrict__ active,
+                                                          const uint32_t* __restrict__ bsel, int mc, int mx, int my,
+                                                          float* __restrict__ mcmin, float* __restrict__ mcmax)
+{
+    __shared__ float s_lo[8], s_hi[8];
+    const long long c = blockIdx.x;
+    const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
+    const int x0 = max(cx * mc - 1, 0), x1 = min(cx * mc + mc, d.nx - 1);
+    const int y0 = max(cy * mc - 1, 0), y1 = min(cy * mc + mc, d.ny - 1);
+    const int z0 = max(cz * mc - 1, 0), z1 = min(cz * mc + mc, d.nz - 1);
+    const float B = __uint_as_float(bsel[1]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ex = x1 - x0 + 1, ey = y1 - y0 + 1, rows = ey * (z1 - z0 + 1);
+    float vmin = INFINITY, vmax = -INFINITY;
+    for (int row = warp; row < rows; row += 8) {
+        const int y = y0 + row % ey, z = z0 + row / ey;
+        const size_t base = ((size_t)z * d.ny + y) * d.nx;
+        const int brow = ((z >> 5) * d.by + (y >> 5)) * d.bx;
+        for (int xi = lane; xi < ex; xi += 32) {
+            const int x = x0 + xi;
+            const bool corner = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
+            const float val = (corner || __ldg(active + brow + (x >> 5))) ? __ldg(v + base + x) : B;
+            vmin = fminf(vmin, val);
+            vmax = fmaxf(vmax, val);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if (lane == 0) { s_lo[warp] = vmin; s_hi[warp] = vmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) { vmin = fminf(vmin, s_lo[w]); vmax = fmaxf(vmax, s_hi[w]); }
+        mcmin[c] = vmin;
+        mcmax[c] = vmax;
+    }
+}
+
 // full decode, one thread per voxel (tests and the decode entry point)
 __global__ void k_decode(GridView g, float* __restrict__ out, long long n)
 {
@@ -1021,7 +1082,18 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
                                                         reinterpret_cast<float2*>(base + g->off_meta)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: tree kernels"); }
-    st = build_macrocells(g, s);
+    if (payload == VDBC_FP32) {
+        // FP32 leaves hold the input's values: the ranges come from the input itself
+        const GridView& gv = g->view;
+        const long long ncell = (long long)gv.mx * gv.my * gv.mz;
+        KLAUNCH(k_macrocells_input<<<(unsigned)ncell, 256, 0, s>>>(
+            vol, d, active, bsel, gv.mc, gv.mx, gv.my, reinterpret_cast<float*>(base + g->off_mcmin),
+            reinterpret_cast<float*>(base + g->off_mcmax)));
+        e = cudaGetLastError();
+        st = e == cudaSuccess ? VDBC_OK : cuda_status(e, "vdbc_encode: macrocells");
+    } else {
+        st = build_macrocells(g, s);
+    }
     if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
     st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
     if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
