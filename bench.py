@@ -69,6 +69,17 @@ def dist_env():
     return rank, world, local
 
 
+def workload_config(world=1):
+    """The benchmark's `config` (both arms): the 512^3 medium at 1:10, 1024^2 x 16 spp."""
+    from volgen import scenes
+
+    w = scenes.TURBULENCE_512
+    return {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
+            "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"], "image": "1024x1024", "spp": 16,
+            "max_bounces": 16, "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "input 512 MiB > L2, re-read every step"}
+
+
 def replica_throughput(total_ms, paths_per_step, steps, world, device=None):
     """Whole-job throughput of N independent replicas: the timed region is the
     max over ranks (one all-reduce of the timing, no data-path collective) and
@@ -328,11 +339,7 @@ def run_vdbc(args):
         "metric": METRIC, "value": round(value, 3), "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
-                   "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"], "image": "1024x1024", "spp": 16,
-                   "max_bounces": 16,
-                   "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "input 512 MiB > L2, re-read every step"},
+        "config": workload_config(world),
         "render_ms": round(render_ms, 3), "encode_ms": round(sum(enc_ms) / len(enc_ms), 3),
         "lookups_per_step": lookups, "glookups_per_s": round(lookups / (render_ms * 1e-3) / 1e9, 3),
         "dense_texture": {"ms_render": round(dense_ms, 3),
@@ -576,7 +583,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Mpaths/s",
             "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": workload_config(world),
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": round(value, 6),
                              "unit": "Mpaths/s"},
             "e2e": {"value": round(value, 6), "unit": "Mpaths/s", "h2d_bytes_per_step": 0,
