@@ -42,7 +42,7 @@ WORKLOAD = "turbulence512_r10_pt1024sq_16spp"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vdbc", choices=["vdbc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -117,10 +117,15 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once samples flow (nvidia-smi takes a while to start)
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
 
@@ -138,7 +143,10 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        during = self.lines[getattr(self, "skip", 0):]
+        if not during:          # a region shorter than the sampling period: the sample just before it
+            during = self.lines[-1:]
+        for l in during:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
