@@ -107,20 +107,27 @@ __device__ __forceinline__ void mlp_tile(const uint32_t* rows, const uint2* __re
     }
 }
 
-// row r of a tile for voxel n of a leaf: the leaf's latent (8 words of bf16
-// pairs, copied), then (i, j, k) / 7 rounded to bf16, zero padded to 32 columns
-__device__ __forceinline__ void mlp_row(uint32_t* rows, int r, int n, const uint32_t* __restrict__ latent)
+// row r of a tile: the leaf's latent (8 words of bf16 pairs, copied), then
+// the voxel's position (i, j, k) / 7 rounded to bf16, zero padded to 32 columns
+__device__ __forceinline__ void mlp_row_at(uint32_t* rows, int r, float u, float v, float w,
+                                           const uint32_t* __restrict__ latent)
 {
     const uint4* lp = reinterpret_cast<const uint4*>(latent);
     const uint4 q0 = __ldg(lp), q1 = __ldg(lp + 1);
-    const float u = __fdiv_rn((float)(n & 7), 7.0f), v = __fdiv_rn((float)((n >> 3) & 7), 7.0f),
-                w = __fdiv_rn((float)(n >> 6), 7.0f);
     uint4* rp = reinterpret_cast<uint4*>(rows) + r * 4;
     const int sw = (r >> 1) & 3;
     rp[0 ^ sw] = q0;
     rp[1 ^ sw] = q1;
     rp[2 ^ sw] = make_uint4(pack_bf16(u, v), pack_bf16(w, 0.0f), 0u, 0u);
     rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ float seventh(int i) { return __fdiv_rn((float)i, 7.0f); }
+
+// the same for voxel n = i + 8j + 64k of the leaf
+__device__ __forceinline__ void mlp_row(uint32_t* rows, int r, int n, const uint32_t* __restrict__ latent)
+{
+    mlp_row_at(rows, r, seventh(n & 7), seventh((n >> 3) & 7), seventh(n >> 6), latent);
 }
 
 // the parameter column of W1 that row column k of a tile multiplies (-1: none)
@@ -215,16 +222,24 @@ struct LearnedSampler {
         const int base = incl - cnt;
         uint32_t* rows = s_rows[wid];
         float* outs = s_out[wid];
+        // the corners' in-leaf positions / 7: two values per axis, six divisions per lookup
+        float pu[2] = {0.f, 0.f}, pv[2] = {0.f, 0.f}, pw[2] = {0.f, 0.f};
+        if (nmask) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                pu[k] = seventh(xs[k] & 7);
+                pv[k] = seventh(ys[k] & 7);
+                pw[k] = seventh(zs[k] & 7);
+            }
+        }
         for (int t0 = 0; t0 < total; t0 += 16) {
             int q = base;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 if (nmask & (1u << c)) {
-                    if (q >= t0 && q < t0 + 16) {
-                        const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
-                        mlp_row(rows, q - t0, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7),
-                                g.latents + (size_t)__float_as_uint(v[c]) * (kMlpLatent / 2));
-                    }
+                    if (q >= t0 && q < t0 + 16)
+                        mlp_row_at(rows, q - t0, pu[c & 1], pv[(c >> 1) & 1], pw[c >> 2],
+                                   g.latents + (size_t)__float_as_uint(v[c]) * (kMlpLatent / 2));
                     ++q;
                 }
             }
