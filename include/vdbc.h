@@ -142,6 +142,10 @@ typedef struct {
     uint64_t events[6];        /* only in builds with VDBC_STATS defined, else 0: tracker loop
                                   iterations, DDA cells examined, coarse blocks crossed, free
                                   flights drawn, rays started, paths fetched */
+    float    kernel_ms;        /* duration of the last render's tracker kernel (k_pt, k_pt_batch,
+                                  k_ea or k_iso), from CUDA events recorded around its launch on
+                                  the render's stream; -1 if none was recorded */
+    int32_t  reserved;
 } vdbc_render_stats;
 
 /*

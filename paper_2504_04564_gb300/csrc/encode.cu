@@ -1169,7 +1169,10 @@ extern "C" void vdbc_grid_free(vdbc_grid* g)
 {
     if (!g) return;
     if (g->block) cudaFree(g->block);
-    if (g->stats) cudaFree(g->stats);
+    if (g->stats) {
+        release_kernel_events(g->stats);
+        cudaFree(g->stats);
+    }
     delete g;
 }
 

@@ -1216,16 +1216,20 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     VDBC_CUDA(cudaMemsetAsync(stats, 0, sizeof(DevStats), s));
     if (med.mode == VDBC_MODE_ISO) {
         if (!mj.mcmin) return set_error(VDBC_ERR_INVALID_ARG, "ISO needs the macrocell minima");
+        record_kernel_start(stats, s);
         KLAUNCH(k_iso<S><<<blocks_for(npix, 128), 128, 0, s>>>(smp, mj, cam, med, out, stats));
+        record_kernel_stop(stats, s);
         VDBC_CUDA(cudaGetLastError());
         return VDBC_OK;
     }
     if (med.mode == VDBC_MODE_EA) {
+        record_kernel_start(stats, s);
         if constexpr (S::kCollective)
             KLAUNCH(k_ea_collective<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out,
                                                                                                 stats));
         else
             KLAUNCH(k_ea<S><<<blocks_for(npix, 128), 128, (size_t)med.tf_n * 16, s>>>(smp, mj, cam, med, out, stats));
+        record_kernel_stop(stats, s);
         VDBC_CUDA(cudaGetLastError());
         return VDBC_OK;
     }
@@ -1247,7 +1251,9 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
     JobView job = make_job(mj, cam, med, spp, seed, path_out);
+    record_kernel_start(stats, s);
     st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, 0, coarse, s);
+    record_kernel_stop(stats, s);
     if (st == VDBC_OK) {
         KLAUNCH(k_pt_reduce<<<blocks_for(npix, 256), 256, 0, s>>>(path_out, (int)npix, spp, out));
         cudaError_t e = cudaGetLastError();
@@ -1357,6 +1363,8 @@ extern "C" vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream
     out->paths = h.paths;
     out->error_flags = h.error_flags;
     for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    out->kernel_ms = kernel_ms_of(grid->stats);
+    out->reserved = 0;
     return VDBC_OK;
 }
 
@@ -1438,7 +1446,10 @@ extern "C" void vdbc_volume_free(vdbc_volume* v)
     if (v->linear) cudaFree(v->linear);
     if (v->mcmin) cudaFree(v->mcmin);
     if (v->mcmax) cudaFree(v->mcmax);
-    if (v->stats) cudaFree(v->stats);
+    if (v->stats) {
+        release_kernel_events(v->stats);
+        cudaFree(v->stats);
+    }
     delete v;
 }
 
@@ -1469,6 +1480,8 @@ extern "C" vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void
     out->paths = h.paths;
     out->error_flags = h.error_flags;
     for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    out->kernel_ms = kernel_ms_of(vol->stats);
+    out->reserved = 0;
     return VDBC_OK;
 }
 
@@ -1865,6 +1878,8 @@ extern "C" vdbc_status vdbc_batch_stats_get(const vdbc_batch* b, void* stream, v
     out->paths = h.paths;
     out->error_flags = h.error_flags;
     for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    out->kernel_ms = -1.0f;   // frames are replayed from a graph; time them around vdbc_batch_render_frames
+    out->reserved = 0;
     return VDBC_OK;
 }
 

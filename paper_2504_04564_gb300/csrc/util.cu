@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 
@@ -94,6 +96,72 @@ vdbc_status wait_stream(cudaStream_t s)
 }
 
 }  // namespace vdbc
+
+// ---------------------------------------------------------------- tracker kernel timing
+namespace vdbc {
+struct KernelEvents {
+    cudaEvent_t start = nullptr, stop = nullptr;
+    bool recorded = false;
+};
+static std::mutex g_ev_mu;
+static std::map<const void*, KernelEvents> g_ev;
+
+static KernelEvents* kernel_events(const void* key)
+{
+    KernelEvents& k = g_ev[key];
+    if (!k.start) {
+        if (cudaEventCreate(&k.start) != cudaSuccess || cudaEventCreate(&k.stop) != cudaSuccess) {
+            cudaGetLastError();
+            g_ev.erase(key);
+            return nullptr;
+        }
+    }
+    return &k;
+}
+
+void record_kernel_start(const void* key, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    if (KernelEvents* k = kernel_events(key)) {
+        k->recorded = false;
+        cudaEventRecord(k->start, s);
+    }
+}
+
+void record_kernel_stop(const void* key, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    if (KernelEvents* k = kernel_events(key)) {
+        cudaEventRecord(k->stop, s);
+        k->recorded = true;
+    }
+}
+
+float kernel_ms_of(const void* key)
+{
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    auto it = g_ev.find(key);
+    float ms = -1.0f;
+    if (it != g_ev.end() && it->second.recorded &&
+        cudaEventElapsedTime(&ms, it->second.start, it->second.stop) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.0f;
+    }
+    return ms;
+}
+
+void release_kernel_events(const void* key)
+{
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    auto it = g_ev.find(key);
+    if (it == g_ev.end()) return;
+    if (it->second.start) cudaEventDestroy(it->second.start);
+    if (it->second.stop) cudaEventDestroy(it->second.stop);
+    g_ev.erase(it);
+}
+
+}  // namespace vdbc
+
 
 using namespace vdbc;
 

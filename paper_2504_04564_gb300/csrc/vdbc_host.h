@@ -55,6 +55,15 @@ void count_launch(int n = 1);
 // waits for `s` with a wall-clock limit (VDBC_TIMEOUT_MS, default 600 s)
 vdbc_status wait_stream(cudaStream_t s);
 
+// CUDA events around the last tracker launch of a stats block (a grid's, a
+// volume's or a batch's): record_kernel_start/stop on the launching stream,
+// kernel_ms_of after the stream has finished (-1 when nothing was recorded),
+// release_kernel_events when the owner is freed
+void record_kernel_start(const void* key, cudaStream_t s);
+void record_kernel_stop(const void* key, cudaStream_t s);
+float kernel_ms_of(const void* key);
+void release_kernel_events(const void* key);
+
 struct Block {
     void* ptr = nullptr;
     size_t bytes = 0;
