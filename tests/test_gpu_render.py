@@ -279,3 +279,23 @@ def test_pt_coarse_level_changes_no_image(env, monkeypatch):
     D = orc.decode_dense(host, e["active"], e["background_bits"])
     ref = oracle_image(env, D, cam, 1, 8, 3, macrocell=4, **sc.pt_medium_args(density_scale=30.0))
     assert np.all(np.abs(on[..., :3] - ref[..., :3]).mean(axis=(0, 1)) <= PT_MEAN_ABS)
+
+
+def test_render_stats_time_the_tracker_kernel(env):
+    """kernel_ms: CUDA events around the tracker's launch, positive for every mode."""
+    torch, v, vg, sc = env["torch"], env["v"], env["vg"], env["sc"]
+    dims = (48, 40, 44)
+    host = vg.generate_host(vg.make_params("blobs", dims, 1))
+    t = torch.from_numpy(host).to(env["dev"])
+    grid = v.vdbc_encode(t, 2.0)
+    vol = v.vdbc_volume_create(t, v.FILTER_TEXTURE)
+    cam = v.make_camera(*sc.pinhole_orbit(dims, 32, 24))
+    out = torch.zeros(24, 32, 4, device=env["dev"])
+    for med, spp in ((v.make_medium(v.MODE_PT, **sc.pt_medium_args()), 4),
+                     (v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf(), step=0.5), 1),
+                     (v.make_medium(v.MODE_ISO, step=0.5, iso=0.3), 1)):
+        v.vdbc_render(grid, cam, med, spp, 1, out)
+        st = v.vdbc_render_stats_get(grid)
+        assert 0.0 < st.kernel_ms < 1e4
+        v.vdbc_render_dense(vol, cam, med, spp, 1, out)
+        assert 0.0 < v.vdbc_volume_render_stats_get(vol).kernel_ms < 1e4
