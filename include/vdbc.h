@@ -31,6 +31,16 @@
  *    same handle reports as VDBC_ERR_DEVICE_FLAG.
  *  - A handle may be used from several threads only if the calls are
  *    serialized by the caller.
+ *  - The library is also built with VDBC_CHECKED=1 as libvdbc_checked.so
+ *    (vdbc_version() ends in "checked"): there every tree lookup checks each
+ *    node, leaf and tile index against the grid's counts before it loads, and
+ *    an index outside its table is read as the background and reported as
+ *    VDBC_ERR_DEVICE_FLAG (bit 2 of vdbc_render_stats.error_flags) by the
+ *    call that made it (encode, learn, decode, or a render that waits).
+ *  - Host-side fault injection, for tests: VDBC_FAULT=oom (every device
+ *    allocation fails), =format (every checksum mismatches), =timeout (every
+ *    host wait times out), =bounds (checked builds only: vdbc_grid_load skips
+ *    the node-table validation, so the lookup checks meet the bad entry).
  */
 #ifndef VDBC_H
 #define VDBC_H
@@ -48,7 +58,7 @@ typedef enum {
     VDBC_ERR_CUDA = 3,          /* a CUDA runtime call failed; see vdbc_last_error() */
     VDBC_ERR_FORMAT = 4,        /* a grid file is truncated, of another version or corrupt */
     VDBC_ERR_TIMEOUT = 5,       /* a host wait ran past its wall-clock limit */
-    VDBC_ERR_DEVICE_FLAG = 6,   /* a kernel hit one of its loop bounds */
+    VDBC_ERR_DEVICE_FLAG = 6,   /* a kernel hit one of its loop bounds (or, checked builds, an index bound) */
     VDBC_ERR_UNSUPPORTED = 7    /* valid request the build does not implement */
 } vdbc_status;
 
@@ -189,7 +199,12 @@ vdbc_status vdbc_grid_macrocells(const vdbc_grid* grid, float* host_min, float* 
  * block (the property Section 2.3 and Section 3.2.1 rely on for copying
  * NanoVDB grids with memcpy), behind a versioned header and a checksum.  No
  * entropy coding, so the file keeps random access (Section 5.5).
- * Errors: INVALID_ARG; FORMAT (bad magic, version, size or checksum); OOM; CUDA.
+ * vdbc_grid_load checks the whole file on the host (magic, version, sizes,
+ * checksum, table offsets against the layout the header's counts give), then
+ * every root, upper and lower entry on the device against the table it
+ * indexes, before it returns the grid.
+ * Errors: INVALID_ARG; FORMAT (bad magic, version, size, checksum or table
+ * layout, or a node entry outside its table); OOM; CUDA.
  */
 vdbc_status vdbc_grid_save(const vdbc_grid* grid, const char* path);
 vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid** out);

@@ -7,7 +7,10 @@ this package.  The product path (``paper_2504_04564_gb300``) never does: it
 shares no code, header, table or helper with this directory.
 
 This module compiles ``liboracle.so`` with gcc (``build()``) and wraps its
-functions with numpy-friendly signatures.
+functions with numpy-friendly signatures.  With ORACLE_SANITIZE=1 in the
+environment it builds and loads ``liboracle_asan.so`` instead, instrumented
+by AddressSanitizer and UndefinedBehaviorSanitizer (the process must then
+start with libasan preloaded).
 """
 from __future__ import annotations
 
@@ -20,8 +23,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-LIB = os.path.join(_BUILD, "liboracle.so")
+SANITIZE = os.environ.get("ORACLE_SANITIZE", "") == "1"
+LIB = os.path.join(_BUILD, "liboracle_asan.so" if SANITIZE else "liboracle.so")
 SOURCES = ["philox.c", "encode.c", "render.c", "mlp.c"]
+SANITIZE_FLAGS = ["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
 
 F1, F2, F3 = 1, 2, 3
 FP32, FP16, FP8 = 0, 1, 2
@@ -38,7 +43,7 @@ def build(verbose: bool = False) -> None:
     if os.path.exists(LIB) and all(os.path.getmtime(d) <= os.path.getmtime(LIB) for d in deps):
         return
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared"] + srcs + ["-o", LIB, "-lm"]
+           "-fPIC", "-shared"] + (SANITIZE_FLAGS if SANITIZE else []) + srcs + ["-o", LIB, "-lm"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("oracle build failed:\n" + r.stdout.decode())

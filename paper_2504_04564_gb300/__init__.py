@@ -18,7 +18,11 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# VDBC_CHECKED=1 in the environment selects the bounds-checked build,
+# VDBC_SANITIZE=1 the build whose host code runs under ASan/UBSan
+CHECKED = os.environ.get("VDBC_CHECKED", "") == "1"
+SANITIZE = not CHECKED and os.environ.get("VDBC_SANITIZE", "") == "1"
+LIB_PATH = _build.LIB_CHECKED if CHECKED else (_build.LIB_ASAN if SANITIZE else _build.LIB)
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_FORMAT, ERR_TIMEOUT, ERR_DEVICE_FLAG, ERR_UNSUPPORTED = range(8)
 F1, F2, F3 = 1, 2, 3
@@ -146,8 +150,9 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libvdbc.so is not built (%s); run __graft_entry__.build() "
-                              "or python -m paper_2504_04564_gb300.build" % LIB_PATH)
+            raise ImportError("%s is not built; run __graft_entry__.build() "
+                              "or python -m paper_2504_04564_gb300.build%s"
+                              % (LIB_PATH, " --checked" if CHECKED else (" --sanitize" if SANITIZE else "")))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

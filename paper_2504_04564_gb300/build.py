@@ -2,6 +2,12 @@
 
 Translation units are compiled in parallel and linked with `nvcc -shared`.
 The output lands in paper_2504_04564_gb300/_build/ (git-ignored).
+``build(checked=True)`` builds the same sources with VDBC_CHECKED=1 into
+_build/checked/libvdbc_checked.so: every tree lookup bounds-checks its node,
+leaf and tile indices and reports a violation through the device error word.
+``build(sanitize=True)`` builds _build/asan/libvdbc_asan.so, whose host code
+is instrumented by AddressSanitizer and UndefinedBehaviorSanitizer (load it
+into a process that starts with libasan preloaded).
 """
 from __future__ import annotations
 
@@ -14,6 +20,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvdbc.so")
+BUILD_CHECKED = os.path.join(BUILD, "checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libvdbc_checked.so")
+BUILD_ASAN = os.path.join(BUILD, "asan")
+LIB_ASAN = os.path.join(BUILD_ASAN, "libvdbc_asan.so")
+# (nvcc splits -Xcompiler values at commas: one sanitizer per flag)
+SANITIZE_LINK = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined"]
+SANITIZE_FLAGS = ["-g", "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=all"] + SANITIZE_LINK
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["encode.cu", "render.cu", "util.cu", "learn.cu"]
@@ -32,24 +45,38 @@ def _deps():
             [os.path.join(INCLUDE, "vdbc.h")])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def _variant(checked: bool, sanitize: bool):
+    """(library, object folder, extra compile flags, extra link flags)."""
+    if checked:
+        return LIB_CHECKED, BUILD_CHECKED, ["-DVDBC_CHECKED=1"], []
+    if sanitize:
+        return LIB_ASAN, BUILD_ASAN, SANITIZE_FLAGS, SANITIZE_LINK
+    return LIB, BUILD, [], []
+
+
+def stale(checked: bool = False, sanitize: bool = False) -> bool:
+    lib = _variant(checked, sanitize)[0]
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.exists(d) and os.path.getmtime(d) > t for d in _deps())
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    """Compile every translation unit in parallel, then link the shared library."""
-    if not force and not stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+def build(verbose: bool = False, force: bool = False, extra_flags=None, checked: bool = False,
+          sanitize: bool = False) -> str:
+    """Compile every translation unit in parallel, then link the shared library
+    (the bounds-checked variant with ``checked=True``, the host-sanitized one
+    with ``sanitize=True``)."""
+    lib, out, vflags, lflags = _variant(checked, sanitize)
+    if not force and not stale(checked, sanitize):
+        return lib
+    os.makedirs(out, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + vflags
     if verbose:
         flags = flags + ["-Xptxas", "-v"]
     objs, procs = [], []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = ["nvcc"] + flags + PER_FILE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -59,15 +86,15 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
             raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode()))
         if verbose and out:
             sys.stdout.write(out.decode())
-    tmp = LIB + ".tmp"
-    cmd = ["nvcc"] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    tmp = lib + ".tmp"
+    cmd = ["nvcc"] + ARCH + lflags + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stdout.decode()))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose="-v" in sys.argv, force="-f" in sys.argv)
-    print(LIB)
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv,
+                sanitize="--sanitize" in sys.argv))

@@ -819,6 +819,14 @@ void bind_view(vdbc_grid* g)
     v.nmeta = reinterpret_cast<const float2*>(base + g->off_nmeta);
     v.mlp_frag = reinterpret_cast<const uint2*>(base + g->off_frag);
     v.mlp_bias = reinterpret_cast<const float*>(base + g->off_bias);
+#if VDBC_CHECKED
+    v.n_upper = (uint32_t)in.n_upper;
+    v.n_lower = (uint32_t)in.n_lower;
+    v.n_tiles = (uint32_t)in.n_tiles;
+    v.n_leaves = (uint32_t)in.n_leaves;
+    v.n_neural = (uint32_t)in.n_neural;
+    v.err = &g->stats->error_flags;   // the grid's stats exist before its view is bound
+#endif
 }
 
 // offsets of every table inside the one linear block, from the counts in g->info
@@ -1064,6 +1072,10 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     layout(g);
     vdbc_status st = dev_alloc(&g->block, g->block_bytes, s);
     if (st != VDBC_OK) { delete g; return st; }
+    st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    cudaError_t e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
+    if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: stats"); }
     bind_view(g);
     char* base = static_cast<char*>(g->block);
     uint32_t* root = reinterpret_cast<uint32_t*>(base + g->off_root);
@@ -1080,7 +1092,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     KLAUNCH(k_fill_leaves<<<grid1d(cap * 32, 256), 256, 0, s>>>(vol, d, list, counts, is_leaf, leaf_rank, bsel, payload,
                                                         base + g->off_leaves,
                                                         reinterpret_cast<float2*>(base + g->off_meta)));
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: tree kernels"); }
     if (payload == VDBC_FP32) {
         // FP32 leaves hold the input's values: the ranges come from the input itself
@@ -1094,11 +1106,8 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     } else {
         st = build_macrocells(g, s);
     }
+    if (st == VDBC_OK) st = checked_flags(g, s);
     if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
-    st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
-    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
-    e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
-    if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_encode: stats"); }
     *out = g;
     return VDBC_OK;
 }
@@ -1133,9 +1142,9 @@ extern "C" vdbc_status vdbc_grid_decode(const vdbc_grid* g, float* out, int32_t 
     if (!out_on_device) {
         vdbc_status st = wait_stream(s);
         dev_free(tmp, s);
-        return st;
+        if (st != VDBC_OK) return st;
     }
-    return VDBC_OK;
+    return checked_flags(g, s);
 }
 
 extern "C" vdbc_status vdbc_grid_active_bricks(const vdbc_grid* g, uint8_t* host_out)

@@ -836,6 +836,10 @@ vdbc_status materialize_learned(const vdbc_grid* g, cudaStream_t s, Materialized
     m->view.payload = VDBC_FP32;
     m->view.lower = static_cast<const uint32_t*>(m->lower);
     m->view.leaves = m->leaves;
+#if VDBC_CHECKED
+    m->view.n_leaves = (uint32_t)(n_raw + n_neu);
+    m->view.n_neural = 0;
+#endif
     return VDBC_OK;
 }
 
@@ -1033,10 +1037,13 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     layout(g);
     vdbc_status st = dev_alloc(&g->block, g->block_bytes, s);
     if (st != VDBC_OK) { delete g; return st; }
+    st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
+    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
     bind_view(g);
     char* b = static_cast<char*>(g->block);
     const char* sb = static_cast<const char*>(src->block);
     cudaError_t e = cudaMemsetAsync(g->block, 0, g->block_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + g->off_root, sb + src->off_root, (size_t)nroot * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && nup > 0) e = cudaMemcpyAsync(b + g->off_upper, sb + src->off_upper, (size_t)nup * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + g->off_tiles, sb + src->off_tiles, (size_t)si.n_tiles * 4, cudaMemcpyDeviceToDevice, s);
@@ -1058,11 +1065,7 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     e = cudaGetLastError();
     if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_learn: assembly"); }
     st = build_macrocells(g, s);
-    if (st == VDBC_OK) st = dev_alloc(reinterpret_cast<void**>(&g->stats), sizeof(DevStats), s);
-    if (st == VDBC_OK) {
-        e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
-        if (e != cudaSuccess) st = cuda_status(e, "vdbc_learn: stats");
-    }
+    if (st == VDBC_OK) st = checked_flags(g, s);
     if (st == VDBC_OK) st = wait_stream(s);
     if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
     *out = g;

@@ -1795,6 +1795,9 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_frame), sizeof(int));
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->stats), sizeof(DevStats));
     if (st != VDBC_OK) return fail(st);
+#if VDBC_CHECKED
+    for (int i = 0; i < n; ++i) grids[i].err = &b->stats->error_flags;   // reported with the batch's flags
+#endif
     size_t po = 0, so = 0;
     for (int i = 0; i < n; ++i) {
         JobView& jv = b->h_jobs[i];

@@ -1,5 +1,6 @@
 // util.cu -- error reporting, allocation, bounded waits, grid save/load and
 // the Philox entry point of libvdbc.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
@@ -95,6 +96,24 @@ vdbc_status wait_stream(cudaStream_t s)
     }
 }
 
+vdbc_status checked_flags(const vdbc_grid* g, cudaStream_t s)
+{
+#if VDBC_CHECKED
+    VDBC_TRY(wait_stream(s));
+    unsigned long long f = 0;
+    VDBC_CUDA(cudaMemcpy(&f, &g->stats->error_flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f & kErrBounds) {
+        unsigned long long rest = f & ~kErrBounds;
+        VDBC_CUDA(cudaMemcpy(&g->stats->error_flags, &rest, sizeof(rest), cudaMemcpyHostToDevice));
+        return set_error(VDBC_ERR_DEVICE_FLAG, "a tree index outside its table (flags %llx)", f);
+    }
+#else
+    (void)g;
+    (void)s;
+#endif
+    return VDBC_OK;
+}
+
 }  // namespace vdbc
 
 // ---------------------------------------------------------------- tracker kernel timing
@@ -167,7 +186,11 @@ using namespace vdbc;
 
 extern "C" const char* vdbc_last_error(void) { return g_last_error.c_str(); }
 
+#if VDBC_CHECKED
+extern "C" const char* vdbc_version(void) { return "vdbc 0.1.0 sm_103a checked"; }
+#else
 extern "C" const char* vdbc_version(void) { return "vdbc 0.1.0 sm_103a"; }
+#endif
 
 extern "C" uint64_t vdbc_kernel_launches(void) { return g_launches.load(); }
 
@@ -202,6 +225,40 @@ extern "C" vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], u
     if (e != cudaSuccess) return cuda_status(e, "vdbc_philox");
     return VDBC_OK;
 }
+
+// ---------------------------------------------------------------- tree validation
+// Counts the node entries that name a child, tile or leaf outside its table
+// (root -> upper, upper -> lower, lower -> leaf / neural leaf; any level ->
+// tile).  A grid that passes holds no index a lookup could follow out of its
+// table, whatever the file it came from.
+namespace {
+__device__ __forceinline__ bool bad_entry(uint32_t e, uint32_t n_child, uint32_t n_tiles, bool leaf_level,
+                                          uint32_t n_neural, bool learned)
+{
+    if (e & kTile) return (e & ~kTile) >= n_tiles;
+    if (leaf_level && learned && (e & kNeural)) return (e & ~kNeural) >= n_neural;
+    return e >= n_child;
+}
+
+__global__ void k_validate_tree(const uint32_t* __restrict__ root, long long nroot, const uint32_t* __restrict__ upper,
+                                long long nup, const uint32_t* __restrict__ lower, long long nlo, uint32_t n_upper,
+                                uint32_t n_lower, uint32_t n_leaves, uint32_t n_tiles, uint32_t n_neural, int learned,
+                                unsigned long long* __restrict__ bad)
+{
+    unsigned long long nbad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nroot + nup + nlo; i += stride) {
+        if (i < nroot)
+            nbad += bad_entry(root[i], n_upper, n_tiles, false, 0, false);
+        else if (i < nroot + nup)
+            nbad += bad_entry(upper[i - nroot], n_lower, n_tiles, false, 0, false);
+        else
+            nbad += bad_entry(lower[i - nroot - nup], n_leaves, n_tiles, true, n_neural, learned != 0);
+    }
+    nbad = __reduce_add_sync(0xffffffffu, (unsigned)nbad);
+    if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(bad, nbad);
+}
+}  // namespace
 
 // ---------------------------------------------------------------- save / load
 // File: header {magic "VDBCGRD1", version, info bytes, activation bytes,
@@ -298,6 +355,24 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
         return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: inconsistent header");
     for (int i = 0; i < 16; ++i)
         if (h.offsets[i] > h.block_bytes || (h.offsets[i] & 255)) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad offsets");
+    // every table where the counts put it: entries are 31-bit indices, and
+    // the block must be exactly the layout the header's counts give
+    const int64_t counts[5] = {info.n_upper, info.n_lower, info.n_leaves, info.n_tiles, info.n_neural};
+    for (int64_t c : counts)
+        if (c < 0 || c >= (int64_t)kTile) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad table counts");
+    if (info.n_tiles < 1 || (info.payload != VDBC_LEARNED && info.n_neural != 0))
+        return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad table counts");
+    {
+        vdbc_grid probe;
+        probe.info = info;
+        layout(&probe);
+        const size_t want[13] = {probe.off_root, probe.off_upper, probe.off_lower, probe.off_tiles, probe.off_leaves,
+                                 probe.off_meta, probe.off_mcmin, probe.off_mcmax, probe.off_latents, probe.off_nmeta,
+                                 probe.off_frag, probe.off_bias, probe.off_params};
+        bool same = probe.block_bytes == h.block_bytes && probe.info.total_bytes == info.total_bytes;
+        for (int i = 0; i < 13; ++i) same = same && want[i] == h.offsets[i];
+        if (!same) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: tables do not match the header's counts");
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     vdbc_grid* g = new vdbc_grid();
@@ -317,7 +392,36 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
     if (e == cudaSuccess) e = cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s);
     if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_grid_load"); }
     bind_view(g);
+    // the node tables are checked on the device before the grid is handed
+    // out (the bad-entry count goes through the stats block's work counter);
+    // checked builds skip this under VDBC_FAULT=bounds, so that their lookup
+    // checks can be tested on a grid that holds a bad entry
+    bool validate = true;
+#if VDBC_CHECKED
+    validate = !fault_injected("bounds");
+#endif
+    if (validate) {
+        const GridView& v = g->view;
+        const long long nroot = (long long)v.rx * v.ry * v.rz, nup = info.n_upper * (long long)kUpperN,
+                        nlo = info.n_lower * (long long)kLowerN;
+        const long long total = nroot + nup + nlo;
+        const unsigned nblk = (unsigned)std::min<long long>((total + 255) / 256, 152 * 8);
+        KLAUNCH(k_validate_tree<<<nblk, 256, 0, s>>>(v.root, nroot, v.upper, nup, v.lower, nlo, (uint32_t)info.n_upper,
+                                                    (uint32_t)info.n_lower, (uint32_t)info.n_leaves,
+                                                    (uint32_t)info.n_tiles, (uint32_t)info.n_neural,
+                                                    info.payload == VDBC_LEARNED ? 1 : 0, &g->stats->work_next));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_grid_load: validation"); }
+    }
     st = wait_stream(s);     // `host` must outlive the copy
+    unsigned long long nbad = 0;
+    if (st == VDBC_OK && validate) {
+        e = cudaMemcpy(&nbad, &g->stats->work_next, sizeof(nbad), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemset(&g->stats->work_next, 0, sizeof(nbad));
+        if (e != cudaSuccess) st = cuda_status(e, "vdbc_grid_load: validation");
+        else if (nbad) st = set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: %llu node entries outside their tables in %s",
+                                      nbad, path);
+    }
     if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
     *out = g;
     return VDBC_OK;

@@ -21,7 +21,22 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+// VDBC_CHECKED=1 builds (a separate library, libvdbc_checked.so) bounds-check
+// every node, leaf and tile index against the grid's counts before the load;
+// a violation sets kErrBounds in the grid's device error word and the lookup
+// returns the background instead of reading outside the table.
+#ifndef VDBC_CHECKED
+#define VDBC_CHECKED 0
+#endif
+
 namespace vdbc {
+
+// bits of the device error word (DevStats::error_flags)
+enum : unsigned long long {
+    kErrTrackSteps = 1ull << 0,    // a tracking loop hit its step bound
+    kErrDdaSteps = 1ull << 1,      // a DDA walk hit its cell bound
+    kErrBounds = 1ull << 2,        // an index outside its table (checked builds)
+};
 
 constexpr uint32_t kTile = 0x80000000u;
 constexpr uint32_t kBackgroundEntry = 0x80000000u;   // tile 0
@@ -50,6 +65,11 @@ struct GridView {
     const float2* nmeta;
     const uint2* mlp_frag;
     const float* mlp_bias;
+#if VDBC_CHECKED
+    // checked builds: table sizes and the word a violation sets
+    uint32_t n_upper, n_lower, n_tiles, n_leaves, n_neural;
+    unsigned long long* err;
+#endif
 };
 
 constexpr uint32_t kNeural = 0x40000000u;   // lower entry of a neural leaf (with bit 31 clear)
@@ -104,15 +124,43 @@ __device__ __forceinline__ float leaf_value(const GridView& g, uint32_t leaf, in
 }
 
 // ---------------------------------------------------------------- descent
+#if VDBC_CHECKED
+static __device__ __noinline__ uint32_t bounds_violation(const GridView& g)
+{
+    atomicOr(g.err, kErrBounds);
+    return kBackgroundEntry;
+}
+
+// a leaf-level entry names an existing tile, raw leaf or neural leaf
+__device__ __forceinline__ bool entry_in_range(const GridView& g, uint32_t e)
+{
+    if (e & kTile) return (e & ~kTile) < g.n_tiles;
+    if (g.payload == kLearned && (e & kNeural)) return (e & ~kNeural) < g.n_neural;
+    return e < g.n_leaves;
+}
+#endif
+
 // entry of the lower level that covers voxel-leaf (li,lj,lk) = (i>>3, j>>3, k>>3)
 __device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, int lj, int lk)
 {
     int i = li << 3, j = lj << 3, k = lk << 3;
+#if VDBC_CHECKED
+    if (li < 0 || lj < 0 || lk < 0 || i >= g.nx || j >= g.ny || k >= g.nz) return bounds_violation(g);
+    uint32_t e = __ldg(g.root + ((k >> 12) * g.ry + (j >> 12)) * g.rx + (i >> 12));
+    if (e & kTile) return entry_in_range(g, e) ? e : bounds_violation(g);
+    if (e >= g.n_upper) return bounds_violation(g);
+    e = __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
+    if (e & kTile) return entry_in_range(g, e) ? e : bounds_violation(g);
+    if (e >= g.n_lower) return bounds_violation(g);
+    e = __ldg(g.lower + (size_t)e * kLowerN + (((k >> 3) & 15) << 8) + (((j >> 3) & 15) << 4) + ((i >> 3) & 15));
+    return entry_in_range(g, e) ? e : bounds_violation(g);
+#else
     uint32_t e = __ldg(g.root + ((k >> 12) * g.ry + (j >> 12)) * g.rx + (i >> 12));
     if (e & kTile) return e;
     e = __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
     if (e & kTile) return e;
     return __ldg(g.lower + (size_t)e * kLowerN + (((k >> 3) & 15) << 8) + (((j >> 3) & 15) << 4) + ((i >> 3) & 15));
+#endif
 }
 
 // per-thread cached accessor: remembers the last leaf-level entry (Section

@@ -20,12 +20,6 @@ struct DevStats {
     unsigned long long ev[6];        // event counts of builds with VDBC_STATS (else 0)
 };
 
-enum : unsigned long long {
-    kErrTrackSteps = 1ull << 0,    // a tracking loop hit its step bound
-    kErrDdaSteps = 1ull << 1,      // a DDA walk hit its cell bound
-    kErrBounds = 1ull << 2,        // an index outside its table (checked builds)
-};
-
 vdbc_status set_error(vdbc_status s, const char* fmt, ...);
 void clear_error();
 vdbc_status cuda_status(cudaError_t e, const char* what);
@@ -63,6 +57,11 @@ void record_kernel_start(const void* key, cudaStream_t s);
 void record_kernel_stop(const void* key, cudaStream_t s);
 float kernel_ms_of(const void* key);
 void release_kernel_events(const void* key);
+
+// checked builds (VDBC_CHECKED=1): waits for `s`, then reports a bounds
+// violation recorded in the grid's error word as VDBC_ERR_DEVICE_FLAG (and
+// clears that bit); other builds return VDBC_OK without waiting
+vdbc_status checked_flags(const vdbc_grid* g, cudaStream_t s);
 
 struct Block {
     void* ptr = nullptr;

@@ -7,14 +7,16 @@ import re
 
 import pytest
 
+from gridfile import write_grid_file
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
 def v():
-    from paper_2504_04564_gb300 import build
-    build.build()
     import paper_2504_04564_gb300 as v
+    from paper_2504_04564_gb300 import build
+    build.build(checked=v.CHECKED, sanitize=v.SANITIZE)
     return v
 
 
@@ -77,3 +79,52 @@ def test_grid_load_rejects_bad_files_on_host(v, tmp_path):
     short.write_bytes(b"VDBCGRD1" + (1).to_bytes(4, "little"))
     assert L.vdbc_grid_load(str(short).encode(), None, ctypes.byref(h)) == v.ERR_FORMAT
     assert h.value is None
+
+
+def fabricated_file(v, path, **counts):
+    """A checksummed one-brick 8^3 FP32 file whose block is 256 zero bytes at
+    offset 0 for every table (the layout of no real grid)."""
+    info = v.GridInfo()
+    info.dims[:] = [8, 8, 8]
+    info.macrocell = 8
+    info.n_bricks = 1
+    info.n_tiles = 1
+    for k, x in counts.items():
+        setattr(info, k, x)
+    write_grid_file(path, dict(magic=b"VDBCGRD1", version=2, offsets=[0] * 16,
+                               info=bytearray(bytes(info)), active=b"\x00", block=bytearray(256)))
+
+
+def test_grid_load_checks_the_layout_on_host(v, tmp_path):
+    """Counts that no grid could have, or tables not where the counts put
+    them, are refused with FORMAT on the host (no device here)."""
+    L = v.lib()
+    h = ctypes.c_void_p()
+    path = str(tmp_path / "fab.vdbc")
+    fabricated_file(v, path)
+    assert L.vdbc_grid_load(path.encode(), None, ctypes.byref(h)) == v.ERR_FORMAT
+    assert "do not match" in v.vdbc_last_error()
+    for bad in (dict(n_tiles=0), dict(n_leaves=-1), dict(n_upper=1 << 31), dict(n_neural=3)):
+        fabricated_file(v, path, **bad)
+        assert L.vdbc_grid_load(path.encode(), None, ctypes.byref(h)) == v.ERR_FORMAT, bad
+        assert "counts" in v.vdbc_last_error(), (bad, v.vdbc_last_error())
+    assert h.value is None
+
+
+@pytest.fixture(scope="module")
+def checked_lib():
+    from paper_2504_04564_gb300 import build
+    L = ctypes.CDLL(build.build(checked=True))
+    L.vdbc_version.restype = ctypes.c_char_p
+    return L
+
+
+def test_checked_build_exports_the_same_surface(v, checked_lib):
+    """libvdbc_checked.so (VDBC_CHECKED=1) declares itself and exports every
+    function of include/*.h, and rejects bad arguments the same way."""
+    for n in sorted(declared_functions()):
+        assert hasattr(checked_lib, n), n
+    assert checked_lib.vdbc_version().decode().endswith("checked")
+    assert not v.vdbc_version().endswith("checked")
+    h = ctypes.c_void_p()
+    assert checked_lib.vdbc_encode(None, None, None, ctypes.byref(h)) == v.ERR_INVALID_ARG
