@@ -335,6 +335,16 @@ vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_t autotune,
 vdbc_status vdbc_batch_render_frames(vdbc_batch* batch, int32_t frames, void* stream);
 /* restarts the accumulation at frame 0 */
 vdbc_status vdbc_batch_reset(vdbc_batch* batch, void* stream);
+/* progressive accumulation state, for checkpoints: the frame counter and
+ * every job's per-pixel radiance sums (4 floats a pixel: the r, g, b sums
+ * and an unused one; jobs in order, pixels row-major), *floats in all.
+ * get_state copies it to host memory and waits for `stream`; set_state
+ * restores one taken from a batch of the same jobs (host memory, frame >= 0)
+ * and waits, after which F more frames give the images of a batch that
+ * rendered frame + F frames in one go. */
+vdbc_status vdbc_batch_state_size(const vdbc_batch* batch, int64_t* floats);
+vdbc_status vdbc_batch_get_state(const vdbc_batch* batch, int32_t* frame, float* host_sums, void* stream);
+vdbc_status vdbc_batch_set_state(vdbc_batch* batch, int32_t frame, const float* host_sums, void* stream);
 vdbc_status vdbc_batch_get_tuning(const vdbc_batch* batch, vdbc_tuning* tuning);
 /* counters of the last frame; waits for `stream` */
 vdbc_status vdbc_batch_stats_get(const vdbc_batch* batch, void* stream, vdbc_render_stats* stats);
@@ -355,6 +365,19 @@ void        vdbc_batch_free(vdbc_batch* batch);
  * corners that falls in a neural leaf; a leaf that the network cannot
  * represent within the error bound keeps a raw FP16 payload instead.
  */
+/* training state of vdbc_learn, for checkpoints: device arrays the caller
+ * owns.  Latent arrays are per leaf POSITION like init_latents (16 floats
+ * each); in a saved state, positions without a leaf hold 0. */
+typedef struct {
+    float*  params;      /* 1729 network parameters */
+    float*  params_m;    /* their Adam first moments */
+    float*  params_v;    /* their Adam second moments */
+    float*  latents;     /* 16 per leaf position */
+    float*  latents_m;   /* the latents' Adam first moments */
+    float*  latents_v;   /* the latents' Adam second moments */
+    int64_t step;        /* Adam steps taken so far */
+} vdbc_learn_state;
+
 typedef struct {
     int32_t  steps;             /* Adam steps (0: keep the initial network and latents) */
     int32_t  samples_per_leaf;  /* S: voxels drawn per leaf per step, 16, 32, 64 or 128 */
@@ -370,6 +393,10 @@ typedef struct {
     const float*   init_latents;  /* device, 16 floats per leaf POSITION (lk*nly + lj)*nlx + li with
                                      nl = ceil(dims/8), or NULL: zeros */
     const uint8_t* force;         /* device, one byte per leaf position: 0 by error, 1 neural, 2 raw; or NULL */
+    const vdbc_learn_state* resume; /* or NULL: continue from this state (then init_params and
+                                       init_latents must be NULL); step t of the call counts as step
+                                       resume->step + t in the voxel draws and Adam's bias corrections */
+    vdbc_learn_state* save;       /* or NULL: receives the state after the last step */
 } vdbc_learn_params;
 
 /*
@@ -385,9 +412,14 @@ typedef struct {
  * (leaf position, t, s, 0x4C454146) and key `seed`; the latents' gradient
  * is the sum over the leaf's samples.  Tree tables, tiles and the
  * background are those of `src`.  loss_out (host, `steps` doubles, or
- * NULL) receives the loss of each step.  Waits for `stream`.
+ * NULL) receives the loss of each step.  Training state can be saved and
+ * resumed: A steps with `save`, then B steps with `resume` from it, give the
+ * same losses, final state and grid, bit for bit, as A + B steps in one call
+ * (same src, S, learning rates and seed).  Waits for `stream`.
  * Errors: INVALID_ARG (null, a learned source, steps outside 0..1e6, S not
- * 16/32/64/128, non-positive learning rates, negative max_error); OOM; CUDA.
+ * 16/32/64/128, non-positive learning rates, negative max_error, a state
+ * with a null array or a step outside 0..2^31-1-steps, resume together with
+ * init_params or init_latents); OOM; CUDA.
  */
 vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params* params, void* stream, vdbc_grid** out,
                        double* loss_out);

@@ -95,11 +95,18 @@ class RenderStats(ctypes.Structure):
                 ("events", ctypes.c_uint64 * 6), ("kernel_ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
+class LearnState(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("params_m", ctypes.c_void_p), ("params_v", ctypes.c_void_p),
+                ("latents", ctypes.c_void_p), ("latents_m", ctypes.c_void_p), ("latents_v", ctypes.c_void_p),
+                ("step", ctypes.c_int64)]
+
+
 class LearnParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("samples_per_leaf", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("lr_latent", ctypes.c_float), ("max_error", ctypes.c_float), ("reserved", ctypes.c_int32),
                 ("max_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("init_params", ctypes.c_void_p),
-                ("init_latents", ctypes.c_void_p), ("force", ctypes.c_void_p)]
+                ("init_latents", ctypes.c_void_p), ("force", ctypes.c_void_p),
+                ("resume", ctypes.POINTER(LearnState)), ("save", ctypes.POINTER(LearnState))]
 
 
 MLP_PARAMS = 1729   # 19 -> 32 -> 32 -> 1: W1, b1, W2, b2, w3, b3
@@ -133,6 +140,9 @@ SIGNATURES = {
                                          ctypes.POINTER(_vp)]),
     "vdbc_batch_render_frames": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "vdbc_batch_reset": (ctypes.c_int, [_vp, _vp]),
+    "vdbc_batch_state_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "vdbc_batch_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), _vp, _vp]),
+    "vdbc_batch_set_state": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
     "vdbc_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     "vdbc_batch_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
     "vdbc_batch_free": (None, [_vp]),
@@ -405,6 +415,25 @@ def vdbc_batch_reset(batch: Batch, stream=None):
     _check(lib().vdbc_batch_reset(batch.handle, _stream(stream)))
 
 
+def vdbc_batch_get_state(batch: Batch, stream=None):
+    """(frame, per-pixel sums as a float32 numpy array of vdbc_batch_state_size floats)."""
+    n = ctypes.c_int64(0)
+    _check(lib().vdbc_batch_state_size(batch.handle, ctypes.byref(n)))
+    sums = np.zeros(n.value, dtype=np.float32)
+    frame = ctypes.c_int32(0)
+    _check(lib().vdbc_batch_get_state(batch.handle, ctypes.byref(frame), sums.ctypes.data, _stream(stream)))
+    return int(frame.value), sums
+
+
+def vdbc_batch_set_state(batch: Batch, frame: int, sums, stream=None):
+    n = ctypes.c_int64(0)
+    _check(lib().vdbc_batch_state_size(batch.handle, ctypes.byref(n)))
+    a = np.ascontiguousarray(sums, dtype=np.float32)
+    if a.size != n.value:
+        raise ValueError("state of %d floats for a batch of %d" % (a.size, n.value))
+    _check(lib().vdbc_batch_set_state(batch.handle, int(frame), a.ctypes.data, _stream(stream)))
+
+
 def vdbc_batch_get_tuning(batch: Batch) -> Tuning:
     t = Tuning()
     _check(lib().vdbc_batch_get_tuning(batch.handle, ctypes.byref(t)))
@@ -427,18 +456,50 @@ def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, coun
                                             _ptr(active_out)[0], _ptr(counts_out)[0], _stream(stream)))
 
 
+class LearnCheckpoint:
+    """The arrays of a vdbc_learn_state (device tensors the caller owns) and
+    its step count.  ``LearnCheckpoint.zeros(grid, torch, device)`` sizes them
+    for `grid`'s leaf positions."""
+    FIELDS = ("params", "params_m", "params_v", "latents", "latents_m", "latents_v")
+
+    def __init__(self, arrays, step=0):
+        self.arrays = dict(arrays)
+        self.step = int(step)
+
+    @classmethod
+    def zeros(cls, grid, torch, device):
+        npos = 1
+        for d in grid.info.dims:
+            npos *= (int(d) + 7) // 8
+        n = dict(params=MLP_PARAMS, params_m=MLP_PARAMS, params_v=MLP_PARAMS, latents=npos * 16,
+                 latents_m=npos * 16, latents_v=npos * 16)
+        return cls({k: torch.zeros(n[k], dtype=torch.float32, device=device) for k in cls.FIELDS})
+
+    def struct(self) -> LearnState:
+        return LearnState(*[_ptr(self.arrays[k])[0] for k in self.FIELDS], self.step)
+
+
 def vdbc_learn(grid: Grid, steps=200, samples_per_leaf=64, lr=1e-3, lr_latent=1e-2, max_error=0.0, max_bytes=0,
-               seed=0, init_params=None, init_latents=None, force=None, stream=None):
+               seed=0, init_params=None, init_latents=None, force=None, resume=None, save=None, stream=None):
     """Learned grid from `grid` (see include/vdbc.h).  init_params (1729),
     init_latents (per leaf position x 16) and force (per leaf position,
-    uint8) are device tensors or None.  Returns (Grid, per-step losses)."""
+    uint8) are device tensors or None; resume / save are LearnCheckpoint or
+    None (save.step is updated).  Returns (Grid, per-step losses)."""
     p = LearnParams(int(steps), int(samples_per_leaf), float(lr), float(lr_latent), float(max_error), 0,
                     int(max_bytes), int(seed), _ptr(init_params)[0] if init_params is not None else None,
                     _ptr(init_latents)[0] if init_latents is not None else None,
                     _ptr(force)[0] if force is not None else None)
+    rs = resume.struct() if resume is not None else None
+    sv = save.struct() if save is not None else None
+    if rs is not None:
+        p.resume = ctypes.pointer(rs)
+    if sv is not None:
+        p.save = ctypes.pointer(sv)
     out = _vp()
     losses = np.zeros(max(int(steps), 1), dtype=np.float64)
     _check(lib().vdbc_learn(grid.handle, ctypes.byref(p), _stream(stream), ctypes.byref(out), losses.ctypes.data))
+    if sv is not None:
+        save.step = int(sv.step)
     return Grid(out.value), losses[:int(steps)]
 
 

@@ -111,6 +111,25 @@ __global__ void k_gather_leaf(const uint32_t* __restrict__ pos, long long nleave
     for (int c = 0; c < kMlpLatent; ++c) lat[l * kMlpLatent + c] = lat_pos ? lat_pos[(size_t)p * kMlpLatent + c] : 0.0f;
 }
 
+// 16-float rows between leaf order and leaf-position order (training states)
+__global__ void k_gather_rows(const uint32_t* __restrict__ pos, long long nleaves, const float* __restrict__ by_pos,
+                              float* __restrict__ by_leaf)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaves * kMlpLatent) return;
+    const long long l = i / kMlpLatent;
+    by_leaf[i] = by_pos[(size_t)pos[l] * kMlpLatent + (i - l * kMlpLatent)];
+}
+
+__global__ void k_scatter_rows(const uint32_t* __restrict__ pos, long long nleaves, const float* __restrict__ by_leaf,
+                               float* __restrict__ by_pos)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaves * kMlpLatent) return;
+    const long long l = i / kMlpLatent;
+    by_pos[(size_t)pos[l] * kMlpLatent + (i - l * kMlpLatent)] = by_leaf[i];
+}
+
 __global__ void k_compact(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ rank, long long n,
                           uint32_t* __restrict__ list)
 {
@@ -871,6 +890,19 @@ vdbc_status check_learn_params(const vdbc_learn_params* p)
     if (p->steps > 0 && (!(p->lr > 0.0f) || !(p->lr_latent > 0.0f) || !std::isfinite(p->lr) || !std::isfinite(p->lr_latent)))
         return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn: learning rates must be positive and finite");
     if (!(p->max_error >= 0.0f)) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn: max_error must be >= 0");
+    for (const vdbc_learn_state* st : {static_cast<const vdbc_learn_state*>(p->resume),
+                                       static_cast<const vdbc_learn_state*>(p->save)}) {
+        if (!st) continue;
+        if (!st->params || !st->params_m || !st->params_v || !st->latents || !st->latents_m || !st->latents_v)
+            return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn: a training state with a null array");
+    }
+    if (p->resume) {
+        if (p->init_params || p->init_latents)
+            return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn: resume excludes init_params and init_latents");
+        if (p->resume->step < 0 || p->resume->step > (int64_t)INT32_MAX - p->steps)
+            return set_error(VDBC_ERR_INVALID_ARG, "vdbc_learn: resume step %lld outside 0..2^31-1-steps",
+                             (long long)p->resume->step);
+    }
     return VDBC_OK;
 }
 }  // namespace
@@ -918,7 +950,9 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     if (nlow > 0) KLAUNCH(k_leaf_pos<<<blocks(nlow, 256), 256, 0, s>>>(src->view.lower, nlow, lo, nlx, nly, pos));
     if (nl > 0) {
         KLAUNCH(k_leaf_range<<<blocks(nl * 32, 256), 256, 0, s>>>(src->view, nl, lmeta));
-        KLAUNCH(k_gather_leaf<<<blocks(nl, 256), 256, 0, s>>>(pos, nl, lp->force, lp->init_latents, force, lat, trains));
+        KLAUNCH(k_gather_leaf<<<blocks(nl, 256), 256, 0, s>>>(pos, nl, lp->force,
+                                                              lp->resume ? lp->resume->latents : lp->init_latents,
+                                                              force, lat, trains));
     }
     scan_u32(trains, trank, nl, scan_tmp, total, s);
     if (nl > 0) KLAUNCH(k_compact<<<blocks(nl, 256), 256, 0, s>>>(trains, trank, nl, list));
@@ -938,11 +972,21 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     VDBC_CUDA(cudaMemsetAsync(lat_m, 0, (size_t)std::max<long long>(nl, 1) * kMlpLatent * 4, s));
     VDBC_CUDA(cudaMemsetAsync(lat_v, 0, (size_t)std::max<long long>(nl, 1) * kMlpLatent * 4, s));
     VDBC_CUDA(cudaMemsetAsync(glat, 0, (size_t)std::max<long long>(nl, 1) * kMlpLatent * 4, s));
-    if (lp->init_params) {
+    const vdbc_learn_state* rs = lp->resume;
+    if (rs) {
+        VDBC_CUDA(cudaMemcpyAsync(params, rs->params, kMlpParams * 4, cudaMemcpyDefault, s));
+        VDBC_CUDA(cudaMemcpyAsync(pm, rs->params_m, kMlpParams * 4, cudaMemcpyDefault, s));
+        VDBC_CUDA(cudaMemcpyAsync(pv, rs->params_v, kMlpParams * 4, cudaMemcpyDefault, s));
+        if (nl > 0) {
+            KLAUNCH(k_gather_rows<<<blocks(nl * kMlpLatent, 256), 256, 0, s>>>(pos, nl, rs->latents_m, lat_m));
+            KLAUNCH(k_gather_rows<<<blocks(nl * kMlpLatent, 256), 256, 0, s>>>(pos, nl, rs->latents_v, lat_v));
+        }
+    } else if (lp->init_params) {
         VDBC_CUDA(cudaMemcpyAsync(params, lp->init_params, kMlpParams * 4, cudaMemcpyDefault, s));
     } else {
         KLAUNCH(k_init_params<<<blocks(kMlpParams, 256), 256, 0, s>>>(params, k0, k1));
     }
+    const long long t0 = rs ? rs->step : 0;     // Adam steps already taken
     const long long nsamp = (long long)n_train << lg_s;
     if (lp->steps > 0 && nsamp > 0) {
         const int grid = grad_grid((long long)n_train);
@@ -951,10 +995,11 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
         VDBC_TRY(pool.get(&loss_hist, lp->steps));
         LeafSamples ls{src->view, list, pos, lmeta, lat, lg_s, 0u, k0, k1};
         for (int t = 0; t < lp->steps; ++t) {
-            ls.step = (uint32_t)t;
+            const long long tg = t0 + t;
+            ls.step = (uint32_t)tg;
             VDBC_TRY(run_grad(ls, (long long)n_train, nsamp, params, part, loss_part, grid, grad, loss_hist + t, glat, s));
-            const float c1 = (float)(1.0 - std::pow((double)kBeta1, (double)(t + 1)));
-            const float c2 = (float)(1.0 - std::pow((double)kBeta2, (double)(t + 1)));
+            const float c1 = (float)(1.0 - std::pow((double)kBeta1, (double)(tg + 1)));
+            const float c2 = (float)(1.0 - std::pow((double)kBeta2, (double)(tg + 1)));
             KLAUNCH(k_adam<<<blocks(kMlpParams, 256), 256, 0, s>>>(params, grad, pm, pv, kMlpParams, lp->lr, c1, c2));
             const long long nz = nl * kMlpLatent;
             KLAUNCH(k_adam<<<(unsigned)std::min<long long>(blocks(nz, 256), 4096), 256, 0, s>>>(lat, glat, lat_m, lat_v, nz,
@@ -964,6 +1009,18 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
         if (loss_out) VDBC_CUDA(cudaMemcpyAsync(loss_out, loss_hist, (size_t)lp->steps * 8, cudaMemcpyDeviceToHost, s));
     } else if (loss_out && lp->steps > 0) {
         for (int t = 0; t < lp->steps; ++t) loss_out[t] = 0.0;
+    }
+    if (vdbc_learn_state* sv = lp->save) {
+        const size_t npos = (size_t)nlx * nly * ((si.dims[2] + 7) / 8) * kMlpLatent;
+        VDBC_CUDA(cudaMemcpyAsync(sv->params, params, kMlpParams * 4, cudaMemcpyDefault, s));
+        VDBC_CUDA(cudaMemcpyAsync(sv->params_m, pm, kMlpParams * 4, cudaMemcpyDefault, s));
+        VDBC_CUDA(cudaMemcpyAsync(sv->params_v, pv, kMlpParams * 4, cudaMemcpyDefault, s));
+        float* rows[3][2] = {{lat, sv->latents}, {lat_m, sv->latents_m}, {lat_v, sv->latents_v}};
+        for (auto& r : rows) {
+            VDBC_CUDA(cudaMemsetAsync(r[1], 0, npos * 4, s));
+            if (nl > 0) KLAUNCH(k_scatter_rows<<<blocks(nl * kMlpLatent, 256), 256, 0, s>>>(pos, nl, r[0], r[1]));
+        }
+        sv->step = t0 + lp->steps;
     }
 
     // ---- 3. bf16 latents, network tables, per-leaf error through the tensor cores

@@ -1862,6 +1862,43 @@ extern "C" vdbc_status vdbc_batch_reset(vdbc_batch* b, void* stream)
     return VDBC_OK;
 }
 
+// progressive accumulation state: the frame counter and the per-pixel sums
+// of every job, one contiguous float4 array in job order
+static size_t batch_state_pixels(const vdbc_batch* b)
+{
+    size_t npix = 0;
+    for (const JobView& j : b->h_jobs) npix += (size_t)j.npix;
+    return npix;
+}
+
+extern "C" vdbc_status vdbc_batch_state_size(const vdbc_batch* b, int64_t* floats)
+{
+    clear_error();
+    if (!b || !floats) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_state_size: null argument");
+    *floats = (int64_t)batch_state_pixels(b) * 4;
+    return VDBC_OK;
+}
+
+extern "C" vdbc_status vdbc_batch_get_state(const vdbc_batch* b, int32_t* frame, float* host_sums, void* stream)
+{
+    clear_error();
+    if (!b || !frame || !host_sums) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_get_state: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VDBC_CUDA(cudaMemcpyAsync(frame, b->d_frame, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    VDBC_CUDA(cudaMemcpyAsync(host_sums, b->sums, batch_state_pixels(b) * sizeof(float4), cudaMemcpyDeviceToHost, s));
+    return wait_stream(s);
+}
+
+extern "C" vdbc_status vdbc_batch_set_state(vdbc_batch* b, int32_t frame, const float* host_sums, void* stream)
+{
+    clear_error();
+    if (!b || !host_sums || frame < 0) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_set_state: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VDBC_CUDA(cudaMemcpyAsync(b->d_frame, &frame, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    VDBC_CUDA(cudaMemcpyAsync(b->sums, host_sums, batch_state_pixels(b) * sizeof(float4), cudaMemcpyHostToDevice, s));
+    return wait_stream(s);     // `frame` and `host_sums` must outlive the copies
+}
+
 extern "C" vdbc_status vdbc_batch_get_tuning(const vdbc_batch* b, vdbc_tuning* t)
 {
     clear_error();

@@ -52,7 +52,10 @@ def run_workload(v, torch, vg, sc):
             torch.cuda.synchronize()
             out["%s_%d" % (name, payload)] = img.cpu().numpy()
             out["flags_%s_%d" % (name, payload)] = np.uint64(v.vdbc_render_stats_get(g).error_flags)
-    learned, _ = v.vdbc_learn(grids[v.FP16], steps=3, samples_per_leaf=16, seed=5)
+    npos = ((DIMS[0] + 7) // 8) * ((DIMS[1] + 7) // 8) * ((DIMS[2] + 7) // 8)
+    half = torch.arange(npos, device=dev) % 2 + 1          # neural and raw leaves, alternating by position
+    learned, _ = v.vdbc_learn(grids[v.FP16], steps=3, samples_per_leaf=16, seed=5, force=half.to(torch.uint8))
+    out["n_neural"] = np.int64(learned.info.n_neural)
     dec = torch.empty_like(vol)
     v.vdbc_grid_decode(learned, dec)
     out["decode_learned"] = dec.cpu().numpy()

@@ -108,3 +108,32 @@ def test_batch_rejects_bad_jobs(env):
     assert ex.value.status == v.ERR_INVALID_ARG
     with pytest.raises(v.VdbcError):
         v.vdbc_batch_create([], autotune=False)
+
+
+def test_batch_accumulation_state_checkpoint(env):
+    """The progressive state (frame counter and per-pixel sums) taken after
+    two frames and restored into a fresh batch of the same jobs: three more
+    frames there give every job the image of five frames in one batch."""
+    torch, v = env["torch"], env["v"]
+    jobs = build_jobs(env)
+    structs = [v.make_job(j["grid"], j["cam"], j["med"], j["spp"], j["seed"], j["img"]) for j in jobs]
+    b = v.vdbc_batch_create(structs, autotune=False, keep=jobs)
+    v.vdbc_batch_render_frames(b, 2)
+    frame, sums = v.vdbc_batch_get_state(b)
+    assert frame == 2 and sums.size == 4 * sum(w * h for (w, h) in (j["wh"] for j in jobs))
+    v.vdbc_batch_render_frames(b, 3)
+    torch.cuda.synchronize()
+    want = [j["img"].cpu().numpy() for j in jobs]
+    imgs = [torch.full_like(j["img"], -1.0) for j in jobs]
+    structs2 = [v.make_job(j["grid"], j["cam"], j["med"], j["spp"], j["seed"], im) for j, im in zip(jobs, imgs)]
+    b2 = v.vdbc_batch_create(structs2, autotune=False, keep=(jobs, imgs))
+    v.vdbc_batch_set_state(b2, frame, sums)
+    v.vdbc_batch_render_frames(b2, 3)
+    torch.cuda.synchronize()
+    for w, im in zip(want, imgs):
+        assert np.array_equal(w.view(np.uint32), im.cpu().numpy().view(np.uint32))
+    assert v.vdbc_batch_get_state(b2)[0] == 5
+    with pytest.raises(ValueError):
+        v.vdbc_batch_set_state(b2, 0, sums[:-4])
+    with pytest.raises(v.VdbcError):
+        v.vdbc_batch_set_state(b2, -1, sums)

@@ -263,6 +263,47 @@ def test_learn_argument_errors(env):
         v.vdbc_batch_create([v.make_job(learned, cam, med, 1, 0, out)], autotune=False)
 
 
+def test_training_checkpoint_resumes_bit_exactly(env):
+    """A + B steps through a saved training state (network, latents, both
+    Adam moment sets, step count), the state passed through host memory as
+    a checkpoint file would, equal A + B steps in one call: the same losses,
+    state and learned grid, bit for bit."""
+    torch, v = env["torch"], env["v"]
+    dims = (40, 36, 44)
+    _, grid, _ = source(env, "blobs", dims, 4, 2.0)
+    npos = int(np.prod(leaf_grid(dims)))
+    every = torch.ones(npos, dtype=torch.uint8, device=env["dev"])           # every leaf neural
+    kw = dict(samples_per_leaf=32, lr=2e-3, lr_latent=2e-2, seed=9, force=every)
+    full = v.LearnCheckpoint.zeros(grid, torch, env["dev"])
+    g_full, l_full = v.vdbc_learn(grid, steps=7, save=full, **kw)
+    assert full.step == 7
+    half = v.LearnCheckpoint.zeros(grid, torch, env["dev"])
+    _, l_a = v.vdbc_learn(grid, steps=3, save=half, **kw)
+    assert half.step == 3
+    host = {k: t.cpu().numpy().copy() for k, t in half.arrays.items()}        # the checkpoint on disk
+    resumed = v.LearnCheckpoint({k: torch.from_numpy(a).to(env["dev"]) for k, a in host.items()}, half.step)
+    again = v.LearnCheckpoint.zeros(grid, torch, env["dev"])
+    g_res, l_b = v.vdbc_learn(grid, steps=4, resume=resumed, save=again, **kw)
+    assert again.step == 7
+    assert np.array_equal(np.concatenate([l_a, l_b]), l_full)
+    for k in v.LearnCheckpoint.FIELDS:
+        a, b = full.arrays[k].cpu().numpy(), again.arrays[k].cpu().numpy()
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), k
+    assert np.array_equal(v.vdbc_learn_get_params(g_full).view(np.uint32), v.vdbc_learn_get_params(g_res).view(np.uint32))
+    assert np.array_equal(decode(env, g_full, dims).view(np.uint32), decode(env, g_res, dims).view(np.uint32))
+    assert g_full.info.n_neural == g_res.info.n_neural == grid.info.n_leaves > 0
+    # the moments moved, positions without a leaf stay 0, and resuming with a
+    # warm start as well is refused
+    assert float(full.arrays["params_v"].abs().sum()) > 0
+    lat = full.arrays["latents"].view(-1, 16).abs().sum(1).cpu().numpy()
+    assert (lat > 0).sum() <= grid.info.n_leaves
+    with pytest.raises(v.VdbcError):
+        v.vdbc_learn(grid, steps=1, resume=resumed, init_params=resumed.arrays["params"], **kw)
+    bad = v.LearnCheckpoint(dict(resumed.arrays), -1)
+    with pytest.raises(v.VdbcError):
+        v.vdbc_learn(grid, steps=1, resume=bad, **kw)
+
+
 # ------------------------------------------------------------------ what the network gains
 def test_trained_network_beats_vdb_at_equal_memory(env):
     """A 96^3 turbulent medium: the method without the network (FP32 VDB at
