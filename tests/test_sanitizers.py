@@ -55,10 +55,22 @@ def loaded_library(module, extra_env):
     return r.stdout.strip().splitlines()[-1]
 
 
+def prebuild(code, extra_env):
+    """Builds an instrumented library in a process without libasan preloaded
+    (the compilers themselves must not run under it)."""
+    e = dict(os.environ)
+    e.update(extra_env)
+    e["PYTHONPATH"] = ROOT + os.pathsep + e.get("PYTHONPATH", "")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=e, stdout=subprocess.PIPE,
+                       stderr=subprocess.STDOUT, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-4000:]
+
+
 def test_oracle_under_asan_and_ubsan():
     """Every oracle pin (encoder, codecs, renderer, network) on the
     instrumented oracle."""
     env = {"ORACLE_SANITIZE": "1"}
+    prebuild("import oracle; oracle.build()", env)
     assert loaded_library("oracle", env).endswith("liboracle_asan.so")
     files = sorted(f for f in os.listdir(HERE) if f.startswith("test_oracle_") and f.endswith(".py"))
     assert len(files) >= 4
@@ -71,6 +83,7 @@ def test_c_abi_host_code_under_asan_and_ubsan():
     error strings, grid-file parsing and validation) on the instrumented
     library."""
     env = {"VDBC_SANITIZE": "1"}
+    prebuild("from paper_2504_04564_gb300 import build; build.build(sanitize=True); build.build(checked=True)", {})
     assert loaded_library("paper_2504_04564_gb300", env).endswith("libvdbc_asan.so")
     out = run_pytest(["test_abi.py"], env)
     assert " passed" in out
