@@ -51,84 +51,200 @@ __device__ __forceinline__ void brick_coords(const Dims& d, int b, int& bx, int&
 // ---------------------------------------------------------------- pass 1
 constexpr int kPassThreads = 256;
 
-// One block per 32^3 brick: the brick's min/max keys, and its counts of the
-// upper 16 bits added to the global level-1 histogram.  The counts are first
-// gathered in a block-private histogram of 16-bit bins in shared memory, two
-// bins per word (a brick has 32768 voxels, so a bin cannot overflow into its
-// neighbour); the lanes of a row that share a key add once (match_any), and
-// only the non-zero bins reach the global histogram.
+// Persistent blocks, one per SM, each taking bricks b = blockIdx.x, +grid,
+// ...: a brick's min/max keys, and its counts of the upper 16 bits added to
+// the global level-1 histogram.  The counts gather in a block-private
+// histogram of 16-bit bins in shared memory, two to a word (a brick has 32768
+// voxels, so no bin overflows into its neighbour); after each brick the block
+// scans it, adds the non-zero bins to the global histogram and clears it.  A
+// warp step whose values all share one key (empty space) adds to a per-warp
+// run in registers; otherwise each lane adds its own values, equal keys
+// merged first (vector path) or lanes of one key merged by match_any (scalar
+// path).
 constexpr int kPass1Threads = 1024;
-constexpr size_t kPass1Smem = 32768 * sizeof(uint32_t);
+constexpr int kPass1Words = 32768;
+constexpr size_t kPass1Smem = (size_t)kPass1Words * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict__ v, Dims d,
+__device__ __forceinline__ void bin_add(uint32_t* h, uint32_t key, uint32_t n)
+{
+    atomicAdd(h + (key >> 1), n << ((key & 1u) * 16));
+}
+
+// adds the block histogram's non-zero bins to the global one and clears it
+__device__ __forceinline__ void pass1_flush(uint32_t* h, unsigned long long* __restrict__ hist)
+{
+    uint4* h4 = reinterpret_cast<uint4*>(h);
+    for (int i = threadIdx.x; i < kPass1Words / 4; i += kPass1Threads) {
+        const uint4 c = h4[i];
+        if ((c.x | c.y | c.z | c.w) == 0u) continue;
+        h4[i] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long bin = 2ll * (4 * i + j);
+            if (w[j] & 0xffffu) atomicAdd(hist + bin, (unsigned long long)(w[j] & 0xffffu));
+            if (w[j] >> 16) atomicAdd(hist + bin + 1, (unsigned long long)(w[j] >> 16));
+        }
+    }
+}
+
+// floor(r / d) for 0 <= r < 1024 and 1 <= d <= 32 by a multiply and a shift
+// (m = ceil(2^21 / d); exact over that whole range, which an exhaustive check
+// confirms, and r * m < 2^31): the row -> (y, z) split of a brick or part
+__host__ __device__ __forceinline__ uint32_t div_magic(int d) { return ((1u << 21) + (uint32_t)d - 1u) / (uint32_t)d; }
+__device__ __forceinline__ int div_small(int r, uint32_t m) { return (int)(((uint32_t)r * m) >> 21); }
+
+// per-warp run of one key (warp-uniform): counts it in registers, and adds
+// it to the block histogram when the key changes
+struct KeyRun {
+    uint32_t key = 0xffffffffu, cnt = 0u;
+    __device__ __forceinline__ void add(uint32_t k, uint32_t n, int lane, uint32_t* h)
+    {
+        if (k == key) {
+            cnt += n;
+        } else {
+            if (cnt && lane == 0) bin_add(h, key, cnt);
+            key = k;
+            cnt = n;
+        }
+    }
+};
+
+// kVec: the volume's rows start on 16-byte boundaries (nx % 4 == 0 and an
+// aligned base), so a lane loads four voxels at once: lane = 8 * rsub + sub
+// takes float4 `sub` of row 4g + rsub, and a warp covers four rows a load.
+template <bool kVec>
+__global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict__ v, Dims d, int nbricks,
                                                          uint32_t* __restrict__ lo_key,
                                                          uint32_t* __restrict__ hi_key,
                                                          unsigned long long* __restrict__ hist,
                                                          int* __restrict__ nonfinite)
 {
-    extern __shared__ uint32_t s_hist[];
-    __shared__ uint32_t s_min[kPass1Threads / 32], s_max[kPass1Threads / 32];
+    extern __shared__ __align__(16) uint32_t s_h[];
+    __shared__ uint32_t s_min[2][kPass1Threads / 32], s_max[2][kPass1Threads / 32];
     __shared__ int s_bad;
-    for (int i = threadIdx.x; i < 32768; i += kPass1Threads) s_hist[i] = 0u;
+    for (int i = threadIdx.x; i < kPass1Words; i += kPass1Threads) s_h[i] = 0u;
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    const int b = blockIdx.x;
-    int bx, by, bz;
-    brick_coords(d, b, bx, by, bz);
-    const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
-    const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    constexpr int U = 8, kWarps = kPass1Threads / 32;
     bool bad = false;
-    const bool valid = lane < ex;
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-    const int rows = ey * ez;
-    // four rows' loads in flight per warp before any of them is used
-    constexpr int U = 4, kWarps = kPass1Threads / 32;
-    for (int r0 = warp; r0 < rows; r0 += kWarps * U) {
-        uint32_t u[U];
+    int p = 0;
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x, p ^= 1) {
+        int bx, by, bz;
+        brick_coords(d, b, bx, by, bz);
+        const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
+        const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
+        const int rows = ey * ez;
+        const uint32_t mey = div_magic(ey);
+        uint32_t kmin = 0xffffffffu, kmax = 0u;
+        KeyRun run;
+        if constexpr (kVec) {
+            const int sub = lane & 7, rsub = lane >> 3;
+            const bool xvalid = sub * 4 < ex;             // ex is a multiple of 4 here
+            const int quads = (rows + 3) >> 2;
+            for (int g0 = warp; g0 < quads; g0 += kWarps * U) {
+                uint4 u[U];
+                bool ok[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int row = r0 + q * kWarps;
-            u[q] = 0u;
-            if (valid && row < rows) {
-                const int y = row % ey, z = row / ey;
-                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+                for (int q = 0; q < U; ++q) {
+                    const int row = 4 * (g0 + q * kWarps) + rsub;
+                    ok[q] = xvalid && row < rows;
+                    u[q] = make_uint4(0u, 0u, 0u, 0u);
+                    if (ok[q]) {
+                        const int z = div_small(row, mey), y = row - z * ey;
+                        u[q] = __ldg(reinterpret_cast<const uint4*>(
+                            v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + 4 * sub));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (g0 + q * kWarps >= quads) break;                // warp-uniform
+                    const unsigned part = __ballot_sync(0xffffffffu, ok[q]);   // holds lane 0
+                    const uint32_t w[4] = {u[q].x, u[q].y, u[q].z, u[q].w};
+                    if (ok[q]) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            bad |= ((w[j] & 0x7f800000u) == 0x7f800000u);
+                            const uint32_t k = okey(w[j]);
+                            kmin = min(kmin, k);
+                            kmax = max(kmax, k);
+                        }
+                    }
+                    const uint32_t k0 = w[0] >> 16;
+                    const uint32_t lead = __shfl_sync(0xffffffffu, k0, 0);
+                    const bool same = !ok[q] || (k0 == lead && (w[1] >> 16) == lead && (w[2] >> 16) == lead &&
+                                                 (w[3] >> 16) == lead);
+                    if (__all_sync(0xffffffffu, same)) {
+                        run.add(lead, 4u * (uint32_t)__popc(part), lane, s_h);
+                    } else if (ok[q]) {
+                        // the lane's four keys, equal ones merged, one add per distinct key
+                        const uint32_t k[4] = {w[0] >> 16, w[1] >> 16, w[2] >> 16, w[3] >> 16};
+                        uint32_t n[4] = {1u, 1u, 1u, 1u};
+#pragma unroll
+                        for (int j = 1; j < 4; ++j)
+#pragma unroll
+                            for (int i = 0; i < j; ++i)
+                                if (n[j] && n[i] && k[i] == k[j]) { n[i] += n[j]; n[j] = 0u; }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (n[j]) bin_add(s_h, k[j], n[j]);
+                    }
+                }
+            }
+        } else {
+            const bool valid = lane < ex;
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            // U rows' loads in flight per warp before any of them is used
+            for (int r0 = warp; r0 < rows; r0 += kWarps * U) {
+                uint32_t u[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int row = r0 + q * kWarps;
+                    u[q] = 0u;
+                    if (valid && row < rows) {
+                        const int z = div_small(row, mey), y = row - z * ey;
+                        u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (r0 + q * kWarps >= rows) break;       // warp-uniform
+                    const uint32_t w = u[q];
+                    const uint32_t key = w >> 16;
+                    if (valid) {
+                        bad |= ((w & 0x7f800000u) == 0x7f800000u);
+                        const uint32_t k = okey(w);
+                        kmin = min(kmin, k);
+                        kmax = max(kmax, k);
+                    }
+                    const unsigned peers = valid ? __match_any_sync(vmask, key) : 0u;
+                    const bool one_key = __shfl_sync(0xffffffffu, peers, 0) == vmask;   // lane 0 is always valid
+                    if (one_key) {
+                        run.add(__shfl_sync(0xffffffffu, key, 0), (uint32_t)__popc(vmask), lane, s_h);
+                    } else if (valid && lane == __ffs(peers) - 1) {
+                        bin_add(s_h, key, (uint32_t)__popc(peers));
+                    }
+                }
             }
         }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            if (r0 + q * kWarps >= rows) break;       // warp-uniform
-            if (valid) {
-                const uint32_t w = u[q];
-                bad |= ((w & 0x7f800000u) == 0x7f800000u);
-                const uint32_t k = okey(w);
-                kmin = min(kmin, k);
-                kmax = max(kmax, k);
-                const uint32_t key = w >> 16;
-                const unsigned peers = __match_any_sync(vmask, key);
-                if (lane == __ffs(peers) - 1)
-                    atomicAdd(s_hist + (key >> 1), (uint32_t)__popc(peers) << ((key & 1u) * 16));
-            }
+        if (run.cnt && lane == 0) bin_add(s_h, run.key, run.cnt);
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) { s_min[p][warp] = kmin; s_max[p][warp] = kmax; }
+        __syncthreads();                                   // the brick's counts and ranges are in
+        if (threadIdx.x == 0) {
+            uint32_t a = s_min[p][0], c = s_max[p][0];
+            for (int w = 1; w < kWarps; ++w) { a = min(a, s_min[p][w]); c = max(c, s_max[p][w]); }
+            lo_key[b] = a;
+            hi_key[b] = c;
         }
+        pass1_flush(s_h, hist);
+        __syncthreads();                                   // histogram clear before the next brick
     }
-    kmin = __reduce_min_sync(0xffffffffu, kmin);
-    kmax = __reduce_max_sync(0xffffffffu, kmax);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
-    if (lane == 0) { s_min[warp] = kmin; s_max[warp] = kmax; }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_bad, 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < 32768; i += kPass1Threads) {
-        const uint32_t c = s_hist[i];
-        if (c & 0xffffu) atomicAdd(hist + 2 * i, (unsigned long long)(c & 0xffffu));
-        if (c >> 16) atomicAdd(hist + 2 * i + 1, (unsigned long long)(c >> 16));
-    }
-    if (threadIdx.x == 0) {
-        uint32_t a = s_min[0], c = s_max[0];
-        for (int w = 1; w < kPass1Threads / 32; ++w) { a = min(a, s_min[w]); c = max(c, s_max[w]); }
-        lo_key[b] = a;
-        hi_key[b] = c;
-        if (s_bad) atomicOr(nonfinite, 1);
-    }
+    if (threadIdx.x == 0 && s_bad) atomicOr(nonfinite, 1);
 }
 
 // most frequent of 65536 bins, ties to the smaller index; writes (out_base | idx)
@@ -158,6 +274,12 @@ __global__ void __launch_bounds__(1024) k_argmax(const unsigned long long* __res
 }
 
 // ---------------------------------------------------------------- pass 2
+// One block per brick whose range reaches the winning bin H: the lower 16 bits
+// of its values inside the bin, counted into the level-2 histogram.  A warp
+// step whose in-bin values all share one key (the background itself, inside
+// empty space and at its edge) adds to a per-warp run in registers instead
+// of an atomic on that one global bin.  kVec as in pass 1.
+template <bool kVec>
 __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict__ v, Dims d,
                                                         const uint32_t* __restrict__ lo_key,
                                                         const uint32_t* __restrict__ hi_key,
@@ -175,46 +297,101 @@ __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict_
     const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
     const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool valid = lane < ex;
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     const int rows = ey * ez;
-    uint32_t run_key = 0xffffffffu;          // per-warp run of one key, as in pass 1
+    const uint32_t mey = div_magic(ey);
+    constexpr int kW = kPassThreads / 32;
+    uint32_t run_key = 0xffffffffu;          // per-warp run of one key (warp-uniform)
     unsigned long long run_cnt = 0;
-    constexpr int U = 4;
-    for (int r0 = warp * U; r0 < rows; r0 += (kPassThreads / 32) * U) {
-        uint32_t u[U];
+    auto run_add = [&](uint32_t k, unsigned long long n) {
+        if (k == run_key) {
+            run_cnt += n;
+        } else {
+            if (run_cnt && lane == 0) atomicAdd(hist + run_key, run_cnt);
+            run_key = k;
+            run_cnt = n;
+        }
+    };
+    if constexpr (kVec) {
+        constexpr int U = 4;
+        const int sub = lane & 7, rsub = lane >> 3;
+        const bool xvalid = sub * 4 < ex;
+        const int quads = (rows + 3) >> 2;
+        for (int g0 = warp; g0 < quads; g0 += kW * U) {
+            uint4 u[U];
+            bool ok[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            int row = r0 + q;
-            u[q] = 0;
-            if (valid && row < rows) {
-                int y = row % ey, z = row / ey;
-                u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
+            for (int q = 0; q < U; ++q) {
+                const int row = 4 * (g0 + q * kW) + rsub;
+                ok[q] = xvalid && row < rows;
+                u[q] = make_uint4(0u, 0u, 0u, 0u);
+                if (ok[q]) {
+                    const int z = div_small(row, mey), y = row - z * ey;
+                    u[q] = __ldg(reinterpret_cast<const uint4*>(
+                        v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + 4 * sub));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                if (g0 + q * kW >= quads) break;                      // warp-uniform
+                const uint32_t w[4] = {u[q].x, u[q].y, u[q].z, u[q].w};
+                unsigned in = 0u;                                     // this lane's values in the bin
+#pragma unroll
+                for (int j = 0; j < 4; ++j) in |= (ok[q] && (w[j] >> 16) == H) ? (1u << j) : 0u;
+                const unsigned m = __ballot_sync(0xffffffffu, in != 0u);
+                if (m == 0u) continue;
+                const uint32_t first = (in & 1u) ? w[0] : (in & 2u) ? w[1] : (in & 4u) ? w[2] : w[3];
+                const uint32_t mine = first & 0xffffu;          // only read from a lane with in != 0
+                const uint32_t lead = __shfl_sync(0xffffffffu, mine, __ffs(m) - 1);
+                bool same = true;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) same &= !((in >> j) & 1u) || (w[j] & 0xffffu) == lead;
+                if (__all_sync(0xffffffffu, same)) {
+                    run_add(lead, (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)__popc(in)));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool inj = (in >> j) & 1u;
+                        const unsigned mj = __ballot_sync(0xffffffffu, inj);
+                        if (mj == 0u) continue;
+                        const unsigned peers = inj ? __match_any_sync(mj, w[j] & 0xffffu) : 0u;
+                        if (inj && lane == __ffs(peers) - 1)
+                            atomicAdd(hist + (w[j] & 0xffffu), (unsigned long long)__popc(peers));
+                    }
+                }
             }
         }
+    } else {
+        constexpr int U = 8;
+        const bool valid = lane < ex;
+        for (int r0 = warp * U; r0 < rows; r0 += kW * U) {
+            uint32_t u[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            if (r0 + q >= rows) break;               // warp-uniform
-            uint32_t w = u[q];
-            bool in = valid && (w >> 16) == H;
-            unsigned m = __ballot_sync(0xffffffffu, in);       // warp-uniform
-            if (m == 0u) continue;
-            unsigned peers = in ? __match_any_sync(m, w & 0xffffu) : 0u;   // only the lanes of m call it
-            bool uniform = __all_sync(0xffffffffu, !valid || peers == vmask) && m == vmask;
-            if (uniform) {                                      // one key in the whole row
-                if ((w & 0xffffu) == run_key) {
-                    run_cnt += (unsigned long long)__popc(vmask);
-                } else {
-                    if (run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
-                    run_key = w & 0xffffu;
-                    run_cnt = (unsigned long long)__popc(vmask);
+            for (int q = 0; q < U; ++q) {
+                const int row = r0 + q;
+                u[q] = 0;
+                if (valid && row < rows) {
+                    const int z = div_small(row, mey), y = row - z * ey;
+                    u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
                 }
-            } else if (in && lane == __ffs(peers) - 1) {
-                atomicAdd(hist + (w & 0xffffu), (unsigned long long)__popc(peers));
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                if (r0 + q >= rows) break;               // warp-uniform
+                const uint32_t w = u[q];
+                const bool in = valid && (w >> 16) == H;
+                const unsigned m = __ballot_sync(0xffffffffu, in);       // warp-uniform
+                if (m == 0u) continue;
+                const unsigned peers = in ? __match_any_sync(m, w & 0xffffu) : 0u;   // only the lanes of m call it
+                const int leader = __ffs(m) - 1;
+                if (__shfl_sync(0xffffffffu, peers, leader) == m) {
+                    run_add(__shfl_sync(0xffffffffu, w & 0xffffu, leader), (unsigned long long)__popc(m));
+                } else if (in && lane == __ffs(peers) - 1) {
+                    atomicAdd(hist + (w & 0xffffu), (unsigned long long)__popc(peers));
+                }
             }
         }
     }
-    if (valid && run_cnt && lane == __ffs(vmask) - 1) atomicAdd(hist + run_key, run_cnt);
+    if (run_cnt && lane == 0) atomicAdd(hist + run_key, run_cnt);
 }
 
 // ---------------------------------------------------------------- scores (Eq. f1-f3)
@@ -705,34 +882,89 @@ __global__ void __launch_bounds__(kGroup == 32 ? 256 : kGroup)
 
 // Macrocell ranges of an FP32 grid straight from the input: the decoded grid
 // is V in the activated bricks and at the two corner voxels and B elsewhere
-// (its definition), so no tree descent is needed; one block per macrocell,
-// the input read only where a brick is active.  Same values, same ranges as
-// k_macrocells on the tree.
-__global__ void __launch_bounds__(256) k_macrocells_input(const float* __restrict__ v, Dims d,
-                                                          const uint8_t* __restrict__ active,
-                                                          const uint32_t* __restrict__ bsel, int mc, int mx, int my,
-                                                          float* __restrict__ mcmin, float* __restrict__ mcmax)
+// (its definition), so no tree descent is needed.  One block per macrocell:
+// a thread per brick that the dilated box overlaps (at most 4 per axis) sorts
+// it out, an inactive brick adding B (when its part of the box holds a voxel
+// other than a corner) and an active one its part to a list; then the whole
+// block reads the listed parts, eight rows in flight per warp, and a corner
+// inside the box adds its own value.  Same values, same ranges as
+// k_macrocells on the tree; the input is read only where a brick is active.
+constexpr int kMcInThreads = 512;
+__global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* __restrict__ v, Dims d,
+                                                                   const uint8_t* __restrict__ active,
+                                                                   const uint32_t* __restrict__ bsel, int mc, int mx,
+                                                                   int my, float* __restrict__ mcmin,
+                                                                   float* __restrict__ mcmax)
 {
-    __shared__ float s_lo[8], s_hi[8];
+    constexpr int kW = kMcInThreads / 32, kMaxParts = 64;
+    __shared__ float s_lo[kW], s_hi[kW];
+    __shared__ int s_part[kMaxParts][4];       // x0, width, y0 | z0 << 16, ey | ez << 16
+    __shared__ int s_nparts, s_hasB;
     const long long c = blockIdx.x;
     const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
     const int x0 = max(cx * mc - 1, 0), x1 = min(cx * mc + mc, d.nx - 1);
     const int y0 = max(cy * mc - 1, 0), y1 = min(cy * mc + mc, d.ny - 1);
     const int z0 = max(cz * mc - 1, 0), z1 = min(cz * mc + mc, d.nz - 1);
-    const float B = __uint_as_float(bsel[1]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ex = x1 - x0 + 1, ey = y1 - y0 + 1, rows = ey * (z1 - z0 + 1);
+    if (threadIdx.x == 0) { s_nparts = 0; s_hasB = 0; }
+    __syncthreads();
+    const int nbx = (x1 >> 5) - (x0 >> 5) + 1, nby = (y1 >> 5) - (y0 >> 5) + 1, nbz = (z1 >> 5) - (z0 >> 5) + 1;
+    if ((int)threadIdx.x < nbx * nby * nbz) {
+        const int t = threadIdx.x;
+        const int bx = (x0 >> 5) + t % nbx, by = (y0 >> 5) + (t / nbx) % nby, bz = (z0 >> 5) + t / (nbx * nby);
+        const int ax0 = max(x0, bx * 32), ax1 = min(x1, bx * 32 + 31);
+        const int ay0 = max(y0, by * 32), ay1 = min(y1, by * 32 + 31);
+        const int az0 = max(z0, bz * 32), az1 = min(z1, bz * 32 + 31);
+        if (__ldg(active + ((size_t)bz * d.by + by) * d.bx + bx)) {
+            const int i = atomicAdd(&s_nparts, 1);
+            s_part[i][0] = ax0;
+            s_part[i][1] = ax1 - ax0 + 1;
+            s_part[i][2] = ay0 | (az0 << 16);
+            s_part[i][3] = (ay1 - ay0 + 1) | ((az1 - az0 + 1) << 16);
+        } else {
+            const bool one_voxel = d.nx == 1 && d.ny == 1 && d.nz == 1;     // both corners are voxel 0
+            const bool c0 = ax0 == 0 && ay0 == 0 && az0 == 0;
+            const bool c1 = ax1 == d.nx - 1 && ay1 == d.ny - 1 && az1 == d.nz - 1;
+            const long long corners = (long long)c0 + (long long)(c1 && !(c0 && one_voxel));
+            if ((long long)(ax1 - ax0 + 1) * (ay1 - ay0 + 1) * (az1 - az0 + 1) > corners) s_hasB = 1;
+        }
+    }
+    __syncthreads();
     float vmin = INFINITY, vmax = -INFINITY;
-    for (int row = warp; row < rows; row += 8) {
-        const int y = y0 + row % ey, z = z0 + row / ey;
-        const size_t base = ((size_t)z * d.ny + y) * d.nx;
-        const int brow = ((z >> 5) * d.by + (y >> 5)) * d.bx;
-        for (int xi = lane; xi < ex; xi += 32) {
-            const int x = x0 + xi;
-            const bool corner = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
-            const float val = (corner || __ldg(active + brow + (x >> 5))) ? __ldg(v + base + x) : B;
-            vmin = fminf(vmin, val);
-            vmax = fmaxf(vmax, val);
+    if (threadIdx.x == 0) {
+        if (s_hasB) { const float B = __uint_as_float(bsel[1]); vmin = B; vmax = B; }
+        if (x0 == 0 && y0 == 0 && z0 == 0) { vmin = fminf(vmin, __ldg(v)); vmax = fmaxf(vmax, __ldg(v)); }
+        if (x1 == d.nx - 1 && y1 == d.ny - 1 && z1 == d.nz - 1) {
+            const float t = __ldg(v + ((size_t)d.nz * d.ny * d.nx - 1));
+            vmin = fminf(vmin, t);
+            vmax = fmaxf(vmax, t);
+        }
+    }
+    const int nparts = s_nparts;
+    for (int i = 0; i < nparts; ++i) {
+        const int ax0 = s_part[i][0], ex = s_part[i][1];
+        const int ay0 = s_part[i][2] & 0xffff, az0 = s_part[i][2] >> 16;
+        const int ey = s_part[i][3] & 0xffff, rows = ey * (s_part[i][3] >> 16);
+        const uint32_t mey = div_magic(ey);
+        constexpr int U = 8;
+        for (int r0 = warp; r0 < rows; r0 += kW * U) {
+            float t[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int row = r0 + kW * q;
+                t[q] = INFINITY;
+                if (lane < ex && row < rows) {
+                    const int z = div_small(row, mey), y = row - z * ey;
+                    t[q] = __ldg(v + ((size_t)(az0 + z) * d.ny + (ay0 + y)) * d.nx + ax0 + lane);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                if (lane < ex && r0 + kW * q < rows) {
+                    vmin = fminf(vmin, t[q]);
+                    vmax = fmaxf(vmax, t[q]);
+                }
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -742,7 +974,7 @@ __global__ void __launch_bounds__(256) k_macrocells_input(const float* __restric
     if (lane == 0) { s_lo[warp] = vmin; s_hi[warp] = vmax; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) { vmin = fminf(vmin, s_lo[w]); vmax = fmaxf(vmax, s_hi[w]); }
+        for (int w = 1; w < kW; ++w) { vmin = fminf(vmin, s_lo[w]); vmax = fmaxf(vmax, s_hi[w]); }
         mcmin[c] = vmin;
         mcmax[c] = vmax;
     }
@@ -760,16 +992,34 @@ __global__ void k_decode(GridView g, float* __restrict__ out, long long n)
 }
 
 // k_pass1's 128 KB of shared memory needs an opt-in, once per device
-vdbc_status pass1_setup()
+// every row of the volume starts on a 16-byte boundary: the float4 passes apply
+bool rows_aligned(const float* v, const Dims& d)
+{
+    return d.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(v) & 15u) == 0;
+}
+
+// opts k_pass1 into its shared memory (once per device) and sizes its
+// persistent grid: the resident blocks of the device, at most one per brick
+vdbc_status pass1_setup(int nbricks, unsigned* grid)
 {
     static std::mutex mu;
-    static std::vector<int> done;
+    static std::vector<std::pair<int, int>> done;     // (device, resident blocks)
     int dev = 0;
     VDBC_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
-    if (std::find(done.begin(), done.end(), dev) != done.end()) return VDBC_OK;
-    VDBC_CUDA(cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
-    done.push_back(dev);
+    int resident = 0;
+    for (const auto& e : done)
+        if (e.first == dev) resident = e.second;
+    if (resident == 0) {
+        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+        int per_sm = 0, sms = 0;
+        VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass1<false>, kPass1Threads, kPass1Smem));
+        VDBC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        resident = std::max(1, per_sm) * std::max(1, sms);
+        done.emplace_back(dev, resident);
+    }
+    *grid = (unsigned)std::max(1, std::min(nbricks, resident));
     return VDBC_OK;
 }
 
@@ -980,11 +1230,18 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     // phase 1: histogram -> B (two levels), brick ranges
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
     VDBC_CUDA(cudaMemsetAsync(nonfinite, 0, 4, s));
-    VDBC_TRY(pass1_setup());
-    KLAUNCH(k_pass1<<<nb, kPass1Threads, kPass1Smem, s>>>(vol, d, lo_key, hi_key, hist, nonfinite));
+    unsigned p1grid = 1;
+    VDBC_TRY(pass1_setup(nb, &p1grid));
+    if (rows_aligned(vol, d))
+        KLAUNCH(k_pass1<true><<<p1grid, kPass1Threads, kPass1Smem, s>>>(vol, d, nb, lo_key, hi_key, hist, nonfinite));
+    else
+        KLAUNCH(k_pass1<false><<<p1grid, kPass1Threads, kPass1Smem, s>>>(vol, d, nb, lo_key, hi_key, hist, nonfinite));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0));
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
-    KLAUNCH(k_pass2<<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
+    if (rows_aligned(vol, d))
+        KLAUNCH(k_pass2<true><<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
+    else
+        KLAUNCH(k_pass2<false><<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 1));
     // phase 2: f per brick, selection of N bricks
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(lo_key, hi_key, nb, bsel, metric, fkey, empty));
@@ -1098,7 +1355,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
         // FP32 leaves hold the input's values: the ranges come from the input itself
         const GridView& gv = g->view;
         const long long ncell = (long long)gv.mx * gv.my * gv.mz;
-        KLAUNCH(k_macrocells_input<<<(unsigned)ncell, 256, 0, s>>>(
+        KLAUNCH(k_macrocells_input<<<(unsigned)ncell, kMcInThreads, 0, s>>>(
             vol, d, active, bsel, gv.mc, gv.mx, gv.my, reinterpret_cast<float*>(base + g->off_mcmin),
             reinterpret_cast<float*>(base + g->off_mcmax)));
         e = cudaGetLastError();
@@ -1287,12 +1544,22 @@ extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vd
     // the scratch keeps the previous call's contents: clear what accumulates
     VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
     VDBC_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
-    VDBC_TRY(pass1_setup());
-    KLAUNCH(k_pass1<<<(unsigned)nb, kPass1Threads, kPass1Smem, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->hist,
-                                                          &sc->nonfinite));
+    unsigned p1grid = 1;
+    VDBC_TRY(pass1_setup(nb, &p1grid));
+    if (rows_aligned(in->data, d))
+        KLAUNCH(k_pass1<true><<<p1grid, kPass1Threads, kPass1Smem, s>>>(in->data, d, nb, sc->lo_key, sc->hi_key,
+                                                                        sc->hist, &sc->nonfinite));
+    else
+        KLAUNCH(k_pass1<false><<<p1grid, kPass1Threads, kPass1Smem, s>>>(in->data, d, nb, sc->lo_key, sc->hi_key,
+                                                                         sc->hist, &sc->nonfinite));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 0));
     VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
-    KLAUNCH(k_pass2<<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel, sc->hist));
+    if (rows_aligned(in->data, d))
+        KLAUNCH(k_pass2<true><<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel,
+                                                                    sc->hist));
+    else
+        KLAUNCH(k_pass2<false><<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel,
+                                                                     sc->hist));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 1));
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(sc->lo_key, sc->hi_key, (int)nb, sc->bsel, metric, sc->fkey,
                                                      sc->empty));
