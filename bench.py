@@ -75,7 +75,8 @@ def workload_config(world=1):
 
     w = scenes.TURBULENCE_512
     return {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
-            "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"], "image": "1024x1024", "spp": 16,
+            "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"],
+            "texture_macrocell": w["texture_macrocell"], "image": "1024x1024", "spp": 16,
             "max_bounces": 16, "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
             "l2": "input 512 MiB > L2, re-read every step"}
 
@@ -304,7 +305,8 @@ def run_vdbc(args):
             "peak_source": peak_kind, "algorithmic_bytes_per_lookup": 32}
 
     # --- comparator: the same renderer on the dense 3D texture; PSNR
-    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w["macrocell"], stream=stream)
+    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w.get("texture_macrocell", w["macrocell"]),
+                               stream=stream)
     dimg = torch.empty_like(img)
     for _ in range(2):
         v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
@@ -482,7 +484,7 @@ def run_learned_section(v, volgen, scenes, dev, stream):
     train_s = time.perf_counter() - t0
     cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], w["width"], w["height"]))
     med = v.make_medium(v.MODE_PT, **w["medium"])
-    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, w["macrocell"], stream=stream)
+    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, w.get("texture_macrocell", w["macrocell"]), stream=stream)
     img = torch.empty((w["height"], w["width"], 4), dtype=torch.float32, device=dev)
     paths = w["width"] * w["height"] * w["spp"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -704,7 +706,7 @@ def study_worstcase():
         g = v.vdbc_encode(vol, 1.0, macrocell=scenes.TURBULENCE_512["macrocell"])
         torch.cuda.synchronize()
         enc_ms = (time.perf_counter() - t0) * 1e3
-        dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, scenes.TURBULENCE_512["macrocell"])
+        dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, scenes.TURBULENCE_512["texture_macrocell"])
         cam = v.make_camera(*scenes.pinhole_orbit(dims, 1024, 1024))
         med = v.make_medium(v.MODE_PT, **scenes.pt_medium_args())
         img = torch.empty((1024, 1024, 4), dtype=torch.float32, device="cuda")

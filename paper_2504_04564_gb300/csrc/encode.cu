@@ -59,8 +59,7 @@ constexpr int kPassThreads = 256;
 // scans it, adds the non-zero bins to the global histogram and clears it.  A
 // warp step whose values all share one key (empty space) adds to a per-warp
 // run in registers; otherwise each lane adds its own values, equal keys
-// merged first (vector path) or lanes of one key merged by match_any (scalar
-// path).
+// merged first (the four of a float4, or a run down the lane's rows).
 constexpr int kPass1Threads = 1024;
 constexpr int kPass1Words = 32768;
 constexpr size_t kPass1Smem = (size_t)kPass1Words * sizeof(uint32_t);
@@ -195,21 +194,24 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
         } else {
             const bool valid = lane < ex;
             const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-            // U rows' loads in flight per warp before any of them is used
-            for (int r0 = warp; r0 < rows; r0 += kWarps * U) {
+            // U consecutive rows per warp, their loads in flight before any is
+            // used; a lane's values are then vertical neighbours, and equal
+            // keys in a row of them merge into one add
+            for (int r0 = warp * U; r0 < rows; r0 += kWarps * U) {
                 uint32_t u[U];
 #pragma unroll
                 for (int q = 0; q < U; ++q) {
-                    const int row = r0 + q * kWarps;
+                    const int row = r0 + q;
                     u[q] = 0u;
                     if (valid && row < rows) {
                         const int z = div_small(row, mey), y = row - z * ey;
                         u[q] = __float_as_uint(__ldg(v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + lane));
                     }
                 }
+                uint32_t lk = 0xffffffffu, ln = 0u;            // the lane's run of one key
 #pragma unroll
                 for (int q = 0; q < U; ++q) {
-                    if (r0 + q * kWarps >= rows) break;       // warp-uniform
+                    if (r0 + q >= rows) break;                 // warp-uniform
                     const uint32_t w = u[q];
                     const uint32_t key = w >> 16;
                     if (valid) {
@@ -218,14 +220,20 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                         kmin = min(kmin, k);
                         kmax = max(kmax, k);
                     }
-                    const unsigned peers = valid ? __match_any_sync(vmask, key) : 0u;
-                    const bool one_key = __shfl_sync(0xffffffffu, peers, 0) == vmask;   // lane 0 is always valid
-                    if (one_key) {
-                        run.add(__shfl_sync(0xffffffffu, key, 0), (uint32_t)__popc(vmask), lane, s_h);
-                    } else if (valid && lane == __ffs(peers) - 1) {
-                        bin_add(s_h, key, (uint32_t)__popc(peers));
+                    const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
+                    if (__all_sync(0xffffffffu, !valid || key == lead)) {
+                        run.add(lead, (uint32_t)__popc(vmask), lane, s_h);
+                    } else if (valid) {
+                        if (key == lk) {
+                            ++ln;
+                        } else {
+                            if (ln) bin_add(s_h, lk, ln);
+                            lk = key;
+                            ln = 1u;
+                        }
                     }
                 }
+                if (ln) bin_add(s_h, lk, ln);
             }
         }
         if (run.cnt && lane == 0) bin_add(s_h, run.key, run.cnt);
@@ -415,68 +423,88 @@ __global__ void k_scores(const uint32_t* __restrict__ lo_key, const uint32_t* __
 }
 
 // ---------------------------------------------------------------- selection
-template <typename T>
-__device__ T block_sum(T x, T* s)
+// sum over the block (1024 threads) of a per-thread count; every thread gets it
+__device__ __forceinline__ unsigned block_count(unsigned x, unsigned* s, unsigned* s_tot)
 {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    x = __reduce_add_sync(0xffffffffu, x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s[w] = x;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
+    if (w == 0) {
+        unsigned t = lane < (int)(blockDim.x >> 5) ? s[lane] : 0u;
+        t = __reduce_add_sync(0xffffffffu, t);
+        if (lane == 0) *s_tot = t;
+    }
     __syncthreads();
-    T t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
-    return t;
+    return *s_tot;
 }
 
 // the N largest keys among non-empty bricks, ties to the lower index; one CTA
-__global__ void __launch_bounds__(1024) k_select(const unsigned long long* __restrict__ fkey,
-                                                 const uint8_t* __restrict__ empty, int nb,
-                                                 long long budget, uint8_t* __restrict__ active,
-                                                 long long* __restrict__ counts)
+// of 1024 threads.  A key is held as fkey + 1 (0 for an empty brick), in
+// registers when there are at most 4096 bricks.
+constexpr int kSelThreads = 1024, kSelCache = 4;
+
+__global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long* __restrict__ fkey,
+                                                        const uint8_t* __restrict__ empty, int nb,
+                                                        long long budget, uint8_t* __restrict__ active,
+                                                        long long* __restrict__ counts)
 {
-    __shared__ long long s[32];
+    __shared__ unsigned s[32];
+    __shared__ unsigned s_tot;
     __shared__ long long s_run;
-    long long m = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) m += empty[i] ? 0 : 1;
-    m = block_sum(m, s);
-    long long take = budget < m ? budget : m;
+    const bool cached = nb <= kSelCache * kSelThreads;
+    unsigned long long ck[kSelCache];
+#pragma unroll
+    for (int q = 0; q < kSelCache; ++q) {
+        const int i = threadIdx.x + q * kSelThreads;
+        ck[q] = (cached && i < nb && !empty[i]) ? fkey[i] + 1ull : 0ull;
+    }
+    auto key1 = [&](int i) -> unsigned long long { return empty[i] ? 0ull : fkey[i] + 1ull; };
+    // number of keys (+1) >= c (c >= 1), and of keys (+1) > c
+    auto count_ge = [&](unsigned long long c) -> unsigned {
+        unsigned n = 0;
+        if (cached) {
+#pragma unroll
+            for (int q = 0; q < kSelCache; ++q) n += ck[q] >= c ? 1u : 0u;
+        } else {
+            for (int i = threadIdx.x; i < nb; i += kSelThreads) n += key1(i) >= c ? 1u : 0u;
+        }
+        return block_count(n, s, &s_tot);
+    };
+    const long long m = count_ge(1ull);
+    const long long take = budget < m ? budget : m;
     if (take == m || take == 0) {
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) active[i] = (take > 0 && !empty[i]) ? 1 : 0;
+        for (int i = threadIdx.x; i < nb; i += kSelThreads) active[i] = (take > 0 && !empty[i]) ? 1 : 0;
         if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
         return;
     }
     // bisection on the bits of the threshold T: the largest T with #{key >= T} >= take
     unsigned long long T = 0;
     for (int bit = 63; bit >= 0; --bit) {
-        unsigned long long cand = T | (1ull << bit);
-        long long c = 0;
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) c += (!empty[i] && fkey[i] >= cand) ? 1 : 0;
-        c = block_sum(c, s);
-        if (c >= take) T = cand;
+        const unsigned long long cand = T | (1ull << bit);
+        if (cand <= 0xFFFFFFFFFFFFFFFEull && (long long)count_ge(cand + 1ull) >= take) T = cand;
     }
-    long long gt = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) gt += (!empty[i] && fkey[i] > T) ? 1 : 0;
-    gt = block_sum(gt, s);
+    const long long gt = T == 0xFFFFFFFFFFFFFFFFull ? 0 : (long long)count_ge(T + 2ull);
     const long long need = take - gt;   // keys equal to T, lowest brick indices first
     if (threadIdx.x == 0) s_run = 0;
     __syncthreads();
-    for (int base = 0; base < nb; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        bool eq = i < nb && !empty[i] && fkey[i] == T;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < nb; base += kSelThreads) {
+        const int i = base + threadIdx.x;
+        const unsigned long long k = i < nb ? key1(i) : 0ull;
+        const bool eq = k != 0ull && k == T + 1ull;
         // exclusive rank of this thread's tie within the chunk
-        unsigned bal = __ballot_sync(0xffffffffu, eq);
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        int in_warp = __popc(bal & ((1u << lane) - 1u));
-        __syncthreads();
+        const unsigned bal = __ballot_sync(0xffffffffu, eq);
+        const int in_warp = __popc(bal & ((1u << lane) - 1u));
         if (lane == 0) s[w] = __popc(bal);
         __syncthreads();
-        long long before = s_run;
+        long long before = s_run + in_warp;
         for (int q = 0; q < w; ++q) before += s[q];
-        before += in_warp;
-        if (i < nb) active[i] = (!empty[i] && (fkey[i] > T || (eq && before < need))) ? 1 : 0;
+        if (i < nb) active[i] = (k != 0ull && (k > T + 1ull || (eq && before < need))) ? 1 : 0;
         __syncthreads();
         if (threadIdx.x == 0) {
             long long t = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s[q];
+            for (int q = 0; q < kSelThreads / 32; ++q) t += s[q];
             s_run += t;
         }
         __syncthreads();
@@ -491,13 +519,14 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(const uint32_t* __rest
                                                           uint32_t* __restrict__ sums)
 {
     __shared__ uint32_t s[32];
+    __shared__ uint32_t s_tot;
     long long base = (long long)blockIdx.x * kScanBlock * kScanItems;
     uint32_t t = 0;
     for (int q = 0; q < kScanItems; ++q) {
         long long i = base + (long long)q * kScanBlock + threadIdx.x;
         if (i < n) t += in[i];
     }
-    t = block_sum(t, s);
+    t = block_count(t, s, &s_tot);
     if (threadIdx.x == 0) sums[blockIdx.x] = t;
 }
 
@@ -560,6 +589,49 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_apply(const uint32_t* __res
     }
 }
 
+// the whole scan in one CTA, for small n: each pass takes 4096 values, four
+// consecutive ones per thread, and carries the running total to the next
+constexpr long long kScanSingleMax = 16ll * kScanBlock * kScanItems;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_single(const uint32_t* __restrict__ in, long long n,
+                                                            uint32_t* __restrict__ out, uint32_t* __restrict__ total)
+{
+    __shared__ uint32_t s[32];
+    __shared__ uint32_t run;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long base = 0; base < n; base += (long long)kScanBlock * kScanItems) {
+        const long long i0 = base + (long long)threadIdx.x * kScanItems;
+        uint32_t x[kScanItems], t = 0;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            x[q] = i0 + q < n ? in[i0 + q] : 0u;
+            t += x[q];
+        }
+        uint32_t incl = t;                      // inclusive scan of the threads' sums in the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s[w] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int q = 0; q < w; ++q) wbase += s[q];
+        const uint32_t r0 = run;
+        uint32_t acc = r0 + wbase + incl - t;   // exclusive prefix of this thread's first value
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            if (i0 + q < n) out[i0 + q] = acc;
+            acc += x[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) run = acc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) total[0] = run;
+}
+
 // exclusive scan of n u32 values; total written to total_dev[0]; tmp holds >= scan_tmp_words(n)
 long long scan_blocks(long long n) { return (n + kScanBlock * kScanItems - 1) / (kScanBlock * kScanItems); }
 
@@ -569,6 +641,10 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, long long n, uint32_t* tm
     long long nb = scan_blocks(n);
     if (nb == 0) {
         cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    if (n <= kScanSingleMax) {
+        KLAUNCH(k_scan_single<<<1, kScanBlock, 0, s>>>(in, n, out, total_dev));
         return;
     }
     KLAUNCH(k_scan_sums<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, tmp));

@@ -72,7 +72,7 @@ def test_encoder_bit_exact_metrics_and_quantized_payloads(env, metric, payload):
     check_encoding(env, host, 6.0, metric=metric, payload=payload)
 
 
-@pytest.mark.parametrize("macrocell,payload", [(4, 0), (8, 0), (13, 0), (48, 0), (64, 1), (48, 2)])
+@pytest.mark.parametrize("macrocell,payload", [(4, 0), (8, 0), (13, 0), (48, 0), (56, 0), (64, 1), (48, 2)])
 def test_macrocell_sizes(env, macrocell, payload):
     """Cells above 4096 dilated voxels take the block-per-cell kernels: the
     input-based one for FP32 leaves, the tree-based one for FP16/FP8."""

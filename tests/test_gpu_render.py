@@ -111,9 +111,9 @@ def test_pt_turbulence_matches_oracle(env, payload):
     assert st.paths == 48 * 40 * 4 and st.error_flags == 0 and st.lookups > 48 * 40 * 4
 
 
-@pytest.mark.parametrize("macrocell", [16, 5, 48])
+@pytest.mark.parametrize("macrocell", [16, 5, 48, 56])
 def test_pt_macrocell_sizes_match_oracle(env, macrocell):
-    """Majorant macrocells of other sizes (the benchmark uses 48^3) change the
+    """Majorant macrocells of other sizes (the benchmark uses 56^3) change the
     free flights but not the parity with the oracle."""
     torch, v, orc, vg, sc = env["torch"], env["v"], env["orc"], env["vg"], env["sc"]
     dims = (112, 96, 80)

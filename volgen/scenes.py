@@ -44,15 +44,18 @@ def pt_medium_args(density_scale=20.0, albedo=0.9, g=0.6, max_bounces=16):
 
 
 # the 512^3 turbulent medium at 1:10, 1024^2 x 16 spp, albedo 0.9, g 0.6, 16 bounces;
-# majorant macrocells of 48^3 voxels for grid and dense texture alike (the
-# fastest size for both: 42.3 / 36.1 ms against 57.2 / 55.7 ms at 16^3)
+# majorant macrocells of 56^3 voxels for the grid and 64^3 for the dense
+# texture, each its fastest size (grid 16.2 ms against 16.4 at 48^3, 18.8 at
+# 32^3; texture 11.5 ms against 13.3 at 48^3)
 TURBULENCE_512 = dict(kind="turbulence", dims=(512, 512, 512), seed=0, ratio=10.0, width=1024, height=1024,
-                      spp=16, medium=pt_medium_args(), macrocell=48)
+                      spp=16, medium=pt_medium_args(), macrocell=56, texture_macrocell=64)
 # the learned-decoder workload: a 994 x 676 x 1225 cloud (Worley-modulated
 # fBm, anvil profile), 1920 x 1080 x 32 spp, albedo 0.95, g 0.8; the learned
-# grid is built from every non-empty brick and held to the bytes of VDB at 1:10
+# grid is built from every non-empty brick and held to the bytes of VDB at 1:10;
+# 64^3 macrocells for grid and texture (grid 28.0 ms, as at 56^3, against 29.6
+# at 48^3; texture 18.6 ms against 20.1 at 56^3 and 22.2 at 48^3)
 CLOUD_994 = dict(kind="cloud", dims=(994, 676, 1225), seed=0, ratio=10.0, width=1920, height=1080, spp=32,
-                 medium=pt_medium_args(albedo=0.95, g=0.8), macrocell=48,
+                 medium=pt_medium_args(albedo=0.95, g=0.8), macrocell=64, texture_macrocell=64,
                  learn=dict(steps=200, samples_per_leaf=64, lr=2e-3, lr_latent=2e-2, seed=1))
 # the 64^3 blobs volume at 1:4, EA, 128^2, step 0.5, ortho +z
 BLOBS_64_EA = dict(kind="blobs", dims=(64, 64, 64), seed=0, ratio=4.0, width=128, height=128, step=0.5)
