@@ -1112,16 +1112,13 @@ vdbc_status make_med(const vdbc_medium* m, const int dims[3], int spp, cudaStrea
     return VDBC_OK;
 }
 
+// SMs of the current device (a host query, no device work)
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
 }
 
 constexpr int kPtThreads = 256;

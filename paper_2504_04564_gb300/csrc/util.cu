@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "vdbc_host.h"
 
@@ -47,13 +48,17 @@ bool fault_injected(const char* name)
     return f && std::strstr(f, name) != nullptr;
 }
 
+// the default pool of the current device keeps freed memory for reuse
+// (once per device; calls may come from several threads)
 static void keep_pool_memory()
 {
-    static bool done = false;
-    if (done) return;
-    done = true;
+    static std::mutex mu;
+    static std::vector<int> done;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    done.push_back(dev);
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
     uint64_t keep = ~0ull;

@@ -299,3 +299,50 @@ def test_render_stats_time_the_tracker_kernel(env):
         assert 0.0 < st.kernel_ms < 1e4
         v.vdbc_render_dense(vol, cam, med, spp, 1, out)
         assert 0.0 < v.vdbc_volume_render_stats_get(vol).kernel_ms < 1e4
+
+
+def test_concurrent_calls_on_two_threads(env):
+    """Two host threads, each on its own stream, encode from pinned host
+    memory and path trace into host memory at the same time, as the
+    end-to-end benchmark does: every image equals the one-thread render of
+    the same grid and samples, and no call fails."""
+    import threading
+
+    torch, v, vg, sc = env["torch"], env["v"], env["vg"], env["sc"]
+    dims = (96, 80, 72)
+    vols = [torch.from_numpy(vg.generate_host(vg.make_params("turbulence", dims, s))).pin_memory() for s in (5, 6)]
+    cam = v.make_camera(*sc.pinhole_orbit(dims, 48, 40))
+    med = v.make_medium(v.MODE_PT, **sc.pt_medium_args(density_scale=30.0, max_bounces=6))
+    want = []
+    for vol in vols:
+        g = v.vdbc_encode(vol, 6.0, macrocell=16)
+        img = np.zeros((40, 48, 4), dtype=np.float32)
+        v.vdbc_render(g, cam, med, 4, 11, img)
+        want.append(img)
+        g.close()
+    got = [[], []]
+    errors = []
+
+    def worker(i):
+        try:
+            torch.cuda.set_device(env["dev"])
+            st = torch.cuda.Stream(device=env["dev"])
+            for _ in range(4):
+                g = v.vdbc_encode(vols[i], 6.0, macrocell=16, stream=st.cuda_stream)
+                img = np.zeros((40, 48, 4), dtype=np.float32)
+                v.vdbc_render(g, cam, med, 4, 11, img, stream=st.cuda_stream)
+                g.close()
+                got[i].append(img)
+        except Exception as ex:     # reported on the test's thread
+            errors.append(ex)
+
+    ts = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    for i in range(2):
+        assert len(got[i]) == 4
+        for img in got[i]:
+            assert np.array_equal(img.view(np.uint32), want[i].view(np.uint32))
