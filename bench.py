@@ -755,7 +755,8 @@ def study_worstcase():
         del vol
         torch.cuda.empty_cache()
     return {"study": "worstcase_dense_noise_lossless",
-            "render": "pt 1024x1024x4spp, density 20/unit, %d^3 cells" % scenes.TURBULENCE_512["macrocell"],
+            "render": "pt 1024x1024x4spp, density 20/unit, %d^3 cells (grid), %d^3 (texture)"
+                      % (scenes.TURBULENCE_512["macrocell"], scenes.TURBULENCE_512["texture_macrocell"]),
             "rows": rows}
 
 
