@@ -137,3 +137,39 @@ def test_batch_accumulation_state_checkpoint(env):
         v.vdbc_batch_set_state(b2, 0, sums[:-4])
     with pytest.raises(v.VdbcError):
         v.vdbc_batch_set_state(b2, -1, sums)
+
+
+def test_full_size_batch_frame_equals_single_renders(env, monkeypatch):
+    """The batch workload at full size, in the launch configuration the
+    benchmark times (32 blob+fBm volumes of edges 64..384, FP16/FP8 leaves at
+    1:4..1:20, 256^2..1024^2 images, 4..32 spp; autotuned, graph-replayed): one
+    frame gives every job the image of its own single render with the tuner's
+    DDA setting, bit for bit, with clean error flags."""
+    torch, v, vg, sc = env["torch"], env["v"], env["vg"], env["sc"]
+    specs = sc.batch_jobs()
+    grids, imgs, structs, views = [], [], [], []
+    for sp in specs:
+        vol = vg.generate_torch(vg.make_params(sp["kind"], sp["dims"], sp["seed"]))
+        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"])
+        del vol
+        cam = v.make_camera(*sc.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
+        med = v.make_medium(v.MODE_PT, **sp["medium"])
+        img = torch.full((sp["height"], sp["width"], 4), -1.0, dtype=torch.float32, device=env["dev"])
+        grids.append(g)
+        imgs.append(img)
+        views.append((cam, med))
+        structs.append(v.make_job(g, cam, med, sp["spp"], sp["seed"], img))
+    b = v.vdbc_batch_create(structs, autotune=True, keep=(grids, imgs))
+    coarse = v.vdbc_batch_get_tuning(b).coarse
+    v.vdbc_batch_render_frames(b, 1)
+    torch.cuda.synchronize()
+    st = v.vdbc_batch_stats_get(b)
+    assert st.error_flags == 0 and st.paths == sum(sp["width"] * sp["height"] * sp["spp"] for sp in specs)
+    monkeypatch.setenv("VDBC_PT_COARSE", str(int(coarse)))
+    one = torch.empty_like(imgs[0])
+    for sp, g, img, (cam, med) in zip(specs, grids, imgs, views):
+        one = torch.empty_like(img)
+        v.vdbc_render(g, cam, med, sp["spp"], sp["seed"], one)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy().view(np.uint32), one.cpu().numpy().view(np.uint32)), sp
+    b.close()

@@ -348,3 +348,36 @@ def test_learn_degenerate_grids(env):
     _, src, _ = source(env, "blobs", (40, 36, 44), 1, 1.0)
     tiny, _ = v.vdbc_learn(src, steps=0, max_bytes=1)
     assert tiny.info.n_leaves == 0 and tiny.info.n_neural == src.info.n_leaves
+
+
+def test_full_size_cloud_learned_render_equals_dense_render_of_its_decode(env):
+    """The learned-grid workload at full size, in the launch configuration the
+    benchmark times (the 994x676x1225 cloud, every non-empty brick learned and
+    held to the bytes of VDB FP32 at 1:10, 1920x1080 x 32 spp, 64^3 cells): the
+    oracle cannot decode 455k neural leaves in a test's time, so the property
+    that holds at any size stands in: the render equals the linear plain-form
+    render of the grid's own decode, bit for bit."""
+    torch, v, vg, sc = env["torch"], env["v"], env["vg"], env["sc"]
+    w = sc.CLOUD_994
+    vol = vg.generate_torch(vg.make_params(w["kind"], w["dims"], w["seed"]))
+    full = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"])
+    budget = int(v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"]).info.total_bytes)
+    learned, losses = v.vdbc_learn(full, max_bytes=budget, **w["learn"])
+    full.close()
+    assert learned.info.total_bytes <= budget and learned.info.n_neural > 100000
+    assert losses[-1] < losses[0]
+    dec = torch.empty_like(vol)
+    del vol
+    v.vdbc_grid_decode(learned, dec)
+    dense = v.vdbc_volume_create(dec, v.FILTER_LINEAR, macrocell=w["macrocell"])
+    del dec
+    cam = v.make_camera(*sc.pinhole_orbit(w["dims"], w["width"], w["height"]))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    a = torch.zeros(w["height"], w["width"], 4, device=env["dev"])
+    b = torch.zeros_like(a)
+    v.vdbc_render(learned, cam, med, w["spp"], 2024, a)
+    v.vdbc_render_dense(dense, cam, med, w["spp"], 2024, b)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
+    st = v.vdbc_render_stats_get(learned)
+    assert st.error_flags == 0 and st.paths == w["width"] * w["height"] * w["spp"]
