@@ -653,8 +653,10 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
 // resident 256-thread blocks per SM the tracker is compiled for: 4 (64
 // registers) measured fastest for the plain samplers without the coarse level
 // (36.4 ms against 40.1 at 2, 44.0 at 3, 37.1 at 5 on the 512^3 medium with
-// 48^3 cells); with the coarse level (8^3 cells) 2 is faster (130.9 against
-// 153.6 ms), and the learned sampler keeps 2 (its tile code needs the registers)
+// 48^3 cells; again with 32-item work chunks and 56^3 cells: 16.1 ms against
+// 16.7 at 5 and 17.0 at 6); with the coarse level (8^3 cells) 2 is faster
+// (130.9 against 153.6 ms), and the learned sampler keeps 2 (its tile code
+// needs the registers)
 #ifndef VDBC_PT_MIN_BLOCKS
 #define VDBC_PT_MIN_BLOCKS 4
 #endif
