@@ -11,8 +11,9 @@
 //
 // Kernels, in order (every one is HBM- or latency-bound, none is a
 // contraction):
-//   k_pass1        one CTA per brick: min/max (total order) + upper-16-bit
-//                  histogram (warp-aggregated atomics) + non-finite check
+//   k_pass1        persistent, one CTA per SM taking bricks in turn: min/max
+//                  (total order) + upper-16-bit histogram (block histogram in
+//                  shared memory, flushed per brick) + non-finite check
 //   k_argmax       one CTA: most frequent bin, ties to the smaller index
 //   k_pass2        one CTA per brick overlapping the winning bin: lower-16-bit
 //                  histogram inside it
@@ -20,7 +21,10 @@
 //   k_select       one CTA: threshold bisection over the FP64 keys (the N-th
 //                  largest), ties by brick index
 //   k_leaf_status  one warp per candidate leaf: constant? (prune) tile value?
-//   scans, k_fill_* tree tables, k_fill_leaves payload copy / quantization
+//   scans (one CTA up to 64K entries), k_fill_* tree tables, k_fill_leaves
+//                  payload copy / quantization
+//   k_macrocells_input  FP32 grids: macrocell ranges from the input where a
+//                  brick is active (else k_macrocells over the tree)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
