@@ -31,8 +31,9 @@
  *    same handle reports as VDBC_ERR_DEVICE_FLAG.
  *  - A handle may be used from several threads only if the calls are
  *    serialized by the caller.
- *  - The library is also built with VDBC_CHECKED=1 as libvdbc_checked.so
- *    (vdbc_version() ends in "checked"): there every tree lookup checks each
+ *  - The library is also built with VDBC_CHECKED=1 (and VDBC_STATS, see
+ *    vdbc_render_stats.events) as libvdbc_checked.so (vdbc_version() ends in
+ *    "checked"): there every tree lookup checks each
  *    node, leaf and tile index against the grid's counts before it loads, and
  *    an index outside its table is read as the background and reported as
  *    VDBC_ERR_DEVICE_FLAG (bit 2 of vdbc_render_stats.error_flags) by the
@@ -149,9 +150,10 @@ typedef struct {
     uint64_t lookups;          /* density lookups (trilinear reconstructions) */
     uint64_t paths;
     uint64_t error_flags;      /* nonzero if a kernel hit one of its bounds */
-    uint64_t events[6];        /* only in builds with VDBC_STATS defined, else 0: tracker loop
-                                  iterations, DDA cells examined, coarse blocks crossed, free
-                                  flights drawn, rays started, paths fetched */
+    uint64_t events[6];        /* only in builds with VDBC_STATS defined (the checked build
+                                  libvdbc_checked.so is one), else 0: tracker loop iterations,
+                                  DDA cells examined, coarse blocks crossed, free flights
+                                  drawn, rays started, paths fetched */
     float    kernel_ms;        /* duration of the last render's tracker kernel (k_pt, k_pt_batch,
                                   k_ea or k_iso), from CUDA events recorded around its launch on
                                   the render's stream; -1 if none was recorded */

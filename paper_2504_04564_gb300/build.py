@@ -2,9 +2,11 @@
 
 Translation units are compiled in parallel and linked with `nvcc -shared`.
 The output lands in paper_2504_04564_gb300/_build/ (git-ignored).
-``build(checked=True)`` builds the same sources with VDBC_CHECKED=1 into
-_build/checked/libvdbc_checked.so: every tree lookup bounds-checks its node,
-leaf and tile indices and reports a violation through the device error word.
+``build(checked=True)`` builds the same sources with VDBC_CHECKED=1 and
+VDBC_STATS into _build/checked/libvdbc_checked.so: every tree lookup
+bounds-checks its node, leaf and tile indices and reports a violation through
+the device error word, and the tracker counts its events (loop iterations,
+DDA cells, coarse blocks, free flights, ray starts, paths fetched).
 ``build(sanitize=True)`` builds _build/asan/libvdbc_asan.so, whose host code
 is instrumented by AddressSanitizer and UndefinedBehaviorSanitizer (load it
 into a process that starts with libasan preloaded).
@@ -48,7 +50,7 @@ def _deps():
 def _variant(checked: bool, sanitize: bool):
     """(library, object folder, extra compile flags, extra link flags)."""
     if checked:
-        return LIB_CHECKED, BUILD_CHECKED, ["-DVDBC_CHECKED=1"], []
+        return LIB_CHECKED, BUILD_CHECKED, ["-DVDBC_CHECKED=1", "-DVDBC_STATS"], []
     if sanitize:
         return LIB_ASAN, BUILD_ASAN, SANITIZE_FLAGS, SANITIZE_LINK
     return LIB, BUILD, [], []

@@ -51,7 +51,10 @@ def run_workload(v, torch, vg, sc):
             v.vdbc_render(g, cam, med, spp, 7, img)
             torch.cuda.synchronize()
             out["%s_%d" % (name, payload)] = img.cpu().numpy()
-            out["flags_%s_%d" % (name, payload)] = np.uint64(v.vdbc_render_stats_get(g).error_flags)
+            st = v.vdbc_render_stats_get(g)
+            out["flags_%s_%d" % (name, payload)] = np.uint64(st.error_flags)
+            if name == "pt":       # the tracker's event counters (zero unless built with them)
+                out["events_pt_%d" % payload] = np.array(list(st.events) + [st.lookups, st.paths], dtype=np.uint64)
     npos = ((DIMS[0] + 7) // 8) * ((DIMS[1] + 7) // 8) * ((DIMS[2] + 7) // 8)
     half = torch.arange(npos, device=dev) % 2 + 1          # neural and raw leaves, alternating by position
     learned, _ = v.vdbc_learn(grids[v.FP16], steps=3, samples_per_leaf=16, seed=5, force=half.to(torch.uint8))

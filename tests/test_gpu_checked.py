@@ -111,7 +111,8 @@ def child(args, extra_env, timeout=600):
 def test_checked_build_computes_the_same_bits(env, tmp_path):
     """Encode, decode, PT/EA/ISO renders of FP32/FP16/FP8 grids, a learned
     grid and a batch: the checked build returns bit-identical outputs with a
-    clean error word, so its checks change nothing on a valid grid."""
+    clean error word, so its checks change nothing on a valid grid; its
+    tracker event counters (VDBC_STATS) agree with the render's own counts."""
     import checked_child
     torch, v = env["torch"], env["v"]
     assert not v.vdbc_version().endswith("checked")
@@ -122,7 +123,15 @@ def test_checked_build_computes_the_same_bits(env, tmp_path):
     assert set(got.files) == set(want)
     for k in sorted(want):
         a, b = np.asarray(want[k]), got[k]
-        if k.startswith("flags"):
+        if k.startswith("events"):
+            # the plain build counts no events; the checked build (VDBC_STATS)
+            # counts every path fetched once, a free flight per lookup at
+            # least, and more loop iterations than flights
+            ev, lookups, paths = [int(x) for x in b[:6]], int(b[6]), int(b[7])
+            assert not np.any(a[:6]) and int(a[6]) == lookups and int(a[7]) == paths, (k, a, b)
+            assert ev[5] == paths and ev[4] > 0 and ev[3] >= lookups > 0, (k, ev, lookups, paths)
+            assert ev[0] >= ev[3] and ev[1] > 0 and ev[2] == 0, (k, ev)
+        elif k.startswith("flags"):
             assert int(a) == 0 and int(b) == 0, (k, a, b)
         elif k == "n_neural":
             assert int(a) == int(b) > 0
