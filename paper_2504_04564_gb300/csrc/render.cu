@@ -466,6 +466,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                     mode = kDone;
                 } else {
                     // item -> (job, sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
+                    // (a 32-bit form of this division measured no faster: 16.2 against 16.1 ms)
                     jb = src.find(item, jb);
                     const JobView& F = src.job(jb);
                     unsigned long long local = item - F.item_begin;
@@ -596,7 +597,8 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             if (mode == kRatio) {
                 T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
             } else if (__fmul_rn(ua, tr.mj) < sigma) {
-                // real collision: scatter, then trace the light ray from here
+                // real collision: scatter, then trace the light ray from here (inline: the
+                // same code out of line cost 17.0 against 16.1 ms on the benchmark frame)
                 beta *= med.albedo;
                 ph = hg_eval(dot3(d, med.sun_dir), med.g);
                 float mu = hg_sample_mu(med.g, ub);
