@@ -20,17 +20,24 @@ def env():
     return dict(torch=torch, v=v, orc=oracle, vg=volgen, dev=torch.device("cuda:0"))
 
 
-def encode_both(env, host, ratio, metric=2, payload=0, macrocell=8):
+def encode_both(env, host, ratio, metric=2, payload=0, macrocell=8, offset=0):
+    """offset > 0 places the volume `offset` floats into a device buffer, so
+    that its base is off a 16-byte boundary (the encoder's scalar loads)."""
     torch, v, orc = env["torch"], env["v"], env["orc"]
-    vol = torch.from_numpy(host).to(env["dev"])
+    if offset:
+        flat = torch.zeros(host.size + offset, dtype=torch.float32, device=env["dev"])
+        vol = flat[offset:].view(host.shape)
+        vol.copy_(torch.from_numpy(host))
+    else:
+        vol = torch.from_numpy(host).to(env["dev"])
     grid = v.vdbc_encode(vol, ratio, metric=metric, payload=payload, macrocell=macrocell)
     e = orc.encode(host, ratio, metric=metric, payload=payload)
     return vol, grid, e
 
 
-def check_encoding(env, host, ratio, metric=2, payload=0, macrocell=8):
+def check_encoding(env, host, ratio, metric=2, payload=0, macrocell=8, offset=0):
     torch, v, orc = env["torch"], env["v"], env["orc"]
-    vol, grid, e = encode_both(env, host, ratio, metric, payload, macrocell)
+    vol, grid, e = encode_both(env, host, ratio, metric, payload, macrocell, offset)
     info = grid.info
     assert info.background_bits == e["background_bits"]
     assert info.n_bricks == e["lo"].size
@@ -63,6 +70,16 @@ def check_encoding(env, host, ratio, metric=2, payload=0, macrocell=8):
 def test_encoder_bit_exact_fp32(env, dims, ratio):
     host = env["vg"].generate_host(env["vg"].make_params("blobs", dims, 1))
     check_encoding(env, host, ratio)
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (97, 70, 33), (1, 1, 1), (130, 8, 129)])
+@pytest.mark.parametrize("offset", [1, 3])
+def test_encoder_bit_exact_unaligned_base(env, dims, offset):
+    """The brick passes' scalar loads on a volume that starts off a 16-byte
+    boundary (offset floats into a buffer), also for widths whose aligned
+    volumes take the float4 loads: the same bits as the oracle."""
+    host = env["vg"].generate_host(env["vg"].make_params("turbulence", dims, 4))
+    check_encoding(env, host, 4.0, offset=offset)
 
 
 @pytest.mark.parametrize("metric", [1, 2, 3])
