@@ -140,7 +140,9 @@ __device__ __forceinline__ bool entry_in_range(const GridView& g, uint32_t e)
 }
 #endif
 
-// entry of the lower level that covers voxel-leaf (li,lj,lk) = (i>>3, j>>3, k>>3)
+// entry of the lower level that covers voxel-leaf (li,lj,lk) = (i>>3, j>>3, k>>3);
+// inlined at every call (the same descent out of line cost the tracker 17.6
+// against 16.1 ms on the benchmark frame)
 __device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, int lj, int lk)
 {
     int i = li << 3, j = lj << 3, k = lk << 3;
