@@ -2,7 +2,7 @@
  * encode.c -- the fixed-rate encoder of Section 3.1 (Algorithm 1, Eq. f1-f3)
  * and the tree of Section 3.2.1, written plainly.
  *
- * Readings of the paper taken here (each listed in the design doc):
+ * Readings of the paper taken here, where it is silent or ambiguous:
  *  - background value: the histogram of Algorithm 1 is a two-level histogram
  *    of the float bit patterns (upper 16 bits, then lower 16 bits inside the
  *    winning upper bin), ties to the smaller pattern;

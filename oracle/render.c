@@ -1,7 +1,7 @@
 /*
  * render.c -- the renderer of Section 4, restated plainly in FP64.
  *
- * Conventions (readings listed in the design doc):
+ * Conventions (readings of what the paper leaves open):
  *  - voxel (i,j,k) sits at index coordinate (i,j,k); the volume is the box
  *    [-1/2, dim-1/2]^3; world space is index space shifted by 1/2 and scaled
  *    so that the longest axis spans one unit: index = world * M - 1/2;

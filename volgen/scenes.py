@@ -1,9 +1,9 @@
 """Scene definitions shared by the tests, smoke and the benchmark.
 
-Each workload is named by what it is; camera and light follow the readings
-listed in the design doc (pinhole at the volume centre + 1.6 x normalize(0.6, 0.4,
-0.7), fov 40 deg; sun along normalize(1, 1, 0.5) with irradiance 3; constant
-environment 0.25; transfer function a linear grey ramp).
+Each workload is named by what it is.  The paper states no camera or light
+for its renders; these are fixed here: a pinhole at the volume centre + 1.6 x
+normalize(0.6, 0.4, 0.7), fov 40 deg; sun along normalize(1, 1, 0.5) with
+irradiance 3; constant environment 0.25; transfer function a linear grey ramp.
 """
 import math
 
