@@ -426,7 +426,7 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
     payload_bytes = 0
     for sp in specs:
         vol = volgen.generate_torch(volgen.make_params(sp["kind"], sp["dims"], sp["seed"]), dev)
-        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"], stream=stream)
+        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"], macrocell=sp["macrocell"], stream=stream)
         del vol
         payload_bytes += int(g.info.payload_bytes)
         cam = v.make_camera(*scenes.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
@@ -476,7 +476,8 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
             "payload_bytes": payload_bytes, "lookups_per_frame": int(st.lookups),
             "tuning": {"threads": tuning.threads, "chunk": tuning.chunk, "coarse": tuning.coarse},
             "create_s_incl_autotune": round(create_s, 3),
-            "workload": "32 blob+fBm volumes, edges 64..384, rates 1:4..1:20, FP16/FP8, 256^2..1024^2, 4..32 spp"}
+            "workload": "32 blob+fBm volumes, edges 64..384, rates 1:4..1:20, FP16/FP8, 256^2..1024^2, 4..32 spp, "
+                        "%d^3 cells" % specs[0]["macrocell"]}
 
 
 def run_learned_section(v, volgen, scenes, dev, stream):

@@ -413,7 +413,9 @@ struct BatchSource {
     __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
     {
         const GridView& g = grids[i];
-        // one dispatch per lookup on the job's payload, not one per voxel
+        // one dispatch per lookup on the job's payload, not one per voxel (one
+        // trilinear switching per voxel measured slower: 162.9 against 150.6 ms
+        // for the 32-job frame)
         if (g.payload == 1) return vdb_trilinear<1>(g, x, y, z, a);
         if (g.payload == 2) return vdb_trilinear<2>(g, x, y, z, a);
         return vdb_trilinear<0>(g, x, y, z, a);
@@ -498,7 +500,9 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         if (__all_sync(0xffffffffu, mode == kDone)) break;
         const JobView& J = src.job(jb);
         // batch: copies in registers (the job table is in shared memory and the
-        // DDA walk reads these per cell); one job: references to kernel parameters
+        // DDA walk reads these per cell; references into it measured 162.6
+        // against 150.6 ms for the 32-job frame despite fewer spills); one
+        // job: references to kernel parameters
         typename std::conditional<Src::kMulti, const Majorants, const Majorants&>::type m = J.m;
         typename std::conditional<Src::kMulti, const MedDev, const MedDev&>::type med = J.med;
         const uint32_t* bits = src.bits(jb);

@@ -150,7 +150,7 @@ def test_full_size_batch_frame_equals_single_renders(env, monkeypatch):
     grids, imgs, structs, views = [], [], [], []
     for sp in specs:
         vol = vg.generate_torch(vg.make_params(sp["kind"], sp["dims"], sp["seed"]))
-        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"])
+        g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"], macrocell=sp["macrocell"])
         del vol
         cam = v.make_camera(*sc.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
         med = v.make_medium(v.MODE_PT, **sp["medium"])
@@ -172,4 +172,45 @@ def test_full_size_batch_frame_equals_single_renders(env, monkeypatch):
         v.vdbc_render(g, cam, med, sp["spp"], sp["seed"], one)
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy().view(np.uint32), one.cpu().numpy().view(np.uint32)), sp
+    b.close()
+
+
+def test_full_size_batch_per_volume_error_against_oracle(env):
+    """The batch workload at full size (the benchmark's 32 volumes, payloads,
+    rates, cameras, spp and cells): per volume, 16 sampled pixels of the batch
+    frame against the FP64 oracle rendering the same samples on its own
+    encode and decode of that volume; mean abs error <= 1e-4 per channel for
+    every volume (the per-volume errors are in the assertion message)."""
+    torch, v, orc, vg, sc = env["torch"], env["v"], env["orc"], env["vg"], env["sc"]
+    specs = sc.batch_jobs()
+    hosts, grids, imgs, structs, cams = [], [], [], [], []
+    for sp in specs:
+        host = vg.generate_host(vg.make_params(sp["kind"], sp["dims"], sp["seed"]))
+        g = v.vdbc_encode(torch.from_numpy(host).to(env["dev"]), sp["ratio"], payload=sp["payload"],
+                          macrocell=sp["macrocell"])
+        cam_args = sc.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"])
+        img = torch.zeros((sp["height"], sp["width"], 4), dtype=torch.float32, device=env["dev"])
+        hosts.append(host)
+        grids.append(g)
+        imgs.append(img)
+        cams.append(cam_args)
+        structs.append(v.make_job(g, v.make_camera(*cam_args), v.make_medium(v.MODE_PT, **sp["medium"]),
+                                  sp["spp"], sp["seed"], img))
+    b = v.vdbc_batch_create(structs, autotune=False, keep=(grids, imgs))
+    v.vdbc_batch_render_frames(b, 1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    errs = []
+    for sp, host, img, cam_args in zip(specs, hosts, imgs, cams):
+        e = orc.encode(host, sp["ratio"], payload=sp["payload"])
+        D = orc.decode_dense(host, e["active"], e["background_bits"], sp["payload"])
+        mx = orc.macrocell_minmax(D, sp["macrocell"])[1]
+        pix = np.sort(rng.choice(sp["width"] * sp["height"], 16, replace=False))
+        ref = orc.render_pixels(D, mx, orc.make_camera(*cam_args),
+                                orc.make_medium(1, macrocell=sp["macrocell"], **sp["medium"]),
+                                sp["spp"], sp["seed"], pix, threads=8)
+        got = img.cpu().numpy().reshape(-1, 4).astype(np.float64)[pix, :3]
+        errs.append(float(np.abs(got - ref[:, :3]).mean(axis=0).max()))
+    report = ", ".join("%d:%.1e" % (i, x) for i, x in enumerate(errs))
+    assert max(errs) <= PT_MEAN_ABS, report
     b.close()
