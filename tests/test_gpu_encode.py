@@ -72,6 +72,17 @@ def test_encoder_bit_exact_fp32(env, dims, ratio):
     check_encoding(env, host, ratio)
 
 
+@pytest.mark.parametrize("dims", [(8192, 4, 5), (4, 8192, 5), (4, 5, 8192)])
+@pytest.mark.parametrize("payload", [0, 1, 2])
+def test_encoder_bit_exact_largest_edge(env, dims, payload):
+    """Volumes 8192 voxels long (the largest edge the encoder takes) along each
+    axis: two entries of the root table along that axis, crossed by the tree
+    descent of every decoded voxel and by the macrocells."""
+    host = env["vg"].generate_host(env["vg"].make_params("turbulence", dims, 3))
+    grid, e, D = check_encoding(env, host, 2.0, payload=payload, macrocell=16)
+    assert grid.info.n_upper == 2
+
+
 @pytest.mark.parametrize("dims", [(64, 64, 64), (97, 70, 33), (1, 1, 1), (130, 8, 129)])
 @pytest.mark.parametrize("offset", [1, 3])
 def test_encoder_bit_exact_unaligned_base(env, dims, offset):

@@ -346,3 +346,28 @@ def test_concurrent_calls_on_two_threads(env):
         assert len(got[i]) == 4
         for img in got[i]:
             assert np.array_equal(img.view(np.uint32), want[i].view(np.uint32))
+
+
+def test_pt_across_the_root_boundary_matches_oracle(env):
+    """A volume 8192 voxels long (the largest edge; two root-table entries
+    along x), path traced by an orthographic camera that looks along +y at
+    the 64 voxels around x = 4096, where lookups switch root entries: mean abs
+    error per channel within the path-tracing tolerance of the FP64 oracle."""
+    torch, v, vg = env["torch"], env["v"], env["vg"]
+    dims = (8192, 4, 6)
+    host = vg.generate_host(vg.make_params("turbulence", dims, 3))
+    grid = v.vdbc_encode(torch.from_numpy(host).to(env["dev"]), 2.0, macrocell=16)
+    assert grid.info.n_upper == 2
+    orc = env["orc"]
+    e = orc.encode(host, 2.0)
+    D = orc.decode_dense(host, e["active"], e["background_bits"])
+    M = 8192.0
+    xc, zc = (4095.5 + 0.5) / M, (2.5 + 0.5) / M
+    cam = (v.CAM_ORTHO, 64, 6, (xc, -1.0, zc), (xc, 0.0, zc), (0, 0, 1), 6.0 / M)
+    kw = env["sc"].pt_medium_args(density_scale=3000.0, g=0.5, max_bounces=4)
+    img = gpu_image(env, grid, cam, v.make_medium(v.MODE_PT, **kw), 8, 5)
+    ref = oracle_image(env, D, cam, 1, 8, 5, macrocell=16, **kw)
+    assert img[..., 3].min() > 0.0
+    err = np.abs(img[..., :3] - ref[..., :3]).mean(axis=(0, 1))
+    assert np.all(err <= PT_MEAN_ABS), err
+    assert np.abs(img[..., :3] - 0.25).max() > 1e-3       # the medium is seen, not just the environment

@@ -179,8 +179,11 @@ def test_decode_dense_matches_definition_fp32(orc, vg, dims, ratio):
 
 
 @pytest.mark.parametrize("payload", [0, 1, 2])
-@pytest.mark.parametrize("dims", [(40, 33, 17), (9, 70, 3)])
+@pytest.mark.parametrize("dims", [(40, 33, 17), (9, 70, 3), (8192, 3, 2), (2, 8192, 3), (3, 2, 8192)])
 def test_tree_descent_equals_decode_every_voxel(orc, vg, dims, payload):
+    """Every voxel through the tree equals the definitional decode; the
+    8192-long volumes (the largest edge the encoder takes) span two entries of
+    the root table along one axis each."""
     v = vg.generate_host(vg.make_params("blobs", dims, 5))
     e = orc.encode(v, 2.0, payload=payload)
     D = orc.decode_dense(v, e["active"], e["background_bits"], payload)
@@ -189,6 +192,8 @@ def test_tree_descent_equals_decode_every_voxel(orc, vg, dims, payload):
     got = np.array([[[t.value(i, j, k) for i in range(nx)] for j in range(ny)] for k in range(nz)],
                    dtype=np.float32)
     assert np.array_equal(got.view(np.uint32), D.view(np.uint32))
+    if max(dims) > 4096:
+        assert t.counts()["root"] == 2
 
 
 def test_prune_keeps_values_and_collapses_constant_leaves(orc):
