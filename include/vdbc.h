@@ -233,7 +233,15 @@ void        vdbc_grid_free(vdbc_grid* grid);
  *            lookups (the result is the plain march's); spp must be 1.
  *   rgba_out width*height*4 floats (RGBA per pixel, row 0 at the top),
  *            device pointer if out_on_device else host (the call then waits).
- * Errors: INVALID_ARG; OOM; CUDA; TIMEOUT; DEVICE_FLAG.
+ * Errors: INVALID_ARG (null pointers; an image outside 1..16384 a side; a
+ * camera without a basis: non-finite vectors, look == eye, up along the
+ * view, a field of view outside (0, 180) degrees or a non-positive ortho
+ * height; spp outside 1..65536 for PT or not 1 for EA/ISO; a PT medium with
+ * a negative or non-finite density scale, albedo outside [0, 1], g outside
+ * (-1, 1), max_bounces outside 1..4096, a zero or non-finite sun direction or
+ * non-finite radiance; an EA transfer function of fewer than 2 or more than
+ * 2048 entries; a non-positive step; a non-finite iso value); OOM; CUDA;
+ * TIMEOUT; DEVICE_FLAG.
  */
 vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* camera, const vdbc_medium* medium,
                         int32_t spp, uint64_t seed, float* rgba_out, int32_t out_on_device,

@@ -1033,8 +1033,23 @@ vdbc_status check_camera(const vdbc_camera* c)
         return set_error(VDBC_ERR_INVALID_ARG, "camera kind %d unknown", c->kind);
     if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
         return set_error(VDBC_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", c->width, c->height);
-    if (!(c->fovy_or_height > 0.0) || (c->kind == VDBC_CAM_PINHOLE && !(c->fovy_or_height < 180.0)))
+    if (!(c->fovy_or_height > 0.0) || !std::isfinite(c->fovy_or_height) ||
+        (c->kind == VDBC_CAM_PINHOLE && !(c->fovy_or_height < 180.0)))
         return set_error(VDBC_ERR_INVALID_ARG, "bad field of view / ortho height");
+    // a basis must exist: finite vectors, look != eye, up not along the view
+    double f[3], fl = 0.0, ul = 0.0, cl = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(c->eye[a]) || !std::isfinite(c->look[a]) || !std::isfinite(c->up[a]))
+            return set_error(VDBC_ERR_INVALID_ARG, "camera vectors must be finite");
+        f[a] = (double)c->look[a] - (double)c->eye[a];
+        fl += f[a] * f[a];
+        ul += (double)c->up[a] * c->up[a];
+    }
+    const double cr[3] = {f[1] * c->up[2] - f[2] * c->up[1], f[2] * c->up[0] - f[0] * c->up[2],
+                          f[0] * c->up[1] - f[1] * c->up[0]};
+    for (double x : cr) cl += x * x;
+    if (!(fl > 0.0) || !(cl > 1e-24 * fl * ul))
+        return set_error(VDBC_ERR_INVALID_ARG, "camera: look must differ from eye and up must not lie along the view");
     return VDBC_OK;
 }
 
@@ -1096,8 +1111,12 @@ vdbc_status make_med(const vdbc_medium* m, const int dims[3], int spp, cudaStrea
         if (spp < 1 || spp > 65536) return set_error(VDBC_ERR_INVALID_ARG, "spp %d outside 1..65536", spp);
         if (m->max_bounces < 1 || m->max_bounces > 4096)
             return set_error(VDBC_ERR_INVALID_ARG, "max_bounces %d outside 1..4096", m->max_bounces);
-        if (!(m->density_scale >= 0.0f) || !(m->albedo >= 0.0f && m->albedo <= 1.0f) || !(m->g > -1.0f && m->g < 1.0f))
+        if (!(m->density_scale >= 0.0f) || !std::isfinite(m->density_scale) ||
+            !(m->albedo >= 0.0f && m->albedo <= 1.0f) || !(m->g > -1.0f && m->g < 1.0f))
             return set_error(VDBC_ERR_INVALID_ARG, "medium parameters out of range");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(m->sun_dir[a]) || !std::isfinite(m->sun_rad[a]) || !std::isfinite(m->env_rad[a]))
+                return set_error(VDBC_ERR_INVALID_ARG, "sun and environment must be finite");
         double sl = std::sqrt((double)m->sun_dir[0] * m->sun_dir[0] + (double)m->sun_dir[1] * m->sun_dir[1] +
                               (double)m->sun_dir[2] * m->sun_dir[2]);
         if (!(sl > 0.0)) return set_error(VDBC_ERR_INVALID_ARG, "sun_dir must be nonzero");

@@ -371,3 +371,51 @@ def test_pt_across_the_root_boundary_matches_oracle(env):
     err = np.abs(img[..., :3] - ref[..., :3]).mean(axis=(0, 1))
     assert np.all(err <= PT_MEAN_ABS), err
     assert np.abs(img[..., :3] - 0.25).max() > 1e-3       # the medium is seen, not just the environment
+
+
+def test_bad_cameras_and_media_rejected_before_any_launch(env):
+    """A camera without a basis or a medium out of range is refused with
+    INVALID_ARG before any device work; the same grid renders afterwards."""
+    torch, v, sc = env["torch"], env["v"], env["sc"]
+    dims = (24, 20, 28)
+    g = v.vdbc_encode(torch.from_numpy(env["vg"].generate_host(env["vg"].make_params("blobs", dims, 2))).to(env["dev"]),
+                      2.0)
+    out = torch.zeros(6, 8, 4, device=env["dev"])
+    good_cam = sc.pinhole_orbit(dims, 8, 6)
+    pt = sc.pt_medium_args()
+    nan = float("nan")
+    bad_cams = [
+        (1, 8, 6, (0.5, 0.5, 0.5), (0.5, 0.5, 0.5), (0, 1, 0), 40.0),      # look == eye
+        (1, 8, 6, (0.5, 2.0, 0.5), (0.5, 0.0, 0.5), (0, 1, 0), 40.0),      # up along the view
+        (1, 8, 6, (nan, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), 40.0),      # non-finite eye
+        (1, 8, 6, (0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 0, 0), 40.0),      # zero up
+        (1, 8, 6, (0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), 180.0),     # field of view
+        (0, 8, 6, (0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), float("inf")),  # ortho height
+        (1, 0, 6, (0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), 40.0),      # width 0
+        (1, 16385, 6, (0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), 40.0),  # width too large
+    ]
+    for cam in bad_cams:
+        with pytest.raises(v.VdbcError) as ex:
+            v.vdbc_render(g, v.make_camera(*cam), v.make_medium(v.MODE_PT, **pt), 1, 0, out)
+        assert ex.value.status == v.ERR_INVALID_ARG, cam
+    bad_media = [
+        (v.make_medium(v.MODE_PT, **dict(pt, density_scale=float("inf"))), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, density_scale=-1.0)), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, albedo=1.5)), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, g=1.0)), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, max_bounces=0)), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, sun_dir=(0, 0, 0))), 1),
+        (v.make_medium(v.MODE_PT, **dict(pt, env_rad=(nan, 0, 0))), 1),
+        (v.make_medium(v.MODE_PT, **pt), 0),
+        (v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf(), step=0.5), 2),
+        (v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf()[:1], step=0.5), 1),
+        (v.make_medium(v.MODE_EA, tf=sc.linear_ramp_tf(), step=0.0), 1),
+        (v.make_medium(v.MODE_ISO, step=0.5, iso=nan), 1),
+    ]
+    for med, spp in bad_media:
+        with pytest.raises(v.VdbcError) as ex:
+            v.vdbc_render(g, v.make_camera(*good_cam), med, spp, 0, out)
+        assert ex.value.status == v.ERR_INVALID_ARG, (med.mode, spp)
+    v.vdbc_render(g, v.make_camera(*good_cam), v.make_medium(v.MODE_PT, **pt), 2, 0, out)
+    torch.cuda.synchronize()
+    assert np.isfinite(out.cpu().numpy()).all() and v.vdbc_render_stats_get(g).paths == 8 * 6 * 2
