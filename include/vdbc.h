@@ -150,10 +150,12 @@ typedef struct {
     uint64_t lookups;          /* density lookups (trilinear reconstructions) */
     uint64_t paths;
     uint64_t error_flags;      /* nonzero if a kernel hit one of its bounds */
-    uint64_t events[6];        /* only in builds with VDBC_STATS defined (the checked build
+    uint64_t events[8];        /* only in builds with VDBC_STATS defined (the checked build
                                   libvdbc_checked.so is one), else 0: tracker loop iterations,
                                   DDA cells examined, coarse blocks crossed, free flights
-                                  drawn, rays started, paths fetched */
+                                  drawn, rays started, paths fetched, leaf queries to the
+                                  per-thread accessor, tree descents (the queries its cached
+                                  leaf did not answer; queries - descents = descents saved) */
     float    kernel_ms;        /* duration of the last render's tracker kernel (k_pt, k_pt_batch,
                                   k_ea or k_iso), from CUDA events recorded around its launch on
                                   the render's stream; -1 if none was recorded */

@@ -92,7 +92,7 @@ class Tuning(ctypes.Structure):
 
 class RenderStats(ctypes.Structure):
     _fields_ = [("lookups", ctypes.c_uint64), ("paths", ctypes.c_uint64), ("error_flags", ctypes.c_uint64),
-                ("events", ctypes.c_uint64 * 6), ("kernel_ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("events", ctypes.c_uint64 * 8), ("kernel_ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class LearnState(ctypes.Structure):

@@ -171,6 +171,10 @@ struct LearnedSampler {
     // leaf from meta (raw) or nmeta (neural)
     __device__ __forceinline__ uint32_t leaf(Accessor& a, int li, int lj, int lk) const
     {
+#ifdef VDBC_STATS
+        ++a.queries;
+        if (li != a.li || lj != a.lj || lk != a.lk) ++a.descents;
+#endif
         if (li != a.li || lj != a.lj || lk != a.lk) {
             a.li = li; a.lj = lj; a.lk = lk;
             a.entry = descend_to_leaf(g, li, lj, lk);

@@ -255,8 +255,8 @@ struct Walk {
     unsigned long long flags;
 #ifdef VDBC_STATS
     // loop iterations, DDA cells examined, coarse blocks crossed, free flights
-    // drawn, rays started, paths fetched
-    unsigned int ev[6];
+    // drawn, rays started, paths fetched, accessor leaf queries, tree descents
+    unsigned int ev[kNumEvents];
 #endif
 };
 
@@ -281,7 +281,7 @@ __device__ __forceinline__ void flush_stats(DevStats* st, const Walk& w, unsigne
         if (f) atomicOr(&st->error_flags, f);
     }
 #ifdef VDBC_STATS
-    for (int k = 0; k < 6; ++k) atomicAdd(&st->ev[k], (unsigned long long)w.ev[k]);
+    for (int k = 0; k < kNumEvents; ++k) atomicAdd(&st->ev[k], (unsigned long long)w.ev[k]);
 #endif
 }
 
@@ -645,6 +645,10 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             }
         }
     }
+#ifdef VDBC_STATS
+    w.ev[6] += acc.queries;
+    w.ev[7] += acc.descents;
+#endif
     flush_stats(st, w, paths);
 }
 
@@ -1385,7 +1389,7 @@ extern "C" vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream
     out->lookups = h.lookups;
     out->paths = h.paths;
     out->error_flags = h.error_flags;
-    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    for (int k = 0; k < kNumEvents; ++k) out->events[k] = h.ev[k];
     out->kernel_ms = kernel_ms_of(grid->stats);
     out->reserved = 0;
     return VDBC_OK;
@@ -1502,7 +1506,7 @@ extern "C" vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void
     out->lookups = h.lookups;
     out->paths = h.paths;
     out->error_flags = h.error_flags;
-    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    for (int k = 0; k < kNumEvents; ++k) out->events[k] = h.ev[k];
     out->kernel_ms = kernel_ms_of(vol->stats);
     out->reserved = 0;
     return VDBC_OK;
@@ -1940,7 +1944,7 @@ extern "C" vdbc_status vdbc_batch_stats_get(const vdbc_batch* b, void* stream, v
     out->lookups = h.lookups;
     out->paths = h.paths;
     out->error_flags = h.error_flags;
-    for (int k = 0; k < 6; ++k) out->events[k] = h.ev[k];
+    for (int k = 0; k < kNumEvents; ++k) out->events[k] = h.ev[k];
     out->kernel_ms = -1.0f;   // frames are replayed from a graph; time them around vdbc_batch_render_frames
     out->reserved = 0;
     return VDBC_OK;

@@ -38,6 +38,9 @@ enum : unsigned long long {
     kErrBounds = 1ull << 2,        // an index outside its table (checked builds)
 };
 
+// tracker event counters of VDBC_STATS builds (vdbc_render_stats.events)
+constexpr int kNumEvents = 8;
+
 constexpr uint32_t kTile = 0x80000000u;
 constexpr uint32_t kBackgroundEntry = 0x80000000u;   // tile 0
 constexpr int kUpperN = 32768, kLowerN = 4096, kLeafN = 512;
@@ -173,9 +176,16 @@ struct Accessor {
     int li, lj, lk;
     uint32_t entry;
     float2 sm;
+#ifdef VDBC_STATS
+    unsigned queries = 0, descents = 0;   // leaf() calls, and those that walked the tree
+#endif
     __device__ __forceinline__ void reset() { li = -1; lj = -1; lk = -1; entry = kBackgroundEntry; sm = make_float2(0.f, 0.f); }
     __device__ __forceinline__ uint32_t leaf(const GridView& g, int a, int b, int c)
     {
+#ifdef VDBC_STATS
+        ++queries;
+        if (a != li || b != lj || c != lk) ++descents;
+#endif
         if (a != li || b != lj || c != lk) {
             li = a; lj = b; lk = c;
             entry = descend_to_leaf(g, a, b, c);

@@ -17,7 +17,7 @@ struct DevStats {
     unsigned long long paths;
     unsigned long long error_flags;
     unsigned long long work_next;    // persistent-kernel work counter
-    unsigned long long ev[6];        // event counts of builds with VDBC_STATS (else 0)
+    unsigned long long ev[kNumEvents];   // event counts of builds with VDBC_STATS (else 0)
 };
 
 vdbc_status set_error(vdbc_status s, const char* fmt, ...);

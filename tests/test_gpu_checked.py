@@ -126,11 +126,13 @@ def test_checked_build_computes_the_same_bits(env, tmp_path):
         if k.startswith("events"):
             # the plain build counts no events; the checked build (VDBC_STATS)
             # counts every path fetched once, a free flight per lookup at
-            # least, and more loop iterations than flights
-            ev, lookups, paths = [int(x) for x in b[:6]], int(b[6]), int(b[7])
-            assert not np.any(a[:6]) and int(a[6]) == lookups and int(a[7]) == paths, (k, a, b)
+            # least, more loop iterations than flights, one to eight accessor
+            # queries per lookup, and tree descents for only some of them
+            ev, lookups, paths = [int(x) for x in b[:8]], int(b[8]), int(b[9])
+            assert not np.any(a[:8]) and int(a[8]) == lookups and int(a[9]) == paths, (k, a, b)
             assert ev[5] == paths and ev[4] > 0 and ev[3] >= lookups > 0, (k, ev, lookups, paths)
             assert ev[0] >= ev[3] and ev[1] > 0 and ev[2] == 0, (k, ev)
+            assert lookups <= ev[6] <= 8 * lookups and 0 < ev[7] < ev[6], (k, ev, lookups)
         elif k.startswith("flags"):
             assert int(a) == 0 and int(b) == 0, (k, a, b)
         elif k == "n_neural":
