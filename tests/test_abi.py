@@ -128,3 +128,42 @@ def test_checked_build_exports_the_same_surface(v, checked_lib):
     assert not v.vdbc_version().endswith("checked")
     h = ctypes.c_void_p()
     assert checked_lib.vdbc_encode(None, None, None, ctypes.byref(h)) == v.ERR_INVALID_ARG
+
+
+def test_null_arguments_rejected_on_every_entry_point(v):
+    """Every entry point that takes a handle or an output refuses a null one
+    with INVALID_ARG before any device work (so this runs without a GPU)."""
+    L = v.lib()
+    h = ctypes.c_void_p()
+    n64 = ctypes.c_int64()
+    n32 = ctypes.c_int32()
+    calls = [
+        lambda: L.vdbc_grid_get_info(None, None),
+        lambda: L.vdbc_grid_decode(None, None, 1, None),
+        lambda: L.vdbc_grid_active_bricks(None, None),
+        lambda: L.vdbc_grid_macrocells(None, None, None),
+        lambda: L.vdbc_grid_save(None, b"/nonexistent"),
+        lambda: L.vdbc_grid_load(None, None, ctypes.byref(h)),
+        lambda: L.vdbc_render_stats_get(None, None, None),
+        lambda: L.vdbc_volume_create(None, 0, 8, None, ctypes.byref(h)),
+        lambda: L.vdbc_render_dense(None, None, None, 1, 0, None, 1, None),
+        lambda: L.vdbc_volume_render_stats_get(None, None, None),
+        lambda: L.vdbc_batch_create(None, 0, 0, None, ctypes.byref(h)),
+        lambda: L.vdbc_batch_render_frames(None, 1, None),
+        lambda: L.vdbc_batch_reset(None, None),
+        lambda: L.vdbc_batch_get_tuning(None, None),
+        lambda: L.vdbc_batch_stats_get(None, None, None),
+        lambda: L.vdbc_batch_state_size(None, ctypes.byref(n64)),
+        lambda: L.vdbc_batch_get_state(None, ctypes.byref(n32), None, None),
+        lambda: L.vdbc_batch_set_state(None, 0, None, None),
+        lambda: L.vdbc_learn(None, None, None, ctypes.byref(h), None),
+        lambda: L.vdbc_learn_loss_grad(None, None, None, 1, None, None, None, None),
+        lambda: L.vdbc_learn_get_params(None, None),
+        lambda: L.vdbc_select_bricks_noalloc(None, None, None, None, None, None),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == v.ERR_INVALID_ARG, i
+        assert v.vdbc_last_error(), i
+    L.vdbc_grid_free(None)
+    L.vdbc_volume_free(None)
+    L.vdbc_batch_free(None)
