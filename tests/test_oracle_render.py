@@ -172,6 +172,33 @@ def test_ortho_camera_pixel_centres(orc):
         assert abs(o[1] - ((127 - py + 0.5) / 2 - 0.5)) < 1e-12
 
 
+def test_pinhole_camera_geometry(orc):
+    """A pinhole camera's rays start at the eye; the image centre looks at
+    `look`; the top and right image edges lie at half the vertical field of
+    view (times the aspect ratio, on tangents) from it; the top row leans
+    toward `up` and the right column toward forward x up."""
+    dims = (40, 30, 20)
+    M = 40.0
+    eye, look, up, fov = (0.9, 0.7, -0.4), (0.45, 0.3, 0.2), (0.0, 1.0, 0.0), 50.0
+    w, h = 64, 48
+    cam = orc.make_camera(orc.CAM_PINHOLE, w, h, eye, look, up, fov)
+    fwd = np.subtract(look, eye)
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    for px, py, jx, jy in ((0, 0, 0.5, 0.5), (17, 30, 0.2, 0.9), (63, 47, 0.5, 0.5)):
+        o, d = orc.camera_ray(cam, dims, px, py, jx, jy)
+        assert np.allclose(o, np.array(eye) * M - 0.5, atol=1e-12) and abs(np.linalg.norm(d) - 1) < 1e-12
+    o, d = orc.camera_ray(cam, dims, w // 2 - 1, h // 2 - 1, 1.0, 1.0)      # the exact image centre
+    assert np.allclose(d, fwd, atol=1e-12)
+    t = math.tan(math.radians(fov / 2))
+    _, top = orc.camera_ray(cam, dims, w // 2 - 1, 0, 1.0, 0.0)               # top edge, centre column
+    assert abs(np.dot(top, upv) / np.dot(top, fwd) - t) < 1e-12 and abs(np.dot(top, right)) < 1e-12
+    _, rgt = orc.camera_ray(cam, dims, w - 1, h // 2 - 1, 1.0, 1.0)           # right edge, centre row
+    assert abs(np.dot(rgt, right) / np.dot(rgt, fwd) - t * w / h) < 1e-12 and abs(np.dot(rgt, upv)) < 1e-12
+
+
 # ------------------------------------------------------------------ EA marcher
 @pytest.mark.parametrize("c,alpha_scale", [(0.5, 0.02), (1.0, 0.2), (0.25, 0.0)])
 def test_ea_constant_slab_closed_form(orc, c, alpha_scale):
