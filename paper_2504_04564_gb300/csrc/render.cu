@@ -392,8 +392,9 @@ struct SingleSource {
     }
 };
 
-// many jobs: their constants and grids staged in shared memory; each lane
-// decodes its job's payload type at run time
+// many jobs of one payload type P: their constants and grids staged in
+// shared memory
+template <int P>
 struct BatchSource {
     static constexpr bool kMulti = true;
     static constexpr bool kCollective = false;
@@ -412,13 +413,10 @@ struct BatchSource {
     __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
     __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
     {
-        const GridView& g = grids[i];
-        // one dispatch per lookup on the job's payload, not one per voxel (one
-        // trilinear switching per voxel measured slower: 162.9 against 150.6 ms
-        // for the 32-job frame)
-        if (g.payload == 1) return vdb_trilinear<1>(g, x, y, z, a);
-        if (g.payload == 2) return vdb_trilinear<2>(g, x, y, z, a);
-        return vdb_trilinear<0>(g, x, y, z, a);
+        // the payload is the group's, fixed at compile time (one kernel with a
+        // run-time dispatch over the three samplers, and one trilinear switching
+        // per voxel, both measured slower: 150.6 and 162.9 ms for the 32-job frame)
+        return vdb_trilinear<P>(grids[i], x, y, z, a);
     }
 };
 
@@ -699,9 +697,9 @@ __global__ void __launch_bounds__(256, (pt_min_blocks<S, kUseCoarse>()))
     pt_loop<kUseCoarse>(src, job.items, st, chunk, 1u);
 }
 
-// all jobs of a batch in one persistent launch; frame[0] numbers the
+// the jobs of one payload type in one persistent launch; frame[0] numbers the
 // progressive frame, so frame f renders sample ids [f*spp, (f+1)*spp)
-template <int kThreads, bool kUseCoarse>
+template <int kThreads, bool kUseCoarse, int kPayload>
 __global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads)
     k_pt_batch(const JobView* __restrict__ jobs, const GridView* __restrict__ grids, int n,
                unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk,
@@ -717,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads
         sg[i] = grids[i];
     }
     __syncthreads();
-    BatchSource src{sj, sg, n};
+    BatchSource<kPayload> src{sj, sg, n};
     pt_loop<kUseCoarse>(src, nitems, st, chunk, stride);
 }
 
@@ -1566,11 +1564,24 @@ void tune_file_store(const std::string& key, const vdbc_tuning& t)
 }  // namespace
 }  // namespace vdbc
 
+// the jobs of one payload type: one persistent launch per frame each
+struct BatchGroup {
+    int payload = 0;
+    std::vector<int> members;                 // job indices, in the caller's order
+    std::vector<vdbc::JobView> h_jobs;        // their job views, work items counted from 0
+    vdbc::JobView* d_jobs = nullptr;
+    vdbc::GridView* d_grids = nullptr;
+    unsigned long long nitems = 0;
+    vdbc::DevStats* stats = nullptr;
+    unsigned blocks[2][2] = {{0, 0}, {0, 0}};     // launch configuration per [256 threads][coarse level]
+    size_t smem[2][2] = {{0, 0}, {0, 0}};
+};
+
 struct vdbc_batch {
     int n = 0;
     std::vector<vdbc_job> jobs;
     vdbc::JobView* d_jobs = nullptr;        // device job table (bits point at the chosen variant)
-    vdbc::GridView* d_grids = nullptr;
+    std::vector<BatchGroup> groups;         // by payload type
     std::vector<vdbc::JobView> h_jobs;
     std::vector<uint32_t*> bits_on, bits_off;   // per job: fine + coarse words, coarse skipping on / off
     std::vector<int> nwords;
@@ -1579,12 +1590,8 @@ struct vdbc_batch {
     float4** d_sums = nullptr;
     float** d_outs = nullptr;
     int* d_frame = nullptr;
-    vdbc::DevStats* stats = nullptr;
-    unsigned long long nitems = 0;
     size_t max_npix = 0;
     vdbc_tuning tuning{256, 256, 1, 0, 0.0f};
-    unsigned blocks[2][2] = {{0, 0}, {0, 0}};     // launch configuration per [256 threads][coarse level]
-    size_t smem[2][2] = {{0, 0}, {0, 0}};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> allocs;
@@ -1611,44 +1618,87 @@ vdbc_status batch_select_bits(vdbc_batch* b, bool coarse, cudaStream_t s)
         b->h_jobs[i].cbits = base + b->nwords[i];
     }
     VDBC_CUDA(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(JobView) * b->n, cudaMemcpyHostToDevice, s));
+    for (BatchGroup& g : b->groups) {
+        unsigned long long items = 0;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            JobView jv = b->h_jobs[g.members[k]];
+            jv.item_begin = items;
+            items += jv.items;
+            g.h_jobs[k] = jv;
+        }
+        VDBC_CUDA(cudaMemcpyAsync(g.d_jobs, g.h_jobs.data(), sizeof(JobView) * g.h_jobs.size(),
+                                  cudaMemcpyHostToDevice, s));
+    }
     return VDBC_OK;
 }
 
 // grid size and shared memory of the batched tracker for a block size; called
 // before any capture (it sets a function attribute and queries occupancy)
-template <int kThreads, bool kUseCoarse>
-vdbc_status batch_config(vdbc_batch* b)
+template <int kThreads, bool kUseCoarse, int P>
+vdbc_status group_config_t(BatchGroup& g)
 {
-    unsigned* blocks = &b->blocks[kThreads == 256][kUseCoarse];
-    size_t* smem = &b->smem[kThreads == 256][kUseCoarse];
-    *smem = (sizeof(JobView) + sizeof(GridView)) * (size_t)b->n;
-    auto kern = k_pt_batch<kThreads, kUseCoarse>;
+    unsigned* blocks = &g.blocks[kThreads == 256][kUseCoarse];
+    size_t* smem = &g.smem[kThreads == 256][kUseCoarse];
+    *smem = (sizeof(JobView) + sizeof(GridView)) * g.members.size();
+    auto kern = k_pt_batch<kThreads, kUseCoarse, P>;
     if (*smem > 48 * 1024)
         VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
     int per_sm = 0;
     VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, *smem));
     if (per_sm < 1) per_sm = 1;
-    long long want = (long long)((b->nitems + kThreads - 1) / kThreads);
+    long long want = (long long)((g.nitems + kThreads - 1) / kThreads);
     *blocks = (unsigned)std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
+    return VDBC_OK;
+}
+
+template <int kThreads, bool kUseCoarse, int P>
+vdbc_status group_launch_t(vdbc_batch* b, BatchGroup& g, int chunk, unsigned stride, cudaStream_t s)
+{
+    if (g.blocks[kThreads == 256][kUseCoarse] == 0) VDBC_TRY((group_config_t<kThreads, kUseCoarse, P>(g)));
+    const unsigned blocks = g.blocks[kThreads == 256][kUseCoarse];
+    const size_t smem = g.smem[kThreads == 256][kUseCoarse];
+    KLAUNCH((k_pt_batch<kThreads, kUseCoarse, P><<<blocks, kThreads, smem, s>>>(
+        g.d_jobs, g.d_grids, (int)g.members.size(), g.nitems, b->d_frame, g.stats, chunk, stride)));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
+
+// the group's kernel for its payload type
+template <int kThreads, bool kUseCoarse>
+vdbc_status group_launch(vdbc_batch* b, BatchGroup& g, int chunk, unsigned stride, cudaStream_t s)
+{
+    if (g.payload == VDBC_FP16) return group_launch_t<kThreads, kUseCoarse, 1>(b, g, chunk, stride, s);
+    if (g.payload == VDBC_FP8) return group_launch_t<kThreads, kUseCoarse, 2>(b, g, chunk, stride, s);
+    return group_launch_t<kThreads, kUseCoarse, 0>(b, g, chunk, stride, s);
+}
+
+template <int kThreads, bool kUseCoarse>
+vdbc_status group_config(BatchGroup& g)
+{
+    if (g.payload == VDBC_FP16) return group_config_t<kThreads, kUseCoarse, 1>(g);
+    if (g.payload == VDBC_FP8) return group_config_t<kThreads, kUseCoarse, 2>(g);
+    return group_config_t<kThreads, kUseCoarse, 0>(g);
+}
+
+template <int kThreads, bool kUseCoarse>
+vdbc_status batch_config(vdbc_batch* b)
+{
+    for (BatchGroup& g : b->groups) VDBC_TRY((group_config<kThreads, kUseCoarse>(g)));
     return VDBC_OK;
 }
 
 template <int kThreads, bool kUseCoarse>
 vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStream_t s)
 {
-    const unsigned& blocks = b->blocks[kThreads == 256][kUseCoarse];
-    const size_t& smem = b->smem[kThreads == 256][kUseCoarse];
-    if (blocks == 0) VDBC_TRY((batch_config<kThreads, kUseCoarse>(b)));
-    KLAUNCH((k_pt_batch<kThreads, kUseCoarse><<<blocks, kThreads, smem, s>>>(b->d_jobs, b->d_grids, b->n, b->nitems,
-                                                                            b->d_frame, b->stats, chunk, stride)));
-    VDBC_CUDA(cudaGetLastError());
+    for (BatchGroup& g : b->groups) VDBC_TRY((group_launch<kThreads, kUseCoarse>(b, g, chunk, stride, s)));
     return VDBC_OK;
 }
 
-// the work of one frame: counters, tracker, accumulation, next frame number
+// the work of one frame: counters, one tracker launch per payload group,
+// accumulation, next frame number
 vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s, unsigned stride = 1)
 {
-    VDBC_CUDA(cudaMemsetAsync(b->stats, 0, sizeof(DevStats), s));
+    for (BatchGroup& g : b->groups) VDBC_CUDA(cudaMemsetAsync(g.stats, 0, sizeof(DevStats), s));
     if (t.threads == 128) {
         if (t.coarse) VDBC_TRY((batch_launch_pt<128, true>(b, t.chunk, stride, s)));
         else VDBC_TRY((batch_launch_pt<128, false>(b, t.chunk, stride, s)));
@@ -1812,19 +1862,40 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
         grids[i] = g;
         outs[i] = j.rgba_out;
     }
-    b->nitems = items;
+    (void)items;
+    // payload groups, each with its own job and grid tables, work counter and stats
+    for (int p = VDBC_FP32; p <= VDBC_FP8; ++p) {
+        BatchGroup g;
+        g.payload = p;
+        for (int i = 0; i < n; ++i)
+            if (jobs[i].grid->info.payload == p) {
+                g.members.push_back(i);
+                g.nitems += b->h_jobs[i].items;
+            }
+        if (!g.members.empty()) b->groups.push_back(std::move(g));
+    }
     vdbc_status st = batch_alloc(b, reinterpret_cast<void**>(&b->path_out), path_floats4 * sizeof(float4));
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->sums), sum_floats4 * sizeof(float4));
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_jobs), sizeof(JobView) * n);
-    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_grids), sizeof(GridView) * n);
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_sums), sizeof(float4*) * n);
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_outs), sizeof(float*) * n);
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_frame), sizeof(int));
-    if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->stats), sizeof(DevStats));
+    for (BatchGroup& g : b->groups) {
+        g.h_jobs.resize(g.members.size());
+        if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&g.d_jobs), sizeof(JobView) * g.members.size());
+        if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&g.d_grids), sizeof(GridView) * g.members.size());
+        if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&g.stats), sizeof(DevStats));
+    }
     if (st != VDBC_OK) return fail(st);
+    std::vector<std::vector<GridView>> ggrids(b->groups.size());
+    for (size_t k = 0; k < b->groups.size(); ++k)
+        for (int m : b->groups[k].members) {
+            GridView gv = grids[m];
 #if VDBC_CHECKED
-    for (int i = 0; i < n; ++i) grids[i].err = &b->stats->error_flags;   // reported with the batch's flags
+            gv.err = &b->groups[k].stats->error_flags;   // reported with the batch's flags
 #endif
+            ggrids[k].push_back(gv);
+        }
     size_t po = 0, so = 0;
     for (int i = 0; i < n; ++i) {
         JobView& jv = b->h_jobs[i];
@@ -1849,7 +1920,10 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
         if (e == cudaSuccess) e = cudaMemsetAsync(b->bits_off[i] + nwords, 0xff, (size_t)ncwords * 4, s);
         if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create bits"));
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_grids, grids.data(), sizeof(GridView) * n, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < b->groups.size() && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(b->groups[k].d_grids, ggrids[k].data(), sizeof(GridView) * ggrids[k].size(),
+                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_sums, sum_ptrs.data(), sizeof(float4*) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_outs, outs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_frame, 0, sizeof(int), s);
@@ -1871,7 +1945,7 @@ extern "C" vdbc_status vdbc_batch_render_frames(vdbc_batch* b, int32_t frames, v
     if (!b || !b->exec || frames < 0) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_render_frames: bad argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int f = 0; f < frames; ++f) {
-        count_launch(b->n > 0 ? 3 : 0);      // tracker, reduce, frame counter
+        count_launch((int)b->groups.size() + 2);      // a tracker per payload group, reduce, frame counter
         VDBC_CUDA(cudaGraphLaunch(b->exec, s));
     }
     return VDBC_OK;
@@ -1939,12 +2013,16 @@ extern "C" vdbc_status vdbc_batch_stats_get(const vdbc_batch* b, void* stream, v
     clear_error();
     if (!b || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_stats_get: null argument");
     VDBC_TRY(wait_stream(static_cast<cudaStream_t>(stream)));
-    DevStats h;
-    VDBC_CUDA(cudaMemcpy(&h, b->stats, sizeof(h), cudaMemcpyDeviceToHost));
-    out->lookups = h.lookups;
-    out->paths = h.paths;
-    out->error_flags = h.error_flags;
-    for (int k = 0; k < kNumEvents; ++k) out->events[k] = h.ev[k];
+    out->lookups = out->paths = out->error_flags = 0;
+    for (int k = 0; k < kNumEvents; ++k) out->events[k] = 0;
+    for (const BatchGroup& g : b->groups) {          // the payload groups' counters, summed
+        DevStats h;
+        VDBC_CUDA(cudaMemcpy(&h, g.stats, sizeof(h), cudaMemcpyDeviceToHost));
+        out->lookups += h.lookups;
+        out->paths += h.paths;
+        out->error_flags |= h.error_flags;
+        for (int k = 0; k < kNumEvents; ++k) out->events[k] += h.ev[k];
+    }
     out->kernel_ms = -1.0f;   // frames are replayed from a graph; time them around vdbc_batch_render_frames
     out->reserved = 0;
     return VDBC_OK;
