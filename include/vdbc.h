@@ -329,13 +329,14 @@ typedef struct vdbc_batch vdbc_batch;
 
 /*
  * vdbc_batch_create -- prepare a batch of up to 64 path-tracing jobs on
- * grids of any size and payload, rendered together by ONE persistent launch
- * per frame (Section 4's tracker; the paper renders one volume at a time).
- * With autotune != 0 the launch shape is chosen by timing every 8th path of a
- * frame per candidate (cached per GPU and batch layout in this process, and in the file
- * named by VDBC_TUNE_CACHE when set).  The per-frame work (work-counter reset,
- * persistent tracker, per-pixel accumulation) is then captured in a CUDA
- * graph on `stream`.  Grids must outlive the batch.  Errors: INVALID_ARG
+ * grids of any size and payload, rendered together per frame by one
+ * persistent launch for each payload type present (FP32, FP16, FP8), each
+ * specialised on its sampler (Section 4's tracker; the paper renders one
+ * volume at a time).  With autotune != 0 the launch shape is chosen by timing
+ * every 8th path of a frame per candidate (cached per GPU and batch layout in
+ * this process, and in the file named by VDBC_TUNE_CACHE when set).  The
+ * per-frame work (work-counter resets, the persistent trackers, per-pixel
+ * accumulation) is then captured in one CUDA graph on `stream`.  Grids must outlive the batch.  Errors: INVALID_ARG
  * (n outside 1..64, a null grid or output, EA media, bad spp/camera/medium);
  * OOM; CUDA.
  */
