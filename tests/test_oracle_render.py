@@ -127,7 +127,6 @@ def test_dda_cells_match_dense_sampling(orc):
 
 def test_onb_orthonormal(orc):
     rng = np.random.default_rng(7)
-    import ctypes
     for _ in range(200):
         n = rng.normal(size=3)
         n /= np.linalg.norm(n)

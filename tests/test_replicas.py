@@ -1,7 +1,6 @@
 """The multi-GPU form is replicas only: N ranks render independently and the
 benchmark reduces nothing but its timing (max over ranks).  Checked on the CPU
 with two gloo ranks; and the reference arm's non-zero ranks exit without work."""
-import json
 import os
 import socket
 import subprocess
