@@ -167,3 +167,22 @@ def test_null_arguments_rejected_on_every_entry_point(v):
     L.vdbc_grid_free(None)
     L.vdbc_volume_free(None)
     L.vdbc_batch_free(None)
+
+
+def test_header_is_c11_and_a_c_program_links_and_runs(v, tmp_path):
+    """include/vdbc.h compiles as C11 with every warning an error, and a C
+    program on it links against the library and runs: it renders where a GPU
+    is present and otherwise exits with the library's error message."""
+    import subprocess
+    exe = str(tmp_path / "encode_render")
+    lib_dir = os.path.dirname(v.LIB_PATH)
+    lib_name = os.path.basename(v.LIB_PATH)[3:-3]
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c", "encode_render.c"), "-L" + lib_dir, "-l" + lib_name,
+                        "-Wl,-rpath," + lib_dir, "-o", exe], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    assert r.returncode == 0, r.stdout
+    r = subprocess.run([exe], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=300)
+    if r.returncode == 0:
+        assert "paths" in r.stdout
+    else:
+        assert r.returncode == 1 and r.stdout.strip(), r.stdout
