@@ -14,6 +14,7 @@ start with libasan preloaded).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -36,19 +37,27 @@ MODE_EA, MODE_PT, MODE_ISO = 0, 1, 2
 c_i64p = ctypes.POINTER(ctypes.c_int64)
 
 
+def compile_library(src_dir: str, out: str, sanitize: bool = False) -> str:
+    """Compile the oracle's C sources found in `src_dir` into the shared
+    library `out` (the flags every build of the oracle uses)."""
+    srcs = [os.path.join(src_dir, s) for s in SOURCES if os.path.exists(os.path.join(src_dir, s))]
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared"] + (SANITIZE_FLAGS if sanitize else []) + srcs + ["-o", out, "-lm"]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle build failed:\n" + r.stdout.decode())
+    return r.stdout.decode()
+
+
 def build(verbose: bool = False) -> None:
     os.makedirs(_BUILD, exist_ok=True)
     srcs = [os.path.join(_HERE, s) for s in SOURCES if os.path.exists(os.path.join(_HERE, s))]
     deps = srcs + [os.path.join(_HERE, "oracle.h")]
     if os.path.exists(LIB) and all(os.path.getmtime(d) <= os.path.getmtime(LIB) for d in deps):
         return
-    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared"] + (SANITIZE_FLAGS if SANITIZE else []) + srcs + ["-o", LIB, "-lm"]
-    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if r.returncode != 0:
-        raise RuntimeError("oracle build failed:\n" + r.stdout.decode())
-    if verbose and r.stdout:
-        print(r.stdout.decode())
+    log = compile_library(_HERE, LIB, SANITIZE)
+    if verbose and log:
+        print(log)
 
 
 class Camera(ctypes.Structure):
@@ -73,56 +82,74 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(LIB)
-        vp = ctypes.c_void_p
-        L.or_philox4x32_10.argtypes = [vp, vp, vp]
-        L.or_u01.argtypes = [ctypes.c_uint32]
-        L.or_u01.restype = ctypes.c_double
-        L.or_background_bits.argtypes = [vp, ctypes.c_int64]
-        L.or_background_bits.restype = ctypes.c_uint32
-        L.or_brick_grid.argtypes = [vp, vp]
-        L.or_brick_ranges.argtypes = [vp, vp, vp, vp]
-        L.or_brick_scores.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, vp, vp]
-        L.or_brick_budget.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int]
-        L.or_brick_budget.restype = ctypes.c_int64
-        L.or_select.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
-        L.or_select.restype = ctypes.c_int64
-        L.or_decode_dense.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_int, vp]
-        L.or_round_fp16.argtypes = [ctypes.c_float]
-        L.or_round_fp16.restype = ctypes.c_float
-        L.or_round_e4m3.argtypes = [ctypes.c_float]
-        L.or_round_e4m3.restype = ctypes.c_float
-        L.or_quantize_leaf.argtypes = [vp, ctypes.c_int, vp, vp, vp]
-        L.or_tree_build.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_int]
-        L.or_tree_build.restype = vp
-        L.or_tree_value.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
-        L.or_tree_value.restype = ctypes.c_float
-        L.or_tree_counts.argtypes = [vp, vp]
-        L.or_tree_free.argtypes = [vp]
-        L.or_trilinear.argtypes = [vp, vp, vp]
-        L.or_trilinear.restype = ctypes.c_double
-        L.or_macrocell_minmax.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
-        L.or_clip_box.argtypes = [vp, vp, vp, vp, vp]
-        L.or_clip_box.restype = ctypes.c_int
-        L.or_dda_cells.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_double, ctypes.c_double,
-                                   vp, vp, vp, ctypes.c_int64]
-        L.or_dda_cells.restype = ctypes.c_int64
-        L.or_hg_eval.argtypes = [ctypes.c_double, ctypes.c_double]
-        L.or_hg_eval.restype = ctypes.c_double
-        L.or_hg_sample_mu.argtypes = [ctypes.c_double, ctypes.c_double]
-        L.or_hg_sample_mu.restype = ctypes.c_double
-        L.or_onb.argtypes = [vp, vp, vp]
-        L.or_camera_ray.argtypes = [ctypes.POINTER(Camera), vp, ctypes.c_int64, ctypes.c_int64,
-                                    ctypes.c_double, ctypes.c_double, vp, vp]
-        L.or_ratio_transmittance.argtypes = [vp, vp, vp, ctypes.POINTER(Medium), vp, vp,
-                                             ctypes.c_uint32, ctypes.c_uint32, vp, vp]
-        L.or_ratio_transmittance.restype = ctypes.c_double
-        L.or_render_pixels.argtypes = [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Medium),
-                                       ctypes.c_int32, ctypes.c_uint64, vp, ctypes.c_int64, vp]
-        if hasattr(L, "or_mlp_forward"):
-            _bind_mlp(L)
-        _lib = L
+        _lib = _bind(ctypes.CDLL(LIB))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Bind every wrapper of this module to another build of the oracle's
+    sources for the duration of the block (the pin tests load a copy with a
+    deliberately planted mistake this way, to show that a pin catches it)."""
+    global _lib
+    saved = _lib
+    _lib = _bind(ctypes.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = saved
+
+
+def _bind(L):
+    vp = ctypes.c_void_p
+    L.or_philox4x32_10.argtypes = [vp, vp, vp]
+    L.or_u01.argtypes = [ctypes.c_uint32]
+    L.or_u01.restype = ctypes.c_double
+    L.or_background_bits.argtypes = [vp, ctypes.c_int64]
+    L.or_background_bits.restype = ctypes.c_uint32
+    L.or_brick_grid.argtypes = [vp, vp]
+    L.or_brick_ranges.argtypes = [vp, vp, vp, vp]
+    L.or_brick_scores.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, vp, vp]
+    L.or_brick_budget.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int]
+    L.or_brick_budget.restype = ctypes.c_int64
+    L.or_select.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
+    L.or_select.restype = ctypes.c_int64
+    L.or_decode_dense.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_int, vp]
+    L.or_round_fp16.argtypes = [ctypes.c_float]
+    L.or_round_fp16.restype = ctypes.c_float
+    L.or_round_e4m3.argtypes = [ctypes.c_float]
+    L.or_round_e4m3.restype = ctypes.c_float
+    L.or_quantize_leaf.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    L.or_tree_build.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_int]
+    L.or_tree_build.restype = vp
+    L.or_tree_value.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+    L.or_tree_value.restype = ctypes.c_float
+    L.or_tree_counts.argtypes = [vp, vp]
+    L.or_tree_free.argtypes = [vp]
+    L.or_trilinear.argtypes = [vp, vp, vp]
+    L.or_trilinear.restype = ctypes.c_double
+    L.or_macrocell_minmax.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
+    L.or_clip_box.argtypes = [vp, vp, vp, vp, vp]
+    L.or_clip_box.restype = ctypes.c_int
+    L.or_dda_cells.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_double, ctypes.c_double,
+                               vp, vp, vp, ctypes.c_int64]
+    L.or_dda_cells.restype = ctypes.c_int64
+    L.or_hg_eval.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_hg_eval.restype = ctypes.c_double
+    L.or_hg_sample_mu.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_hg_sample_mu.restype = ctypes.c_double
+    L.or_onb.argtypes = [vp, vp, vp]
+    L.or_scatter_dir.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp]
+    L.or_camera_ray.argtypes = [ctypes.POINTER(Camera), vp, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_double, ctypes.c_double, vp, vp]
+    L.or_ratio_transmittance.argtypes = [vp, vp, vp, ctypes.POINTER(Medium), vp, vp,
+                                         ctypes.c_uint32, ctypes.c_uint32, vp, vp]
+    L.or_ratio_transmittance.restype = ctypes.c_double
+    L.or_render_pixels.argtypes = [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Medium),
+                                   ctypes.c_int32, ctypes.c_uint64, vp, ctypes.c_int64, vp]
+    if hasattr(L, "or_mlp_forward"):
+        _bind_mlp(L)
+    return L
 
 
 def _bind_mlp(L):
@@ -335,6 +362,14 @@ def clip_box(dims, o, d):
     tout = ctypes.c_double()
     hit = lib().or_clip_box(_p(dd), _p(oo), _p(di), ctypes.byref(tin), ctypes.byref(tout))
     return bool(hit), tin.value, tout.value
+
+
+def scatter_dir(dirn, mu: float, phi: float) -> np.ndarray:
+    """The direction after scattering from `dirn` at polar cosine mu and azimuth phi (radians)."""
+    d = np.ascontiguousarray(dirn, dtype=np.float64)
+    out = np.zeros(3)
+    lib().or_scatter_dir(_p(d), float(mu), float(phi), _p(out))
+    return out
 
 
 def camera_ray(cam: Camera, dims, px, py, jx=0.5, jy=0.5):

@@ -97,6 +97,7 @@ int64_t or_dda_cells(const int64_t dims[3], int32_t cell, const double o[3], con
 double or_hg_eval(double mu, double g);
 double or_hg_sample_mu(double g, double xi);
 void   or_onb(const double n[3], double b1[3], double b2[3]);
+void   or_scatter_dir(const double dir[3], double mu, double phi, double out[3]);
 void   or_camera_ray(const or_camera* cam, const int64_t dims[3], int64_t px, int64_t py,
                      double jx, double jy, double o[3], double dir[3]);
 double or_ratio_transmittance(const float* d, const int64_t dims[3], const float* cell_max,

@@ -202,6 +202,21 @@ void or_onb(const double n[3], double b1[3], double b2[3])
     b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
 }
 
+/* Direction after a scattering event (Section 4: the path goes on in a
+ * direction drawn from the phase function around the incoming one): the
+ * polar cosine mu is measured from the incoming direction `dir`, the azimuth
+ * phi (radians) turns about it in the plane of the basis (b1, b2) of or_onb.
+ * out = sin(theta) cos(phi) b1 + sin(theta) sin(phi) b2 + mu dir, normalized. */
+void or_scatter_dir(const double dir[3], double mu, double phi, double out[3])
+{
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double b1[3], b2[3];
+    or_onb(dir, b1, b2);
+    for (int a = 0; a < 3; ++a) out[a] = st * cos(phi) * b1[a] + st * sin(phi) * b2[a] + mu * dir[a];
+    double l = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+    for (int a = 0; a < 3; ++a) out[a] /= l;
+}
+
 /* ---- camera ------------------------------------------------------------- */
 static void normalize3(double v[3])
 {
@@ -482,13 +497,9 @@ static void pt_path(const walk_ctx* w, const or_camera* cam, int64_t px, int64_t
         if (bounce + 1 == m->max_bounces) return;
         /* scatter: new direction from the phase function around dir */
         double mu = or_hg_sample_mu(m->g, xi[0]);
-        double st = sqrt(fmax(0.0, 1.0 - mu * mu));
         double phi = 2.0 * M_PI * xi[1];
-        double b1[3], b2[3];
-        or_onb(dir, b1, b2);
         double nd[3];
-        for (int a = 0; a < 3; ++a) nd[a] = st * cos(phi) * b1[a] + st * sin(phi) * b2[a] + mu * dir[a];
-        normalize3(nd);
+        or_scatter_dir(dir, mu, phi, nd);
         for (int a = 0; a < 3; ++a) { o[a] = x[a]; dir[a] = nd[a]; }
         if (!or_clip_box(w->dims, o, dir, &tin, &tout)) {
             for (int c = 0; c < 3; ++c) L[c] += beta * m->env_rad[c];
