@@ -26,6 +26,17 @@
  *    waiting; calls that return host results wait for it, polling with a
  *    wall-clock limit (VDBC_TIMEOUT_MS, default 600000 ms) after which they
  *    return VDBC_ERR_TIMEOUT.
+ *  - After VDBC_ERR_TIMEOUT the call's GPU work is still queued on `stream`
+ *    and may still read the call's inputs and write its outputs.  The
+ *    library frees nothing that work uses: a handle the call would have
+ *    returned (a grid, a batch) is not returned, and its memory is released
+ *    once the work has finished (at the entry of a later call of this
+ *    library).  The caller must keep every buffer it passed (host or device)
+ *    and every handle it passed valid, and must not free those handles,
+ *    until `stream` has been synchronized (cudaStreamSynchronize, or
+ *    cudaStreamQuery returning cudaSuccess).  Once it has, the handles are
+ *    usable as before and an output buffer holds what the call would have
+ *    given.
  *  - Device kernels bound every loop; a path or lookup that exceeds its bound
  *    sets a device error word, which the next host-synchronizing call of the
  *    same handle reports as VDBC_ERR_DEVICE_FLAG.
@@ -294,9 +305,15 @@ vdbc_status vdbc_volume_render_stats_get(const vdbc_volume* vol, void* stream,
  * a device looks up the array's device address; make that call before any
  * stream capture.  Every call reuses the same array, so calls whose GPU work
  * overlaps (different streams, or unordered threads) race: serialize them.
+ * The caller guarantees the outputs' lengths (active_out: one byte per 32^3
+ * brick, ceil(nx/32) * ceil(ny/32) * ceil(nz/32)); the call checks that the
+ * volume and every output are device (or managed) memory, aligned for their
+ * element types.
  * Errors: INVALID_ARG for null pointers, a host volume, dims outside 1..8192,
- * bad ratio/metric/payload, or more than 65,536 bricks (the array's limit,
- * e.g. a 1024 x 1024 x 2048 volume); CUDA.
+ * bad ratio/metric/payload, more than 65,536 bricks (the array's limit:
+ * 1024 x 1024 x 2048 voxels is exactly 65,536 and accepted, one more brick
+ * along any axis is refused), or an input or output that is not device
+ * memory or is misaligned; CUDA.
  */
 vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vdbc_encode_params* params,
                                        uint32_t* background_bits_out, uint8_t* active_out,

@@ -449,7 +449,22 @@ def vdbc_batch_stats_get(batch: Batch, stream=None) -> RenderStats:
 def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, counts_out, metric=F2, payload=FP32,
                                stream=None):
     """Brick selection of vdbc_encode without allocating (device tensors in
-    and out; see include/vdbc.h for who needs it and its limits)."""
+    and out; see include/vdbc.h for who needs it and its limits).  The
+    outputs must be CUDA tensors: one uint32 (or int32) word, one uint8 per
+    32^3 brick and three int64."""
+    dims = [int(x) for x in vol.shape[::-1]]
+    nb = 1
+    for n in dims:
+        nb *= (n + 31) // 32
+    for name, t, dtypes, need in (("background_bits_out", background_bits_out, ("torch.uint32", "torch.int32"), 1),
+                                  ("active_out", active_out, ("torch.uint8",), nb),
+                                  ("counts_out", counts_out, ("torch.int64",), 3)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if str(t.dtype) not in dtypes:
+            raise TypeError("%s must have dtype %s, not %s" % (name, " or ".join(dtypes), t.dtype))
+        if not t.is_contiguous() or t.numel() < need:
+            raise ValueError("%s must be contiguous with at least %d elements (has %d)" % (name, need, t.numel()))
     d = make_dense(vol)
     p = EncodeParams(float(ratio), int(metric), int(payload), 8, 0)
     _check(lib().vdbc_select_bricks_noalloc(ctypes.byref(d), ctypes.byref(p), _ptr(background_bits_out)[0],

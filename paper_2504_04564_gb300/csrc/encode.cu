@@ -1395,7 +1395,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     g->active.resize(nb);
     VDBC_CUDA(cudaMemcpyAsync(g->active.data(), active, nb, cudaMemcpyDeviceToHost, s));
     vdbc_status ws = wait_stream(s);
-    if (ws != VDBC_OK) { delete g; return ws; }
+    if (ws != VDBC_OK) return release_or_defer(ws, s, [g] { delete g; });   // g->active is a copy's target
     if (h_bad) {
         delete g;
         return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: the volume holds non-finite values");
@@ -1454,7 +1454,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
         st = build_macrocells(g, s);
     }
     if (st == VDBC_OK) st = checked_flags(g, s);
-    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    if (st != VDBC_OK) return release_or_defer(st, s, [g] { vdbc_grid_free(g); });
     *out = g;
     return VDBC_OK;
 }
@@ -1560,14 +1560,17 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // device address of g_noalloc_scratch, looked up once per device (with that
-// device current) and cached; host code must not use the symbol itself
+// device current) and cached; host code must not use the symbol itself.  The
+// cache is shared by every host thread, so the lookup runs under a lock.
 vdbc_status noalloc_scratch(NoAllocScratch** out)
 {
     constexpr int kMaxDevices = 64;
+    static std::mutex mu;
     static NoAllocScratch* cache[kMaxDevices] = {nullptr};
     int dev = 0;
     VDBC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return set_error(VDBC_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(mu);
     if (!cache[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -1575,6 +1578,24 @@ vdbc_status noalloc_scratch(NoAllocScratch** out)
         cache[dev] = static_cast<NoAllocScratch*>(p);
     }
     *out = cache[dev];
+    return VDBC_OK;
+}
+
+// a caller's pointer that kernels will read or write: device (or managed)
+// memory of any device, aligned for its element type; anything else (a host
+// pointer, an unregistered address) is refused before a kernel could touch it
+vdbc_status check_device_pointer(const void* p, size_t align, const char* what)
+{
+    if (reinterpret_cast<uintptr_t>(p) % align != 0)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: %s is not %zu-byte aligned", what, align);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e, "cudaPointerGetAttributes");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_select_bricks_noalloc: %s is not device memory", what);
     return VDBC_OK;
 }
 
@@ -1626,6 +1647,12 @@ extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vd
         return set_error(VDBC_ERR_INVALID_ARG,
                          "vdbc_select_bricks_noalloc: %lld bricks of 32^3 exceed the fixed scratch limit of %lld",
                          nb, kNoAllocMaxBricks);
+    // the outputs' lengths (1 word, nb bytes, 3 words) are the caller's to
+    // guarantee; their kind and alignment are checked here
+    VDBC_TRY(check_device_pointer(in->data, 4, "the volume"));
+    VDBC_TRY(check_device_pointer(background_bits_out, 4, "background_bits_out"));
+    VDBC_TRY(check_device_pointer(active_out, 1, "active_out"));
+    VDBC_TRY(check_device_pointer(counts_out, 8, "counts_out"));
     NoAllocScratch* sc = nullptr;
     VDBC_TRY(noalloc_scratch(&sc));
     cudaStream_t s = static_cast<cudaStream_t>(stream);

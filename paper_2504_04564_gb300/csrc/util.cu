@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -33,7 +35,73 @@ vdbc_status set_error(vdbc_status s, const char* fmt, ...)
     return s;
 }
 
-void clear_error() { g_last_error.clear(); }
+// ---- releases held back by timeouts: a call whose bounded wait ran out
+// returns VDBC_ERR_TIMEOUT with its GPU work still queued, so whatever that
+// work reads or writes must outlive it.  Such a call hands the release of what
+// it created to defer_release: an event is recorded on the stream behind the
+// queued work, and the release runs at the entry of a later API call once the
+// event has completed (never on the timeout path itself, which therefore
+// never blocks in cudaFree either).
+struct Deferred {
+    cudaEvent_t done;
+    std::function<void()> release;
+};
+static std::mutex g_deferred_mu;
+static std::vector<Deferred> g_deferred;
+static std::atomic<int> g_deferred_n{0};
+static thread_local bool g_in_release = false;
+
+void defer_release(cudaStream_t s, std::function<void()> release)
+{
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, s) != cudaSuccess) {
+        // the stream cannot be tracked: keep the objects for the life of the
+        // process rather than free memory that queued work may still use
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_deferred_mu);
+    g_deferred.push_back(Deferred{ev, std::move(release)});
+    g_deferred_n.store((int)g_deferred.size());
+}
+
+int run_ready_releases()
+{
+    if (g_deferred_n.load() == 0 || g_in_release) return 0;
+    std::vector<Deferred> ready;
+    {
+        std::lock_guard<std::mutex> lock(g_deferred_mu);
+        for (size_t i = 0; i < g_deferred.size();) {
+            cudaError_t q = cudaEventQuery(g_deferred[i].done);
+            if (q == cudaErrorNotReady) { ++i; continue; }
+            cudaGetLastError();
+            ready.push_back(std::move(g_deferred[i]));
+            g_deferred.erase(g_deferred.begin() + (long)i);
+        }
+        g_deferred_n.store((int)g_deferred.size());
+    }
+    g_in_release = true;
+    for (Deferred& d : ready) {
+        d.release();
+        cudaEventDestroy(d.done);
+    }
+    g_in_release = false;
+    return (int)ready.size();
+}
+
+vdbc_status release_or_defer(vdbc_status st, cudaStream_t s, std::function<void()> release)
+{
+    if (st == VDBC_ERR_TIMEOUT) defer_release(s, std::move(release));
+    else release();
+    return st;
+}
+
+void clear_error()
+{
+    g_last_error.clear();
+    run_ready_releases();
+}
 
 vdbc_status cuda_status(cudaError_t e, const char* what)
 {
@@ -418,7 +486,12 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
         e = cudaGetLastError();
         if (e != cudaSuccess) { vdbc_grid_free(g); return cuda_status(e, "vdbc_grid_load: validation"); }
     }
-    st = wait_stream(s);     // `host` must outlive the copy
+    st = wait_stream(s);
+    if (st == VDBC_ERR_TIMEOUT) {
+        // the copy from `host` and the validation may still be running
+        auto keep = std::make_shared<std::vector<uint8_t>>(std::move(host));
+        return release_or_defer(st, s, [g, keep] { vdbc_grid_free(g); });
+    }
     unsigned long long nbad = 0;
     if (st == VDBC_OK && validate) {
         e = cudaMemcpy(&nbad, &g->stats->work_next, sizeof(nbad), cudaMemcpyDeviceToHost);

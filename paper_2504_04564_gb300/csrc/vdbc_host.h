@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -48,6 +49,15 @@ void count_launch(int n = 1);
 
 // waits for `s` with a wall-clock limit (VDBC_TIMEOUT_MS, default 600 s)
 vdbc_status wait_stream(cudaStream_t s);
+
+// After VDBC_ERR_TIMEOUT the call's GPU work is still queued on `s`: what it
+// uses must not be freed yet.  defer_release runs `release` once the work
+// queued on `s` so far has finished (checked at the entry of later API calls);
+// release_or_defer runs it now unless `st` is a timeout, and returns `st`.
+void defer_release(cudaStream_t s, std::function<void()> release);
+vdbc_status release_or_defer(vdbc_status st, cudaStream_t s, std::function<void()> release);
+// runs the deferred releases whose work has finished; returns how many ran
+int run_ready_releases();
 
 // CUDA events around the last tracker launch of a stats block (a grid's, a
 // volume's or a batch's): record_kernel_start/stop on the launching stream,

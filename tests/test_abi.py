@@ -169,6 +169,28 @@ def test_null_arguments_rejected_on_every_entry_point(v):
     L.vdbc_batch_free(None)
 
 
+def test_noalloc_size_limit_is_checked_before_device_work(v):
+    """The allocation-free selection's brick limit, argument-only: a
+    1024 x 1024 x 2048 descriptor (exactly 65,536 bricks) passes the size
+    check and only then meets the device checks (which fail here, with no
+    GPU); one more brick along any axis is refused for its size.  No kernel
+    can run on either path: the descriptor's pointer is a dummy."""
+    import numpy as np
+    L = v.lib()
+    dummy = np.zeros(8, dtype=np.int64)
+    ptr = dummy.ctypes.data
+    p = v.EncodeParams(4.0, 2, 0, 8, 0)
+    for dims, refused in (((1024, 1024, 2048), False), ((1025, 1024, 2048), True), ((1024, 1056, 2048), True),
+                          ((1024, 1024, 2049), True)):
+        d = v.Dense()
+        d.dims[0], d.dims[1], d.dims[2] = dims
+        d.on_device = 1
+        d.data = ptr
+        st = L.vdbc_select_bricks_noalloc(ctypes.byref(d), ctypes.byref(p), ptr, ptr, ptr, None)
+        assert st != v.OK
+        assert ("65536" in v.vdbc_last_error()) == refused, (dims, v.vdbc_last_error())
+
+
 def test_header_is_c11_and_a_c_program_links_and_runs(v, tmp_path):
     """include/vdbc.h compiles as C11 with every warning an error, and a C
     program on it links against the library and runs: it renders where a GPU
