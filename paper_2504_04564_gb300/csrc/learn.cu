@@ -1124,7 +1124,7 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     st = build_macrocells(g, s);
     if (st == VDBC_OK) st = checked_flags(g, s);
     if (st == VDBC_OK) st = wait_stream(s);
-    if (st != VDBC_OK) { vdbc_grid_free(g); return st; }
+    if (st != VDBC_OK) return release_or_defer(st, s, [g] { vdbc_grid_free(g); });
     *out = g;
     return VDBC_OK;
 }

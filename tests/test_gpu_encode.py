@@ -108,6 +108,53 @@ def test_macrocell_sizes(env, macrocell, payload):
     check_encoding(env, host, 2.0, payload=payload, macrocell=macrocell)
 
 
+def tie_volume(dims, levels=37):
+    """One non-background voxel per 32^3 brick (two, one of them negative, in
+    every third brick; every fifth brick empty), drawn from `levels` values:
+    thousands of bricks share a few (lo, hi) ranges, so the scores tie at the
+    selection's budget edge and the lower brick index must decide."""
+    nx, ny, nz = dims
+    v = np.zeros((nz, ny, nx), dtype=np.float32)
+    bx, by, bz = (nx + 31) // 32, (ny + 31) // 32, (nz + 31) // 32
+    k, j, i = np.meshgrid(np.arange(bz), np.arange(by), np.arange(bx), indexing="ij")
+    b = (k * by + j) * bx + i
+    lvl = (1 + (i * 7 + j * 3 + k * 5) % levels).astype(np.float32) / levels
+    keep = b % 5 != 0
+    x, y, z = np.minimum(i * 32 + 3, nx - 1), np.minimum(j * 32 + 5, ny - 1), np.minimum(k * 32 + 2, nz - 1)
+    v[z[keep], y[keep], x[keep]] = lvl[keep]
+    neg = keep & (b % 3 == 0)
+    x2, y2 = np.minimum(i * 32 + 17, nx - 1), np.minimum(j * 32 + 9, ny - 1)
+    v[z[neg], y2[neg], x2[neg]] = -lvl[neg] / 2
+    return v
+
+
+@pytest.mark.parametrize("metric", [1, 2, 3])
+@pytest.mark.parametrize("ratio", [10.0, 3.0])
+def test_selection_above_4096_bricks_with_ties(env, metric, ratio):
+    """More than 4096 bricks (4290 here) take the selection's branch that
+    keeps the keys in global memory; with scores tied across hundreds of
+    bricks, the activated set must be the oracle's exactly (Algorithm 1:
+    largest f first, ties to the lower brick index)."""
+    host = tie_volume((4160, 1056, 8))
+    grid, e, D = check_encoding(env, host, ratio, metric=metric, macrocell=16)
+    assert e["lo"].size == 4290
+    f = e["f"][e["active"] == 1]
+    rest = e["f"][(e["active"] == 0) & (e["empty"] == 0)]
+    assert rest.size and f.size and f.min() == rest.max()     # the budget edge falls inside a tie
+
+
+def test_encoder_bit_exact_cloud_above_4096_bricks(env):
+    """The cloud generator at 1040 x 544 x 256 (4488 bricks), made on the
+    device (the generator's host and device builds are bit-identical): B, the
+    activated bricks, every decoded voxel and the macrocells at 1:10."""
+    vg = env["vg"]
+    vol = vg.generate_torch(vg.make_params("cloud", (1040, 544, 256), 0))
+    host = vol.cpu().numpy()
+    del vol
+    grid, e, D = check_encoding(env, host, 10.0, macrocell=64)
+    assert e["lo"].size == 4488 and grid.info.n_active == e["n_active"] > 0
+
+
 def test_degenerate_volumes(env):
     vg = env["vg"]
     # all zero: every brick is empty, only the (background) corners remain -> no leaves
