@@ -475,6 +475,24 @@ vdbc_status vdbc_learn_get_params(const vdbc_grid* grid, float* host_params);
  * ctr: 4*n counters, key: 2 words, out: 4*n words; all host arrays. */
 vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int32_t n);
 
+/* vdbc_compare -- error of one float array against another, summed in FP64
+ * on the device: `count` elements of `stride` floats each, of which the first
+ * `channels` are compared (an RGBA image: stride 4, channels 3; a volume:
+ * stride 1, channels 1).  mse = mean squared difference over the count *
+ * channels values, rmse its root, mean_abs / max_abs the mean and largest
+ * absolute difference, psnr = 10 log10(1 / mse) (peak 1, the convention of
+ * the paper's Table tab:stats; infinite when the arrays are equal), n the
+ * number of values.  a and b are device arrays; the call waits for `stream`
+ * (a fixed summation order: the same result every run).
+ * Errors: INVALID_ARG (null pointers, count < 0, channels outside
+ * 1..stride); OOM; CUDA; TIMEOUT. */
+typedef struct {
+    double mse, rmse, mean_abs, max_abs, psnr;
+    int64_t n;
+} vdbc_error_stats;
+vdbc_status vdbc_compare(const float* a, const float* b, int64_t count, int32_t stride, int32_t channels,
+                         void* stream, vdbc_error_stats* out);
+
 /* number of kernels this library has launched in the process so far (every
  * launch increments it on the host); for counting device work per step */
 uint64_t    vdbc_kernel_launches(void);

@@ -115,6 +115,14 @@ _lib = None
 
 # name -> (restype, argtypes); the exported surface of include/vdbc.h
 _vp = ctypes.c_void_p
+class ErrorStats(ctypes.Structure):
+    _fields_ = [("mse", ctypes.c_double), ("rmse", ctypes.c_double), ("mean_abs", ctypes.c_double),
+                ("max_abs", ctypes.c_double), ("psnr", ctypes.c_double), ("n", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 SIGNATURES = {
     "vdbc_encode": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.POINTER(EncodeParams), _vp, ctypes.POINTER(_vp)]),
     "vdbc_grid_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(GridInfo)]),
@@ -134,6 +142,8 @@ SIGNATURES = {
                                          ctypes.c_uint64, _vp, ctypes.c_int32, _vp]),
     "vdbc_volume_render_stats_get": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RenderStats)]),
     "vdbc_philox": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "vdbc_compare": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _vp,
+                                    ctypes.POINTER(ErrorStats)]),
     "vdbc_select_bricks_noalloc": (ctypes.c_int, [ctypes.POINTER(Dense), ctypes.POINTER(EncodeParams), _vp, _vp,
                                                   _vp, _vp]),
     "vdbc_batch_create": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_int32, ctypes.c_int32, _vp,
@@ -444,6 +454,20 @@ def vdbc_batch_stats_get(batch: Batch, stream=None) -> RenderStats:
     st = RenderStats()
     _check(lib().vdbc_batch_stats_get(batch.handle, _stream(stream), ctypes.byref(st)))
     return st
+
+
+def vdbc_compare(a, b, stride=1, channels=1, stream=None) -> ErrorStats:
+    """FP64 error of device array `a` against `b` (same shape): elements of
+    `stride` floats, the first `channels` of each compared (an RGBA image:
+    stride=4, channels=3)."""
+    if not (a.is_cuda and b.is_cuda) or a.numel() != b.numel() or a.numel() % stride:
+        raise ValueError("vdbc_compare: two CUDA arrays of the same size, a multiple of the stride")
+    if not (a.is_contiguous() and b.is_contiguous()) or str(a.dtype) != "torch.float32" or str(b.dtype) != "torch.float32":
+        raise ValueError("vdbc_compare: contiguous float32 arrays")
+    out = ErrorStats()
+    _check(lib().vdbc_compare(a.data_ptr(), b.data_ptr(), a.numel() // stride, int(stride), int(channels),
+                              _stream(stream), ctypes.byref(out)))
+    return out
 
 
 def vdbc_select_bricks_noalloc(vol, ratio, background_bits_out, active_out, counts_out, metric=F2, payload=FP32,

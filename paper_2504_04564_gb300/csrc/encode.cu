@@ -16,10 +16,12 @@
 //                  shared memory, flushed per brick) + non-finite check
 //   k_argmax       one CTA: most frequent bin, ties to the smaller index
 //   k_pass2        one CTA per brick overlapping the winning bin: lower-16-bit
-//                  histogram inside it
+//                  histogram inside it (a brick of one bit pattern, known
+//                  from its range, is counted without being read)
 //   k_scores       one thread per brick: FP64 f with no contraction
-//   k_select       one CTA: threshold bisection over the FP64 keys (the N-th
-//                  largest), ties by brick index
+//   k_select       one CTA: the N-th largest FP64 key (bisection on keys in
+//                  registers up to 4096 bricks, radix selection by bytes
+//                  above), ties by brick index
 //   k_leaf_status  one warp per candidate leaf: constant? (prune) tile value?
 //   scans (one CTA up to 64K entries), k_fill_* tree tables, k_fill_leaves
 //                  payload copy / quantization
@@ -28,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -119,7 +122,7 @@ struct KeyRun {
 // kMode 0: scalar loads, one voxel a lane, for every other volume.  (Float4
 // loads of misaligned rows, masked to the brick row, measured slower than
 // the scalar loads on the 994-wide cloud: 2.39 against 2.24 ms.)
-template <int kMode>
+template <int kMode, int kRowsInFlight = 8>
 __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict__ v, Dims d, int nbricks,
                                                          uint32_t* __restrict__ lo_key,
                                                          uint32_t* __restrict__ hi_key,
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int U = 8, kWarps = kPass1Threads / 32;
+    constexpr int U = kRowsInFlight, kWarps = kPass1Threads / 32;
     bool bad = false;
     int p = 0;
     for (int b = blockIdx.x; b < nbricks; b += gridDim.x, p ^= 1) {
@@ -183,10 +186,18 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                                                  (w[3] >> 16) == lead);
                     if (__all_sync(0xffffffffu, same)) {
                         run.add(lead, 4u * (uint32_t)__popc(part), lane, s_h);
-                    } else if (ok[q]) {
-                        // the lane's four keys, equal ones merged, one add per distinct key
+                    } else {
+                        // keys equal to the warp's run join it; the lane's other
+                        // keys, equal ones merged, take one add per distinct key
                         const uint32_t k[4] = {w[0] >> 16, w[1] >> 16, w[2] >> 16, w[3] >> 16};
-                        uint32_t n[4] = {1u, 1u, 1u, 1u};
+                        uint32_t n[4], c = 0u;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const bool in = ok[q] && k[j] == run.key;
+                            c += in ? 1u : 0u;
+                            n[j] = (ok[q] && !in) ? 1u : 0u;
+                        }
+                        run.cnt += __reduce_add_sync(0xffffffffu, c);
 #pragma unroll
                         for (int j = 1; j < 4; ++j)
 #pragma unroll
@@ -230,7 +241,13 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                     const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
                     if (__all_sync(0xffffffffu, !valid || key == lead)) {
                         run.add(lead, (uint32_t)__popc(vmask), lane, s_h);
-                    } else if (valid) {
+                        continue;
+                    }
+                    // lanes holding the warp run's key join it; the others keep
+                    // their own runs
+                    const bool inrun = valid && key == run.key;
+                    run.cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, inrun));
+                    if (valid && !inrun) {
                         if (key == lk) {
                             ++ln;
                         } else {
@@ -311,6 +328,13 @@ __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict_
     brick_coords(d, b, bx, by, bz);
     const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
     const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
+    if (lo_key[b] == hi_key[b]) {
+        // every voxel holds one bit pattern (the key order is a bijection on
+        // patterns), and it lies in the bin: count the brick without reading it
+        if (threadIdx.x == 0)
+            atomicAdd(hist + (okey_inv(lo_key[b]) & 0xffffu), (unsigned long long)ex * ey * ez);
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rows = ey * ez;
     const uint32_t mey = div_magic(ey);
@@ -485,13 +509,62 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
         if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
         return;
     }
-    // bisection on the bits of the threshold T: the largest T with #{key >= T} >= take
-    unsigned long long T = 0;
-    for (int bit = 63; bit >= 0; --bit) {
-        const unsigned long long cand = T | (1ull << bit);
-        if (cand <= 0xFFFFFFFFFFFFFFFEull && (long long)count_ge(cand + 1ull) >= take) T = cand;
+    // V = the take-th largest key (+1); gt = #{keys (+1) > V}
+    unsigned long long V = 0;
+    long long gt = 0;
+    if (cached) {
+        // bisection on the bits of the threshold T: the largest T with #{key >= T} >= take
+        unsigned long long T = 0;
+        for (int bit = 63; bit >= 0; --bit) {
+            const unsigned long long cand = T | (1ull << bit);
+            if (cand <= 0xFFFFFFFFFFFFFFFEull && (long long)count_ge(cand + 1ull) >= take) T = cand;
+        }
+        V = T + 1ull;
+        gt = T == 0xFFFFFFFFFFFFFFFFull ? 0 : (long long)count_ge(T + 2ull);
+    } else {
+        // keys in global memory: radix selection from the top byte down, one
+        // pass over the keys per byte (8 instead of 64 bisection passes); a
+        // pass counts the byte of every key whose higher bytes equal the
+        // prefix chosen so far, and keeps the byte at which the count from the
+        // top reaches the rank still wanted
+        __shared__ unsigned s_hist[256];
+        __shared__ unsigned long long s_prefix;
+        __shared__ long long s_rank;
+        unsigned long long prefix = 0, pmask = 0;
+        long long rank = take;
+        const int lane = threadIdx.x & 31;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int i = threadIdx.x; i < 256; i += kSelThreads) s_hist[i] = 0u;
+            __syncthreads();
+            for (int base = 0; base < nb; base += kSelThreads) {
+                const int i = base + threadIdx.x;
+                const unsigned long long k = i < nb ? key1(i) : 0ull;
+                const bool in = k != 0ull && (k & pmask) == prefix;
+                const unsigned digit = in ? (unsigned)(k >> shift) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, digit);
+                if (in && lane == __ffs(peers) - 1) atomicAdd(&s_hist[digit], (unsigned)__popc(peers));
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long above = 0;
+                int d = 255;
+                for (; d > 0; --d) {
+                    if (above + (long long)s_hist[d] >= rank) break;
+                    above += s_hist[d];
+                }
+                s_prefix = prefix | ((unsigned long long)d << shift);
+                s_rank = rank - above;
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            rank = s_rank;
+            pmask |= 255ull << shift;
+            __syncthreads();
+        }
+        V = prefix;
+        gt = take - rank;
     }
-    const long long gt = T == 0xFFFFFFFFFFFFFFFFull ? 0 : (long long)count_ge(T + 2ull);
+    const unsigned long long T = V - 1ull;
     const long long need = take - gt;   // keys equal to T, lowest brick indices first
     if (threadIdx.x == 0) s_run = 0;
     __syncthreads();
@@ -1085,8 +1158,11 @@ bool rows_aligned(const float* v, const Dims& d)
 void launch_pass1(const float* v, const Dims& d, int nb, unsigned grid, uint32_t* lo_key, uint32_t* hi_key,
                   unsigned long long* hist, int* nonfinite, cudaStream_t s)
 {
+    static const bool rows16 = [] { const char* e = std::getenv("VDBC_PASS1_ROWS"); return e && std::atoi(e) == 16; }();
     if (rows_aligned(v, d))
         KLAUNCH(k_pass1<1><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
+    else if (rows16)
+        KLAUNCH((k_pass1<0, 16><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
     else
         KLAUNCH(k_pass1<0><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
 }
@@ -1105,6 +1181,7 @@ vdbc_status pass1_setup(int nbricks, unsigned* grid)
         if (e.first == dev) resident = e.second;
     if (resident == 0) {
         VDBC_CUDA(cudaFuncSetAttribute(k_pass1<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
         VDBC_CUDA(cudaFuncSetAttribute(k_pass1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
         int per_sm = 0, sms = 0;
         VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass1<0>, kPass1Threads, kPass1Smem));

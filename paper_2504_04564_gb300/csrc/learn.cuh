@@ -171,16 +171,8 @@ struct LearnedSampler {
     // leaf from meta (raw) or nmeta (neural)
     __device__ __forceinline__ uint32_t leaf(Accessor& a, int li, int lj, int lk) const
     {
-#ifdef VDBC_STATS
-        ++a.queries;
-        if (li != a.li || lj != a.lj || lk != a.lk) ++a.descents;
-#endif
-        if (li != a.li || lj != a.lj || lk != a.lk) {
-            a.li = li; a.lj = lj; a.lk = lk;
-            a.entry = descend_to_leaf(g, li, lj, lk);
-            if (!(a.entry & kTile))
-                a.sm = (a.entry & kNeural) ? __ldg(g.nmeta + (a.entry & ~kNeural)) : __ldg(g.meta + a.entry);
-        }
+        if (a.find(g, li, lj, lk) && !(a.entry & kTile))
+            a.sm = (a.entry & kNeural) ? __ldg(g.nmeta + (a.entry & ~kNeural)) : __ldg(g.meta + a.entry);
         return a.entry;
     }
 

@@ -13,9 +13,11 @@
 //         et al. 2011 that Section 4 cites), Henyey-Greenstein scattering, the
 //         directional light's transmittance by ratio tracking, a constant
 //         environment on escape.  Persistent lanes each carry one path and
-//         fetch the next when it ends; path radiance is averaged per pixel in
-//         sample order by k_pt_reduce.  k_pt_batch runs the same loop over
-//         many jobs (grids, cameras, media) in one launch.
+//         fetch the next when it ends; a finished path adds its radiance to
+//         its pixel's sums in 32.32 fixed point (integer adds: the sums do
+//         not depend on the order the paths finish in), and k_pt_resolve
+//         turns the sums into the per-pixel mean.  k_pt_batch runs the same
+//         loop over many jobs (grids, cameras, media) in one launch.
 // All are templated on the sampler: VdbSamplerT<payload> (tree descent + leaf
 // decode + trilinear, every lookup), LearnedSampler (the same, with neural
 // leaves decoded by the network in warp-wide tensor-core tiles), LinearSampler
@@ -295,10 +297,21 @@ __device__ __forceinline__ void flush_stats(DevStats* st, const Walk& w, unsigne
 // lookups together.  Random-number use per path is the oracle's: the camera
 // takes call 0 of stream 0, each tentative step of the walk the next call of
 // stream 0, each tentative step of a light ray the next call of stream 1.
-// Path radiance goes to path_out[sample * npix + pixel]; k_pt_reduce averages
-// the samples of every pixel in sample order (deterministic).
+// A finished path adds its radiance to accum[3 * pixel + c] as a 32.32
+// fixed-point integer (fix32 below): integer addition is associative, so the
+// frame's sums are the same bits whatever order the paths finish in, and no
+// per-path buffer is needed.
 
 enum : int { kNeed = 0, kDone = 1, kDelta = 2, kRatio = 3 };
+
+// radiance (>= 0) as a 32.32 fixed-point integer, rounded to nearest: exact
+// for values of 2^-8 and above, within 2^-33 below; a frame's per-pixel sum
+// stays far below 2^64 (radiance < 2^31 per path, clamped, times spp < 2^31)
+__device__ __forceinline__ unsigned long long fix32(float x)
+{
+    x = fminf(fmaxf(x, 0.0f), 2147483648.0f);      // (a NaN becomes 0)
+    return __float2ull_rn(__fmul_rn(x, 4294967296.0f));
+}
 
 struct Track {
     Dda dda;
@@ -365,7 +378,7 @@ struct JobView {
     const uint32_t* bits;      // occupancy bit per macrocell (majorant > 0)
     const uint32_t* cbits;     // occupancy bit per kCoarse^3 block of macrocells
     int cx_n, cy_n;            // coarse grid size along x and y
-    float4* path_out;          // spp x npix path radiances of the frame
+    unsigned long long* accum; // 3 per pixel: the frame's radiance sums, 32.32 fixed point
     int npix, spp, tiles_x;
     uint32_t k0, k1;           // Philox key = the seed
     uint32_t sample_base;      // sample id of the frame's first sample (progressive frames)
@@ -637,7 +650,10 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 }
             }
             if (finished) {
-                J.path_out[(size_t)sample * J.npix + pixel] = make_float4(L.x, L.y, L.z, 1.0f);
+                unsigned long long* a = J.accum + 3 * (size_t)pixel;
+                atomicAdd(a + 0, fix32(L.x));
+                atomicAdd(a + 1, fix32(L.y));
+                atomicAdd(a + 2, fix32(L.z));
                 ++paths;
                 mode = kNeed;
             }
@@ -719,33 +735,34 @@ __global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads
     pt_loop<kUseCoarse>(src, nitems, st, chunk, stride);
 }
 
-// average of the spp path radiances of each pixel, in sample order
-__global__ void k_pt_reduce(const float4* __restrict__ path_out, int npix, int spp, float4* __restrict__ out)
+// a pixel's fixed-point sum as a float (2^-32 times the integer, rounded once)
+__device__ __forceinline__ float unfix32(unsigned long long a)
+{
+    return __fmul_rn(__ull2float_rn(a), 2.3283064365386963e-10f);
+}
+
+// the per-pixel mean of the frame's spp path radiances
+__global__ void k_pt_resolve(const unsigned long long* __restrict__ accum, int npix, int spp,
+                             float4* __restrict__ out)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    float r = 0.f, g = 0.f, b = 0.f;
-    for (int s = 0; s < spp; ++s) {
-        float4 v = path_out[(size_t)s * npix + p];
-        r += v.x; g += v.y; b += v.z;
-    }
-    float inv = 1.0f / (float)spp;
-    out[p] = make_float4(r * inv, g * inv, b * inv, 1.0f);
+    // the batch's first frame computes the same expression (equal bits)
+    const float inv = 1.0f / (float)spp;
+    const unsigned long long* a = accum + 3 * (size_t)p;
+    out[p] = make_float4(unfix32(a[0]) * inv, unfix32(a[1]) * inv, unfix32(a[2]) * inv, 1.0f);
 }
 
-// batch accumulation: per job (blockIdx.y) and pixel, add this frame's spp
-// path radiances (in sample order) to the running sum and write the mean
+// batch accumulation: per job (blockIdx.y) and pixel, add this frame's
+// radiance sums to the running sum and write the mean
 __global__ void k_batch_reduce(const JobView* __restrict__ jobs, float4* const* __restrict__ sums,
                                float* const* __restrict__ outs, const int* __restrict__ frame)
 {
     const JobView& J = jobs[blockIdx.y];
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= J.npix) return;
-    float r = 0.f, g = 0.f, b = 0.f;
-    for (int s = 0; s < J.spp; ++s) {
-        float4 v = J.path_out[(size_t)s * J.npix + p];
-        r += v.x; g += v.y; b += v.z;
-    }
+    const unsigned long long* a = J.accum + 3 * (size_t)p;
+    float r = unfix32(a[0]), g = unfix32(a[1]), b = unfix32(a[2]);
     float4 acc = sums[blockIdx.y][p];
     acc.x += r; acc.y += g; acc.z += b;
     sums[blockIdx.y][p] = acc;
@@ -1181,7 +1198,7 @@ constexpr size_t kSmemBitsMax = 96 * 1024;
 
 // the job's constants for the tracker (bits are filled in by the caller)
 JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int spp, uint64_t seed,
-                 float4* path_out)
+                 unsigned long long* accum)
 {
     JobView j;
     std::memset(&j, 0, sizeof(j));
@@ -1190,7 +1207,7 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     j.med = med;
     j.cx_n = (mj.mx + kCoarse - 1) / kCoarse;
     j.cy_n = (mj.my + kCoarse - 1) / kCoarse;
-    j.path_out = path_out;
+    j.accum = accum;
     j.npix = cam.w * cam.h;
     j.spp = spp;
     j.tiles_x = (cam.w + 7) / 8;
@@ -1263,10 +1280,11 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     int cxn = (mj.mx + kCoarse - 1) / kCoarse, cyn = (mj.my + kCoarse - 1) / kCoarse, czn = (mj.mz + kCoarse - 1) / kCoarse;
     int ncwords = (cxn * cyn * czn + 31) / 32;
     uint32_t* bits = nullptr;
-    float4* path_out = nullptr;
+    unsigned long long* accum = nullptr;
     VDBC_TRY(dev_alloc(reinterpret_cast<void**>(&bits), (size_t)(nwords + ncwords) * 4, s));
-    vdbc_status st = dev_alloc(reinterpret_cast<void**>(&path_out), (size_t)spp * npix * sizeof(float4), s);
+    vdbc_status st = dev_alloc(reinterpret_cast<void**>(&accum), (size_t)npix * 3 * sizeof(unsigned long long), s);
     if (st != VDBC_OK) { dev_free(bits, s); return st; }
+    VDBC_CUDA(cudaMemsetAsync(accum, 0, (size_t)npix * 3 * sizeof(unsigned long long), s));
     KLAUNCH(k_occupancy<<<blocks_for(ncell, 256), 256, 0, s>>>(mj.mcmax, ncell, med.sigma_scale, bits));
     const bool coarse = !S::kCollective && coarse_skipping(mj.mc);
     if (coarse) {
@@ -1275,16 +1293,16 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     } else {
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
-    JobView job = make_job(mj, cam, med, spp, seed, path_out);
+    JobView job = make_job(mj, cam, med, spp, seed, accum);
     record_kernel_start(stats, s);
     st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, 0, coarse, s);
     record_kernel_stop(stats, s);
     if (st == VDBC_OK) {
-        KLAUNCH(k_pt_reduce<<<blocks_for(npix, 256), 256, 0, s>>>(path_out, (int)npix, spp, out));
+        KLAUNCH(k_pt_resolve<<<blocks_for(npix, 256), 256, 0, s>>>(accum, (int)npix, spp, out));
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) st = cuda_status(e, "k_pt_reduce");
+        if (e != cudaSuccess) st = cuda_status(e, "k_pt_resolve");
     }
-    dev_free(path_out, s);
+    dev_free(accum, s);
     dev_free(bits, s);
     return st;
 }
@@ -1373,6 +1391,18 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
     if (g.payload == VDBC_FP8)
         return render_common(VdbSamplerT<2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                              out_on_device, stream);
+    // VDBC_PT_LOOKUP = <depth><straddle> picks another accessor depth (1, 2) and
+    // straddle mode (1, 2) for FP32 grids, for measuring them against each other
+    const char* lk = std::getenv("VDBC_PT_LOOKUP");
+    if (lk && std::strcmp(lk, "22") == 0)
+        return render_common(VdbSamplerT<0, 2, 2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+                             rgba_out, out_on_device, stream);
+    if (lk && std::strcmp(lk, "12") == 0)
+        return render_common(VdbSamplerT<0, 1, 2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+                             rgba_out, out_on_device, stream);
+    if (lk && std::strcmp(lk, "21") == 0)
+        return render_common(VdbSamplerT<0, 2, 1>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+                             rgba_out, out_on_device, stream);
     return render_common(VdbSamplerT<0>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                          out_on_device, stream);
 }
@@ -1585,7 +1615,8 @@ struct vdbc_batch {
     std::vector<vdbc::JobView> h_jobs;
     std::vector<uint32_t*> bits_on, bits_off;   // per job: fine + coarse words, coarse skipping on / off
     std::vector<int> nwords;
-    float4* path_out = nullptr;
+    unsigned long long* accum = nullptr;    // the frame's fixed-point radiance sums, 3 per pixel of every job
+    size_t accum_words = 0;
     float4* sums = nullptr;
     float4** d_sums = nullptr;
     float** d_outs = nullptr;
@@ -1699,6 +1730,7 @@ vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStrea
 vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cudaStream_t s, unsigned stride = 1)
 {
     for (BatchGroup& g : b->groups) VDBC_CUDA(cudaMemsetAsync(g.stats, 0, sizeof(DevStats), s));
+    VDBC_CUDA(cudaMemsetAsync(b->accum, 0, b->accum_words * sizeof(unsigned long long), s));
     if (t.threads == 128) {
         if (t.coarse) VDBC_TRY((batch_launch_pt<128, true>(b, t.chunk, stride, s)));
         else VDBC_TRY((batch_launch_pt<128, false>(b, t.chunk, stride, s)));
@@ -1826,7 +1858,7 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     if (n < 1 || n > 64) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_batch_create: %d jobs outside 1..64", n);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     vdbc_batch* b = new vdbc_batch();
-    auto fail = [&](vdbc_status st) { vdbc_batch_free(b); return st; };
+    auto fail = [&](vdbc_status st) { return release_or_defer(st, s, [b] { vdbc_batch_free(b); }); };
     b->n = n;
     b->jobs.assign(jobs, jobs + n);
     b->h_jobs.resize(n);
@@ -1837,7 +1869,7 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     std::vector<float4*> sum_ptrs(n);
     std::vector<float*> outs(n);
     unsigned long long items = 0;
-    size_t path_floats4 = 0, sum_floats4 = 0;
+    size_t accum_pixels = 0, sum_floats4 = 0;
     for (int i = 0; i < n; ++i) {
         const vdbc_job& j = jobs[i];
         if (!j.grid || !j.rgba_out) return fail(set_error(VDBC_ERR_INVALID_ARG, "job %d: null grid or output", i));
@@ -1855,7 +1887,7 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
         JobView jv = make_job(mj, cam, mh.dev, j.spp, j.seed, nullptr);
         jv.item_begin = items;
         items += jv.items;
-        path_floats4 += (size_t)j.spp * jv.npix;
+        accum_pixels += (size_t)jv.npix;
         sum_floats4 += (size_t)jv.npix;
         b->max_npix = std::max<size_t>(b->max_npix, (size_t)jv.npix);
         b->h_jobs[i] = jv;
@@ -1874,7 +1906,8 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
             }
         if (!g.members.empty()) b->groups.push_back(std::move(g));
     }
-    vdbc_status st = batch_alloc(b, reinterpret_cast<void**>(&b->path_out), path_floats4 * sizeof(float4));
+    b->accum_words = accum_pixels * 3;
+    vdbc_status st = batch_alloc(b, reinterpret_cast<void**>(&b->accum), b->accum_words * sizeof(unsigned long long));
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->sums), sum_floats4 * sizeof(float4));
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_jobs), sizeof(JobView) * n);
     if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&b->d_sums), sizeof(float4*) * n);
@@ -1899,8 +1932,8 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     size_t po = 0, so = 0;
     for (int i = 0; i < n; ++i) {
         JobView& jv = b->h_jobs[i];
-        jv.path_out = b->path_out + po;
-        po += (size_t)jv.spp * jv.npix;
+        jv.accum = b->accum + po;
+        po += 3 * (size_t)jv.npix;
         sum_ptrs[i] = b->sums + so;
         so += (size_t)jv.npix;
         // occupancy bits, once with coarse skipping and once without
@@ -1930,7 +1963,7 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(b->sums, 0, sum_floats4 * sizeof(float4), s);
     if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create upload"));
     st = batch_select_bits(b, true, s);
-    if (st == VDBC_OK) st = wait_stream(s);      // host vectors above must outlive their copies
+    if (st == VDBC_OK) st = wait_stream(s);      // (pageable host sources: the copies staged them already)
     if (st == VDBC_OK && autotune) st = batch_autotune(b, s);
     if (st == VDBC_OK) st = vdbc_batch_reset(b, stream);
     if (st == VDBC_OK) st = batch_capture(b, s);

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -296,6 +297,90 @@ extern "C" vdbc_status vdbc_philox(const uint32_t* ctr, const uint32_t key[2], u
     cudaFree(dc);
     cudaFree(dout);
     if (e != cudaSuccess) return cuda_status(e, "vdbc_philox");
+    return VDBC_OK;
+}
+
+// ---------------------------------------------------------------- FP64 error of one array against another
+// The image and volume error measures (MSE, PSNR with peak 1 as in the
+// paper's Table tab:stats, mean and largest absolute difference) in FP64 on
+// the device: each block sums a grid-stride share of the elements, the last
+// kernel adds the blocks' partials in block order (the same bits every run).
+namespace {
+constexpr int kCmpThreads = 256, kCmpBlocks = 152 * 4;
+
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* s)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { s[3 * w] = a; s[3 * w + 1] = b; s[3 * w + 2] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { a += s[3 * q]; b += s[3 * q + 1]; c = fmax(c, s[3 * q + 2]); }
+    }
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_compare(const float* __restrict__ x, const float* __restrict__ y,
+                                                         long long count, int stride, int channels,
+                                                         double* __restrict__ part)
+{
+    __shared__ double s[3 * (kCmpThreads / 32)];
+    double sq = 0.0, ab = 0.0, mx = 0.0;
+    const long long n = count * channels;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long e = i / channels, c = i - e * channels;
+        const double d = (double)x[e * stride + c] - (double)y[e * stride + c];
+        sq = fma(d, d, sq);
+        ab += fabs(d);
+        mx = fmax(mx, fabs(d));
+    }
+    block_sum3(sq, ab, mx, s);
+    if (threadIdx.x == 0) { part[3 * blockIdx.x] = sq; part[3 * blockIdx.x + 1] = ab; part[3 * blockIdx.x + 2] = mx; }
+}
+
+__global__ void k_compare_total(const double* __restrict__ part, int nparts, double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sq = 0.0, ab = 0.0, mx = 0.0;
+    for (int q = 0; q < nparts; ++q) { sq += part[3 * q]; ab += part[3 * q + 1]; mx = fmax(mx, part[3 * q + 2]); }
+    out[0] = sq; out[1] = ab; out[2] = mx;
+}
+}  // namespace
+
+extern "C" vdbc_status vdbc_compare(const float* a, const float* b, int64_t count, int32_t stride, int32_t channels,
+                                    void* stream, vdbc_error_stats* out)
+{
+    clear_error();
+    if (!a || !b || !out) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_compare: null argument");
+    if (count < 0 || stride < 1 || channels < 1 || channels > stride)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_compare: count %lld, stride %d, channels %d", (long long)count,
+                         stride, channels);
+    std::memset(out, 0, sizeof(*out));
+    out->n = count * channels;
+    if (count == 0) return VDBC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)count * channels;
+    const int blocks = (int)std::min<long long>((n + kCmpThreads - 1) / kCmpThreads, kCmpBlocks);
+    void* buf = nullptr;
+    VDBC_TRY(dev_alloc(&buf, (size_t)(3 * blocks + 3) * sizeof(double), s));
+    double* part = static_cast<double*>(buf);
+    KLAUNCH(k_compare<<<blocks, kCmpThreads, 0, s>>>(a, b, count, stride, channels, part));
+    KLAUNCH(k_compare_total<<<1, 32, 0, s>>>(part, blocks, part + 3 * blocks));
+    double h[3] = {0, 0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, part + 3 * blocks, sizeof(h), cudaMemcpyDeviceToHost, s);
+    vdbc_status st = e == cudaSuccess ? VDBC_OK : cuda_status(e, "vdbc_compare");
+    if (st == VDBC_OK) st = wait_stream(s);
+    dev_free(buf, s);
+    if (st != VDBC_OK) return st;
+    out->mse = h[0] / (double)n;
+    out->rmse = std::sqrt(out->mse);
+    out->mean_abs = h[1] / (double)n;
+    out->max_abs = h[2];
+    out->psnr = out->mse > 0.0 ? 10.0 * std::log10(1.0 / out->mse) : INFINITY;
     return VDBC_OK;
 }
 

@@ -143,10 +143,10 @@ __device__ __forceinline__ bool entry_in_range(const GridView& g, uint32_t e)
 }
 #endif
 
-// entry of the lower level that covers voxel-leaf (li,lj,lk) = (i>>3, j>>3, k>>3);
-// inlined at every call (the same descent out of line cost the tracker 17.6
-// against 16.1 ms on the benchmark frame)
-__device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, int lj, int lk)
+// entry of the upper level that covers the lower node of voxel-leaf
+// (li,lj,lk) = (i>>3, j>>3, k>>3): the lower node's index, or a tile entry
+// (bit 31) when the node's whole 128^3 region is one value
+__device__ __forceinline__ uint32_t descend_to_node(const GridView& g, int li, int lj, int lk)
 {
     int i = li << 3, j = lj << 3, k = lk << 3;
 #if VDBC_CHECKED
@@ -156,49 +156,106 @@ __device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, i
     if (e >= g.n_upper) return bounds_violation(g);
     e = __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
     if (e & kTile) return entry_in_range(g, e) ? e : bounds_violation(g);
-    if (e >= g.n_lower) return bounds_violation(g);
-    e = __ldg(g.lower + (size_t)e * kLowerN + (((k >> 3) & 15) << 8) + (((j >> 3) & 15) << 4) + ((i >> 3) & 15));
-    return entry_in_range(g, e) ? e : bounds_violation(g);
+    return e < g.n_lower ? e : bounds_violation(g);
 #else
     uint32_t e = __ldg(g.root + ((k >> 12) * g.ry + (j >> 12)) * g.rx + (i >> 12));
     if (e & kTile) return e;
-    e = __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
-    if (e & kTile) return e;
-    return __ldg(g.lower + (size_t)e * kLowerN + (((k >> 3) & 15) << 8) + (((j >> 3) & 15) << 4) + ((i >> 3) & 15));
+    return __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
 #endif
 }
 
-// per-thread cached accessor: remembers the last leaf-level entry (Section
-// 3.2.2: NanoVDB's accessors cache the path of the last lookup).  leaf() is
-// for FP32/FP16/FP8 grids; learned grids resolve entries through
-// LearnedSampler::leaf, which knows the neural entries.
-struct Accessor {
-    int li, lj, lk;
-    uint32_t entry;
-    float2 sm;
-#ifdef VDBC_STATS
-    unsigned queries = 0, descents = 0;   // leaf() calls, and those that walked the tree
+// leaf-level entry of voxel-leaf (li,lj,lk) inside the lower node `node`
+// (an entry from descend_to_node)
+__device__ __forceinline__ uint32_t lower_entry(const GridView& g, uint32_t node, int li, int lj, int lk)
+{
+    if (node & kTile) return node;
+    uint32_t e = __ldg(g.lower + (size_t)node * kLowerN + ((lk & 15) << 8) + ((lj & 15) << 4) + (li & 15));
+#if VDBC_CHECKED
+    return entry_in_range(g, e) ? e : bounds_violation(g);
+#else
+    return e;
 #endif
-    __device__ __forceinline__ void reset() { li = -1; lj = -1; lk = -1; entry = kBackgroundEntry; sm = make_float2(0.f, 0.f); }
-    __device__ __forceinline__ uint32_t leaf(const GridView& g, int a, int b, int c)
+}
+
+// entry of the lower level that covers voxel-leaf (li,lj,lk): the whole
+// descent root -> upper -> lower
+__device__ __forceinline__ uint32_t descend_to_leaf(const GridView& g, int li, int lj, int lk)
+{
+    return lower_entry(g, descend_to_node(g, li, lj, lk), li, lj, lk);
+}
+
+// leaf coordinates (each below 1024, since no edge exceeds 8192 voxels)
+// packed ten bits apiece; two keys with equal kNodeBits lie in one lower node
+// (16^3 leaves).  Bit 30 never occurs in a key, so a reset accessor (key with
+// every bit set) matches no leaf and no node.
+__device__ __forceinline__ uint32_t leaf_key(int li, int lj, int lk)
+{
+    return (uint32_t)li | ((uint32_t)lj << 10) | ((uint32_t)lk << 20);
+}
+constexpr uint32_t kNodeBits = 0x3F0u | (0x3F0u << 10) | (0x3F0u << 20) | (1u << 30);
+
+// Accessor cache depth (Section 3.2.2: NanoVDB's accessors cache the path of
+// the last lookup).  1: the last leaf-level entry only, so another leaf costs
+// the whole descent (three dependent loads); 2: also the lower node holding
+// it, so another leaf of the same 128^3 region costs one load.  Depth 1 is
+// the default: the tracker is bound by instruction issue, not by the load
+// latency the deeper cache saves (1024^2 x 16 spp frame of the 512^3 medium:
+// 15.6 ms at depth 1, 16.3 at depth 2; 1920x1080 x 64 spp of the
+// 1987x1351x2449 cloud at 1:10: 67.5 against 70.6 ms).
+#ifndef VDBC_ACC_DEPTH
+#define VDBC_ACC_DEPTH 1
+#endif
+constexpr int kAccDepth = VDBC_ACC_DEPTH;
+
+// per-thread cached accessor.  leaf() is for FP32/FP16/FP8 grids; learned
+// grids resolve entries through LearnedSampler::leaf, which calls find() and
+// knows the neural entries.
+struct Accessor {
+    uint32_t key;        // packed coordinates of the cached leaf (all ones: none)
+    uint32_t entry;      // its leaf-level entry
+    uint32_t node;       // depth 2: the lower node holding it (descend_to_node's answer)
+    float2 sm;           // (scale, offset) of the cached leaf (quantized payloads)
+#ifdef VDBC_STATS
+    unsigned queries = 0, descents = 0;   // leaf queries, and those that changed the cached leaf
+#endif
+    __device__ __forceinline__ void reset()
     {
+        key = 0xffffffffu;
+        entry = kBackgroundEntry;
+        node = kBackgroundEntry;
+        sm = make_float2(0.f, 0.f);
+    }
+    // makes (a,b,c) the cached leaf; true when it was not already
+    template <int D = kAccDepth>
+    __device__ __forceinline__ bool find(const GridView& g, int a, int b, int c)
+    {
+        const uint32_t k = leaf_key(a, b, c);
 #ifdef VDBC_STATS
         ++queries;
-        if (a != li || b != lj || c != lk) ++descents;
+        if (k != key) ++descents;
 #endif
-        if (a != li || b != lj || c != lk) {
-            li = a; lj = b; lk = c;
+        if (k == key) return false;
+        if constexpr (D >= 2) {
+            if ((k ^ key) & kNodeBits) node = descend_to_node(g, a, b, c);
+            entry = lower_entry(g, node, a, b, c);
+        } else {
             entry = descend_to_leaf(g, a, b, c);
-            if (g.payload != 0 && !(entry & kTile)) sm = __ldg(g.meta + entry);
         }
+        key = k;
+        return true;
+    }
+    template <int D = kAccDepth>
+    __device__ __forceinline__ uint32_t leaf(const GridView& g, int a, int b, int c)
+    {
+        if (find<D>(g, a, b, c) && g.payload != 0 && !(entry & kTile)) sm = __ldg(g.meta + entry);
         return entry;
     }
 };
 
-template <int P>
+template <int P, int D = kAccDepth>
 __device__ __forceinline__ float voxel_t(const GridView& g, Accessor& acc, int i, int j, int k)
 {
-    uint32_t e = acc.leaf(g, i >> 3, j >> 3, k >> 3);
+    uint32_t e = acc.leaf<D>(g, i >> 3, j >> 3, k >> 3);
     if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
     return leaf_value_t<P>(g, e, ((k & 7) << 6) | ((j & 7) << 3) | (i & 7), acc.sm);
 }
@@ -210,10 +267,24 @@ __device__ __forceinline__ float voxel(const GridView& g, Accessor& acc, int i, 
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
+// corners of a trilinear stencil that straddles a leaf boundary:
+// 1: corner by corner through the accessor (a corner in another leaf than the
+//    previous corner moves the cached leaf);
+// 2: stencils across one face (two leaves, the most frequent straddle) take
+//    each leaf's entry once, the rest go corner by corner.
+// 1 is the default: the second path's extra code costs more than the
+// descents it saves (15.6 against 17.5 ms on the 512^3 frame, 67.5 against
+// 70.3 ms on the cloud; the images are bit-identical).
+#ifndef VDBC_TRI_STRADDLE
+#define VDBC_TRI_STRADDLE 1
+#endif
+constexpr int kTriStraddle = VDBC_TRI_STRADDLE;
+
 // trilinear reconstruction at index-space position p, clamp to edge; every
 // call descends the tree (through the accessor's cached leaf) and decodes the
-// eight voxels; P is the payload type of the grid (-1: read at run time)
-template <int P>
+// eight voxels; P is the payload type of the grid (-1: read at run time), D
+// the accessor's cache depth, T the straddle mode (kTriStraddle)
+template <int P, int D = kAccDepth, int T = kTriStraddle>
 __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, float py, float pz, Accessor& acc)
 {
     float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
@@ -223,8 +294,10 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
     int y0 = min(max(j0, 0), g.ny - 1), y1 = min(max(j0 + 1, 0), g.ny - 1);
     int z0 = min(max(k0, 0), g.nz - 1), z1 = min(max(k0 + 1, 0), g.nz - 1);
     float v000, v100, v010, v110, v001, v101, v011, v111;
-    if ((x0 >> 3) == (x1 >> 3) && (y0 >> 3) == (y1 >> 3) && (z0 >> 3) == (z1 >> 3)) {
-        uint32_t e = acc.leaf(g, x0 >> 3, y0 >> 3, z0 >> 3);
+    const int lx0 = x0 >> 3, ly0 = y0 >> 3, lz0 = z0 >> 3;
+    const int S = (lx0 != (x1 >> 3) ? 1 : 0) | (ly0 != (y1 >> 3) ? 2 : 0) | (lz0 != (z1 >> 3) ? 4 : 0);
+    if (S == 0) {
+        uint32_t e = acc.leaf<D>(g, lx0, ly0, lz0);
         if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
         int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
         int az = (z0 & 7) << 6, bz = (z1 & 7) << 6;
@@ -233,11 +306,29 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
         v010 = leaf_value_t<P>(g, e, az | by | ax, sm); v110 = leaf_value_t<P>(g, e, az | by | bx, sm);
         v001 = leaf_value_t<P>(g, e, bz | ay | ax, sm); v101 = leaf_value_t<P>(g, e, bz | ay | bx, sm);
         v011 = leaf_value_t<P>(g, e, bz | by | ax, sm); v111 = leaf_value_t<P>(g, e, bz | by | bx, sm);
+    } else if (T == 2 && (S & (S - 1)) == 0) {
+        // two leaves across one face: leaf A holds the corners whose bit S is
+        // clear, leaf B the others
+        const uint32_t eA = acc.leaf<D>(g, lx0, ly0, lz0);
+        const float2 smA = acc.sm;
+        const uint32_t eB = acc.leaf<D>(g, x1 >> 3, y1 >> 3, z1 >> 3);
+        const float2 smB = acc.sm;
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int x = (c & 1) ? x1 : x0, y = (c & 2) ? y1 : y0, z = (c & 4) ? z1 : z0;
+            const bool b = (c & S) != 0;
+            const uint32_t e = b ? eB : eA;
+            v[c] = (e & kTile) ? __ldg(g.tiles + (e & ~kTile))
+                               : leaf_value_t<P>(g, e, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7), b ? smB : smA);
+        }
+        v000 = v[0]; v100 = v[1]; v010 = v[2]; v110 = v[3];
+        v001 = v[4]; v101 = v[5]; v011 = v[6]; v111 = v[7];
     } else {
-        v000 = voxel_t<P>(g, acc, x0, y0, z0); v100 = voxel_t<P>(g, acc, x1, y0, z0);
-        v010 = voxel_t<P>(g, acc, x0, y1, z0); v110 = voxel_t<P>(g, acc, x1, y1, z0);
-        v001 = voxel_t<P>(g, acc, x0, y0, z1); v101 = voxel_t<P>(g, acc, x1, y0, z1);
-        v011 = voxel_t<P>(g, acc, x0, y1, z1); v111 = voxel_t<P>(g, acc, x1, y1, z1);
+        v000 = voxel_t<P, D>(g, acc, x0, y0, z0); v100 = voxel_t<P, D>(g, acc, x1, y0, z0);
+        v010 = voxel_t<P, D>(g, acc, x0, y1, z0); v110 = voxel_t<P, D>(g, acc, x1, y1, z0);
+        v001 = voxel_t<P, D>(g, acc, x0, y0, z1); v101 = voxel_t<P, D>(g, acc, x1, y0, z1);
+        v011 = voxel_t<P, D>(g, acc, x0, y1, z1); v111 = voxel_t<P, D>(g, acc, x1, y1, z1);
     }
     float c00 = lerpf(v000, v100, tx), c10 = lerpf(v010, v110, tx);
     float c01 = lerpf(v001, v101, tx), c11 = lerpf(v011, v111, tx);
@@ -245,13 +336,13 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
     return lerpf(c0, c1, tz);
 }
 
-template <int P>
+template <int P, int D = kAccDepth, int T = kTriStraddle>
 struct VdbSamplerT {
     static constexpr bool kCollective = false;
     GridView g;
     __device__ __forceinline__ float operator()(float px, float py, float pz, Accessor& acc) const
     {
-        return vdb_trilinear<P>(g, px, py, pz, acc);
+        return vdb_trilinear<P, D, T>(g, px, py, pz, acc);
     }
 };
 

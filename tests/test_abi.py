@@ -160,6 +160,7 @@ def test_null_arguments_rejected_on_every_entry_point(v):
         lambda: L.vdbc_learn_loss_grad(None, None, None, 1, None, None, None, None),
         lambda: L.vdbc_learn_get_params(None, None),
         lambda: L.vdbc_select_bricks_noalloc(None, None, None, None, None, None),
+        lambda: L.vdbc_compare(None, None, 1, 1, 1, None, None),
     ]
     for i, call in enumerate(calls):
         assert call() == v.ERR_INVALID_ARG, i

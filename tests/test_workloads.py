@@ -12,6 +12,10 @@ def test_benchmark_scenes():
     c = scenes.CLOUD_994
     assert c["dims"] == (994, 676, 1225) and c["ratio"] == 10.0 and (c["width"], c["height"], c["spp"]) == (1920, 1080, 32)
     assert c["medium"]["albedo"] == 0.95 and c["medium"]["g"] == 0.8
+    f = scenes.CLOUD_1987
+    assert f["dims"] == (1987, 1351, 2449) and f["ratio"] == 10.0 and (f["width"], f["height"], f["spp"]) == (1920, 1080, 64)
+    assert f["medium"]["albedo"] == 0.95 and f["medium"]["g"] == 0.8 and f["medium"]["max_bounces"] == 32
+    assert f["kind"] == c["kind"] and (f["macrocell"], f["texture_macrocell"]) == (64, 64)
     e = scenes.BLOBS_64_EA
     assert e["dims"] == (64, 64, 64) and e["ratio"] == 4.0 and (e["width"], e["height"]) == (128, 128) and e["step"] == 0.5
 
