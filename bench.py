@@ -1,21 +1,27 @@
 """Benchmark: compressed-VDB path tracing on one GB300 (or N replicas).
 
-Workload (the 512^3 turbulent medium): a seeded 512^3 float32 volume (6-octave
-fBm x spherical falloff, ~50 % exactly 0), encoded at 1:10 into the VDB grid
-(409 of 4096 32^3 bricks), path traced at 1024x1024 x 16 spp with delta
-tracking, albedo 0.9, Henyey-Greenstein g = 0.6, up to 16 bounces, one
-directional light plus a constant environment; the same renderer on the dense
-volume in a 3D CUDA texture is the comparator.
+Workload (the headline): the full-scale cloud, a seeded 1987 x 1351 x 2449
+float32 volume (26.3 GB; Worley-modulated 8-octave fBm with an anvil height
+profile, ~73 % exactly 0; it stands in for the paper's WDAS cloud, whose
+dimensions it has), encoded at 1:10 into the VDB grid, path traced at
+1920 x 1080 x 64 spp with delta tracking, albedo 0.95, Henyey-Greenstein
+g = 0.8, up to 32 bounces, one directional light plus a constant environment;
+the same renderer on the dense volume in a 3D CUDA texture is the comparator.
 
 A step is one pass of the whole hot path over the input already in HBM:
 encode (histogram/background, brick ranges, scores, selection, tree build,
 prune, macrocell ranges) + render (majorants, DDA, Woodcock tracking,
 ratio-tracked light, scattering, accumulation).  `value` is Mpaths/s of those
-steps, timed with CUDA events on the launching stream (the 512 MiB input is
-larger than L2, and every step re-reads it, so L2 holds no stale grid).
-`e2e` runs the same step through the C ABI with host buffers: the volume is
-copied from pinned host memory inside vdbc_encode and the image is read back
-to the host inside vdbc_render.
+steps, timed with CUDA events on the launching stream (the 26.3 GB input is
+far larger than L2 and every step re-reads it).  `e2e` runs the same step
+through the C ABI with host buffers: the volume is copied from pinned host
+memory inside vdbc_encode and the image is read back to the host inside
+vdbc_render.  Errors are stated for every image: PSNR against the lossless
+render and against the dense texture (FP64 reductions on the device,
+vdbc_compare), and the mean / largest absolute difference from the FP64 CPU
+oracle's render of the same pixels with the same random numbers
+(`cpu_baseline.error_vs_oracle`).  The 512^3 turbulent medium at 1:10
+(1024^2 x 16 spp) is reported beside it (`turbulence512`).
 
 --impl reference times the FP64 CPU oracle (the test oracle, as it stands)
 on the host cores over a bounded pixel sample of the same frame.
@@ -36,7 +42,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpaths/s and density lookups/s vs dense-texture render at stated PSNR; HBM GB/s"
-WORKLOAD = "turbulence512_r10_pt1024sq_16spp"
+WORKLOAD = "cloud1987x1351x2449_r10_pt1920x1080_64spp"
+PROFILE = "k_pt_vdb_cloud1987_r10"          # the committed ncu summary of the headline's tracker launch
+PROFILE_512 = "k_pt_vdb_turbulence512"
+SEED = 2024
 
 
 def parse():
@@ -49,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-volume batched section")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-decoder section")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 512^3 medium section")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--study", choices=["worstcase", "metrics", "hdda", "fullscale"],
                     help="one of the studies beside the benchmark (one JSON line each): lossless dense-noise "
@@ -58,7 +68,12 @@ def parse():
                     help="ncu capture case of the learned codec: 50 training steps and two 512^2 x 16 spp "
                          "renders of a learned 512^3 medium")
     ap.add_argument("--profile-case", action="store_true",
-                    help="the ncu capture case: the same workload at a 512x512 image, two renders")
+                    help="the ncu capture case: the 512^3 medium's grid at a 512x512 image, two renders")
+    ap.add_argument("--save-cloud-grid", metavar="PATH",
+                    help="encode the full-scale cloud at 1:10 and save the grid to PATH (for --profile-grid)")
+    ap.add_argument("--profile-grid", metavar="PATH",
+                    help="the headline's ncu capture case: the grid file PATH loaded alone on the device "
+                         "(no dense volume or texture) and rendered twice at the headline's frame")
     return ap.parse_args()
 
 
@@ -70,15 +85,17 @@ def dist_env():
 
 
 def workload_config(world=1):
-    """The benchmark's `config` (both arms): the 512^3 medium at 1:10, 1024^2 x 16 spp."""
+    """The benchmark's `config` (both arms): the 1987x1351x2449 cloud at 1:10, 1920x1080 x 64 spp."""
     from volgen import scenes
 
-    w = scenes.TURBULENCE_512
-    return {"workload": WORKLOAD, "volume": "512^3 f32 fBm x spherical falloff (~50% zero)",
+    w = scenes.CLOUD_1987
+    return {"workload": WORKLOAD, "volume": "1987x1351x2449 f32 cloud (Worley-modulated 8-octave fBm, anvil "
+                                            "profile, ~73% zero; the WDAS cloud's dimensions)",
             "ratio": "1:10", "payload": "fp32", "macrocell": w["macrocell"],
-            "texture_macrocell": w["texture_macrocell"], "image": "1024x1024", "spp": 16,
-            "max_bounces": 16, "albedo": 0.9, "g": 0.6, "parallelism": "replicas" if world > 1 else "single",
-            "l2": "input 512 MiB > L2, re-read every step"}
+            "texture_macrocell": w["texture_macrocell"], "image": "%dx%d" % (w["width"], w["height"]),
+            "spp": w["spp"], "max_bounces": w["medium"]["max_bounces"], "albedo": w["medium"]["albedo"],
+            "g": w["medium"]["g"], "parallelism": "replicas" if world > 1 else "single",
+            "l2": "input 26.3 GB > L2, re-read every step"}
 
 
 def replica_throughput(total_ms, paths_per_step, steps, world, device=None):
@@ -180,23 +197,32 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the path-tracing kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_pt_vdb_turbulence512.md")
+def profiled_fields(name=PROFILE_512):
+    """The `key: value` figures of the committed ncu summary profiles/<name>.md,
+    if it was taken on the current tracker source; else None."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
     try:
         txt = open(path).read()
     except OSError:
         return None
-    src, traffic = None, None
+    fields = {}
     for line in txt.splitlines():
-        if line.startswith("kernel_source_sha256_16:"):
-            src = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch_full_size:"):
-            traffic = float(line.split(":", 1)[1].strip())
-    if src == kernel_source_hash() and traffic is not None:
-        return traffic
-    return None
+        if ":" in line and not line.startswith(("#", "|", " ", "-")):
+            k, val = line.split(":", 1)
+            fields[k.strip()] = val.strip()
+    if fields.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return fields
+
+
+def profiled_traffic(name=PROFILE_512):
+    """DRAM bytes per launch of the path-tracing kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    f = profiled_fields(name)
+    try:
+        return float(f["dram_bytes_per_launch_full_size"]) if f else None
+    except (KeyError, ValueError):
+        return None
 
 
 def scene(w):
@@ -205,8 +231,7 @@ def scene(w):
     return cam, w["medium"]
 
 
-def run_vdbc(args):
-    import numpy as np
+def _env(local=0):
     import torch
 
     import __graft_entry__ as ge
@@ -214,34 +239,87 @@ def run_vdbc(args):
     import paper_2504_04564_gb300 as v
     import volgen
     from volgen import scenes
+    return torch, v, volgen, scenes
 
+
+def timed_steps(torch, v, vol, w, cam, med, img, stream, steps, warmup, barrier):
+    """W untimed and K timed encode + render steps; per-step event times and
+    the last step's grid (still open)."""
+    for _ in range(max(warmup, 3)):
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img, stream=stream)
+        g.close()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    grids = []
+    for i in range(steps):
+        a, b, c = ev[i]
+        a.record(stream)
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
+        b.record(stream)
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img, stream=stream)
+        c.record(stream)
+        grids.append(g)
+    t_end.record(stream)
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    enc_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
+    ren_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(steps)]
+    for g in grids[:-1]:
+        g.close()
+    return total_ms, enc_ms, ren_ms, grids[-1]
+
+
+def tracker_roofline(v, g, cam, med, w, img, stream, first_kernel_ms, lookups, profile_name):
+    """Roofline of the dominant kernel (the path tracer): algorithmic bytes per
+    density lookup = 8 FP32 voxel values = 32 B, over the tracker kernel's own
+    duration (CUDA events the library records around its launch on the
+    render's stream): the last timed step and four more launches."""
+    kms = [float(first_kernel_ms)]
+    for _ in range(4):
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img, stream=stream)
+        kms.append(float(v.vdbc_render_stats_get(g, stream=stream).kernel_ms))
+    kms = [k for k in kms if k > 0]
+    kernel_ms = sum(kms) / len(kms)
+    peak, peak_kind = measured_peaks()
+    achieved = lookups * 32.0 / (kernel_ms * 1e-3) / 1e9
+    prof = profiled_fields(profile_name)
+
+    def num(k):
+        try:
+            return float(prof[k]) if prof and k in prof else None
+        except ValueError:
+            return None
+    return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 5), "traffic": num("dram_bytes_per_launch_full_size"),
+            "kernel": "k_pt<VdbSamplerT<0>>", "kernel_ms": round(kernel_ms, 3), "kernel_launches_timed": len(kms),
+            "peak_source": peak_kind, "algorithmic_bytes_per_lookup": 32,
+            "l2_hit_rate_pct": num("lts_sector_hit_rate_pct"), "sectors_per_request": num("l1tex_sectors_per_request"),
+            "dram_gbs_profiled": num("dram_gbs_profiled"), "profile": "profiles/%s.md" % profile_name if prof else None}
+
+
+def compare(v, a, b, stream=None):
+    """FP64 error of image b against image a on the device (RGB)."""
+    st = v.vdbc_compare(a, b, stride=4, channels=3, stream=stream)
+    return {"psnr_db": (round(st.psnr, 3) if math.isfinite(st.psnr) else "inf"), "rmse": st.rmse,
+            "mean_abs": st.mean_abs, "max_abs": st.max_abs}
+
+
+def run_vdbc(args):
+    import numpy as np
+
+    torch, v, volgen, scenes = _env()
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    w = scenes.TURBULENCE_512
-    cam_args, med_args = scene(w)
-    cam = v.make_camera(*cam_args)
-    med = v.make_medium(v.MODE_PT, **med_args)
-    p = volgen.make_params(w["kind"], w["dims"], w["seed"])
-    vol = volgen.generate_torch(p, dev)
-    stream = torch.cuda.current_stream(dev)
-    H, W = w["height"], w["width"]
-    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
-    paths_per_step = H * W * w["spp"]
-    seed = 2024
-
-    def step():
-        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
-        v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
-        return g
-
-    for _ in range(max(args.warmup, 3)):
-        g = step()
-        g.close()
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
@@ -249,137 +327,77 @@ def run_vdbc(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # --- timed region: K whole steps; the render launch is also bracketed alone
+    w = scenes.CLOUD_1987
+    cam_args, med_args = scene(w)
+    cam = v.make_camera(*cam_args)
+    med = v.make_medium(v.MODE_PT, **med_args)
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev)
+    stream = torch.cuda.current_stream(dev)
+    H, W = w["height"], w["width"]
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    paths_per_step = H * W * w["spp"]
+
+    # --- timed region: K whole steps (encode + render) with clocks sampled
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = v.vdbc_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    grids = []
-    for i in range(args.steps):
-        a, b, c = ev[i]
-        a.record(stream)
-        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
-        b.record(stream)
-        v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
-        c.record(stream)
-        grids.append(g)
-    t_end.record(stream)
-    barrier()
+    total_ms, enc_ms, ren_ms, g = timed_steps(torch, v, vol, w, cam, med, img, stream, args.steps, args.warmup,
+                                              barrier)
     launches = v.vdbc_kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    enc_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    ren_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    stats = v.vdbc_render_stats_get(grids[-1], stream=stream)
-    info = grids[-1].info
-    for g in grids:
-        g.close()
+    stats = v.vdbc_render_stats_get(g, stream=stream)
+    info = g.info
     total_ms, value = replica_throughput(total_ms, paths_per_step, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
     render_ms = sum(ren_ms) / len(ren_ms)
     lookups = int(stats.lookups)
     vdb_img = img.clone()
-
-    # --- roofline of the dominant kernel (the path tracer): algorithmic bytes
-    # per density lookup = 8 FP32 voxel values = 32 B, over the tracker
-    # kernel's own duration (CUDA events the library records around its launch
-    # on the render's stream): the last timed step and four more launches
-    kms = [float(stats.kernel_ms)]
-    g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
-    for _ in range(4):
-        v.vdbc_render(g, cam, med, w["spp"], seed, img, stream=stream)
-        kms.append(float(v.vdbc_render_stats_get(g, stream=stream).kernel_ms))
+    roof = tracker_roofline(v, g, cam, med, w, img, stream, stats.kernel_ms, lookups, PROFILE)
     g.close()
-    kms = [k for k in kms if k > 0]
-    kernel_ms = sum(kms) / len(kms) if kms else render_ms
-    peak, peak_kind = measured_peaks()
-    achieved = lookups * 32.0 / (kernel_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-            "kernel": "k_pt<VdbSamplerT<0>>", "kernel_ms": round(kernel_ms, 3), "kernel_launches_timed": len(kms),
-            "peak_source": peak_kind, "algorithmic_bytes_per_lookup": 32}
 
-    # --- comparator: the same renderer on the dense 3D texture; PSNR
-    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w.get("texture_macrocell", w["macrocell"]),
-                               stream=stream)
+    # --- comparator: the same renderer on the dense 3D texture; the lossless
+    # (1:1) render; image errors in FP64 on the device
+    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w["texture_macrocell"], stream=stream)
     dimg = torch.empty_like(img)
     for _ in range(2):
-        v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
+        v.vdbc_render_dense(tex, cam, med, w["spp"], SEED, dimg, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, min(args.steps, 3))
     e0.record(stream)
     for _ in range(reps):
-        v.vdbc_render_dense(tex, cam, med, w["spp"], seed, dimg, stream=stream)
+        v.vdbc_render_dense(tex, cam, med, w["spp"], SEED, dimg, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     dense_ms = e0.elapsed_time(e1) / reps
     dstats = v.vdbc_volume_render_stats_get(tex, stream=stream)
     tex.close()
+    torch.cuda.empty_cache()
     g1 = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"], stream=stream)   # the uncompressed (lossless) render
     ref_img = torch.empty_like(img)
-    v.vdbc_render(g1, cam, med, w["spp"], seed, ref_img, stream=stream)
+    v.vdbc_render(g1, cam, med, w["spp"], SEED, ref_img, stream=stream)
     torch.cuda.synchronize()
+    lossless_bytes = int(g1.info.total_bytes)
     g1.close()
-
-    def psnr(a, b):
-        mse = float(((a[..., :3] - b[..., :3]) ** 2).mean().item())
-        return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+    errors = {"vdb_r10_vs_lossless_r1": compare(v, ref_img, vdb_img), "vdb_r10_vs_dense_texture": compare(v, dimg, vdb_img),
+              "lossless_r1_vs_dense_texture": compare(v, dimg, ref_img),
+              "reduction": "FP64 on the device (vdbc_compare), RGB of every pixel, peak 1"}
+    host_vol = None
+    if rank == 0 and not args.no_cpu_baseline:
+        host_vol = vol.cpu().numpy()           # the oracle's input: the same generator output
+    del vol
+    torch.cuda.empty_cache()
 
     # --- end to end through the C ABI with host buffers: every step uploads
     # the volume from pinned host memory (vdbc_encode on a host pointer) and
     # reads the image back (vdbc_render into host memory).  Two host threads,
-    # one stream each, take alternate steps, so one step's upload (the link
-    # moves ~208 GB/s, 2.6 ms for the 512 MiB volume) overlaps the other's
-    # tracker; calls on different handles may run concurrently.
+    # one stream each, take alternate steps, so one step's upload overlaps the
+    # other's tracker; calls on different handles may run concurrently.
     e2e = None
     if not args.no_e2e:
-        import threading
+        e2e = run_e2e(torch, v, volgen, w, cam, med, dev, args, barrier, world, paths_per_step)
 
-        host_vol = vol.cpu().pin_memory()
-        lanes = [dict(stream=torch.cuda.Stream(device=dev), img=np.empty((H, W, 4), dtype=np.float32))
-                 for _ in range(2)]
-
-        def e2e_steps(lane, n):
-            torch.cuda.set_device(dev)
-            st = lane["stream"].cuda_stream
-            for _ in range(n):
-                g = v.vdbc_encode(host_vol, w["ratio"], macrocell=w["macrocell"], stream=st)
-                v.vdbc_render(g, cam, med, w["spp"], seed, lane["img"], stream=st)
-                g.close()
-
-        def run_pair(counts):
-            errs = []
-
-            def body(lane, n):
-                try:
-                    e2e_steps(lane, n)
-                except Exception as ex:       # surfaced below, on the calling thread
-                    errs.append(ex)
-            ts = [threading.Thread(target=body, args=(lanes[i], counts[i])) for i in range(2)]
-            for t in ts:
-                t.start()
-            for t in ts:
-                t.join()
-            if errs:
-                raise errs[0]
-
-        torch.cuda.synchronize()
-        run_pair((1, 1))
-        barrier()
-        t0 = time.perf_counter()
-        run_pair(((args.steps + 1) // 2, args.steps // 2))
-        barrier()
-        e2e_s = time.perf_counter() - t0
-        e2e = {"value": round(world * paths_per_step * args.steps / e2e_s / 1e6, 3), "unit": "Mpaths/s",
-               "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16),
-               "pipeline": "2 host threads, a stream each; one step's upload overlaps the other's tracker"}
-
+    secondary = None if args.no_secondary else run_turbulence_section(torch, v, volgen, scenes, dev, stream, args)
     batch = None if args.no_batch else run_batch_section(v, volgen, scenes, dev, stream, args)
     learned = None if args.no_learned else run_learned_section(v, volgen, scenes, dev, stream)
 
@@ -395,24 +413,131 @@ def run_vdbc(args):
                           "vdb_over_dense_render_only": round(dense_ms / render_ms, 4),
                           "vdb_over_dense_step": round(dense_ms / ms_per_step, 4),
                           "lookups": int(dstats.lookups)},
-        "psnr_db": {"vdb_r10_vs_uncompressed_r1": round(psnr(vdb_img, ref_img), 3),
-                    "vdb_r10_vs_dense_texture": round(psnr(vdb_img, dimg), 3)},
+        "errors": errors,
+        "psnr_db": {"vdb_r10_vs_uncompressed_r1": errors["vdb_r10_vs_lossless_r1"]["psnr_db"],
+                    "vdb_r10_vs_dense_texture": errors["vdb_r10_vs_dense_texture"]["psnr_db"]},
         "grid": {"total_bytes": int(info.total_bytes), "payload_bytes": int(info.payload_bytes),
-                 "n_active_bricks": int(info.n_active), "n_leaves": int(info.n_leaves)},
+                 "n_active_bricks": int(info.n_active), "n_bricks": int(info.n_bricks),
+                 "n_leaves": int(info.n_leaves), "lossless_total_bytes": lossless_bytes,
+                 "dense_bytes": int(np.prod(w["dims"])) * 4},
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,
+        "turbulence512": secondary,
         "batch": batch,
         "learned": learned,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        oc = CpuOracle(host=host_vol)
+        del host_vol
+        line["cpu_baseline"] = oc.measure(args.cpu_seconds)
+        line["cpu_baseline"]["error_vs_oracle"] = oc.error_against(vdb_img.cpu().numpy())
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_e2e(torch, v, volgen, w, cam, med, dev, args, barrier, world, paths_per_step):
+    import numpy as np
+
+    H, W = w["height"], w["width"]
+    host_vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev).cpu().pin_memory()
+    torch.cuda.empty_cache()
+    lanes = [dict(stream=torch.cuda.Stream(device=dev), img=np.empty((H, W, 4), dtype=np.float32))
+             for _ in range(2)]
+
+    def e2e_steps(lane, n):
+        torch.cuda.set_device(dev)
+        st = lane["stream"].cuda_stream
+        for _ in range(n):
+            g = v.vdbc_encode(host_vol, w["ratio"], macrocell=w["macrocell"], stream=st)
+            v.vdbc_render(g, cam, med, w["spp"], SEED, lane["img"], stream=st)
+            g.close()
+
+    def run_pair(counts):
+        errs = []
+
+        def body(lane, n):
+            try:
+                e2e_steps(lane, n)
+            except Exception as ex:       # surfaced below, on the calling thread
+                errs.append(ex)
+        ts = [threading.Thread(target=body, args=(lanes[i], counts[i])) for i in range(2)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    torch.cuda.synchronize()
+    run_pair((1, 1))
+    barrier()
+    t0 = time.perf_counter()
+    run_pair(((args.steps + 1) // 2, args.steps // 2))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    out = {"value": round(world * paths_per_step * args.steps / e2e_s / 1e6, 3), "unit": "Mpaths/s",
+           "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16),
+           "pipeline": "2 host threads, a stream each; one step's upload overlaps the other's tracker"}
+    del host_vol
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_turbulence_section(torch, v, volgen, scenes, dev, stream, args):
+    """The 512^3 turbulent medium at 1:10 (1024^2 x 16 spp): the same step
+    (encode + render) timed the same way, its roofline, the dense texture and
+    PSNR.  Its 54 MB grid stays in L2, so this block shows the tracker with
+    the grid on chip, beside the headline's HBM-resident cloud grid."""
+    w = scenes.TURBULENCE_512
+    cam_args, med_args = scene(w)
+    cam = v.make_camera(*cam_args)
+    med = v.make_medium(v.MODE_PT, **med_args)
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev)
+    H, W = w["height"], w["width"]
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    paths = H * W * w["spp"]
+    steps = max(3, min(args.steps, 10))
+    total_ms, enc_ms, ren_ms, g = timed_steps(torch, v, vol, w, cam, med, img, stream, steps, 3,
+                                              torch.cuda.synchronize)
+    stats = v.vdbc_render_stats_get(g, stream=stream)
+    render_ms = sum(ren_ms) / len(ren_ms)
+    vdb_img = img.clone()
+    roof = tracker_roofline(v, g, cam, med, w, img, stream, stats.kernel_ms, int(stats.lookups), PROFILE_512)
+    g.close()
+    tex = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, macrocell=w["texture_macrocell"], stream=stream)
+    dimg = torch.empty_like(img)
+    v.vdbc_render_dense(tex, cam, med, w["spp"], SEED, dimg, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        v.vdbc_render_dense(tex, cam, med, w["spp"], SEED, dimg, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dense_ms = e0.elapsed_time(e1) / 3
+    tex.close()
+    g1 = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"], stream=stream)
+    ref_img = torch.empty_like(img)
+    v.vdbc_render(g1, cam, med, w["spp"], SEED, ref_img, stream=stream)
+    torch.cuda.synchronize()
+    g1.close()
+    del vol
+    torch.cuda.empty_cache()
+    ms_per_step = total_ms / steps
+    return {"workload": "turbulence512_r10_pt1024sq_16spp", "steps": steps,
+            "mpaths_per_s": round(paths / (ms_per_step * 1e-3) / 1e6, 3), "ms_per_step": round(ms_per_step, 3),
+            "render_ms": round(render_ms, 3), "encode_ms": round(sum(enc_ms) / len(enc_ms), 3),
+            "lookups_per_frame": int(stats.lookups), "roofline": roof,
+            "dense_texture": {"ms_render": round(dense_ms, 3),
+                              "mpaths_per_s": round(paths / (dense_ms * 1e-3) / 1e6, 3),
+                              "vdb_over_dense_render_only": round(dense_ms / render_ms, 4)},
+            "errors": {"vdb_r10_vs_lossless_r1": compare(v, ref_img, vdb_img),
+                       "vdb_r10_vs_dense_texture": compare(v, dimg, vdb_img)}}
 
 
 def run_batch_section(v, volgen, scenes, dev, stream, args):
@@ -493,14 +618,13 @@ def run_learned_section(v, volgen, scenes, dev, stream):
     w = scenes.CLOUD_994
     vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev)
     torch.cuda.synchronize()
-    peak = float(vol.max() - vol.min())
 
     def vpsnr(g):
+        # volume PSNR (peak 1, the paper's convention) from the FP64 device reduction
         out = torch.empty_like(vol)
         v.vdbc_grid_decode(g, out, stream=stream)
-        torch.cuda.synchronize()
-        mse = float(((out.double() - vol.double()) ** 2).mean())
-        return round(10 * math.log10(peak * peak / max(mse, 1e-30)), 3)
+        st = v.vdbc_compare(vol, out, stream=stream)
+        return round(st.psnr, 3) if math.isfinite(st.psnr) else "inf"
 
     full = v.vdbc_encode(vol, 1.0, macrocell=w["macrocell"], stream=stream)
     vdb32 = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
@@ -532,10 +656,10 @@ def run_learned_section(v, volgen, scenes, dev, stream):
 
     def entry(g, name):
         ms, im, lk = timed_render(g)
-        mse = float(((im[..., :3].double() - ref[..., :3].double()) ** 2).mean())
+        err = compare(v, ref, im, stream)
         info = g.info
         return {"total_bytes": int(info.total_bytes), "volume_psnr_db": vpsnr(g),
-                "image_psnr_vs_dense_db": round(10 * math.log10(1.0 / max(mse, 1e-30)), 3),
+                "image_psnr_vs_dense_db": err["psnr_db"], "image_rmse_vs_dense": err["rmse"],
                 "render_ms": round(ms, 3), "mpaths_per_s": round(paths / (ms * 1e-3) / 1e6, 3),
                 "lookups": lk}
 
@@ -558,26 +682,48 @@ def run_learned_section(v, volgen, scenes, dev, stream):
     return res
 
 
-class CpuOracle:
-    """The FP64 oracle (unchanged) on the host cores: the full 512^3 volume is
-    encoded once; a measurement then traces a random pixel sample of the frame
-    (all 16 spp), sized to about budget_s seconds and capped at the whole frame."""
+def input_volume(w):
+    """The workload's input on the host: the seeded generator's output, made
+    on the device when one is present (its device and host builds give the
+    same bits; the host build alone takes minutes at 6.57 G voxels)."""
+    import volgen
 
-    def __init__(self):
+    p = volgen.make_params(w["kind"], w["dims"], w["seed"])
+    try:
+        import torch
+        if torch.cuda.is_available():
+            out = volgen.generate_torch(p).cpu().numpy()
+            torch.cuda.empty_cache()
+            return out
+    except ImportError:
+        pass
+    return volgen.generate_host(p, threads=os.cpu_count() or 1)
+
+
+class CpuOracle:
+    """The FP64 oracle (unchanged) on the host cores.  The workload's volume is
+    encoded once by the oracle (B, brick ranges, scores, selection) and decoded
+    to the dense grid D that its renderer samples.  A measurement traces a
+    random pixel sample of the frame (every spp of each pixel) sized to about
+    budget_s seconds; error_against() traces every 16th row and column of the
+    frame and compares the GPU image there."""
+
+    def __init__(self, host=None, w=None):
         import numpy as np
 
         import oracle
-        import volgen
         from volgen import scenes
 
         self.np, self.oracle = np, oracle
-        self.w = w = scenes.TURBULENCE_512
+        self.w = w = w or scenes.CLOUD_1987
         self.cores = os.cpu_count() or 1
-        p = volgen.make_params(w["kind"], w["dims"], w["seed"])
-        host = volgen.generate_host(p, threads=self.cores)
+        if host is None:
+            host = input_volume(w)
         t0 = time.perf_counter()
         e = oracle.encode(host, w["ratio"])
+        self.n_active = int(e["n_active"])
         self.D = oracle.decode_dense(host, e["active"], e["background_bits"])
+        del host, e
         self.mx = oracle.macrocell_minmax(self.D, w["macrocell"])[1]
         self.enc_s = time.perf_counter() - t0
         cam_args, med_args = scene(w)
@@ -589,24 +735,46 @@ class CpuOracle:
         self.pix = pix
         self.n = min(4096, pix.size)
 
+    def _render(self, pixels):
+        w = self.w
+        return self.oracle.render_pixels(self.D, self.mx, self.cam, self.med, w["spp"], SEED, pixels,
+                                         threads=self.cores)
+
     def measure(self, budget_s):
         w = self.w
         t0 = time.perf_counter()
-        self.oracle.render_pixels(self.D, self.mx, self.cam, self.med, w["spp"], 2024, self.pix[:self.n],
-                                  threads=self.cores)
+        self._render(self.pix[:self.n])
         dt = time.perf_counter() - t0
         # size the next sample to about budget_s
         self.n = int(min(self.pix.size, max(16, self.n * budget_s / max(dt, 1e-3))))
         paths = self.n * w["spp"]
         t0 = time.perf_counter()
-        self.oracle.render_pixels(self.D, self.mx, self.cam, self.med, w["spp"], 2024, self.pix[:self.n],
-                                  threads=self.cores)
+        self._render(self.pix[:self.n])
         dt = time.perf_counter() - t0
         return {"value": round(paths / dt / 1e6, 6), "unit": "Mpaths/s", "cores": self.cores, "kind": "oracle",
-                "sample": "%d random pixels of the 1024^2 frame (all of it when it fits the %.0f s budget) "
-                          "x %d spp = %d paths in %.2f s; oracle encode+decode+macrocells of the full 512^3 "
-                          "volume took %.1f s (not in the rate)" % (self.n, budget_s, w["spp"], paths, dt,
-                                                                     self.enc_s)}
+                "sample": "%d random pixels of the %dx%d frame x %d spp = %d paths in %.2f s; the oracle's "
+                          "encode + decode + macrocells of the full %dx%dx%d volume took %.1f s (not in the rate)"
+                          % (self.n, w["width"], w["height"], w["spp"], paths, dt, *w["dims"], self.enc_s)}
+
+    def error_against(self, gpu_rgba):
+        """Mean and largest absolute difference per channel between the GPU
+        image and the oracle's FP64 render at every 16th row and column (the
+        same pixels, samples and random numbers)."""
+        np, w = self.np, self.w
+        W, H = w["width"], w["height"]
+        ys, xs = np.meshgrid(np.arange(8, H, 16), np.arange(8, W, 16), indexing="ij")
+        pix = (ys * W + xs).ravel().astype(np.int64)
+        t0 = time.perf_counter()
+        ref = self._render(pix)
+        dt = time.perf_counter() - t0
+        got = np.asarray(gpu_rgba, dtype=np.float64).reshape(-1, 4)[pix]
+        d = np.abs(got[:, :3] - ref[:, :3])
+        mean_abs = [float(x) for x in d.mean(axis=0)]
+        return {"pixels": int(pix.size), "spp": w["spp"], "paths": int(pix.size) * w["spp"],
+                "sample": "every 16th row and column of the frame", "mean_abs_rgb": mean_abs,
+                "max_abs": float(d.max()), "tolerance_mean_abs": 1e-4,
+                "within_tolerance": bool(max(mean_abs) <= 1e-4), "oracle_s": round(dt, 2),
+                "oracle_active_bricks": self.n_active}
 
 
 def cpu_baseline(budget_s):
@@ -619,7 +787,7 @@ def run_reference(args):
         return
     steps = max(1, args.steps)
     co = CpuOracle()
-    per = max(2.0, min(20.0, 150.0 / (2 * (steps + max(args.warmup, 0)))))
+    per = max(1.0, min(20.0, 100.0 / (steps + max(args.warmup, 0))))
     for _ in range(max(args.warmup, 0)):
         co.measure(per)
     vals, cb = [], None
@@ -642,16 +810,9 @@ def run_reference(args):
 
 def run_profile_case():
     """The capture case for `ncu --set full`: the 512^3 medium at 1:10 (same
-    grid as the benchmark), rendered twice at 512x512 x 16 spp so that a
-    full-section capture of the second launch stays small."""
-    import torch
-
-    import __graft_entry__ as ge
-    ge.build()
-    import paper_2504_04564_gb300 as v
-    import volgen
-    from volgen import scenes
-
+    grid as the benchmark's 512^3 block), rendered twice at 512x512 x 16 spp so
+    that a full-section capture of the second launch stays small."""
+    torch, v, volgen, scenes = _env()
     w = scenes.TURBULENCE_512
     cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 512, 512))
     med = v.make_medium(v.MODE_PT, **w["medium"])
@@ -659,11 +820,40 @@ def run_profile_case():
     g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"])
     img = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
     for _ in range(2):
-        v.vdbc_render(g, cam, med, w["spp"], 2024, img)
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img)
     torch.cuda.synchronize()
     st = v.vdbc_render_stats_get(g)
     print(json.dumps({"profile_case": "turbulence512_r10_pt512sq_16spp", "lookups": int(st.lookups),
                       "paths": int(st.paths)}))
+
+
+def run_save_cloud_grid(path):
+    """Encodes the headline's volume at its rate and saves the grid (the input
+    of --profile-grid, which then holds nothing else on the device)."""
+    torch, v, volgen, scenes = _env()
+    w = scenes.CLOUD_1987
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
+    g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"])
+    v.vdbc_grid_save(g, path)
+    print(json.dumps({"saved": path, "total_bytes": int(g.info.total_bytes), "n_active": int(g.info.n_active)}))
+
+
+def run_profile_grid(path):
+    """The headline's capture case: the saved grid loaded alone on the device
+    (about 2.6 GB) and rendered twice at the headline's frame (1920x1080 x
+    64 spp, albedo 0.95, g 0.8, 32 bounces)."""
+    torch, v, volgen, scenes = _env()
+    w = scenes.CLOUD_1987
+    g = v.vdbc_grid_load(path)
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], w["width"], w["height"]))
+    med = v.make_medium(v.MODE_PT, **w["medium"])
+    img = torch.empty((w["height"], w["width"], 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img)
+    torch.cuda.synchronize()
+    st = v.vdbc_render_stats_get(g)
+    print(json.dumps({"profile_case": WORKLOAD, "grid_bytes": int(g.info.total_bytes), "lookups": int(st.lookups),
+                      "paths": int(st.paths), "kernel_ms": float(st.kernel_ms)}))
 
 
 def run_profile_learned():
@@ -687,7 +877,7 @@ def run_profile_learned():
     g, losses = v.vdbc_learn(full, steps=50, samples_per_leaf=64, lr=2e-3, lr_latent=2e-2, max_bytes=budget, seed=1)
     img = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
     for _ in range(2):
-        v.vdbc_render(g, cam, med, w["spp"], 2024, img)
+        v.vdbc_render(g, cam, med, w["spp"], SEED, img)
     torch.cuda.synchronize()
     st = v.vdbc_render_stats_get(g)
     print(json.dumps({"profile_case": "turbulence512_learned_pt512sq_16spp", "lookups": int(st.lookups),
@@ -870,6 +1060,10 @@ if __name__ == "__main__":
         print(json.dumps(res), flush=True)
     elif a.profile_learned:
         run_profile_learned()
+    elif a.save_cloud_grid:
+        run_save_cloud_grid(a.save_cloud_grid)
+    elif a.profile_grid:
+        run_profile_grid(a.profile_grid)
     elif a.profile_case:
         run_profile_case()
     elif a.impl == "reference":
