@@ -540,18 +540,54 @@ def run_turbulence_section(torch, v, volgen, scenes, dev, stream, args):
                        "vdb_r10_vs_dense_texture": compare(v, dimg, vdb_img)}}
 
 
+def batch_oracle_errors(specs, hosts, images, spp_total, pixels_per_job=32):
+    """Per volume of the batch: the FP64 oracle encodes and decodes the volume
+    itself and renders `pixels_per_job` random pixels with the samples the
+    batch images hold (spp_total per pixel, the same random numbers); the
+    mean absolute error per channel (largest of R, G, B) and the largest
+    absolute error of the GPU image there.  Volumes are done on host threads."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from volgen import scenes
+
+    def one(i):
+        sp, host = specs[i], hosts[i]
+        e = oracle.encode(host, sp["ratio"], payload=sp["payload"])
+        D = oracle.decode_dense(host, e["active"], e["background_bits"], sp["payload"])
+        mx = oracle.macrocell_minmax(D, sp["macrocell"])[1]
+        pix = np.sort(np.random.default_rng(100 + i).choice(sp["width"] * sp["height"], pixels_per_job, replace=False))
+        cam = oracle.make_camera(*scenes.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
+        ref = oracle.render_pixels(D, mx, cam, oracle.make_medium(1, macrocell=sp["macrocell"], **sp["medium"]),
+                                   sp["spp"] * spp_total, sp["seed"], pix)
+        d = np.abs(images[i].reshape(-1, 4).astype(np.float64)[pix, :3] - ref[:, :3])
+        return float(d.mean(axis=0).max()), float(d.max())
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        res = list(ex.map(one, range(len(specs))))
+    return {"mean_abs_per_volume": [r[0] for r in res], "max_abs_per_volume": [r[1] for r in res],
+            "worst_mean_abs": max(r[0] for r in res), "tolerance_mean_abs": 1e-4,
+            "within_tolerance": bool(max(r[0] for r in res) <= 1e-4), "pixels_per_volume": pixels_per_job,
+            "samples_per_pixel": "each job's spp x %d frames" % spp_total, "oracle_s": round(time.perf_counter() - t0, 2)}
+
+
 def run_batch_section(v, volgen, scenes, dev, stream, args):
     """The batched form: 32 volumes of uneven size (FP16/FP8 leaves, rates 1:4..1:20,
-    images 256^2..1024^2, 4..32 spp) in one persistent launch per frame from a
-    captured CUDA graph, against rendering the same jobs one by one."""
+    images 256^2..1024^2, 4..32 spp) in one persistent launch per payload group
+    per frame from a captured CUDA graph, against rendering the same jobs one
+    by one; every volume's image checked against the FP64 oracle."""
     import torch
 
     specs = scenes.batch_jobs()
-    grids, imgs, jobs = [], [], []
+    grids, imgs, jobs, hosts = [], [], [], []
     payload_bytes = 0
     for sp in specs:
         vol = volgen.generate_torch(volgen.make_params(sp["kind"], sp["dims"], sp["seed"]), dev)
         g = v.vdbc_encode(vol, sp["ratio"], payload=sp["payload"], macrocell=sp["macrocell"], stream=stream)
+        if not args.no_cpu_baseline:
+            hosts.append(vol.cpu().numpy())
         del vol
         payload_bytes += int(g.info.payload_bytes)
         cam = v.make_camera(*scenes.pinhole_orbit(sp["dims"], sp["width"], sp["height"], direction=sp["direction"]))
@@ -577,6 +613,7 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / frames
     st = v.vdbc_batch_stats_get(b, stream=stream)
+    batch_imgs = [im.cpu().numpy() for im in imgs]          # the running mean of 1 + frames frames
     # the plain form: one vdbc_render per job, same samples, with the coarse
     # DDA level the tuner chose for the batch
     os.environ["VDBC_PT_COARSE"] = str(int(tuning.coarse))
@@ -593,13 +630,15 @@ def run_batch_section(v, volgen, scenes, dev, stream, args):
     b.close()
     for g in grids:
         g.close()
-    return {"jobs": len(specs), "paths_per_frame": paths, "frame_ms": round(batch_ms, 3),
+    errors = batch_oracle_errors(specs, hosts, batch_imgs, 1 + frames) if hosts else None
+    return {"jobs": len(specs), "paths_per_frame": paths, "frame_ms": round(batch_ms, 3), "error_vs_oracle": errors,
             "mpaths_per_s": round(paths / (batch_ms * 1e-3) / 1e6, 3),
             "one_by_one_ms": round(plain_ms, 3),
             "one_by_one_mpaths_per_s": round(paths / (plain_ms * 1e-3) / 1e6, 3),
             "speedup_vs_one_by_one": round(plain_ms / batch_ms, 4),
             "payload_bytes": payload_bytes, "lookups_per_frame": int(st.lookups),
-            "tuning": {"threads": tuning.threads, "chunk": tuning.chunk, "coarse": tuning.coarse},
+            "tuning": {"threads": tuning.threads, "chunk": tuning.chunk, "paths_per_lane_per_refill": tuning.chunk // 32,
+                       "coarse": tuning.coarse, "accessor_depth": tuning.depth},
             "create_s_incl_autotune": round(create_s, 3),
             "workload": "32 blob+fBm volumes, edges 64..384, rates 1:4..1:20, FP16/FP8, 256^2..1024^2, 4..32 spp, "
                         "%d^3 cells" % specs[0]["macrocell"]}

@@ -336,9 +336,10 @@ typedef struct {
 /* launch shape of the batched path tracer, chosen by the autotuner */
 typedef struct {
     int32_t threads;       /* threads per block: 128 or 256 */
-    int32_t chunk;         /* paths a warp takes from the work counter at once (>= 32) */
+    int32_t chunk;         /* paths a warp takes from the work counter at once (>= 32);
+                              chunk / 32 is the paths each lane claims per refill */
     int32_t coarse;        /* 1: cross empty 8^3 blocks of macrocells in one DDA step */
-    int32_t reserved;
+    int32_t depth;         /* accessor cache depth: 1 the last leaf, 2 also its lower node */
     float   frame_ms;      /* the tuner's time for every 8th path of a frame with this shape */
 } vdbc_tuning;
 

@@ -87,7 +87,7 @@ class Job(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("chunk", ctypes.c_int32), ("coarse", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("frame_ms", ctypes.c_float)]
+                ("depth", ctypes.c_int32), ("frame_ms", ctypes.c_float)]
 
 
 class RenderStats(ctypes.Structure):

@@ -77,19 +77,67 @@ constexpr int kCoarse = 8;
 
 constexpr int kMaxStepsPerCell = 1 << 20;
 
+// Division in the tracker: with VDBC_PT_FASTDIV=1 (the default) the
+// hardware's approximate reciprocal times the dividend (__fdividef, within
+// 2 ulp for the magnitudes here), a few instructions instead of the correctly
+// rounded sequence; 0 restores IEEE division.  The tracker is bound by
+// instruction issue: 13.4 against 16.0 ms for the 1024^2 x 16 spp frame of
+// the 512^3 medium, 61.4 against 69.4 ms for the 1920x1080 x 64 spp frame of
+// the full-scale cloud, with the oracle parity tests unchanged.  Both forms
+// are deterministic, so every sampler instantiation computes the same bits.
+#ifndef VDBC_PT_FASTDIV
+#define VDBC_PT_FASTDIV 1
+#endif
+__device__ __forceinline__ float fdiv(float a, float b)
+{
+#if VDBC_PT_FASTDIV
+    return __fdividef(a, b);
+#else
+    return __fdiv_rn(a, b);
+#endif
+}
+
+// Square root and logarithm in the tracker: with VDBC_PT_FASTMATH=1 (the
+// default) the hardware approximations (sqrt.approx, __logf: a base-2
+// logarithm instruction times ln 2) instead of the correctly rounded square
+// root and the accurate logf (12.3 against 12.8 ms on the 512^3 frame, 59.7
+// against 60.2 on the cloud; oracle parity unchanged); 0 keeps sqrtf and logf.
+#ifndef VDBC_PT_FASTMATH
+#define VDBC_PT_FASTMATH 1
+#endif
+__device__ __forceinline__ float fsqrt(float x)
+{
+#if VDBC_PT_FASTMATH
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return sqrtf(x);
+#endif
+}
+
+__device__ __forceinline__ float flog(float x)
+{
+#if VDBC_PT_FASTMATH
+    return __logf(x);
+#else
+    return logf(x);
+#endif
+}
+
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 norm3(float3 a)
 {
-    float l = sqrtf(dot3(a, a));
-    return f3(a.x / l, a.y / l, a.z / l);
+    float l = fsqrt(dot3(a, a));
+    return f3(fdiv(a.x, l), fdiv(a.y, l), fdiv(a.z, l));
 }
 
 // ray / box [-1/2, dim-1/2]^3, t >= 0
 __device__ __forceinline__ bool clip_axis(float o, float d, float hi, float& t0, float& t1)
 {
     if (d == 0.0f) return !(o < -0.5f || o > hi);
-    float ta = (-0.5f - o) / d, tb = (hi - o) / d;
+    float ta = fdiv(-0.5f - o, d), tb = fdiv(hi - o, d);
     if (ta > tb) { float s = ta; ta = tb; tb = s; }
     t0 = fmaxf(t0, ta);
     t1 = fminf(t1, tb);
@@ -124,7 +172,7 @@ struct Dda {
     __device__ __forceinline__ static int first_cell(float o, float d, float tmin, float mc, int n)
     {
         float p = __fmaf_rn(tmin, d, o);
-        int ci = (int)floorf(__fdiv_rn(__fadd_rn(p, 0.5f), mc));
+        int ci = (int)floorf(fdiv(__fadd_rn(p, 0.5f), mc));
         return min(max(ci, 0), n - 1);
     }
     __device__ __forceinline__ void init(const Majorants& m, float3 o, float3 d, float tmin, float tmax_)
@@ -135,7 +183,7 @@ struct Dda {
         sx = d.x > 0.0f ? 1 : (d.x < 0.0f ? -1 : 0);
         sy = d.y > 0.0f ? 1 : (d.y < 0.0f ? -1 : 0);
         sz = d.z > 0.0f ? 1 : (d.z < 0.0f ? -1 : 0);
-        ix = 1.0f / d.x; iy = 1.0f / d.y; iz = 1.0f / d.z;
+        ix = fdiv(1.0f, d.x); iy = fdiv(1.0f, d.y); iz = fdiv(1.0f, d.z);
         cx = first_cell(o.x, d.x, tmin, mc, m.mx);
         cy = first_cell(o.y, d.y, tmin, mc, m.my);
         cz = first_cell(o.z, d.z, tmin, mc, m.mz);
@@ -200,7 +248,7 @@ struct Dda {
 __device__ __forceinline__ float hg_eval(float mu, float g)
 {
     float den = 1.0f + g * g - 2.0f * g * mu;
-    return (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
+    return fdiv(1.0f - g * g, 4.0f * 3.14159265358979f * den * fsqrt(den));
 }
 
 __device__ __forceinline__ float hg_sample_mu(float g, float xi)
@@ -208,8 +256,8 @@ __device__ __forceinline__ float hg_sample_mu(float g, float xi)
     float mu;
     if (fabsf(g) < 1e-3f) mu = 1.0f - 2.0f * xi;
     else {
-        float s = (1.0f - g * g) / (1.0f - g + 2.0f * g * xi);
-        mu = (1.0f + g * g - s * s) / (2.0f * g);
+        float s = fdiv(1.0f - g * g, 1.0f - g + 2.0f * g * xi);
+        mu = fdiv(1.0f + g * g - s * s, 2.0f * g);
     }
     return fminf(fmaxf(mu, -1.0f), 1.0f);
 }
@@ -218,7 +266,7 @@ __device__ __forceinline__ float hg_sample_mu(float g, float xi)
 __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2)
 {
     float sign = n.z >= 0.0f ? 1.0f : -1.0f;
-    float a = -1.0f / (sign + n.z);
+    float a = fdiv(-1.0f, sign + n.z);
     float b = n.x * n.y * a;
     b1 = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
     b2 = f3(b, sign + n.y * n.y * a, -n.y);
@@ -227,8 +275,8 @@ __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2)
 __device__ __forceinline__ void camera_ray(const CamDev& cam, int px, int py, float jx, float jy, float3& o,
                                            float3& d)
 {
-    float sx = 2.0f * ((float)px + jx) / (float)cam.w - 1.0f;
-    float sy = 1.0f - 2.0f * ((float)py + jy) / (float)cam.h;
+    float sx = fdiv(2.0f * ((float)px + jx), (float)cam.w) - 1.0f;
+    float sy = 1.0f - fdiv(2.0f * ((float)py + jy), (float)cam.h);
     if (cam.kind == VDBC_CAM_ORTHO) {
         float a = sx * cam.sxs, b = sy * cam.sys;
         o = f3(__fmaf_rn(b, cam.up.x, __fmaf_rn(a, cam.right.x, cam.eye.x)),
@@ -407,7 +455,7 @@ struct SingleSource {
 
 // many jobs of one payload type P: their constants and grids staged in
 // shared memory
-template <int P>
+template <int P, int D>
 struct BatchSource {
     static constexpr bool kMulti = true;
     static constexpr bool kCollective = false;
@@ -429,13 +477,22 @@ struct BatchSource {
         // the payload is the group's, fixed at compile time (one kernel with a
         // run-time dispatch over the three samplers, and one trilinear switching
         // per voxel, both measured slower: 150.6 and 162.9 ms for the 32-job frame)
-        return vdb_trilinear<P>(grids[i], x, y, z, a);
+        return vdb_trilinear<P, D>(grids[i], x, y, z, a);
     }
 };
 
 // The tracker loop shared by the single-job and the batch kernels.
 // stride > 1 renders every stride-th path only (the autotuner's sample of a frame)
-template <bool kUseCoarse, class Src>
+//
+// kPhased = false: in one iteration a lane goes through every block its path
+// needs (ray start, free flight, lookup and collision, ray end), so the warp
+// runs every block that any of its lanes needs.  kPhased = true: the warp
+// runs one block per iteration, the one the most of its lanes wait for (ties:
+// lookup, flight, start, end); a lane moves one block forward when its block
+// runs.  Each lane's arithmetic is the same either way (equal images).
+enum : int { kPhLook = 0, kPhFlight = 1, kPhStart = 2, kPhEnd = 3 };
+
+template <bool kUseCoarse, class Src, bool kPhased = false>
 __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
                                         int chunk, unsigned stride)
 {
@@ -453,6 +510,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
     int steps_in_cell = 0, guard = 0;
     bool start = false;   // a ray to start before the next free flight
     bool searching = false;   // the ray's next occupied cell is still being searched for
+    bool pend_look = false;   // (phased) a lookup waits at o + tcur d
     unsigned long long pool_next = 0, pool_end = 0;   // this warp's share of the work counter
     Track tr;
     Accessor acc;
@@ -520,9 +578,25 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         const uint32_t* cbits = src.cbits(jb);
         const int cx_n = J.cx_n, cy_n = J.cy_n;
 
+        int P = kPhLook;      // (phased) the block this iteration runs
+        if constexpr (kPhased) {
+            const bool live = mode == kDelta || mode == kRatio;
+            const int cl = __popc(__ballot_sync(0xffffffffu, live && !start && pend_look));
+            const int cf = __popc(__ballot_sync(0xffffffffu, live && !start && !pend_look));
+            const int cs = __popc(__ballot_sync(0xffffffffu, start));
+            const int ce = __popc(__ballot_sync(0xffffffffu, mode < 0));
+            int best = cl;
+            if (cf > best) { P = kPhFlight; best = cf; }
+            if (cs > best) { P = kPhStart; best = cs; }
+            if (ce > best) { P = kPhEnd; best = ce; }
+        }
+
         // ---- the lane's pending ray (camera ray, light ray or next bounce):
-        // box clip and first occupied cell, from one place in the code
-        if (start) {
+        // box clip and first occupied cell, from one place in the code.
+        // (Holding starts back until more lanes wait for one, and running the
+        // block then for all of them, measured slower at every threshold:
+        // 16.0 ms with no hold, 16.3 at 8 waiting lanes, 17.5 at 16.)
+        if (start && (!kPhased || P == kPhStart)) {
             start = false;
             searching = false;
             float tin, tout;
@@ -545,7 +619,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         // ratio: attenuate)
         bool look = false;
         float3 x = f3(0.f, 0.f, 0.f);
-        if (mode == kDelta || mode == kRatio) {
+        if ((mode == kDelta || mode == kRatio) && !start && (!kPhased || (P == kPhFlight && !pend_look))) {
             bool ended = false, parked = false;
             if (searching) {   // the search for the ray's next occupied cell goes on
                 const int st = next_cell<kUseCoarse>(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w);
@@ -557,7 +631,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 Rng rng{pixel, J.sample_base + sample, J.k0, J.k1};
                 U4 r = (mode == kDelta) ? rng.draw(call++, 0) : rng.draw(lcall++, 1);
                 VDBC_EVENT(w, 3);
-                tau = -logf(1.0f - u01(r.x));
+                tau = -flog(1.0f - u01(r.x));
                 ua = u01(r.y); ub = u01(r.z); uc = u01(r.w);
             }
             // spend tau over as many cells as it lasts (cheap inner walk), so
@@ -591,33 +665,47 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 w.flags |= kErrTrackSteps;
                 mode = -mode;            // give up on this ray (reported through the error word)
             } else {
-                float t = __fadd_rn(tr.tcur, __fdiv_rn(tau, tr.mj));
+                float t = __fadd_rn(tr.tcur, fdiv(tau, tr.mj));
                 tr.tcur = t;
                 tau = -1.0f;
+                if constexpr (kPhased) {
+                    pend_look = true;
+                } else {
+                    x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
+                    look = true;
+                }
+            }
+        }
+        if constexpr (kPhased) {
+            if (P == kPhLook && pend_look) {
+                const float t = tr.tcur;
                 x = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
                 look = true;
+                pend_look = false;
             }
         }
         // ---- the density lookup: per lane, or for a learned grid by the whole
         // warp at once (its network runs on warp-wide tiles)
         float dens = 0.0f;
         if constexpr (Src::kCollective) {
-            __syncwarp();
-            dens = src.collective(look, x.x, x.y, x.z, acc);
+            if (!kPhased || P == kPhLook) {      // P is the same in every lane
+                __syncwarp();
+                dens = src.collective(look, x.x, x.y, x.z, acc);
+            }
         }
         if (look) {
             if constexpr (!Src::kCollective) dens = src.sample(jb, x.x, x.y, x.z, acc);
             float sigma = __fmul_rn(med.sigma_scale, dens);
             ++w.lookups;
             if (mode == kRatio) {
-                T = __fmul_rn(T, __fsub_rn(1.0f, __fdiv_rn(sigma, tr.mj)));
+                T = __fmul_rn(T, __fsub_rn(1.0f, fdiv(sigma, tr.mj)));
             } else if (__fmul_rn(ua, tr.mj) < sigma) {
                 // real collision: scatter, then trace the light ray from here (inline: the
                 // same code out of line cost 17.0 against 16.1 ms on the benchmark frame)
                 beta *= med.albedo;
                 ph = hg_eval(dot3(d, med.sun_dir), med.g);
                 float mu = hg_sample_mu(med.g, ub);
-                float st_ = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+                float st_ = fsqrt(fmaxf(0.0f, 1.0f - mu * mu));
                 float sphi, cphi;
                 sincospif(2.0f * uc, &sphi, &cphi);
                 float3 b1, b2;
@@ -633,7 +721,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             }
         }
         // ---- a ray ended (negative mode): escape, or the light ray's contribution
-        if (mode < 0) {
+        if (mode < 0 && (!kPhased || P == kPhEnd)) {
             bool finished = false;
             if (mode == -kDelta) {
                 L.x += beta * med.env_rad.x; L.y += beta * med.env_rad.y; L.z += beta * med.env_rad.z;
@@ -692,8 +780,8 @@ constexpr int pt_min_blocks()
 
 // gbits: nwords fine occupancy words followed by ncwords coarse words; the
 // parts that fit in `smem_words` are staged in shared memory (coarse first)
-template <class S, bool kUseCoarse>
-__global__ void __launch_bounds__(256, (pt_min_blocks<S, kUseCoarse>()))
+template <class S, bool kUseCoarse, bool kPhased = false, int kBlocks = pt_min_blocks<S, kUseCoarse>()>
+__global__ void __launch_bounds__(256, kBlocks)
     k_pt(S smp, JobView job, const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
          DevStats* __restrict__ st, int chunk)
 {
@@ -710,12 +798,12 @@ __global__ void __launch_bounds__(256, (pt_min_blocks<S, kUseCoarse>()))
     }
     __syncthreads();
     SingleSource<S> src{job, smp, bits, cbits};
-    pt_loop<kUseCoarse>(src, job.items, st, chunk, 1u);
+    pt_loop<kUseCoarse, SingleSource<S>, kPhased>(src, job.items, st, chunk, 1u);
 }
 
 // the jobs of one payload type in one persistent launch; frame[0] numbers the
 // progressive frame, so frame f renders sample ids [f*spp, (f+1)*spp)
-template <int kThreads, bool kUseCoarse, int kPayload>
+template <int kThreads, bool kUseCoarse, int kPayload, int kDepth>
 __global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads)
     k_pt_batch(const JobView* __restrict__ jobs, const GridView* __restrict__ grids, int n,
                unsigned long long nitems, const int* __restrict__ frame, DevStats* __restrict__ st, int chunk,
@@ -731,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, (kUseCoarse ? 512 : 1024) / kThreads
         sg[i] = grids[i];
     }
     __syncthreads();
-    BatchSource<kPayload> src{sj, sg, n};
+    BatchSource<kPayload, kDepth> src{sj, sg, n};
     pt_loop<kUseCoarse>(src, nitems, st, chunk, stride);
 }
 
@@ -1219,14 +1307,14 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     return j;
 }
 
-template <class S, bool kUseCoarse>
+template <class S, bool kUseCoarse, bool kPhased = false, int kBlocks = pt_min_blocks<S, kUseCoarse>()>
 vdbc_status launch_pt_t(const S& smp, const JobView& job, const uint32_t* bits, int nwords, int ncwords,
                         DevStats* stats, int chunk, cudaStream_t s)
 {
     int smem_words = std::min<int>(nwords + ncwords, (int)(kSmemBitsMax / 4));
     if (smem_words < ncwords) smem_words = 0;
     size_t smem = (size_t)smem_words * 4;
-    auto kern = k_pt<S, kUseCoarse>;
+    auto kern = k_pt<S, kUseCoarse, kPhased, kBlocks>;
     if (smem > 48 * 1024) VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
@@ -1247,8 +1335,72 @@ vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, in
     if constexpr (!S::kCollective) {
         if (coarse) return launch_pt_t<S, true>(smp, job, bits, nwords, ncwords, stats, chunk, s);
     }
+    if constexpr (std::is_same<S, VdbSamplerT<0>>::value) {
+        // VDBC_PT_PHASED=1: the one-block-per-iteration loop, for measuring it
+        // against the default.  Measured equal: 12.28 against 12.34 ms on the
+        // 512^3 frame, 59.48 against 59.49 ms on the cloud (and at 5 or 6 blocks
+        // per SM, fused or phased, within 0.1 ms of these)
+        static const bool phased = [] { const char* e = std::getenv("VDBC_PT_PHASED"); return e && e[0] == '1'; }();
+        if (phased) return launch_pt_t<S, false, true>(smp, job, bits, nwords, ncwords, stats, chunk, s);
+    }
     return launch_pt_t<S, false>(smp, job, bits, nwords, ncwords, stats, chunk, s);
 }
+
+// The grid's node tables (root, upper and lower nodes, tiles: the front of
+// its block, before the leaves) as a persisting L2 window on the render's
+// stream while the path tracer runs: every tree descent reads them.
+// VDBC_L2_NODES=1 turns it on; the window is cleared after the launch.  Off
+// by default: measured no faster (12.30 against 12.34 ms on the 512^3 frame,
+// whose 54 MB grid L2 holds anyway; 59.47 against 59.50 ms on the cloud, whose
+// node tables stay hot in L2 without the window).
+template <class S>
+struct NodeWindow {
+    static void set(const S&, cudaStream_t) {}
+    static void clear(cudaStream_t) {}
+};
+
+template <int P, int D, int T>
+struct NodeWindow<VdbSamplerT<P, D, T>> {
+    static bool enabled()
+    {
+        static const bool on = [] {
+            const char* e = std::getenv("VDBC_L2_NODES");
+            if (!(e && e[0] == '1')) return false;
+            int dev = 0, maxp = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess || maxp <= 0) {
+                cudaGetLastError();
+                return false;
+            }
+            // a context limit: it ends with this process
+            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            return true;
+        }();
+        return on;
+    }
+    static void set(const VdbSamplerT<P, D, T>& smp, cudaStream_t s)
+    {
+        if (!enabled()) return;
+        cudaStreamAttrValue a{};
+        a.accessPolicyWindow.base_ptr = const_cast<uint32_t*>(smp.g.root);
+        a.accessPolicyWindow.num_bytes = (size_t)(static_cast<const char*>(smp.g.leaves) -
+                                                  reinterpret_cast<const char*>(smp.g.root));
+        a.accessPolicyWindow.hitRatio = 1.0f;
+        a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        if (cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a) != cudaSuccess) cudaGetLastError();
+    }
+    static void clear(cudaStream_t s)
+    {
+        if (!enabled()) return;
+        cudaStreamAttrValue a{};
+        a.accessPolicyWindow.num_bytes = 0;
+        if (cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a) != cudaSuccess) cudaGetLastError();
+    }
+};
 
 template <class S>
 vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const MedDev& med, int spp, uint64_t seed,
@@ -1294,9 +1446,11 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
     JobView job = make_job(mj, cam, med, spp, seed, accum);
+    NodeWindow<S>::set(smp, s);
     record_kernel_start(stats, s);
     st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, 0, coarse, s);
     record_kernel_stop(stats, s);
+    NodeWindow<S>::clear(s);
     if (st == VDBC_OK) {
         KLAUNCH(k_pt_resolve<<<blocks_for(npix, 256), 256, 0, s>>>(accum, (int)npix, spp, out));
         cudaError_t e = cudaGetLastError();
@@ -1571,8 +1725,8 @@ bool tune_file_lookup(const std::string& key, vdbc_tuning* t)
     while (std::fgets(line, sizeof(line), f)) {
         char k[900];
         vdbc_tuning v{};
-        if (std::sscanf(line, "%899s %d %d %d %f", k, &v.threads, &v.chunk, &v.coarse, &v.frame_ms) == 5 &&
-            key == k) {
+        if (std::sscanf(line, "%899s %d %d %d %d %f", k, &v.threads, &v.chunk, &v.coarse, &v.depth, &v.frame_ms) == 6 &&
+            key == k && (v.depth == 1 || v.depth == 2)) {
             *t = v;
             found = true;
         }
@@ -1587,7 +1741,7 @@ void tune_file_store(const std::string& key, const vdbc_tuning& t)
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), t.threads, t.chunk, t.coarse, t.frame_ms);
+    std::fprintf(f, "%s %d %d %d %d %.4f\n", key.c_str(), t.threads, t.chunk, t.coarse, t.depth, t.frame_ms);
     std::fclose(f);
 }
 
@@ -1603,8 +1757,8 @@ struct BatchGroup {
     vdbc::GridView* d_grids = nullptr;
     unsigned long long nitems = 0;
     vdbc::DevStats* stats = nullptr;
-    unsigned blocks[2][2] = {{0, 0}, {0, 0}};     // launch configuration per [256 threads][coarse level]
-    size_t smem[2][2] = {{0, 0}, {0, 0}};
+    unsigned blocks[2][2][2] = {};     // launch configuration per [256 threads][coarse level][accessor depth 2]
+    size_t smem[2][2][2] = {};
 };
 
 struct vdbc_batch {
@@ -1622,7 +1776,7 @@ struct vdbc_batch {
     float** d_outs = nullptr;
     int* d_frame = nullptr;
     size_t max_npix = 0;
-    vdbc_tuning tuning{256, 256, 1, 0, 0.0f};
+    vdbc_tuning tuning{256, 256, 1, 1, 0.0f};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> allocs;
@@ -1665,13 +1819,13 @@ vdbc_status batch_select_bits(vdbc_batch* b, bool coarse, cudaStream_t s)
 
 // grid size and shared memory of the batched tracker for a block size; called
 // before any capture (it sets a function attribute and queries occupancy)
-template <int kThreads, bool kUseCoarse, int P>
+template <int kThreads, bool kUseCoarse, int P, int D>
 vdbc_status group_config_t(BatchGroup& g)
 {
-    unsigned* blocks = &g.blocks[kThreads == 256][kUseCoarse];
-    size_t* smem = &g.smem[kThreads == 256][kUseCoarse];
+    unsigned* blocks = &g.blocks[kThreads == 256][kUseCoarse][D == 2];
+    size_t* smem = &g.smem[kThreads == 256][kUseCoarse][D == 2];
     *smem = (sizeof(JobView) + sizeof(GridView)) * g.members.size();
-    auto kern = k_pt_batch<kThreads, kUseCoarse, P>;
+    auto kern = k_pt_batch<kThreads, kUseCoarse, P, D>;
     if (*smem > 48 * 1024)
         VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
     int per_sm = 0;
@@ -1682,46 +1836,46 @@ vdbc_status group_config_t(BatchGroup& g)
     return VDBC_OK;
 }
 
-template <int kThreads, bool kUseCoarse, int P>
+template <int kThreads, bool kUseCoarse, int P, int D>
 vdbc_status group_launch_t(vdbc_batch* b, BatchGroup& g, int chunk, unsigned stride, cudaStream_t s)
 {
-    if (g.blocks[kThreads == 256][kUseCoarse] == 0) VDBC_TRY((group_config_t<kThreads, kUseCoarse, P>(g)));
-    const unsigned blocks = g.blocks[kThreads == 256][kUseCoarse];
-    const size_t smem = g.smem[kThreads == 256][kUseCoarse];
-    KLAUNCH((k_pt_batch<kThreads, kUseCoarse, P><<<blocks, kThreads, smem, s>>>(
+    if (g.blocks[kThreads == 256][kUseCoarse][D == 2] == 0) VDBC_TRY((group_config_t<kThreads, kUseCoarse, P, D>(g)));
+    const unsigned blocks = g.blocks[kThreads == 256][kUseCoarse][D == 2];
+    const size_t smem = g.smem[kThreads == 256][kUseCoarse][D == 2];
+    KLAUNCH((k_pt_batch<kThreads, kUseCoarse, P, D><<<blocks, kThreads, smem, s>>>(
         g.d_jobs, g.d_grids, (int)g.members.size(), g.nitems, b->d_frame, g.stats, chunk, stride)));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
 
 // the group's kernel for its payload type
-template <int kThreads, bool kUseCoarse>
+template <int kThreads, bool kUseCoarse, int D>
 vdbc_status group_launch(vdbc_batch* b, BatchGroup& g, int chunk, unsigned stride, cudaStream_t s)
 {
-    if (g.payload == VDBC_FP16) return group_launch_t<kThreads, kUseCoarse, 1>(b, g, chunk, stride, s);
-    if (g.payload == VDBC_FP8) return group_launch_t<kThreads, kUseCoarse, 2>(b, g, chunk, stride, s);
-    return group_launch_t<kThreads, kUseCoarse, 0>(b, g, chunk, stride, s);
+    if (g.payload == VDBC_FP16) return group_launch_t<kThreads, kUseCoarse, 1, D>(b, g, chunk, stride, s);
+    if (g.payload == VDBC_FP8) return group_launch_t<kThreads, kUseCoarse, 2, D>(b, g, chunk, stride, s);
+    return group_launch_t<kThreads, kUseCoarse, 0, D>(b, g, chunk, stride, s);
 }
 
-template <int kThreads, bool kUseCoarse>
+template <int kThreads, bool kUseCoarse, int D>
 vdbc_status group_config(BatchGroup& g)
 {
-    if (g.payload == VDBC_FP16) return group_config_t<kThreads, kUseCoarse, 1>(g);
-    if (g.payload == VDBC_FP8) return group_config_t<kThreads, kUseCoarse, 2>(g);
-    return group_config_t<kThreads, kUseCoarse, 0>(g);
+    if (g.payload == VDBC_FP16) return group_config_t<kThreads, kUseCoarse, 1, D>(g);
+    if (g.payload == VDBC_FP8) return group_config_t<kThreads, kUseCoarse, 2, D>(g);
+    return group_config_t<kThreads, kUseCoarse, 0, D>(g);
 }
 
-template <int kThreads, bool kUseCoarse>
+template <int kThreads, bool kUseCoarse, int D>
 vdbc_status batch_config(vdbc_batch* b)
 {
-    for (BatchGroup& g : b->groups) VDBC_TRY((group_config<kThreads, kUseCoarse>(g)));
+    for (BatchGroup& g : b->groups) VDBC_TRY((group_config<kThreads, kUseCoarse, D>(g)));
     return VDBC_OK;
 }
 
-template <int kThreads, bool kUseCoarse>
+template <int kThreads, bool kUseCoarse, int D>
 vdbc_status batch_launch_pt(vdbc_batch* b, int chunk, unsigned stride, cudaStream_t s)
 {
-    for (BatchGroup& g : b->groups) VDBC_TRY((group_launch<kThreads, kUseCoarse>(b, g, chunk, stride, s)));
+    for (BatchGroup& g : b->groups) VDBC_TRY((group_launch<kThreads, kUseCoarse, D>(b, g, chunk, stride, s)));
     return VDBC_OK;
 }
 
@@ -1732,11 +1886,14 @@ vdbc_status batch_frame(vdbc_batch* b, const vdbc_tuning& t, bool accumulate, cu
     for (BatchGroup& g : b->groups) VDBC_CUDA(cudaMemsetAsync(g.stats, 0, sizeof(DevStats), s));
     VDBC_CUDA(cudaMemsetAsync(b->accum, 0, b->accum_words * sizeof(unsigned long long), s));
     if (t.threads == 128) {
-        if (t.coarse) VDBC_TRY((batch_launch_pt<128, true>(b, t.chunk, stride, s)));
-        else VDBC_TRY((batch_launch_pt<128, false>(b, t.chunk, stride, s)));
+        if (t.coarse) VDBC_TRY((batch_launch_pt<128, true, 1>(b, t.chunk, stride, s)));
+        else VDBC_TRY((batch_launch_pt<128, false, 1>(b, t.chunk, stride, s)));
+    } else if (t.depth == 2) {
+        if (t.coarse) VDBC_TRY((batch_launch_pt<256, true, 2>(b, t.chunk, stride, s)));
+        else VDBC_TRY((batch_launch_pt<256, false, 2>(b, t.chunk, stride, s)));
     } else {
-        if (t.coarse) VDBC_TRY((batch_launch_pt<256, true>(b, t.chunk, stride, s)));
-        else VDBC_TRY((batch_launch_pt<256, false>(b, t.chunk, stride, s)));
+        if (t.coarse) VDBC_TRY((batch_launch_pt<256, true, 1>(b, t.chunk, stride, s)));
+        else VDBC_TRY((batch_launch_pt<256, false, 1>(b, t.chunk, stride, s)));
     }
     if (accumulate) {
         dim3 grid((unsigned)((b->max_npix + 255) / 256), (unsigned)b->n);
@@ -1782,20 +1939,23 @@ vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
         g_tune_cache[key] = cached;
         return VDBC_OK;
     }
-    const int threads[] = {128, 256};
+    // launch shapes: (threads per block, accessor cache depth) pairs, work
+    // items a warp takes per refill (32, 64, 256: one, two or eight paths per
+    // lane per refill), coarse DDA level on or off
+    const int shapes[][2] = {{128, 1}, {256, 1}, {256, 2}};
     const int chunks[] = {32, 64, 256};
     const int coarses[] = {1, 0};
     cudaEvent_t e0, e1;
     VDBC_CUDA(cudaEventCreate(&e0));
     VDBC_CUDA(cudaEventCreate(&e1));
-    vdbc_tuning best{256, 256, 1, 0, 1e30f};
+    vdbc_tuning best{256, 256, 1, 1, 1e30f};
     vdbc_status st = VDBC_OK;
     for (int co : coarses) {
         st = batch_select_bits(b, co != 0, s);
         if (st != VDBC_OK) break;
-        for (int th : threads)
+        for (const auto& sh : shapes)
             for (int ch : chunks) {
-                vdbc_tuning t{th, ch, co, 0, 0.0f};
+                vdbc_tuning t{sh[0], ch, co, sh[1], 0.0f};
                 // every kTuneStride-th path of a frame: a sample spread over all jobs
                 st = batch_frame(b, t, false, s, kTuneStride);           // warm-up
                 if (st == VDBC_OK && cudaEventRecord(e0, s) != cudaSuccess) st = set_error(VDBC_ERR_CUDA, "tune event");
@@ -1828,8 +1988,9 @@ vdbc_status batch_capture(vdbc_batch* b, cudaStream_t s)
 {
     VDBC_TRY(batch_select_bits(b, b->tuning.coarse != 0, s));
     const bool c = b->tuning.coarse != 0;
-    if (b->tuning.threads == 128) VDBC_TRY(c ? (batch_config<128, true>(b)) : (batch_config<128, false>(b)));
-    else VDBC_TRY(c ? (batch_config<256, true>(b)) : (batch_config<256, false>(b)));
+    if (b->tuning.threads == 128) VDBC_TRY(c ? (batch_config<128, true, 1>(b)) : (batch_config<128, false, 1>(b)));
+    else if (b->tuning.depth == 2) VDBC_TRY(c ? (batch_config<256, true, 2>(b)) : (batch_config<256, false, 2>(b)));
+    else VDBC_TRY(c ? (batch_config<256, true, 1>(b)) : (batch_config<256, false, 1>(b)));
     VDBC_TRY(wait_stream(s));
     cudaStream_t cs = nullptr;
     VDBC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

@@ -83,6 +83,7 @@ def test_batch_matches_oracle_per_volume(env):
     b = v.vdbc_batch_create(structs, autotune=True, keep=jobs)
     t = v.vdbc_batch_get_tuning(b)
     assert t.threads in (128, 256) and t.chunk >= 32 and t.coarse in (0, 1) and t.frame_ms > 0
+    assert t.depth in (1, 2) and (t.depth == 1 or t.threads == 256)
     v.vdbc_batch_render_frames(b, 2)
     torch.cuda.synchronize()
     for j in jobs:
