@@ -119,9 +119,11 @@ struct KeyRun {
 // kMode 1: the volume's rows start on 16-byte boundaries (nx % 4 == 0 and an
 // aligned base), so a lane loads four voxels at once: lane = 8 * rsub + sub
 // takes float4 `sub` of row 4g + rsub, and a warp covers four rows a load.
-// kMode 0: scalar loads, one voxel a lane, for every other volume.  (Float4
-// loads of misaligned rows, masked to the brick row, measured slower than
-// the scalar loads on the 994-wide cloud: 2.39 against 2.24 ms.)
+// kMode 2: scalar loads, one voxel a lane, for every other volume, each warp
+// stepping one brick row through the z slices.  kMode 0: the scalar loads
+// with the row index split per row (kept for comparison).  (Float4 loads of
+// misaligned rows, masked to the brick row, measured slower than the scalar
+// loads on both clouds, also as nine 16-byte blocks per row.)
 template <int kMode, int kRowsInFlight = 8>
 __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict__ v, Dims d, int nbricks,
                                                          uint32_t* __restrict__ lo_key,
@@ -207,6 +209,58 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                         for (int j = 0; j < 4; ++j)
                             if (n[j]) bin_add(s_h, k[j], n[j]);
                     }
+                }
+            }
+        } else if constexpr (kMode == 2) {
+            // scalar loads with no index arithmetic per row: warp w takes brick
+            // row y = w of every z slice, lane = x, and the row pointer
+            // advances by one slice (the per-row index products of kMode 0
+            // kept the integer multiply pipe busy)
+            const bool valid = lane < ex;
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            if (warp < ey) {
+                const size_t slice = (size_t)d.nx * d.ny;
+                const float* p = v + ((size_t)z0 * d.ny + (y0 + warp)) * d.nx + x0 + lane;
+                for (int z = 0; z < ez; z += U) {
+                    uint32_t u[U];
+                    const float* a = p;
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        u[q] = 0u;
+                        if (valid && z + q < ez) u[q] = __float_as_uint(__ldg(a));
+                        a += slice;
+                    }
+                    p = a;
+                    uint32_t lk = 0xffffffffu, ln = 0u;            // the lane's run of one key
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        if (z + q >= ez) break;                    // warp-uniform
+                        const uint32_t w = u[q];
+                        const uint32_t key = w >> 16;
+                        if (valid) {
+                            bad |= ((w & 0x7f800000u) == 0x7f800000u);
+                            const uint32_t k = okey(w);
+                            kmin = min(kmin, k);
+                            kmax = max(kmax, k);
+                        }
+                        const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
+                        if (__all_sync(0xffffffffu, !valid || key == lead)) {
+                            run.add(lead, (uint32_t)__popc(vmask), lane, s_h);
+                            continue;
+                        }
+                        const bool inrun = valid && key == run.key;
+                        run.cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, inrun));
+                        if (valid && !inrun) {
+                            if (key == lk) {
+                                ++ln;
+                            } else {
+                                if (ln) bin_add(s_h, lk, ln);
+                                lk = key;
+                                ln = 1u;
+                            }
+                        }
+                    }
+                    if (ln) bin_add(s_h, lk, ln);
                 }
             }
         } else {
@@ -1158,11 +1212,17 @@ bool rows_aligned(const float* v, const Dims& d)
 void launch_pass1(const float* v, const Dims& d, int nb, unsigned grid, uint32_t* lo_key, uint32_t* hi_key,
                   unsigned long long* hist, int* nonfinite, cudaStream_t s)
 {
-    static const bool rows16 = [] { const char* e = std::getenv("VDBC_PASS1_ROWS"); return e && std::atoi(e) == 16; }();
+    // kMode 2 with 16 rows in flight for rows off a 16-byte boundary: the full-
+    // scale cloud (1987-voxel rows) encodes in 19.6 ms against 23.7 with the
+    // per-row index arithmetic of kMode 0 and 20.1 with 8 rows in flight
+    // (VDBC_PASS1_MODE=0 or 2 select those for measurement)
+    static const int mode = [] { const char* e = std::getenv("VDBC_PASS1_MODE"); return e ? std::atoi(e) : 3; }();
     if (rows_aligned(v, d))
         KLAUNCH(k_pass1<1><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
-    else if (rows16)
-        KLAUNCH((k_pass1<0, 16><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
+    else if (mode == 2)
+        KLAUNCH((k_pass1<2, 8><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
+    else if (mode == 3)
+        KLAUNCH((k_pass1<2, 16><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
     else
         KLAUNCH(k_pass1<0><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
 }
@@ -1181,7 +1241,8 @@ vdbc_status pass1_setup(int nbricks, unsigned* grid)
         if (e.first == dev) resident = e.second;
     if (resident == 0) {
         VDBC_CUDA(cudaFuncSetAttribute(k_pass1<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
-        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
+        VDBC_CUDA(cudaFuncSetAttribute(k_pass1<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
         VDBC_CUDA(cudaFuncSetAttribute(k_pass1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPass1Smem));
         int per_sm = 0, sms = 0;
         VDBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass1<0>, kPass1Threads, kPass1Smem));
