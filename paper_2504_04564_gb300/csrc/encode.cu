@@ -101,15 +101,17 @@ __host__ __device__ __forceinline__ uint32_t div_magic(int d) { return ((1u << 2
 __device__ __forceinline__ int div_small(int r, uint32_t m) { return (int)(((uint32_t)r * m) >> 21); }
 
 // per-warp run of one key (warp-uniform): counts it in registers, and adds
-// it to the block histogram when the key changes
+// it to the global histogram when the key changes (runs are long: empty
+// space, where a brick's every voxel may be one run; keeping them out of the
+// block histogram lets a brick with no other counts skip the flush)
 struct KeyRun {
     uint32_t key = 0xffffffffu, cnt = 0u;
-    __device__ __forceinline__ void add(uint32_t k, uint32_t n, int lane, uint32_t* h)
+    __device__ __forceinline__ void add(uint32_t k, uint32_t n, int lane, unsigned long long* g)
     {
         if (k == key) {
             cnt += n;
         } else {
-            if (cnt && lane == 0) bin_add(h, key, cnt);
+            if (cnt && lane == 0) atomicAdd(g + key, (unsigned long long)cnt);
             key = k;
             cnt = n;
         }
@@ -134,12 +136,18 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
     extern __shared__ __align__(16) uint32_t s_h[];
     __shared__ uint32_t s_min[2][kPass1Threads / 32], s_max[2][kPass1Threads / 32];
     __shared__ int s_bad;
+    __shared__ int s_dirty[2];      // the block histogram holds counts of the brick (parity p)
     for (int i = threadIdx.x; i < kPass1Words; i += kPass1Threads) s_h[i] = 0u;
-    if (threadIdx.x == 0) s_bad = 0;
+    if (threadIdx.x == 0) { s_bad = 0; s_dirty[0] = 0; s_dirty[1] = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int U = kRowsInFlight, kWarps = kPass1Threads / 32;
     bool bad = false;
+    bool dirty = false;             // this thread added to the block histogram in this brick
+    auto sadd = [&](uint32_t k, uint32_t n) {
+        bin_add(s_h, k, n);
+        dirty = true;
+    };
     int p = 0;
     for (int b = blockIdx.x; b < nbricks; b += gridDim.x, p ^= 1) {
         int bx, by, bz;
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                     const bool same = !ok[q] || (k0 == lead && (w[1] >> 16) == lead && (w[2] >> 16) == lead &&
                                                  (w[3] >> 16) == lead);
                     if (__all_sync(0xffffffffu, same)) {
-                        run.add(lead, 4u * (uint32_t)__popc(part), lane, s_h);
+                        run.add(lead, 4u * (uint32_t)__popc(part), lane, hist);
                     } else {
                         // keys equal to the warp's run join it; the lane's other
                         // keys, equal ones merged, take one add per distinct key
@@ -207,7 +215,7 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                                 if (n[j] && n[i] && k[i] == k[j]) { n[i] += n[j]; n[j] = 0u; }
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            if (n[j]) bin_add(s_h, k[j], n[j]);
+                            if (n[j]) sadd(k[j], n[j]);
                     }
                 }
             }
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                         }
                         const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
                         if (__all_sync(0xffffffffu, !valid || key == lead)) {
-                            run.add(lead, (uint32_t)__popc(vmask), lane, s_h);
+                            run.add(lead, (uint32_t)__popc(vmask), lane, hist);
                             continue;
                         }
                         const bool inrun = valid && key == run.key;
@@ -254,13 +262,13 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                             if (key == lk) {
                                 ++ln;
                             } else {
-                                if (ln) bin_add(s_h, lk, ln);
+                                if (ln) sadd(lk, ln);
                                 lk = key;
                                 ln = 1u;
                             }
                         }
                     }
-                    if (ln) bin_add(s_h, lk, ln);
+                    if (ln) sadd(lk, ln);
                 }
             }
         } else {
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                     }
                     const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
                     if (__all_sync(0xffffffffu, !valid || key == lead)) {
-                        run.add(lead, (uint32_t)__popc(vmask), lane, s_h);
+                        run.add(lead, (uint32_t)__popc(vmask), lane, hist);
                         continue;
                     }
                     // lanes holding the warp run's key join it; the others keep
@@ -305,16 +313,18 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                         if (key == lk) {
                             ++ln;
                         } else {
-                            if (ln) bin_add(s_h, lk, ln);
+                            if (ln) sadd(lk, ln);
                             lk = key;
                             ln = 1u;
                         }
                     }
                 }
-                if (ln) bin_add(s_h, lk, ln);
+                if (ln) sadd(lk, ln);
             }
         }
-        if (run.cnt && lane == 0) bin_add(s_h, run.key, run.cnt);
+        if (run.cnt && lane == 0) atomicAdd(hist + run.key, (unsigned long long)run.cnt);
+        if (__any_sync(0xffffffffu, dirty) && lane == 0) s_dirty[p] = 1;
+        dirty = false;
         kmin = __reduce_min_sync(0xffffffffu, kmin);
         kmax = __reduce_max_sync(0xffffffffu, kmax);
         if (lane == 0) { s_min[p][warp] = kmin; s_max[p][warp] = kmax; }
@@ -325,7 +335,8 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
             lo_key[b] = a;
             hi_key[b] = c;
         }
-        pass1_flush(s_h, hist);
+        if (s_dirty[p]) pass1_flush(s_h, hist);            // (a brick of runs alone left it empty)
+        if (threadIdx.x == 0) s_dirty[p ^ 1] = 0;
         __syncthreads();                                   // histogram clear before the next brick
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_bad, 1);

@@ -155,6 +155,27 @@ __device__ __forceinline__ bool clip_box(const Majorants& m, float3 o, float3 d,
     return t0 < t1;
 }
 
+// ray / box [lo, hi] (three lower then three upper bounds), t >= 0
+__device__ __forceinline__ bool clip_span(const float* box, float3 o, float3 d, float& tin, float& tout)
+{
+    float t0 = 0.0f, t1 = INFINITY;
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0.0f) {
+            if (oo[a] < box[a] || oo[a] > box[3 + a]) return false;
+        } else {
+            float ta = fdiv(box[a] - oo[a], dd[a]), tb = fdiv(box[3 + a] - oo[a], dd[a]);
+            if (ta > tb) { float s = ta; ta = tb; tb = s; }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        }
+    }
+    tin = t0;
+    tout = t1;
+    return t0 < t1;
+}
+
 // 3D-DDA over the macrocells (Amanatides-Woo stepping).  The next boundary of
 // each axis is kept and only the stepped axis is recomputed, from its cell
 // index (-1/2 + (c + [s > 0]) * cell - o) / d, so no error accumulates.
@@ -418,6 +439,29 @@ __device__ __forceinline__ int next_cell(Track& tr, const Majorants& m, const Me
     return kCellEnded;
 }
 
+// Division of a 32-bit n by an invariant d >= 1 with one high multiply, the
+// round-up method of Granlund and Montgomery ("Division by Invariant Integers
+// using Multiplication", PLDI 1994, Section 4): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), exact for every n.
+struct DivU32 {
+    uint32_t m;
+    int s1, s2;
+    __host__ void init(uint32_t d)
+    {
+        int l = 0;
+        while ((1ull << l) < (unsigned long long)d) ++l;
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / d + 1ull);
+        s1 = l > 0 ? 1 : 0;
+        s2 = l > 0 ? l - 1 : 0;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const
+    {
+        const uint32_t t = __umulhi(m, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+};
+
 // Constants of one render job as the tracker sees them.
 struct JobView {
     Majorants m;
@@ -427,10 +471,14 @@ struct JobView {
     const uint32_t* cbits;     // occupancy bit per kCoarse^3 block of macrocells
     int cx_n, cy_n;            // coarse grid size along x and y
     unsigned long long* accum; // 3 per pixel: the frame's radiance sums, 32.32 fixed point
+    const int* occ_box;        // macrocell index box of the positive majorants (lo xyz, hi xyz), or null
     int npix, spp, tiles_x;
     uint32_t k0, k1;           // Philox key = the seed
     uint32_t sample_base;      // sample id of the frame's first sample (progressive frames)
     unsigned long long item_begin, items;   // this job's range of the work counter
+    uint32_t per;              // work items per sample (8x4 tiles x 32)
+    int items32;               // items < 2^32: item decode by the invariant divisions below
+    DivU32 div_per, div_tiles_x;
 };
 
 // one job: constants in kernel parameters, the grid's payload fixed at compile time
@@ -442,6 +490,14 @@ struct SingleSource {
     const S& smp;
     const uint32_t* b;
     const uint32_t* cb;
+    const float* box;     // the clip box in index space (shared memory)
+    // rays are clipped to the box of the cells with a positive majorant: no
+    // free flight starts outside it, so starting the walk at its boundary
+    // changes no path
+    __device__ __forceinline__ bool clip(int, const Majorants&, float3 o, float3 d, float& tin, float& tout) const
+    {
+        return clip_span(box, o, d, tin, tout);
+    }
     __device__ __forceinline__ int find(unsigned long long, int) const { return 0; }
     __device__ __forceinline__ const JobView& job(int) const { return j; }
     __device__ __forceinline__ const uint32_t* bits(int) const { return b; }
@@ -470,6 +526,10 @@ struct BatchSource {
         return j;
     }
     __device__ __forceinline__ const JobView& job(int i) const { return jobs[i]; }
+    __device__ __forceinline__ bool clip(int, const Majorants& m, float3 o, float3 d, float& tin, float& tout) const
+    {
+        return clip_box(m, o, d, tin, tout);
+    }
     __device__ __forceinline__ const uint32_t* bits(int i) const { return jobs[i].bits; }
     __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
     __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
@@ -537,15 +597,28 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                     mode = kDone;
                 } else {
                     // item -> (job, sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
-                    // (a 32-bit form of this division measured no faster: 16.2 against 16.1 ms)
+                    // (the divisions by invariants take one high multiply each;
+                    // 64-bit division only for frames of 2^32 items or more)
                     jb = src.find(item, jb);
                     const JobView& F = src.job(jb);
-                    unsigned long long local = item - F.item_begin;
-                    unsigned long long per = F.items / (unsigned long long)F.spp;
-                    sample = (uint32_t)(local / per);
-                    uint32_t q = (uint32_t)(local % per), tile = q >> 5, in = q & 31;
-                    int px = (int)(tile % F.tiles_x) * 8 + (int)(in & 7);
-                    int py = (int)(tile / F.tiles_x) * 4 + (int)(in >> 3);
+                    const unsigned long long local = item - F.item_begin;
+                    uint32_t q, ty, tx;
+                    if (F.items32) {
+                        const uint32_t l32 = (uint32_t)local;
+                        sample = F.div_per.div(l32);
+                        q = l32 - sample * F.per;
+                        ty = F.div_tiles_x.div(q >> 5);
+                        tx = (q >> 5) - ty * (uint32_t)F.tiles_x;
+                    } else {
+                        const unsigned long long per = F.per;
+                        sample = (uint32_t)(local / per);
+                        q = (uint32_t)(local - (unsigned long long)sample * per);
+                        ty = (q >> 5) / (uint32_t)F.tiles_x;
+                        tx = (q >> 5) - ty * (uint32_t)F.tiles_x;
+                    }
+                    const uint32_t in = q & 31;
+                    int px = (int)tx * 8 + (int)(in & 7);
+                    int py = (int)ty * 4 + (int)(in >> 3);
                     if (px < F.cam.w && py < F.cam.h) {
                         VDBC_EVENT(w, 5);
                         pixel = (uint32_t)(py * F.cam.w + px);
@@ -600,7 +673,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             start = false;
             searching = false;
             float tin, tout;
-            if (clip_box(m, o, d, tin, tout)) {
+            if (src.clip(jb, m, o, d, tin, tout)) {
                 tr.dda.init(m, o, d, tin, tout);
                 tau = -1.0f;   // every ray starts a new free flight
                 VDBC_EVENT(w, 4);
@@ -786,6 +859,21 @@ __global__ void __launch_bounds__(256, kBlocks)
          DevStats* __restrict__ st, int chunk)
 {
     extern __shared__ uint32_t s_bits[];
+    __shared__ float s_box[6];
+    if (threadIdx.x == 0) {
+        const Majorants& m = job.m;
+        const float dims[3] = {(float)m.nx, (float)m.ny, (float)m.nz};
+        for (int a = 0; a < 3; ++a) { s_box[a] = -0.5f; s_box[3 + a] = dims[a] - 0.5f; }
+        if (job.occ_box) {
+            const float mc = (float)m.mc;
+            for (int a = 0; a < 3; ++a) {
+                const int lo = job.occ_box[a], hi = job.occ_box[3 + a];
+                // (no positive majorant anywhere: an empty box, every ray misses)
+                s_box[a] = lo <= hi ? __fsub_rn(__fmul_rn((float)lo, mc), 0.5f) : 1.0f;
+                s_box[3 + a] = lo <= hi ? fminf(__fsub_rn(__fmul_rn((float)(hi + 1), mc), 0.5f), dims[a] - 0.5f) : 0.0f;
+            }
+        }
+    }
     const uint32_t* cbits = gbits + nwords;
     const uint32_t* bits = gbits;
     if (ncwords <= smem_words) {
@@ -797,7 +885,7 @@ __global__ void __launch_bounds__(256, kBlocks)
         }
     }
     __syncthreads();
-    SingleSource<S> src{job, smp, bits, cbits};
+    SingleSource<S> src{job, smp, bits, cbits, s_box};
     pt_loop<kUseCoarse, SingleSource<S>, kPhased>(src, job.items, st, chunk, 1u);
 }
 
@@ -892,6 +980,17 @@ __global__ void k_occupancy(const float* __restrict__ mcmax, long long ncell, fl
     bool on = i < ncell && sigma_scale * mcmax[i] > 0.0f;
     unsigned b = __ballot_sync(0xffffffffu, on);
     if ((threadIdx.x & 31) == 0 && i < ncell) bits[i >> 5] = b;
+}
+
+// index box (lo xyz, hi xyz) of the macrocells whose occupancy bit is set;
+// box starts as (INT_MAX.., -1..)
+__global__ void k_occupied_box(const uint32_t* __restrict__ bits, int mx, int my, long long ncell, int* __restrict__ box)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell || !((bits[i >> 5] >> (i & 31)) & 1u)) return;
+    const int cx = (int)(i % mx), cy = (int)((i / mx) % my), cz = (int)(i / ((long long)mx * my));
+    atomicMin(box + 0, cx); atomicMin(box + 1, cy); atomicMin(box + 2, cz);
+    atomicMax(box + 3, cx); atomicMax(box + 4, cy); atomicMax(box + 5, cz);
 }
 
 template <class S>
@@ -1304,6 +1403,10 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     j.sample_base = 0;
     j.item_begin = 0;
     j.items = (unsigned long long)spp * (unsigned long long)j.tiles_x * (unsigned long long)((cam.h + 3) / 4) * 32ull;
+    j.per = (uint32_t)((unsigned long long)j.tiles_x * (unsigned long long)((cam.h + 3) / 4) * 32ull);
+    j.items32 = j.items < (1ull << 32) ? 1 : 0;
+    j.div_per.init(j.per);
+    j.div_tiles_x.init((uint32_t)j.tiles_x);
     return j;
 }
 
@@ -1342,6 +1445,19 @@ vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, in
         // per SM, fused or phased, within 0.1 ms of these)
         static const bool phased = [] { const char* e = std::getenv("VDBC_PT_PHASED"); return e && e[0] == '1'; }();
         if (phased) return launch_pt_t<S, false, true>(smp, job, bits, nwords, ncwords, stats, chunk, s);
+    }
+    if constexpr (S::kCollective) {
+        // learned grids: VDBC_PT_LEARNED = p2 / p3 (one block per iteration at
+        // 2 or 3 blocks per SM), f3 (fused at 3 blocks), for measuring them
+        // against the default (fused, 2 blocks)
+        static const int variant = [] {
+            const char* e = std::getenv("VDBC_PT_LEARNED");
+            if (!e || std::strlen(e) != 2) return 0;
+            return (e[0] == 'p' ? 10 : 0) + (e[1] - '0');
+        }();
+        if (variant == 12) return launch_pt_t<S, false, true, 2>(smp, job, bits, nwords, ncwords, stats, chunk, s);
+        if (variant == 13) return launch_pt_t<S, false, true, 3>(smp, job, bits, nwords, ncwords, stats, chunk, s);
+        if (variant == 3) return launch_pt_t<S, false, false, 3>(smp, job, bits, nwords, ncwords, stats, chunk, s);
     }
     return launch_pt_t<S, false>(smp, job, bits, nwords, ncwords, stats, chunk, s);
 }
@@ -1433,7 +1549,7 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
     int ncwords = (cxn * cyn * czn + 31) / 32;
     uint32_t* bits = nullptr;
     unsigned long long* accum = nullptr;
-    VDBC_TRY(dev_alloc(reinterpret_cast<void**>(&bits), (size_t)(nwords + ncwords) * 4, s));
+    VDBC_TRY(dev_alloc(reinterpret_cast<void**>(&bits), (size_t)(nwords + ncwords + 8) * 4, s));
     vdbc_status st = dev_alloc(reinterpret_cast<void**>(&accum), (size_t)npix * 3 * sizeof(unsigned long long), s);
     if (st != VDBC_OK) { dev_free(bits, s); return st; }
     VDBC_CUDA(cudaMemsetAsync(accum, 0, (size_t)npix * 3 * sizeof(unsigned long long), s));
@@ -1446,6 +1562,15 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
     JobView job = make_job(mj, cam, med, spp, seed, accum);
+    static const bool use_box = [] { const char* e = std::getenv("VDBC_PT_BOX"); return !(e && e[0] == '0'); }();
+    if (use_box) {
+        // the clip box of the occupied macrocells, after the occupancy words
+        int* box = reinterpret_cast<int*>(bits + nwords + ncwords);
+        VDBC_CUDA(cudaMemsetAsync(box, 0x7f, 3 * sizeof(int), s));
+        VDBC_CUDA(cudaMemsetAsync(box + 3, 0xff, 3 * sizeof(int), s));
+        KLAUNCH(k_occupied_box<<<blocks_for(ncell, 256), 256, 0, s>>>(bits, mj.mx, mj.my, ncell, box));
+        job.occ_box = box;
+    }
     NodeWindow<S>::set(smp, s);
     record_kernel_start(stats, s);
     st = launch_pt<S>(smp, job, bits, nwords, ncwords, stats, 0, coarse, s);
