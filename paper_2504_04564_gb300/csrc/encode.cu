@@ -223,19 +223,26 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
             // scalar loads with no index arithmetic per row: warp w takes brick
             // row y = w of every z slice, lane = x, and the row pointer
             // advances by one slice (the per-row index products of kMode 0
-            // kept the integer multiply pipe busy)
+            // kept the integer multiply pipe busy).  Lanes past the brick's
+            // edge load lane ex - 1's voxel again: a duplicate changes neither
+            // the range nor whether a step is one key, so only the histogram
+            // adds test `valid`.  The range is kept on the raw bits (unsigned
+            // max, signed min and max) and mapped to the total-order keys once
+            // per brick; non-finite values are found from the brick's keys.
             const bool valid = lane < ex;
-            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            const uint32_t nvalid = (uint32_t)ex;
             if (warp < ey) {
                 const size_t slice = (size_t)d.nx * d.ny;
-                const float* p = v + ((size_t)z0 * d.ny + (y0 + warp)) * d.nx + x0 + lane;
+                const float* p = v + ((size_t)z0 * d.ny + (y0 + warp)) * d.nx + x0 + min(lane, ex - 1);
+                uint32_t umax = 0u;
+                int imin = 0x7fffffff, imax = (int)0x80000000;
                 for (int z = 0; z < ez; z += U) {
                     uint32_t u[U];
                     const float* a = p;
 #pragma unroll
                     for (int q = 0; q < U; ++q) {
                         u[q] = 0u;
-                        if (valid && z + q < ez) u[q] = __float_as_uint(__ldg(a));
+                        if (z + q < ez) u[q] = __float_as_uint(__ldg(a));
                         a += slice;
                     }
                     p = a;
@@ -245,15 +252,16 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                         if (z + q >= ez) break;                    // warp-uniform
                         const uint32_t w = u[q];
                         const uint32_t key = w >> 16;
-                        if (valid) {
-                            bad |= ((w & 0x7f800000u) == 0x7f800000u);
-                            const uint32_t k = okey(w);
-                            kmin = min(kmin, k);
-                            kmax = max(kmax, k);
+                        umax = max(umax, w);
+                        imin = min(imin, (int)w);
+                        imax = max(imax, (int)w);
+                        if (__all_sync(0xffffffffu, key == run.key)) {
+                            run.cnt += nvalid;
+                            continue;
                         }
-                        const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);     // lane 0 is always valid
-                        if (__all_sync(0xffffffffu, !valid || key == lead)) {
-                            run.add(lead, (uint32_t)__popc(vmask), lane, hist);
+                        const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);
+                        if (__all_sync(0xffffffffu, key == lead)) {
+                            run.add(lead, nvalid, lane, hist);
                             continue;
                         }
                         const bool inrun = valid && key == run.key;
@@ -270,6 +278,12 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                     }
                     if (ln) sadd(lk, ln);
                 }
+                // smallest in the total order: the largest negative pattern if
+                // there is one, else the smallest non-negative; largest: the
+                // largest non-negative if there is one, else the negative
+                // pattern nearest -0
+                kmin = okey((umax & 0x80000000u) ? umax : (uint32_t)imin);
+                kmax = okey(imax >= 0 ? (uint32_t)imax : (uint32_t)imin);
             }
         } else {
             const bool valid = lane < ex;
@@ -334,6 +348,8 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
             for (int w = 1; w < kWarps; ++w) { a = min(a, s_min[p][w]); c = max(c, s_max[p][w]); }
             lo_key[b] = a;
             hi_key[b] = c;
+            // a NaN or infinity has a key beyond okey(+inf) or below okey(-inf)
+            if (c >= 0xff800000u || a <= 0x007fffffu) bad = true;
         }
         if (s_dirty[p]) pass1_flush(s_h, hist);            // (a brick of runs alone left it empty)
         if (threadIdx.x == 0) s_dirty[p ^ 1] = 0;
@@ -538,7 +554,7 @@ __device__ __forceinline__ unsigned block_count(unsigned x, unsigned* s, unsigne
 // the N largest keys among non-empty bricks, ties to the lower index; one CTA
 // of 1024 threads.  A key is held as fkey + 1 (0 for an empty brick), in
 // registers when there are at most 4096 bricks.
-constexpr int kSelThreads = 1024, kSelCache = 4;
+constexpr int kSelThreads = 1024, kSelCache = 4, kSelBatch = 8;
 
 __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long* __restrict__ fkey,
                                                         const uint8_t* __restrict__ empty, int nb,
@@ -601,13 +617,23 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
         for (int shift = 56; shift >= 0; shift -= 8) {
             for (int i = threadIdx.x; i < 256; i += kSelThreads) s_hist[i] = 0u;
             __syncthreads();
-            for (int base = 0; base < nb; base += kSelThreads) {
-                const int i = base + threadIdx.x;
-                const unsigned long long k = i < nb ? key1(i) : 0ull;
-                const bool in = k != 0ull && (k & pmask) == prefix;
-                const unsigned digit = in ? (unsigned)(k >> shift) & 255u : 256u;
-                const unsigned peers = __match_any_sync(0xffffffffu, digit);
-                if (in && lane == __ffs(peers) - 1) atomicAdd(&s_hist[digit], (unsigned)__popc(peers));
+            // kSelBatch keys a thread loaded before any is counted, so that
+            // their L2 latencies overlap
+            for (int base = 0; base < nb; base += kSelThreads * kSelBatch) {
+                unsigned long long kk[kSelBatch];
+#pragma unroll
+                for (int j = 0; j < kSelBatch; ++j) {
+                    const int i = base + j * kSelThreads + threadIdx.x;
+                    kk[j] = i < nb ? key1(i) : 0ull;
+                }
+#pragma unroll
+                for (int j = 0; j < kSelBatch; ++j) {
+                    const unsigned long long k = kk[j];
+                    const bool in = k != 0ull && (k & pmask) == prefix;
+                    const unsigned digit = in ? (unsigned)(k >> shift) & 255u : 256u;
+                    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+                    if (in && lane == __ffs(peers) - 1) atomicAdd(&s_hist[digit], (unsigned)__popc(peers));
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -631,27 +657,40 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
     }
     const unsigned long long T = V - 1ull;
     const long long need = take - gt;   // keys equal to T, lowest brick indices first
+    // kSelBatch chunks of kSelThreads bricks a round: a tie's rank is the ties
+    // of earlier rounds, of earlier chunks of this round, of earlier warps of
+    // its chunk and of earlier lanes of its warp
+    __shared__ unsigned s_ties[kSelBatch][kSelThreads / 32];
     if (threadIdx.x == 0) s_run = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < nb; base += kSelThreads) {
-        const int i = base + threadIdx.x;
-        const unsigned long long k = i < nb ? key1(i) : 0ull;
-        const bool eq = k != 0ull && k == T + 1ull;
-        // exclusive rank of this thread's tie within the chunk
-        const unsigned bal = __ballot_sync(0xffffffffu, eq);
-        const int in_warp = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) s[w] = __popc(bal);
-        __syncthreads();
-        long long before = s_run + in_warp;
-        for (int q = 0; q < w; ++q) before += s[q];
-        if (i < nb) active[i] = (k != 0ull && (k > T + 1ull || (eq && before < need))) ? 1 : 0;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long t = 0;
-            for (int q = 0; q < kSelThreads / 32; ++q) t += s[q];
-            s_run += t;
+    for (int base = 0; base < nb; base += kSelThreads * kSelBatch) {
+        unsigned long long kk[kSelBatch];
+        unsigned bal[kSelBatch];
+#pragma unroll
+        for (int j = 0; j < kSelBatch; ++j) {
+            const int i = base + j * kSelThreads + threadIdx.x;
+            kk[j] = i < nb ? key1(i) : 0ull;
         }
+#pragma unroll
+        for (int j = 0; j < kSelBatch; ++j) {
+            bal[j] = __ballot_sync(0xffffffffu, kk[j] != 0ull && kk[j] == T + 1ull);
+            if (lane == 0) s_ties[j][w] = __popc(bal[j]);
+        }
+        __syncthreads();
+        long long before = s_run;
+#pragma unroll
+        for (int j = 0; j < kSelBatch; ++j) {
+            const int i = base + j * kSelThreads + threadIdx.x;
+            long long mine = before + __popc(bal[j] & ((1u << lane) - 1u));
+            for (int q = 0; q < w; ++q) mine += s_ties[j][q];
+            const unsigned long long k = kk[j];
+            const bool eq = k != 0ull && k == T + 1ull;
+            if (i < nb) active[i] = (k != 0ull && (k > T + 1ull || (eq && mine < need))) ? 1 : 0;
+            for (int q = 0; q < kSelThreads / 32; ++q) before += s_ties[j][q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_run = before;
         __syncthreads();
     }
     if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
@@ -878,21 +917,40 @@ __global__ void k_leaf_status(const float* __restrict__ v, Dims d, const int* __
     }
     uint32_t first = 0;
     bool same = true;
-#pragma unroll 4
-    for (int r = 0; r < 16; ++r) {
-        int n = lane + 32 * r;
-        float val;
-        if (cd.corner == 0 && d.nx <= 8 && d.ny <= 8 && d.nz <= 8) {
-            // a single leaf holds both corners
-            int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
-            bool at = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
-            val = (x < d.nx && y < d.ny && z < d.nz && at) ? __ldg(v + ((size_t)z * d.ny + y) * d.nx + x) : B;
-        } else {
-            val = cand_value(v, d, cd, n, B);
+    if (cd.corner < 0) {
+        // a leaf of an active brick: lane = x + 8 (y & 3), step r covers
+        // y + 4 (r & 1), z = r >> 1; the 16 loads are in flight before any
+        // is compared
+        const int x = cd.li * 8 + (lane & 7), yb = cd.lj * 8 + (lane >> 3), zb = cd.lk * 8;
+        const bool xv = x < d.nx;
+        const size_t slice = (size_t)d.nx * d.ny;
+        const float* p = v + ((size_t)zb * d.ny + yb) * d.nx + x;
+        uint32_t u[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const bool in = xv && yb + 4 * (r & 1) < d.ny && zb + (r >> 1) < d.nz;
+            u[r] = in ? __float_as_uint(__ldg(p + (size_t)(r >> 1) * slice + (size_t)((r & 1) * 4) * d.nx)) : bsel[1];
         }
-        uint32_t u = __float_as_uint(val);
-        if (r == 0) first = __shfl_sync(0xffffffffu, u, 0);
-        same &= (u == first);
+        first = __shfl_sync(0xffffffffu, u[0], 0);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) same &= (u[r] == first);
+    } else {
+#pragma unroll 4
+        for (int r = 0; r < 16; ++r) {
+            int n = lane + 32 * r;
+            float val;
+            if (cd.corner == 0 && d.nx <= 8 && d.ny <= 8 && d.nz <= 8) {
+                // a single leaf holds both corners
+                int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
+                bool at = (x == 0 && y == 0 && z == 0) || (x == d.nx - 1 && y == d.ny - 1 && z == d.nz - 1);
+                val = (x < d.nx && y < d.ny && z < d.nz && at) ? __ldg(v + ((size_t)z * d.ny + y) * d.nx + x) : B;
+            } else {
+                val = cand_value(v, d, cd, n, B);
+            }
+            uint32_t u = __float_as_uint(val);
+            if (r == 0) first = __shfl_sync(0xffffffffu, u, 0);
+            same &= (u == first);
+        }
     }
     bool constant = __all_sync(0xffffffffu, same);
     if (lane == 0) {
@@ -1162,29 +1220,32 @@ __global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* 
         }
     }
     const int nparts = s_nparts;
+    const size_t slice = (size_t)d.nx * d.ny;
     for (int i = 0; i < nparts; ++i) {
         const int ax0 = s_part[i][0], ex = s_part[i][1];
         const int ay0 = s_part[i][2] & 0xffff, az0 = s_part[i][2] >> 16;
-        const int ey = s_part[i][3] & 0xffff, rows = ey * (s_part[i][3] >> 16);
-        const uint32_t mey = div_magic(ey);
+        const int ey = s_part[i][3] & 0xffff, ez = s_part[i][3] >> 16;
+        // a warp task: row y of the part over U consecutive z slices, the
+        // row pointer stepping one slice a load (no index products per row);
+        // lanes past the part's width read its last column again, which
+        // changes neither extreme
         constexpr int U = 8;
-        for (int r0 = warp; r0 < rows; r0 += kW * U) {
-            float t[U];
+        const int nzc = (ez + U - 1) / U;
+        const uint32_t mey = div_magic(ey);
+        for (int t = warp; t < ey * nzc; t += kW) {
+            const int zc = div_small(t, mey), y = t - zc * ey;
+            const int nz = min(U, ez - zc * U);
+            const float* p = v + ((size_t)(az0 + zc * U) * d.ny + (ay0 + y)) * d.nx + ax0 + min(lane, ex - 1);
+            float t8[U];
 #pragma unroll
             for (int q = 0; q < U; ++q) {
-                const int row = r0 + kW * q;
-                t[q] = INFINITY;
-                if (lane < ex && row < rows) {
-                    const int z = div_small(row, mey), y = row - z * ey;
-                    t[q] = __ldg(v + ((size_t)(az0 + z) * d.ny + (ay0 + y)) * d.nx + ax0 + lane);
-                }
+                t8[q] = q < nz ? __ldg(p) : t8[0];
+                p += slice;
             }
 #pragma unroll
             for (int q = 0; q < U; ++q) {
-                if (lane < ex && r0 + kW * q < rows) {
-                    vmin = fminf(vmin, t[q]);
-                    vmax = fmaxf(vmax, t[q]);
-                }
+                vmin = fminf(vmin, t8[q]);
+                vmax = fmaxf(vmax, t8[q]);
             }
         }
     }

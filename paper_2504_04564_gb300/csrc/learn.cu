@@ -20,10 +20,12 @@
 //     its macrocell ranges are taken from the decoded values.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
 #include "learn.cuh"
+#include "tcgen05.cuh"
 #include "vdbc_host.h"
 
 namespace vdbc {
@@ -237,6 +239,21 @@ struct ExplicitSamples {
         rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
         return ok ? __ldg(T + q) : 0.0f;
     }
+    struct Next {};            // (rows are read when their tile starts)
+    // one thread's whole row q (the tensor-memory kernel): the 32 bf16 row
+    // columns as 16 words, the target, and whether the row exists
+    __device__ __forceinline__ float row1(long long q, uint32_t (&w)[16], bool& ok) const
+    {
+        ok = q < n;
+        const float* x = X + q * kMlpIn;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = ok ? pack_bf16(__ldg(x + 3 + 2 * k), __ldg(x + 4 + 2 * k)) : 0u;
+        w[8] = ok ? pack_bf16(__ldg(x), __ldg(x + 1)) : 0u;
+        w[9] = ok ? pack_bf16(__ldg(x + 2), 0.0f) : 0u;
+#pragma unroll
+        for (int k = 10; k < 16; ++k) w[k] = 0u;
+        return ok ? __ldg(T + q) : 0.0f;
+    }
 };
 
 // samples drawn from the leaves: sample s of training leaf a is voxel
@@ -272,6 +289,67 @@ struct LeafSamples {
         rp[2 ^ sw] = make_uint4(pack_bf16(u, vv), pack_bf16(w, 0.0f), 0u, 0u);
         rp[3 ^ sw] = make_uint4(0u, 0u, 0u, 0u);
         return lm.x != 0.0f ? __fdiv_rn(__fsub_rn(v, lm.y), lm.x) : 0.0f;
+    }
+    // one thread's next row for the tensor-memory kernel, the same draw and
+    // values as row(), fetched in three stages so that each dependent load
+    // (leaf index; leaf position, latent and metadata; the drawn voxel) is in
+    // flight during one contraction round of the current tile
+    struct Next {
+        bool ok;
+        int s, nv;
+        uint32_t leaf, p, raw;
+        uint32_t zw[8];
+        float2 sm, lm;
+    };
+    __device__ __forceinline__ void fetch1(Next& f, long long q, long long n) const
+    {
+        f.ok = q < n;
+        f.s = (int)(q & ((1 << lg_s) - 1));
+        f.leaf = f.ok ? __ldg(list + (q >> lg_s)) : 0u;
+    }
+    __device__ __forceinline__ void fetch2(Next& f) const
+    {
+        if (!f.ok) return;
+        f.p = __ldg(pos + f.leaf);
+        // (the latent is in L2; its wait overlaps the round's MMA)
+        const float4* L = reinterpret_cast<const float4*>(lat + (size_t)f.leaf * kMlpLatent);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 z = __ldg(L + k);
+            f.zw[2 * k] = pack_bf16(z.x, z.y);
+            f.zw[2 * k + 1] = pack_bf16(z.z, z.w);
+        }
+    }
+    __device__ __forceinline__ void fetch3(Next& f) const
+    {
+        if (!f.ok) return;
+        const int stratum = kLeafN >> lg_s;
+        const U4 rr = philox4x32_10(f.p, step, (uint32_t)f.s, kDrawTag, k0, k1);
+        f.nv = f.s * stratum + (int)(rr.x & (uint32_t)(stratum - 1));
+        f.sm = src.payload != 0 ? __ldg(src.meta + f.leaf) : make_float2(0.f, 0.f);
+        f.lm = __ldg(lmeta + f.leaf);
+        const size_t o = (size_t)f.leaf * kLeafN + f.nv;
+        if (src.payload == 0) f.raw = __ldg(reinterpret_cast<const uint32_t*>(src.leaves) + o);
+        else if (src.payload == 1) f.raw = __ldg(reinterpret_cast<const unsigned short*>(src.leaves) + o);
+        else f.raw = __ldg(reinterpret_cast<const unsigned char*>(src.leaves) + o);
+    }
+    // the fetched row as 16 words (latent, position, zeros) and its target
+    // (a voxel decoded as leaf_value_t does)
+    __device__ __forceinline__ float finish(const Next& f, uint32_t (&w)[16]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = 0u;
+        if (!f.ok) return 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = f.zw[k];
+        const float v = src.payload == 0 ? __uint_as_float(f.raw)
+                        : src.payload == 1 ? __fmaf_rn(f.sm.x, __half2float(__ushort_as_half((unsigned short)f.raw)), f.sm.y)
+                                           : __fmaf_rn(f.sm.x, e4m3_to_float((uint8_t)f.raw), f.sm.y);
+        const float u = __fdiv_rn((float)(f.nv & 7), 7.0f), vv = __fdiv_rn((float)((f.nv >> 3) & 7), 7.0f),
+                    ww = __fdiv_rn((float)(f.nv >> 6), 7.0f);
+        w[8] = pack_bf16(u, vv);
+        w[9] = pack_bf16(ww, 0.0f);
+        return f.lm.x != 0.0f ? __fdiv_rn(__fsub_rn(v, f.lm.y), f.lm.x) : 0.0f;
     }
 };
 
@@ -605,6 +683,378 @@ __global__ void k_sum_parts(const float* __restrict__ part, int nb, float* __res
     }
 }
 
+// ---------------------------------------------------------------- training on tcgen05
+// The gradient of k_mlp_grad (same bf16 roundings of the operands, FP32
+// sums, FP32 bias and w3 gradients) on the fifth-generation tensor cores.  A
+// CTA of 128 threads takes tiles of 128 samples, one row a thread; every
+// contraction is one M = 128, N = 32 MMA (K = 32 as two K = 16 steps) issued
+// by one thread into tensor memory, and read back a row a thread:
+//   a1 = X W1^T, a2 = H W2^T (H = bf(relu(a1 + b1))), dh1 = (bf(dh2) W2)
+//   masked, dx = bf(dh1) W1, and the weight gradients
+//   [gW2; gW1] += G^T [H | X] over the tile's 128 samples, where G holds
+//   bf(dh2) in columns 0-31 and bf(dh1) in 32-63: M = 128 rows of G's
+//   columns, K = the 128 samples, accumulated in tensor memory over all of
+//   the CTA's tiles.
+// Accumulator lanes 64-127 of the weight gradients are never read, so G's
+// columns 64-127 are free: each warp sums its 32 rows of the bias and w3
+// gradient terms (and of the latent gradients) per column through them, in
+// a fixed order, so a thread keeps three running sums instead of 96.  The
+// next tile's samples are fetched in three dependent stages, one per
+// contraction round, so their gathers overlap the current tile's MMAs.  With
+// 56 KB of shared memory, 128 tensor-memory columns and at most 128
+// registers a thread, four CTAs share an SM.
+// The same shared-memory tile is the K-major A of one MMA and the MN-major
+// A or B of another: core matrices are 8 rows by 8 bf16 along the row.
+constexpr int kT5Rows = 128;
+constexpr uint32_t kT5SrX = 384;       // row-block stride of X: column blocks 0-2 (row columns 0-23)
+constexpr uint32_t kT5Sr = 512;        // row-block stride of a 32-column tile (4 column blocks)
+constexpr uint32_t kT5SrG = 2048;      // row-block stride of the 128-column tile G
+constexpr uint32_t kT5Sc = 128;        // column-block stride
+constexpr uint32_t kT5Cols = 128;      // tensor-memory columns: scratch 0-31, gW2 32-63, gW1 64-95
+// X's fourth column block (row columns 24-31) is not stored: the MMAs read
+// the next row block's first block (or H's, after the last row block) in its
+// place, finite values that meet zero weights in a1 and land in gW1 columns
+// that are never read
+constexpr size_t kT5OffX = 0, kT5OffH = 6144, kT5OffG = 14336, kT5OffW = 47104, kT5OffP = 55296,
+                 kT5OffZ = kT5OffP + 3 * kMlpHid * 4, kT5OffL = kT5OffZ + 4 * kMlpLatent * 4,
+                 kT5OffBar = kT5OffL + 4 * 8, kT5Smem = kT5OffBar + 16;
+static_assert(kT5OffH == 16 * kT5SrX && kT5OffG == kT5OffH + 16 * kT5Sr && kT5OffW == kT5OffG + 16 * kT5SrG,
+              "tile layout");
+static_assert(kT5Smem <= 56 * 1024, "four CTAs an SM");
+constexpr int kT5WaitPolls = 1 << 26;
+
+__device__ __forceinline__ void t5_store_floats(uint8_t* tile, uint32_t sr, int r, int col0, const float* v)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<uint4*>(tile + tc::tile_off(r, col0 + 8 * k, sr, kT5Sc)) =
+            make_uint4(pack_bf16(v[8 * k], v[8 * k + 1]), pack_bf16(v[8 * k + 2], v[8 * k + 3]),
+                       pack_bf16(v[8 * k + 4], v[8 * k + 5]), pack_bf16(v[8 * k + 6], v[8 * k + 7]));
+}
+
+// the warp's 4 KB of staging in G's columns 64-127 (one 1 KB piece in each of
+// its four row blocks), column-major: value (row r of the warp, column c) at
+// piece c >> 3, byte (c & 7) * 128 + 4 r.  A row's stores have fixed offsets
+// and consecutive lanes hit consecutive banks; a column is 128 contiguous
+// bytes, read as eight 16-byte groups, lane c starting at group c & 7 so that
+// the eight lanes of a quarter-warp read eight different bank groups.
+__device__ __forceinline__ uint8_t* t5_stage(uint8_t* G, int warp) { return G + (uint32_t)warp * 4u * kT5SrG + 1024u; }
+
+template <int kCols>
+__device__ __forceinline__ void t5_stage_store(uint8_t* G, int warp, int lane, const float (&v)[32])
+{
+    float* p = reinterpret_cast<float*>(t5_stage(G, warp)) + lane;
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) p[(c >> 3) * (kT5SrG / 4) + (c & 7) * 32] = v[c];
+}
+
+// the warp's 32 rows of v summed per column: lane c returns column c (a
+// fixed order of rows for each lane)
+__device__ __forceinline__ float t5_colsum(uint8_t* G, int tid, const float (&v)[32])
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    t5_stage_store<32>(G, warp, lane, v);
+    __syncwarp();
+    const uint8_t* col = t5_stage(G, warp) + (lane >> 3) * kT5SrG + (lane & 7) * 128;
+    float s[2] = {0.0f, 0.0f};
+#pragma unroll 4
+    for (int g = 0; g < 8; ++g) {
+        const float4 q = *reinterpret_cast<const float4*>(col + (((g + lane) & 7) << 4));
+        s[g & 1] += (q.x + q.y) + (q.z + q.w);
+    }
+    __syncwarp();
+    return s[0] + s[1];
+}
+
+// latent columns 0-15 of the warp's rows: lane c + 16 h returns column c
+// summed over rows 16 h .. 16 h + 15
+__device__ __forceinline__ float t5_latsum(uint8_t* G, int tid, const float (&v)[32])
+{
+    const int lane = tid & 31, warp = tid >> 5, c = lane & 15, h = lane >> 4;
+    t5_stage_store<kMlpLatent>(G, warp, lane, v);
+    __syncwarp();
+    const uint8_t* col = t5_stage(G, warp) + (c >> 3) * kT5SrG + (c & 7) * 128 + h * 64;
+    float s = 0.0f;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const float4 q = *reinterpret_cast<const float4*>(col + (((g + c) & 3) << 4));
+        s += (q.x + q.y) + (q.z + q.w);
+    }
+    __syncwarp();
+    return s;
+}
+
+template <class Src>
+__global__ void __launch_bounds__(kT5Rows, 4) k_mlp_grad_tc(Src src, long long nsamples, int lg_s, float inv_n,
+                                                            const float* __restrict__ params, float* __restrict__ part,
+                                                            double* __restrict__ loss_part, float* __restrict__ gx)
+{
+    extern __shared__ __align__(1024) uint8_t s5[];
+    uint8_t* X = s5 + kT5OffX;
+    uint8_t* H = s5 + kT5OffH;
+    uint8_t* G = s5 + kT5OffG;
+    uint8_t* W1B = s5 + kT5OffW;              // [n = i][k = row column c]: W1[i][w1_column(c)]
+    uint8_t* W2B = W1B + 2048;                // [n = j][k = i]: W2[j][i]
+    uint8_t* W2T = W2B + 2048;                // [n = i][k = j]: W2[j][i]
+    uint8_t* W1T = W2T + 2048;                // [n = c][k = i]: W1[i][w1_column(c)]
+    float* b1s = reinterpret_cast<float*>(s5 + kT5OffP);
+    float* b2s = b1s + kMlpHid;
+    float* w3s = b2s + kMlpHid;
+    float* zpart = reinterpret_cast<float*>(s5 + kT5OffZ);   // [warp][16] latent column sums
+    double* lsum = reinterpret_cast<double*>(s5 + kT5OffL);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(s5 + kT5OffBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(s5 + kT5OffBar + 8);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // the network's bf16 operand tiles, FP32 biases, bf(w3)
+    for (int e = tid; e < 32 * 32; e += kT5Rows) {
+        const int n = e >> 5, k = e & 31, c1 = w1_column(k), c2 = w1_column(n);
+        const uint32_t o = tc::tile_off(n, k, kT5Sr, kT5Sc);
+        *reinterpret_cast<__nv_bfloat16*>(W1B + o) = __float2bfloat16_rn(c1 >= 0 ? params[kOffW1 + n * kMlpIn + c1] : 0.0f);
+        *reinterpret_cast<__nv_bfloat16*>(W2B + o) = __float2bfloat16_rn(params[kOffW2 + n * kMlpHid + k]);
+        *reinterpret_cast<__nv_bfloat16*>(W2T + o) = __float2bfloat16_rn(params[kOffW2 + k * kMlpHid + n]);
+        *reinterpret_cast<__nv_bfloat16*>(W1T + o) = __float2bfloat16_rn(c2 >= 0 ? params[kOffW1 + k * kMlpIn + c2] : 0.0f);
+    }
+    // H is read in place of X's missing column block before the first H is written
+    for (int e = tid; e < (int)(16 * kT5Sr / 16); e += kT5Rows) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid < kMlpHid) {
+        b1s[tid] = params[kOffB1 + tid];
+        b2s[tid] = params[kOffB2 + tid];
+        w3s[tid] = bfr(params[kOffW3 + tid]);
+    }
+    if (tid == 0) tc::mbar_init(bar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, kT5Cols);
+    tc::fence_smem_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+    const float b3 = params[kOffB3];
+    constexpr uint32_t kIdK = tc::idesc_bf16(128, 32, 0, 0), kIdMN = tc::idesc_bf16(128, 32, 1, 1);
+    const uint32_t aX = tc::smem_u32(X), aH = tc::smem_u32(H), aG = tc::smem_u32(G);
+    const uint32_t aW1B = tc::smem_u32(W1B), aW2B = tc::smem_u32(W2B), aW2T = tc::smem_u32(W2T), aW1T = tc::smem_u32(W1T);
+
+    // thread (warp w, lane c): column c of the bias and w3 gradients over warp w's rows
+    float sb1 = 0.0f, sb2 = 0.0f, sw3 = 0.0f, gb3 = 0.0f;
+    double loss = 0.0;
+    uint32_t phase = 0;
+    bool first = true, stalled = false;
+    const int S = Src::kLeaf ? (1 << lg_s) : kT5Rows;     // 16 .. 128: whole leaves per tile
+    const long long ntasks = (nsamples + kT5Rows - 1) / kT5Rows;
+    long long pend = -1;       // a tile whose leaves span warps: latents combined after the next barrier
+    // the pre-issue barrier of a round: the tile's shared-memory operands
+    // visible to the tensor core, the tensor-memory reads of the last round
+    // done, and a wait that ran out anywhere seen by every thread
+    auto round_barrier = [&]() {
+        tc::fence_smem_async();
+        tc::fence_before_sync();
+        stalled = __syncthreads_or(stalled) != 0;
+    };
+    // the round's MMAs complete; the warp reads its 32 lanes of scratch
+    auto round_wait = [&](float (&a)[32]) {
+        bool ok = tc::mbar_wait(bar, phase, kT5WaitPolls);
+        phase ^= 1u;
+        ok = __all_sync(0xffffffffu, ok);
+        tc::fence_after_sync();
+        if (ok) {
+            tc::tmem_ld32(tlane, a);
+        } else {
+            stalled = true;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) a[i] = 0.0f;
+        }
+    };
+    // latent gradients of the pending tile's leaves (S = 64, 128): warp k sums leaf slot k's warps in order
+    auto flush_pending = [&]() {
+        if (pend < 0) return;
+        const int per = S >> 5;
+        if (warp < kT5Rows / S && lane < kMlpLatent) {
+            float z = 0.0f;
+            for (int w2 = warp * per; w2 < warp * per + per; ++w2) z += zpart[w2 * kMlpLatent + lane];
+            const long long q0 = pend * kT5Rows + (long long)warp * S;
+            if constexpr (Src::kLeaf)
+                if (q0 < nsamples) gx[(size_t)__ldg(src.list + (q0 >> lg_s)) * kMlpLatent + lane] = z;
+        }
+        pend = -1;
+    };
+
+    typename Src::Next nx;
+    if constexpr (Src::kLeaf) {
+        src.fetch1(nx, (long long)blockIdx.x * kT5Rows + tid, nsamples);
+        src.fetch2(nx);
+        src.fetch3(nx);
+    }
+    for (long long task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const long long q = task * kT5Rows + tid;
+        const long long qn = q + (long long)gridDim.x * kT5Rows;
+        uint32_t w[16];
+        bool valid;
+        float tgt;
+        if constexpr (Src::kLeaf) {
+            valid = nx.ok;
+            tgt = src.finish(nx, w);
+        } else {
+            tgt = src.row1(q, w, valid);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            *reinterpret_cast<uint4*>(X + tc::tile_off(tid, 8 * k, kT5SrX, kT5Sc)) =
+                make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        round_barrier();
+        if (stalled) break;
+        flush_pending();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int k = 0; k < 2; ++k)
+                tc::mma_bf16(tbase, tc::smem_desc(aX + 256 * k, kT5Sc, kT5SrX), tc::smem_desc(aW1B + 256 * k, kT5Sc, kT5Sr),
+                             kIdK, k > 0);
+            tc::mma_commit(bar);
+        }
+        if constexpr (Src::kLeaf) src.fetch1(nx, qn, nsamples);
+        float a[kMlpHid];
+        round_wait(a);
+        uint32_t m1 = 0u, m2 = 0u;
+#pragma unroll
+        for (int i = 0; i < kMlpHid; ++i) {
+            const float v = __fadd_rn(a[i], b1s[i]);
+            if (v > 0.0f) { m1 |= 1u << i; a[i] = v; } else a[i] = 0.0f;
+        }
+        t5_store_floats(H, kT5Sr, tid, 0, a);
+        round_barrier();
+        if (stalled) break;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int k = 0; k < 2; ++k)
+                tc::mma_bf16(tbase, tc::smem_desc(aH + 256 * k, kT5Sc, kT5Sr), tc::smem_desc(aW2B + 256 * k, kT5Sc, kT5Sr),
+                             kIdK, k > 0);
+            tc::mma_commit(bar);
+        }
+        if constexpr (Src::kLeaf) src.fetch2(nx);
+        round_wait(a);
+        float y = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kMlpHid; ++j) {
+            const float v = __fadd_rn(a[j], b2s[j]);
+            if (v > 0.0f) { m2 |= 1u << j; a[j] = bfr(v); } else a[j] = 0.0f;
+            y = fmaf(w3s[j], a[j], y);
+        }
+        const float e = valid ? __fadd_rn(y, b3) - tgt : 0.0f;
+        loss += (double)e * e;
+        const float dy = 2.0f * e * inv_n;
+        gb3 += dy;
+#pragma unroll
+        for (int j = 0; j < kMlpHid; ++j) a[j] = dy * a[j];
+        sw3 += t5_colsum(G, tid, a);
+#pragma unroll
+        for (int j = 0; j < kMlpHid; ++j) a[j] = (m2 >> j) & 1u ? dy * w3s[j] : 0.0f;
+        sb2 += t5_colsum(G, tid, a);
+        t5_store_floats(G, kT5SrG, tid, 0, a);
+        round_barrier();
+        if (stalled) break;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int k = 0; k < 2; ++k)
+                tc::mma_bf16(tbase, tc::smem_desc(aG + 256 * k, kT5Sc, kT5SrG), tc::smem_desc(aW2T + 256 * k, kT5Sc, kT5Sr),
+                             kIdK, k > 0);
+            tc::mma_commit(bar);
+        }
+        if constexpr (Src::kLeaf) src.fetch3(nx);
+        round_wait(a);
+#pragma unroll
+        for (int i = 0; i < kMlpHid; ++i)
+            if (!((m1 >> i) & 1u)) a[i] = 0.0f;
+        sb1 += t5_colsum(G, tid, a);
+        t5_store_floats(G, kT5SrG, tid, 32, a);
+        round_barrier();
+        if (stalled) break;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int k = 0; k < 2; ++k)
+                tc::mma_bf16(tbase, tc::smem_desc(aG + 4 * kT5Sc + 256 * k, kT5Sc, kT5SrG),
+                             tc::smem_desc(aW1T + 256 * k, kT5Sc, kT5Sr), kIdK, k > 0);
+            // weight gradients: K = the 128 samples, 16 (two row blocks) a step
+            for (int k = 0; k < 8; ++k) {
+                const uint64_t ga = tc::smem_desc(aG + 2 * kT5SrG * k, kT5SrG, kT5Sc);
+                tc::mma_bf16(tbase + 32, ga, tc::smem_desc(aH + 2 * kT5Sr * k, kT5Sr, kT5Sc), kIdMN, !(first && k == 0));
+                tc::mma_bf16(tbase + 64, ga, tc::smem_desc(aX + 2 * kT5SrX * k, kT5SrX, kT5Sc), kIdMN, !(first && k == 0));
+            }
+            tc::mma_commit(bar);
+        }
+        first = false;
+        round_wait(a);                          // dx: row columns 0-15 latent, 16-18 position
+        if constexpr (Src::kLeaf) {
+            float z = t5_latsum(G, tid, a);     // lane c + 16 h: column c over rows 16 h .. 16 h + 15
+            if (S == 16) {
+                const long long q0 = task * kT5Rows + warp * 32 + (lane >> 4) * 16;
+                if (q0 < nsamples) gx[(size_t)__ldg(src.list + (q0 >> lg_s)) * kMlpLatent + (lane & 15)] = z;
+            } else {
+                z += __shfl_xor_sync(0xffffffffu, z, 16);
+                if (S == 32) {
+                    const long long q0 = task * kT5Rows + warp * 32;
+                    if (lane < kMlpLatent && q0 < nsamples) gx[(size_t)__ldg(src.list + (q0 >> lg_s)) * kMlpLatent + lane] = z;
+                } else {
+                    if (lane < kMlpLatent) zpart[warp * kMlpLatent + lane] = z;
+                    pend = task;
+                }
+            }
+        } else {
+            if (gx && valid) {
+#pragma unroll
+                for (int c = 0; c < kMlpIn; ++c) gx[q * kMlpIn + w1_column(c)] = a[c];
+            }
+        }
+    }
+    tc::fence_before_sync();
+    stalled = __syncthreads_or(stalled) != 0;
+    if (!stalled) flush_pending();
+    // the CTA's partial gradient in parameter order: weight gradients from
+    // tensor memory (warp 0: gW2 rows, warp 1: gW1 rows), the rest reduced
+    // over the warps in a fixed order through G (no MMA reads it any more)
+    float* P = part + (size_t)blockIdx.x * kPart;
+    tc::fence_after_sync();
+    if (warp < 2) {
+        float v[32];
+        if (!first && !stalled) tc::tmem_ld32(tlane + 32 + 32 * warp, v);
+        else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = 0.0f;
+        }
+        if (warp == 0) {
+#pragma unroll
+            for (int i = 0; i < kMlpHid; ++i) P[kOffW2 + lane * kMlpHid + i] = v[i];
+        } else {
+#pragma unroll
+            for (int c = 0; c < kMlpIn; ++c) P[kOffW1 + lane * kMlpIn + w1_column(c)] = v[c];
+        }
+    }
+    float* red = reinterpret_cast<float*>(G);     // [warp][100]
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
+        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    }
+    red[warp * 100 + lane] = sb1;
+    red[warp * 100 + 32 + lane] = sb2;
+    red[warp * 100 + 64 + lane] = sw3;
+    if (lane == 0) { red[warp * 100 + 96] = gb3; lsum[warp] = loss; }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 97) {
+        float v = red[tid];
+        for (int w2 = 1; w2 < 4; ++w2) v += red[w2 * 100 + tid];
+        const int dst = tid < 32 ? kOffB1 + tid : tid < 64 ? kOffB2 + tid - 32 : tid < 96 ? kOffW3 + tid - 64 : kOffB3;
+        P[dst] = v;
+    }
+    if (tid == 0) {
+        const double l = lsum[0] + lsum[1] + lsum[2] + lsum[3];
+        loss_part[blockIdx.x] = stalled ? (double)NAN : l;
+    }
+    if (stalled) tc::mbar_wait(bar, phase ^ 1u, kT5WaitPolls);    // (a stalled MMA: wait once more before freeing)
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, kT5Cols);
+}
+
 // one Adam step (Kingma and Ba, 2015) with bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, long long n, float lr, float c1, float c2)
@@ -801,27 +1251,55 @@ struct Pool {
     }
 };
 
-// gradient of the loss over n explicit or drawn samples into grad (and the
-// loss, if asked); part / loss_part hold grid partials
-// gradient of the loss over n samples (ntasks warp tasks) into grad, and the
-// loss if asked; part / loss_part hold the grid's partials
+// the training kernel: the tcgen05 one, or the mma.sync one with VDBC_MLP_TC=0
+// (200 steps over the 994 x 676 x 1225 cloud's 455,433 leaves at 64 samples:
+// 0.79 s with mma.sync)
+bool mlp_tc()
+{
+    static const bool on = [] { const char* e = std::getenv("VDBC_MLP_TC"); return !(e && e[0] == '0'); }();
+    return on;
+}
+
+// gradient of the loss over n samples (ntasks warp tasks of the mma.sync
+// kernel) into grad, and the loss if asked; part / loss_part hold the
+// grid's partials
 template <class Src>
 vdbc_status run_grad(const Src& src, long long ntasks, long long n, const float* params, float* part,
                      double* loss_part, int grid, float* grad, double* loss, float* gx, cudaStream_t s)
 {
-    auto kern = k_mlp_grad<Src>;
-    VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-    KLAUNCH(kern<<<grid, kTcWarps * 32, kTcSmem, s>>>(src, ntasks, (float)(1.0 / (double)n), params, part, loss_part,
-                                                      gx));
+    if (mlp_tc()) {
+        int lg_s = 0;
+        if constexpr (Src::kLeaf) lg_s = src.lg_s;
+        auto k5 = k_mlp_grad_tc<Src>;
+        VDBC_CUDA(cudaFuncSetAttribute(k5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem));
+        VDBC_CUDA(cudaFuncSetAttribute(k5, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        KLAUNCH(k5<<<grid, kT5Rows, kT5Smem, s>>>(src, n, lg_s, (float)(1.0 / (double)n), params, part, loss_part, gx));
+    } else {
+        auto kern = k_mlp_grad<Src>;
+        VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+        KLAUNCH(kern<<<grid, kTcWarps * 32, kTcSmem, s>>>(src, ntasks, (float)(1.0 / (double)n), params, part,
+                                                          loss_part, gx));
+    }
     KLAUNCH(k_sum_parts<<<blocks(kMlpParams, 256), 256, 0, s>>>(part, grid, grad, loss_part, 1.0 / (double)n, loss));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
 
-// blocks of the training kernel for ntasks warp tasks: at most one wave
-int grad_grid(long long ntasks)
+// blocks of the training kernel for ntasks warp tasks (mma.sync) or n
+// samples (tcgen05: 128-sample tiles): at most one wave
+int grad_grid(long long ntasks, long long n)
 {
     static int per_sm = -1;
+    if (mlp_tc()) {
+        // four CTAs an SM by construction: 128 registers a thread (launch
+        // bounds), at most 56 KB of shared memory, 128 of the SM's 512
+        // tensor-memory columns.  (The occupancy query answers 1 for this
+        // kernel; sized by it, the grid left three quarters of every SM idle:
+        // 200 steps on the cloud took 1.73 s, against 0.59 s at four.)
+        constexpr int per_sm5 = 512 / (int)kT5Cols;
+        const long long need = (n + kT5Rows - 1) / kT5Rows;
+        return (int)std::max<long long>(1, std::min<long long>(need, (long long)sm_count_dev() * per_sm5));
+    }
     if (per_sm < 0) {
         auto kern = k_mlp_grad<LeafSamples>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
@@ -989,7 +1467,7 @@ extern "C" vdbc_status vdbc_learn(const vdbc_grid* src, const vdbc_learn_params*
     const long long t0 = rs ? rs->step : 0;     // Adam steps already taken
     const long long nsamp = (long long)n_train << lg_s;
     if (lp->steps > 0 && nsamp > 0) {
-        const int grid = grad_grid((long long)n_train);
+        const int grid = grad_grid((long long)n_train, nsamp);
         VDBC_TRY(pool.get(&part, (size_t)grid * kPart));
         VDBC_TRY(pool.get(&loss_part, grid));
         VDBC_TRY(pool.get(&loss_hist, lp->steps));
@@ -1138,7 +1616,7 @@ extern "C" vdbc_status vdbc_learn_loss_grad(const float* params, const float* in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pool pool(s);
     const long long ntiles = (n + 15) / 16;
-    const int grid = grad_grid(ntiles);
+    const int grid = grad_grid(ntiles, (long long)n);
     float* part = nullptr;
     double *loss_part = nullptr, *dloss = nullptr;
     VDBC_TRY(pool.get(&part, (size_t)grid * kPart));

@@ -158,6 +158,9 @@ __device__ __forceinline__ uint32_t descend_to_node(const GridView& g, int li, i
     if (e & kTile) return entry_in_range(g, e) ? e : bounds_violation(g);
     return e < g.n_lower ? e : bounds_violation(g);
 #else
+    // (skipping the root load when the table is one entry naming upper node 0,
+    // as it is for every volume up to 4096 voxels an edge, measured slower:
+    // 8.97 against 8.59 ms on the 512^3 frame, 44.5 against 44.0 on the cloud)
     uint32_t e = __ldg(g.root + ((k >> 12) * g.ry + (j >> 12)) * g.rx + (i >> 12));
     if (e & kTile) return e;
     return __ldg(g.upper + (size_t)e * kUpperN + (((k >> 7) & 31) << 10) + (((j >> 7) & 31) << 5) + ((i >> 7) & 31));
@@ -200,8 +203,8 @@ constexpr uint32_t kNodeBits = 0x3F0u | (0x3F0u << 10) | (0x3F0u << 20) | (1u <<
 // it, so another leaf of the same 128^3 region costs one load.  Depth 1 is
 // the default: the tracker is bound by instruction issue, not by the load
 // latency the deeper cache saves (1024^2 x 16 spp frame of the 512^3 medium:
-// 15.6 ms at depth 1, 16.3 at depth 2; 1920x1080 x 64 spp of the
-// 1987x1351x2449 cloud at 1:10: 67.5 against 70.6 ms).
+// 9.0 ms at depth 1, 9.6 at depth 2; 1920x1080 x 64 spp of the
+// 1987x1351x2449 cloud at 1:10: 44.5 against 47.2 ms).
 #ifndef VDBC_ACC_DEPTH
 #define VDBC_ACC_DEPTH 1
 #endif
@@ -273,8 +276,8 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 // 2: stencils across one face (two leaves, the most frequent straddle) take
 //    each leaf's entry once, the rest go corner by corner.
 // 1 is the default: the second path's extra code costs more than the
-// descents it saves (15.6 against 17.5 ms on the 512^3 frame, 67.5 against
-// 70.3 ms on the cloud; the images are bit-identical).
+// descents it saves (9.0 against 9.9 ms on the 512^3 frame, 44.5 against
+// 46.4 ms on the cloud; the images are bit-identical).
 #ifndef VDBC_TRI_STRADDLE
 #define VDBC_TRI_STRADDLE 1
 #endif

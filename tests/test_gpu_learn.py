@@ -103,24 +103,30 @@ def test_loss_grad_matches_oracle(env, n):
     assert far.mean() <= 0.01 + 1.0 / n
 
 
-def test_one_training_step_matches_oracle(env):
+@pytest.mark.parametrize("S", [16, 32, 64, 128])
+def test_one_training_step_matches_oracle(env, S):
     """Step 0 replayed on the CPU: the same Philox draws pick the voxels, the
     targets are (v - offset) / scale in FP32, the oracle's FP64 gradient and
-    Adam step give the parameters after the step."""
+    Adam step give the parameters after the step.  The latents' first Adam
+    moment after one step from zero is (1 - beta1) g, so the saved state
+    also gives each leaf's latent gradient: the sum over its S samples of
+    the oracle's input gradient (leaves sit in one warp for S <= 32, across
+    two or four warps of a 128-sample tile for S = 64, 128)."""
     torch, v, orc = env["torch"], env["v"], env["orc"]
-    dims, S, seed, lr, lr_lat = (40, 36, 44), 16, 7, 1e-3, 1e-2
+    dims, seed, lr, lr_lat = (40, 36, 44), 7, 1e-3, 1e-2
     host, grid, e = source(env, "blobs", dims, 0, 1.0)
     nl = leaf_grid(dims)
     rng = np.random.default_rng(11)
     p0 = he_params(orc, rng)
     lat = (rng.random((nl[0] * nl[1] * nl[2], 16)) * 0.2 - 0.1).astype(np.float32)
     dev = env["dev"]
+    state = v.LearnCheckpoint.zeros(grid, torch, dev)
     learned, losses = v.vdbc_learn(grid, steps=1, samples_per_leaf=S, lr=lr, lr_latent=lr_lat, seed=seed,
                                    init_params=torch.from_numpy(p0).to(dev),
-                                   init_latents=torch.from_numpy(lat).to(dev))
+                                   init_latents=torch.from_numpy(lat).to(dev), save=state)
     p1 = v.vdbc_learn_get_params(learned)
     tree = orc.Tree(host, e["active"], e["background_bits"])
-    X, T = [], []
+    X, T, P = [], [], []
     stratum = 512 // S
     for lk in range(nl[2]):
         for lj in range(nl[1]):
@@ -137,9 +143,10 @@ def test_one_training_step_matches_oracle(env):
                     uvw = [np.float32(k / 7.0) for k in (nv & 7, (nv >> 3) & 7, nv >> 6)]
                     X.append(np.concatenate([uvw, lat[pos]]).astype(np.float64))
                     T.append(float(tgt))
-    X, T = np.array(X), np.array(T)
+                    P.append(pos)
+    X, T, P = np.array(X), np.array(T), np.array(P)
     assert len(T) == S * tree.counts()["leaves"]
-    rl, rg, _ = orc.mlp_loss_grad_bf16(p0.astype(np.float64), X, T)
+    rl, rg, rx = orc.mlp_loss_grad_bf16(p0.astype(np.float64), X, T)
     assert abs(losses[0] - rl) <= 1e-5 * rl
     ref = p0.astype(np.float64)
     m, vv = np.zeros_like(ref), np.zeros_like(ref)
@@ -148,6 +155,32 @@ def test_one_training_step_matches_oracle(env):
     assert big.sum() > 500
     assert np.max(np.abs(p1[big] - ref[big])) <= 1e-2 * lr
     assert np.max(np.abs(p1 - ref)) <= 2.0 * lr
+    # latent gradients, leaf by leaf
+    want = np.zeros((nl[0] * nl[1] * nl[2], 16))
+    np.add.at(want, P, rx[:, 3:19])
+    got = state.arrays["latents_m"].view(-1, 16).cpu().numpy().astype(np.float64) / (1.0 - 0.9)
+    leaves = np.unique(P)
+    assert np.abs(got[np.setdiff1d(np.arange(len(got)), leaves)]).max(initial=0.0) == 0.0
+    tol = 2e-3 * np.abs(want[leaves]).max()
+    far = np.abs(got[leaves] - want[leaves]).max(axis=1) > tol
+    assert far.mean() <= 0.01
+    assert np.abs(got[leaves] - want[leaves]).mean() <= 0.1 * tol
+
+
+def test_mma_sync_training_kernel_matches_oracle():
+    """The warp-level (mma.sync) training kernel, selected with VDBC_MLP_TC=0:
+    the same gradient and one-step checks, in a child process (the choice is
+    read once per process)."""
+    import os
+    import re
+    import subprocess
+    import sys
+    env = dict(os.environ, VDBC_MLP_TC="0")
+    r = subprocess.run([sys.executable, "-m", "pytest", __file__, "-q", "-x", "-p", "no:cacheprovider",
+                        "-k", "test_loss_grad_matches_oracle or test_one_training_step_matches_oracle"],
+                       env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    assert re.search(r"\b7 passed", r.stdout), r.stdout[-500:]
 
 
 # ------------------------------------------------------------------ decode and render
