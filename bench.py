@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--profile-learned", action="store_true",
                     help="ncu capture case of the learned codec: 50 training steps and two 512^2 x 16 spp "
                          "renders of a learned 512^3 medium")
+    ap.add_argument("--profile-encode", action="store_true",
+                    help="the encoder's capture case: the 994x676x1225 cloud encoded twice at 1:10")
+    ap.add_argument("--profile-case-full", action="store_true",
+                    help="the same grid rendered twice at the 512^3 block's 1024x1024 x 16 spp")
     ap.add_argument("--profile-case", action="store_true",
                     help="the ncu capture case: the 512^3 medium's grid at a 512x512 image, two renders")
     ap.add_argument("--save-cloud-grid", metavar="PATH",
@@ -847,23 +851,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_profile_case():
+def run_profile_case(full=False):
     """The capture case for `ncu --set full`: the 512^3 medium at 1:10 (same
     grid as the benchmark's 512^3 block), rendered twice at 512x512 x 16 spp so
-    that a full-section capture of the second launch stays small."""
+    that a full-section capture of the second launch stays small; with `full`,
+    at the block's own 1024x1024 x 16 spp (for one-pass DRAM counters)."""
     torch, v, volgen, scenes = _env()
     w = scenes.TURBULENCE_512
-    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], 512, 512))
+    n = w["width"] if full else 512
+    cam = v.make_camera(*scenes.pinhole_orbit(w["dims"], n, n))
     med = v.make_medium(v.MODE_PT, **w["medium"])
     vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
     g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"])
-    img = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
+    img = torch.empty((n, n, 4), dtype=torch.float32, device="cuda")
     for _ in range(2):
         v.vdbc_render(g, cam, med, w["spp"], SEED, img)
     torch.cuda.synchronize()
     st = v.vdbc_render_stats_get(g)
-    print(json.dumps({"profile_case": "turbulence512_r10_pt512sq_16spp", "lookups": int(st.lookups),
-                      "paths": int(st.paths)}))
+    print(json.dumps({"profile_case": "turbulence512_r10_pt%dsq_16spp" % n, "lookups": int(st.lookups),
+                      "paths": int(st.paths), "kernel_ms": float(st.kernel_ms)}))
+
+
+def run_profile_encode():
+    """The encoder's capture case: the 994 x 676 x 1225 cloud (3.3 GB, the
+    full-scale cloud's generator at half the edge) encoded twice at 1:10."""
+    torch, v, volgen, scenes = _env()
+    w = scenes.CLOUD_994
+    vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]))
+    for _ in range(2):
+        g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"])
+        torch.cuda.synchronize()
+        n_active = int(g.info.n_active)
+        g.close()
+    print(json.dumps({"profile_case": "cloud994x676x1225_encode_r10", "n_active": n_active}))
 
 
 def run_save_cloud_grid(path):
@@ -1105,6 +1125,10 @@ if __name__ == "__main__":
         run_profile_grid(a.profile_grid)
     elif a.profile_case:
         run_profile_case()
+    elif a.profile_case_full:
+        run_profile_case(full=True)
+    elif a.profile_encode:
+        run_profile_encode()
     elif a.impl == "reference":
         run_reference(a)
     else:

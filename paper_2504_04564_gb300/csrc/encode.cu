@@ -236,6 +236,11 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                 const float* p = v + ((size_t)z0 * d.ny + (y0 + warp)) * d.nx + x0 + min(lane, ex - 1);
                 uint32_t umax = 0u;
                 int imin = 0x7fffffff, imax = (int)0x80000000;
+                // the value of the warp's run when a step of it was one value
+                // (already in the range; its key is run.key): a step of only
+                // that value adds nothing to the range and joins the run
+                uint32_t rv = 0u;
+                bool rvok = false;
                 for (int z = 0; z < ez; z += U) {
                     uint32_t u[U];
                     const float* a = p;
@@ -251,17 +256,27 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                     for (int q = 0; q < U; ++q) {
                         if (z + q >= ez) break;                    // warp-uniform
                         const uint32_t w = u[q];
+                        if (rvok && __all_sync(0xffffffffu, w == rv)) {
+                            run.cnt += nvalid;
+                            continue;
+                        }
                         const uint32_t key = w >> 16;
                         umax = max(umax, w);
                         imin = min(imin, (int)w);
                         imax = max(imax, (int)w);
                         if (__all_sync(0xffffffffu, key == run.key)) {
                             run.cnt += nvalid;
+                            if (!rvok) {                           // (warp-uniform)
+                                rv = __shfl_sync(0xffffffffu, w, 0);
+                                rvok = __all_sync(0xffffffffu, w == rv);
+                            }
                             continue;
                         }
-                        const uint32_t lead = __shfl_sync(0xffffffffu, key, 0);
+                        const uint32_t lw = __shfl_sync(0xffffffffu, w, 0), lead = lw >> 16;
                         if (__all_sync(0xffffffffu, key == lead)) {
                             run.add(lead, nvalid, lane, hist);
+                            rv = lw;
+                            rvok = __all_sync(0xffffffffu, w == lw);
                             continue;
                         }
                         const bool inrun = valid && key == run.key;

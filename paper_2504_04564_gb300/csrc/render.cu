@@ -472,6 +472,7 @@ struct JobView {
     int cx_n, cy_n;            // coarse grid size along x and y
     unsigned long long* accum; // 3 per pixel: the frame's radiance sums, 32.32 fixed point
     const int* occ_box;        // macrocell index box of the positive majorants (lo xyz, hi xyz), or null
+    float clip[6];             // (batch jobs) the clip box in index space built from it, as k_pt builds it
     int npix, spp, tiles_x;
     uint32_t k0, k1;           // Philox key = the seed
     uint32_t sample_base;      // sample id of the frame's first sample (progressive frames)
@@ -526,9 +527,11 @@ struct BatchSource {
         return j;
     }
     __device__ __forceinline__ const JobView& job(int i) const { return jobs[i]; }
-    __device__ __forceinline__ bool clip(int, const Majorants& m, float3 o, float3 d, float& tin, float& tout) const
+    // each job's rays are clipped to the box of its occupied macrocells, as
+    // single renders' (1:1 bit-identical images)
+    __device__ __forceinline__ bool clip(int i, const Majorants&, float3 o, float3 d, float& tin, float& tout) const
     {
-        return clip_box(m, o, d, tin, tout);
+        return clip_span(jobs[i].clip, o, d, tin, tout);
     }
     __device__ __forceinline__ const uint32_t* bits(int i) const { return jobs[i].bits; }
     __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
@@ -851,6 +854,23 @@ constexpr int pt_min_blocks()
     return (S::kCollective || kUseCoarse) ? 2 : VDBC_PT_MIN_BLOCKS;
 }
 
+// the ray clip box in index space (lo xyz, hi xyz): the volume's, or with
+// `occ` (a macrocell index box) that of its cells, clamped to the volume
+__device__ __forceinline__ void occupied_clip_box(const Majorants& m, const int* occ, float* box)
+{
+    const float dims[3] = {(float)m.nx, (float)m.ny, (float)m.nz};
+    for (int a = 0; a < 3; ++a) { box[a] = -0.5f; box[3 + a] = dims[a] - 0.5f; }
+    if (occ) {
+        const float mc = (float)m.mc;
+        for (int a = 0; a < 3; ++a) {
+            const int lo = occ[a], hi = occ[3 + a];
+            // (no positive majorant anywhere: an empty box, every ray misses)
+            box[a] = lo <= hi ? __fsub_rn(__fmul_rn((float)lo, mc), 0.5f) : 1.0f;
+            box[3 + a] = lo <= hi ? fminf(__fsub_rn(__fmul_rn((float)(hi + 1), mc), 0.5f), dims[a] - 0.5f) : 0.0f;
+        }
+    }
+}
+
 // gbits: nwords fine occupancy words followed by ncwords coarse words; the
 // parts that fit in `smem_words` are staged in shared memory (coarse first)
 template <class S, bool kUseCoarse, bool kPhased = false, int kBlocks = pt_min_blocks<S, kUseCoarse>()>
@@ -860,20 +880,7 @@ __global__ void __launch_bounds__(256, kBlocks)
 {
     extern __shared__ uint32_t s_bits[];
     __shared__ float s_box[6];
-    if (threadIdx.x == 0) {
-        const Majorants& m = job.m;
-        const float dims[3] = {(float)m.nx, (float)m.ny, (float)m.nz};
-        for (int a = 0; a < 3; ++a) { s_box[a] = -0.5f; s_box[3 + a] = dims[a] - 0.5f; }
-        if (job.occ_box) {
-            const float mc = (float)m.mc;
-            for (int a = 0; a < 3; ++a) {
-                const int lo = job.occ_box[a], hi = job.occ_box[3 + a];
-                // (no positive majorant anywhere: an empty box, every ray misses)
-                s_box[a] = lo <= hi ? __fsub_rn(__fmul_rn((float)lo, mc), 0.5f) : 1.0f;
-                s_box[3 + a] = lo <= hi ? fminf(__fsub_rn(__fmul_rn((float)(hi + 1), mc), 0.5f), dims[a] - 0.5f) : 0.0f;
-            }
-        }
-    }
+    if (threadIdx.x == 0) occupied_clip_box(job.m, job.occ_box, s_box);
     const uint32_t* cbits = gbits + nwords;
     const uint32_t* bits = gbits;
     if (ncwords <= smem_words) {
@@ -980,6 +987,12 @@ __global__ void k_occupancy(const float* __restrict__ mcmax, long long ncell, fl
     bool on = i < ncell && sigma_scale * mcmax[i] > 0.0f;
     unsigned b = __ballot_sync(0xffffffffu, on);
     if ((threadIdx.x & 31) == 0 && i < ncell) bits[i >> 5] = b;
+}
+
+// a batch job's clip box (one thread)
+__global__ void k_clip_box(Majorants m, const int* __restrict__ occ, float* __restrict__ box)
+{
+    occupied_clip_box(m, occ, box);
 }
 
 // index box (lo xyz, hi xyz) of the macrocells whose occupancy bit is set;
@@ -2243,6 +2256,31 @@ extern "C" vdbc_status vdbc_batch_create(const vdbc_job* jobs, int32_t n, int32_
         cudaError_t e = cudaMemcpyAsync(b->bits_off[i], b->bits_on[i], (size_t)nwords * 4, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->bits_off[i] + nwords, 0xff, (size_t)ncwords * 4, s);
         if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create bits"));
+    }
+    {
+        // each job's clip box: the box of its occupied macrocells, built on
+        // the device as k_pt builds it, then held in the job table
+        int* d_occ = nullptr;
+        float* d_clip = nullptr;
+        st = batch_alloc(b, reinterpret_cast<void**>(&d_occ), sizeof(int) * 6 * (size_t)n);
+        if (st == VDBC_OK) st = batch_alloc(b, reinterpret_cast<void**>(&d_clip), sizeof(float) * 6 * (size_t)n);
+        if (st != VDBC_OK) return fail(st);
+        for (int i = 0; i < n; ++i) {
+            const Majorants& mj = b->h_jobs[i].m;
+            const long long ncell = (long long)mj.mx * mj.my * mj.mz;
+            cudaError_t e = cudaMemsetAsync(d_occ + 6 * i, 0x7f, 3 * sizeof(int), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_occ + 6 * i + 3, 0xff, 3 * sizeof(int), s);
+            if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create box"));
+            KLAUNCH(k_occupied_box<<<blocks_for(ncell, 256), 256, 0, s>>>(b->bits_on[i], mj.mx, mj.my, ncell,
+                                                                          d_occ + 6 * i));
+            KLAUNCH(k_clip_box<<<1, 1, 0, s>>>(mj, d_occ + 6 * i, d_clip + 6 * i));
+        }
+        std::vector<float> clip(6 * (size_t)n);
+        cudaError_t e = cudaMemcpyAsync(clip.data(), d_clip, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return fail(cuda_status(e, "vdbc_batch_create box"));
+        st = wait_stream(s);
+        if (st != VDBC_OK) return fail(st);
+        for (int i = 0; i < n; ++i) std::memcpy(b->h_jobs[i].clip, clip.data() + 6 * i, sizeof(float) * 6);
     }
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < b->groups.size() && e == cudaSuccess; ++k)
