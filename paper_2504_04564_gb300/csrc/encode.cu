@@ -118,6 +118,187 @@ struct KeyRun {
     }
 };
 
+// ---------------------------------------------------------------- majority shortcut
+// A bit pattern held by more than half of the voxels is the mode: its upper
+// 16 bits win level 1 of the histogram and the pattern wins level 2, with no
+// tie.  Sparse volumes are mostly one value (the cloud: 73 % zeros), so the
+// encoder first samples a candidate, then counts it exactly while it takes
+// the brick ranges (k_pass1_maj, no histogram); the histogram passes
+// (k_pass1, k_pass2) and the argmax read the count and stand aside when the
+// candidate holds the majority.  Otherwise they run in full and B comes from
+// the histogram as before: the result is the same either way.
+struct Majority {
+    unsigned long long count;    // voxels holding `bits`
+    uint32_t bits;               // the candidate pattern
+    uint32_t pad;
+};
+
+__device__ __forceinline__ bool is_majority(const Majority* m, long long nvox)
+{
+    return m && 2ull * m->count > (unsigned long long)nvox;
+}
+
+// the candidate: the most frequent pattern among 1024 voxels on a 16 x 8 x 8
+// lattice spanning the volume (ties to the smaller pattern); zeroes the count
+__global__ void __launch_bounds__(1024) k_candidate(const float* __restrict__ v, Dims d, Majority* __restrict__ m)
+{
+    __shared__ uint32_t s_v[1024];
+    __shared__ unsigned long long s_best[32];
+    const int i = threadIdx.x;
+    const int x = (int)((long long)(i & 15) * (d.nx - 1) / 15), y = (int)((long long)((i >> 4) & 7) * (d.ny - 1) / 7),
+              z = (int)((long long)(i >> 7) * (d.nz - 1) / 7);
+    s_v[i] = __float_as_uint(__ldg(v + ((size_t)z * d.ny + y) * d.nx + x));
+    __syncthreads();
+    const uint32_t mine = s_v[i];
+    uint32_t n = 0;
+    for (int j = 0; j < 1024; ++j) n += s_v[j] == mine ? 1u : 0u;
+    unsigned long long best = ((unsigned long long)n << 32) | (uint32_t)~mine;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+        best = t > best ? t : best;
+    }
+    if ((i & 31) == 0) s_best[i >> 5] = best;
+    __syncthreads();
+    if (i == 0) {
+        for (int w = 1; w < 32; ++w) best = s_best[w] > best ? s_best[w] : best;
+        m->bits = ~(uint32_t)best;
+        m->count = 0ull;
+    }
+}
+
+// pass 1 of the majority shortcut: every brick's min/max keys and the exact
+// count of the candidate pattern c, with the loads of k_pass1 (kMode 1: float4
+// rows; kMode 2: a warp steps one brick row through the z slices).  A step
+// whose values all equal c only adds to the count; c joins the brick's range
+// once at its end.  Non-finite input is found from the brick's keys.
+template <int kMode>
+__global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __restrict__ v, Dims d, int nbricks,
+                                                             uint32_t* __restrict__ lo_key, uint32_t* __restrict__ hi_key,
+                                                             Majority* __restrict__ maj, int* __restrict__ nonfinite)
+{
+    constexpr int kWarps = kPass1Threads / 32;
+    __shared__ uint32_t s_min[kWarps], s_max[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t c = maj->bits;
+    unsigned long long cnt = 0;          // (warp-uniform) voxels holding c
+    bool bad = false;
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        int bx, by, bz;
+        brick_coords(d, b, bx, by, bz);
+        const int x0 = bx * 32, y0 = by * 32, z0 = bz * 32;
+        const int ex = min(32, d.nx - x0), ey = min(32, d.ny - y0), ez = min(32, d.nz - z0);
+        uint32_t umax = 0u;
+        int imin = 0x7fffffff, imax = (int)0x80000000;
+        bool any = false, seen = false;
+        if constexpr (kMode == 2) {
+            constexpr int U = 16;
+            const bool valid = lane < ex;
+            if (warp < ey) {
+                const size_t slice = (size_t)d.nx * d.ny;
+                const float* p = v + ((size_t)z0 * d.ny + (y0 + warp)) * d.nx + x0 + min(lane, ex - 1);
+                for (int z = 0; z < ez; z += U) {
+                    uint32_t u[U];
+                    const float* a = p;
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        u[q] = 0u;
+                        if (z + q < ez) u[q] = __float_as_uint(__ldg(a));
+                        a += slice;
+                    }
+                    p = a;
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        if (z + q >= ez) break;                    // warp-uniform
+                        const uint32_t w = u[q];
+                        const bool eq = w == c;
+                        if (__all_sync(0xffffffffu, eq)) {         // (lanes past the edge repeat a valid voxel)
+                            cnt += (unsigned long long)ex;
+                            seen = true;
+                            continue;
+                        }
+                        any = true;
+                        umax = max(umax, w);
+                        imin = min(imin, (int)w);
+                        imax = max(imax, (int)w);
+                        cnt += (unsigned long long)__popc(__ballot_sync(0xffffffffu, eq && valid));
+                    }
+                }
+            }
+        } else {
+            constexpr int U = 8;
+            const int sub = lane & 7, rsub = lane >> 3;
+            const bool xvalid = sub * 4 < ex;                      // ex is a multiple of 4 here
+            const int rows = ey * ez;
+            const uint32_t mey = div_magic(ey);
+            const int quads = (rows + 3) >> 2;
+            for (int g0 = warp; g0 < quads; g0 += kWarps * U) {
+                uint4 u[U];
+                bool ok[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int row = 4 * (g0 + q * kWarps) + rsub;
+                    ok[q] = xvalid && row < rows;
+                    u[q] = make_uint4(c, c, c, c);
+                    if (ok[q]) {
+                        const int z = div_small(row, mey), y = row - z * ey;
+                        u[q] = __ldg(reinterpret_cast<const uint4*>(
+                            v + ((size_t)(z0 + z) * d.ny + (y0 + y)) * d.nx + x0 + 4 * sub));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (g0 + q * kWarps >= quads) break;                // warp-uniform
+                    const uint32_t w[4] = {u[q].x, u[q].y, u[q].z, u[q].w};
+                    const unsigned part = __ballot_sync(0xffffffffu, ok[q]);
+                    const bool eq4 = w[0] == c && w[1] == c && w[2] == c && w[3] == c;   // (true where !ok)
+                    if (__all_sync(0xffffffffu, eq4)) {
+                        cnt += 4ull * (unsigned long long)__popc(part);
+                        seen |= part != 0u;
+                        continue;
+                    }
+                    unsigned n = 0u;
+                    if (ok[q]) {
+                        any = true;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            umax = max(umax, w[j]);
+                            imin = min(imin, (int)w[j]);
+                            imax = max(imax, (int)w[j]);
+                            n += w[j] == c ? 1u : 0u;
+                        }
+                    }
+                    cnt += (unsigned long long)__reduce_add_sync(0xffffffffu, n);
+                }
+            }
+        }
+        if (seen) {                                               // (warp-uniform)
+            any = true;
+            umax = max(umax, c);
+            imin = min(imin, (int)c);
+            imax = max(imax, (int)c);
+        }
+        uint32_t kmin = 0xffffffffu, kmax = 0u;
+        if (any) {
+            kmin = okey((umax & 0x80000000u) ? umax : (uint32_t)imin);
+            kmax = okey(imax >= 0 ? (uint32_t)imax : (uint32_t)imin);
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) { s_min[warp] = kmin; s_max[warp] = kmax; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = s_min[0], e = s_max[0];
+            for (int w = 1; w < kWarps; ++w) { a = min(a, s_min[w]); e = max(e, s_max[w]); }
+            lo_key[b] = a;
+            hi_key[b] = e;
+            if (e >= 0xff800000u || a <= 0x007fffffu) bad = true;   // a NaN or infinity in the brick
+        }
+        __syncthreads();
+    }
+    if (lane == 0 && cnt) atomicAdd(&maj->count, cnt);
+    if (threadIdx.x == 0 && bad) atomicOr(nonfinite, 1);
+}
+
 // kMode 1: the volume's rows start on 16-byte boundaries (nx % 4 == 0 and an
 // aligned base), so a lane loads four voxels at once: lane = 8 * rsub + sub
 // takes float4 `sub` of row 4g + rsub, and a warp covers four rows a load.
@@ -131,8 +312,10 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
                                                          uint32_t* __restrict__ lo_key,
                                                          uint32_t* __restrict__ hi_key,
                                                          unsigned long long* __restrict__ hist,
-                                                         int* __restrict__ nonfinite)
+                                                         int* __restrict__ nonfinite,
+                                                         const Majority* __restrict__ maj, long long nvox)
 {
+    if (is_majority(maj, nvox)) return;          // B is the counted candidate
     extern __shared__ __align__(16) uint32_t s_h[];
     __shared__ uint32_t s_min[2][kPass1Threads / 32], s_max[2][kPass1Threads / 32];
     __shared__ int s_bad;
@@ -377,8 +560,16 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1(const float* __restrict
 
 // most frequent of 65536 bins, ties to the smaller index; writes (out_base | idx)
 __global__ void __launch_bounds__(1024) k_argmax(const unsigned long long* __restrict__ hist,
-                                                 uint32_t* __restrict__ out, int stage)
+                                                 uint32_t* __restrict__ out, int stage,
+                                                 const Majority* __restrict__ maj, long long nvox)
 {
+    if (is_majority(maj, nvox)) {                // the counted candidate is the mode
+        if (threadIdx.x == 0) {
+            if (stage == 0) out[0] = maj->bits >> 16;
+            else out[1] = maj->bits;
+        }
+        return;
+    }
     __shared__ unsigned long long s[32];
     unsigned long long best = 0;
     for (int i = threadIdx.x; i < 65536; i += 1024) {
@@ -412,8 +603,10 @@ __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict_
                                                         const uint32_t* __restrict__ lo_key,
                                                         const uint32_t* __restrict__ hi_key,
                                                         const uint32_t* __restrict__ bsel,
-                                                        unsigned long long* __restrict__ hist)
+                                                        unsigned long long* __restrict__ hist,
+                                                        const Majority* __restrict__ maj, long long nvox)
 {
+    if (is_majority(maj, nvox)) return;          // B is the counted candidate
     const int b = blockIdx.x;
     const uint32_t H = bsel[0];
     // key range of the bit patterns [H<<16, H<<16 | 0xffff]
@@ -1295,23 +1488,49 @@ bool rows_aligned(const float* v, const Dims& d)
     return d.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(v) & 15u) == 0;
 }
 
-// pass 1 in the load mode the volume allows: float4 rows (1) or scalar (0)
-void launch_pass1(const float* v, const Dims& d, int nb, unsigned grid, uint32_t* lo_key, uint32_t* hi_key,
-                  unsigned long long* hist, int* nonfinite, cudaStream_t s)
+// the background B (Algorithm 1's histogram, both levels) and the brick
+// ranges, into bsel and lo_key / hi_key: the candidate and its exact count
+// with the ranges, then the histogram passes, which stand aside when the
+// candidate holds the majority.  hist and *nonfinite are zero on entry.
+// (VDBC_MAJORITY=0 leaves the histogram to every volume, for measurement;
+// VDBC_PASS1_MODE picks the row loads of the histogram pass for rows off a
+// 16-byte boundary: 3 (the default) steps each warp's brick row through
+// 16 z slices, 2 through 8, 0 splits the row index per row -- the full-scale
+// cloud encoded in 19.6, 20.1 and 23.7 ms that way before the shortcut)
+vdbc_status launch_background(const float* v, const Dims& d, int nb, unsigned grid, uint32_t* lo_key,
+                              uint32_t* hi_key, unsigned long long* hist, uint32_t* bsel, int* nonfinite, Majority* maj,
+                              cudaStream_t s)
 {
-    // kMode 2 with 16 rows in flight for rows off a 16-byte boundary: the full-
-    // scale cloud (1987-voxel rows) encodes in 19.6 ms against 23.7 with the
-    // per-row index arithmetic of kMode 0 and 20.1 with 8 rows in flight
-    // (VDBC_PASS1_MODE=0 or 2 select those for measurement)
     static const int mode = [] { const char* e = std::getenv("VDBC_PASS1_MODE"); return e ? std::atoi(e) : 3; }();
-    if (rows_aligned(v, d))
-        KLAUNCH(k_pass1<1><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
+    static const bool shortcut = [] { const char* e = std::getenv("VDBC_MAJORITY"); return !(e && e[0] == '0'); }();
+    const long long nvox = (long long)d.nx * d.ny * d.nz;
+    const bool aligned = rows_aligned(v, d);
+    const Majority* m = shortcut ? maj : nullptr;
+    if (shortcut) {
+        KLAUNCH(k_candidate<<<1, 1024, 0, s>>>(v, d, maj));
+        if (aligned)
+            KLAUNCH(k_pass1_maj<1><<<grid, kPass1Threads, 0, s>>>(v, d, nb, lo_key, hi_key, maj, nonfinite));
+        else
+            KLAUNCH(k_pass1_maj<2><<<grid, kPass1Threads, 0, s>>>(v, d, nb, lo_key, hi_key, maj, nonfinite));
+    }
+    if (aligned)
+        KLAUNCH(k_pass1<1><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite, m, nvox));
     else if (mode == 2)
-        KLAUNCH((k_pass1<2, 8><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
+        KLAUNCH((k_pass1<2, 8><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite, m,
+                                                                       nvox)));
     else if (mode == 3)
-        KLAUNCH((k_pass1<2, 16><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite)));
+        KLAUNCH((k_pass1<2, 16><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite, m,
+                                                                        nvox)));
     else
-        KLAUNCH(k_pass1<0><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite));
+        KLAUNCH(k_pass1<0><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite, m, nvox));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0, m, nvox));
+    VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * sizeof(unsigned long long), s));
+    if (aligned)
+        KLAUNCH(k_pass2<true><<<(unsigned)nb, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox));
+    else
+        KLAUNCH(k_pass2<false><<<(unsigned)nb, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox));
+    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 1, m, nvox));
+    return VDBC_OK;
 }
 
 // opts k_pass1 into its shared memory (once per device) and sizes its
@@ -1544,20 +1763,15 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     VDBC_TRY(sc.get(&nonfinite, 1));
     VDBC_TRY(sc.get(&counts, 2));
     VDBC_TRY(sc.get(&total, 8));
+    Majority* maj = nullptr;
+    VDBC_TRY(sc.get(&maj, 1));
 
     // phase 1: histogram -> B (two levels), brick ranges
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
     VDBC_CUDA(cudaMemsetAsync(nonfinite, 0, 4, s));
     unsigned p1grid = 1;
     VDBC_TRY(pass1_setup(nb, &p1grid));
-    launch_pass1(vol, d, nb, p1grid, lo_key, hi_key, hist, nonfinite, s);
-    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0));
-    VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
-    if (rows_aligned(vol, d))
-        KLAUNCH(k_pass2<true><<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
-    else
-        KLAUNCH(k_pass2<false><<<nb, kPassThreads, 0, s>>>(vol, d, lo_key, hi_key, bsel, hist));
-    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 1));
+    VDBC_TRY(launch_background(vol, d, nb, p1grid, lo_key, hi_key, hist, bsel, nonfinite, maj, s));
     // phase 2: f per brick, selection of N bricks
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(lo_key, hi_key, nb, bsel, metric, fkey, empty));
     double nbud = std::floor((double)nb * 131072.0 / (ratio * (double)brick_bytes(payload)));
@@ -1780,6 +1994,7 @@ struct NoAllocScratch {
     uint8_t empty[kNoAllocMaxBricks];
     uint32_t bsel[2];
     int nonfinite;
+    Majority maj;                            // the background's candidate pattern and its count
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -1888,16 +2103,8 @@ extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vd
     VDBC_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
     unsigned p1grid = 1;
     VDBC_TRY(pass1_setup(nb, &p1grid));
-    launch_pass1(in->data, d, nb, p1grid, sc->lo_key, sc->hi_key, sc->hist, &sc->nonfinite, s);
-    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 0));
-    VDBC_CUDA(cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist), s));
-    if (rows_aligned(in->data, d))
-        KLAUNCH(k_pass2<true><<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel,
-                                                                    sc->hist));
-    else
-        KLAUNCH(k_pass2<false><<<(unsigned)nb, kPassThreads, 0, s>>>(in->data, d, sc->lo_key, sc->hi_key, sc->bsel,
-                                                                     sc->hist));
-    KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(sc->hist, sc->bsel, 1));
+    VDBC_TRY(launch_background(in->data, d, (int)nb, p1grid, sc->lo_key, sc->hi_key, sc->hist, sc->bsel,
+                               &sc->nonfinite, &sc->maj, s));
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(sc->lo_key, sc->hi_key, (int)nb, sc->bsel, metric, sc->fkey,
                                                      sc->empty));
     KLAUNCH(k_select<<<1, 1024, 0, s>>>(sc->fkey, sc->empty, (int)nb, budget, active_out,

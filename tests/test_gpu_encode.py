@@ -180,6 +180,45 @@ def test_degenerate_volumes(env):
     assert grid.info.n_active == 8 and grid.info.n_leaves == 512
 
 
+def candidate_lattice(dims):
+    """The 16 x 8 x 8 voxel lattice spanning the volume on which the encoder
+    draws its candidate for a majority background pattern."""
+    nx, ny, nz = dims
+    m = np.zeros((nz, ny, nx), dtype=bool)
+    for i in range(1024):
+        m[(i >> 7) * (nz - 1) // 7, ((i >> 4) & 7) * (ny - 1) // 7, (i & 15) * (nx - 1) // 15] = True
+    return m
+
+
+@pytest.mark.parametrize("case", ["wrong_candidate", "exact_half", "no_majority"])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_background_without_a_sampled_majority(env, case, offset):
+    """B where the encoder's majority shortcut cannot decide it: the sampled
+    candidate is not the majority pattern (zeros hold 70 % of the voxels, the
+    sampled lattice holds 1.0); the candidate holds exactly half of the
+    voxels (no strict majority: level 1 ties between two bins and takes the
+    smaller); no pattern repeats at all.  Aligned rows and rows off a 16-byte
+    boundary take the two load modes of both passes."""
+    rng = np.random.default_rng(5)
+    dims = (96, 80, 72)
+    n = dims[0] * dims[1] * dims[2]
+    lat = candidate_lattice(dims)
+    if case == "wrong_candidate":
+        host = np.where(rng.random(n).reshape(lat.shape) < 0.7, 0.0, rng.random(n).reshape(lat.shape))
+        host[lat] = 1.0
+    elif case == "exact_half":
+        order = np.concatenate([np.flatnonzero(lat), rng.permutation(np.flatnonzero(~lat))])
+        host = np.full(n, 0.5)
+        host[order[: n // 2]] = 0.0
+        host = host.reshape(lat.shape)
+    else:
+        host = rng.random(n).reshape(lat.shape) + 0.5
+    host = np.ascontiguousarray(host.astype(np.float32))
+    grid, e, _ = check_encoding(env, host, 10.0, offset=offset)
+    if case != "no_majority":
+        assert e["background_bits"] == 0
+
+
 def test_encoder_rejects_non_finite(env):
     torch, v = env["torch"], env["v"]
     a = np.zeros((16, 16, 16), dtype=np.float32)
