@@ -1057,7 +1057,7 @@ def study_hdda():
                          "mpaths_per_s": round(paths / (ms * 1e-3) / 1e6, 2), "lookups": lk})
         g.close()
     os.environ.pop("VDBC_PT_COARSE", None)
-    return {"study": "hierarchical_vs_uniform_dda", "workload": WORKLOAD, "rows": rows}
+    return {"study": "hierarchical_vs_uniform_dda", "workload": "turbulence512_r10_pt1024sq_16spp", "rows": rows}
 
 
 def study_fullscale():

@@ -11,6 +11,10 @@
 //
 // Kernels, in order (every one is HBM- or latency-bound, none is a
 // contraction):
+//   k_candidate    one CTA: the most frequent of 1024 lattice voxels
+//   k_pass1_maj    persistent: brick min/max and the exact count of that
+//                  candidate; when it holds more than half of the voxels it
+//                  is B, and the histogram kernels below return at once
 //   k_pass1        persistent, one CTA per SM taking bricks in turn: min/max
 //                  (total order) + upper-16-bit histogram (block histogram in
 //                  shared memory, flushed per brick) + non-finite check

@@ -1453,8 +1453,8 @@ vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, in
     }
     if constexpr (std::is_same<S, VdbSamplerT<0>>::value) {
         // VDBC_PT_PHASED=1: the one-block-per-iteration loop, for measuring it
-        // against the default.  Measured slower: 10.5 against 9.0 ms on the
-        // 512^3 frame, 48.7 against 44.5 ms on the cloud (the warp then runs
+        // against the default.  Measured slower: 10.01 against 8.57 ms on the
+        // 512^3 frame, 47.83 against 44.01 ms on the cloud (the warp then runs
         // more iterations per path than the lanes it regroups save)
         static const bool phased = [] { const char* e = std::getenv("VDBC_PT_PHASED"); return e && e[0] == '1'; }();
         if (phased) return launch_pt_t<S, false, true>(smp, job, bits, nwords, ncwords, stats, chunk, s);
@@ -1481,8 +1481,8 @@ vdbc_status launch_pt(const S& smp, const JobView& job, const uint32_t* bits, in
 // its block, before the leaves) as a persisting L2 window on the render's
 // stream while the path tracer runs: every tree descent reads them.
 // VDBC_L2_NODES=1 turns it on; the window is cleared after the launch.  Off
-// by default: measured no faster (9.11 against 8.98 ms on the 512^3 frame,
-// whose 54 MB grid L2 holds anyway; 45.07 against 44.54 ms on the cloud, whose
+// by default: measured no faster (8.63 against 8.57 ms on the 512^3 frame,
+// whose 54 MB grid L2 holds anyway; 44.45 against 44.01 ms on the cloud, whose
 // node tables stay hot in L2 without the window).
 template <class S>
 struct NodeWindow {
@@ -1577,9 +1577,9 @@ vdbc_status launch(const S& smp, const Majorants& mj, const CamDev& cam, const M
         VDBC_CUDA(cudaMemsetAsync(bits + nwords, 0xff, (size_t)ncwords * 4, s));   // every block "occupied"
     }
     JobView job = make_job(mj, cam, med, spp, seed, accum);
-    // (rays walk only the box of the occupied macrocells: 12.2 -> 9.0 ms on the
+    // (rays walk only the box of the occupied macrocells: 12.08 -> 8.57 ms on the
     // 1024^2 x 16 spp frame of the 512^3 medium, whose occupied cells fill a
-    // quarter of its grid; 59.0 -> 44.5 ms on the cloud; VDBC_PT_BOX=0 turns it off)
+    // quarter of its grid; 58.89 -> 44.01 ms on the cloud; VDBC_PT_BOX=0 turns it off)
     static const bool use_box = [] { const char* e = std::getenv("VDBC_PT_BOX"); return !(e && e[0] == '0'); }();
     if (use_box) {
         // the clip box of the occupied macrocells, after the occupancy words

@@ -203,8 +203,8 @@ constexpr uint32_t kNodeBits = 0x3F0u | (0x3F0u << 10) | (0x3F0u << 20) | (1u <<
 // it, so another leaf of the same 128^3 region costs one load.  Depth 1 is
 // the default: the tracker is bound by instruction issue, not by the load
 // latency the deeper cache saves (1024^2 x 16 spp frame of the 512^3 medium:
-// 9.0 ms at depth 1, 9.6 at depth 2; 1920x1080 x 64 spp of the
-// 1987x1351x2449 cloud at 1:10: 44.5 against 47.2 ms).
+// 8.57 ms at depth 1, 9.34 at depth 2; 1920x1080 x 64 spp of the
+// 1987x1351x2449 cloud at 1:10: 44.01 against 45.53 ms).
 #ifndef VDBC_ACC_DEPTH
 #define VDBC_ACC_DEPTH 1
 #endif
@@ -276,8 +276,8 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 // 2: stencils across one face (two leaves, the most frequent straddle) take
 //    each leaf's entry once, the rest go corner by corner.
 // 1 is the default: the second path's extra code costs more than the
-// descents it saves (9.0 against 9.9 ms on the 512^3 frame, 44.5 against
-// 46.4 ms on the cloud; the images are bit-identical).
+// descents it saves (8.57 against 9.98 ms on the 512^3 frame, 44.01 against
+// 45.28 ms on the cloud; the images are bit-identical).
 #ifndef VDBC_TRI_STRADDLE
 #define VDBC_TRI_STRADDLE 1
 #endif
