@@ -260,23 +260,22 @@ def timed_steps(torch, v, vol, w, cam, med, img, stream, steps, warmup, barrier)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    grids = []
+    g = None
     for i in range(steps):
         a, b, c = ev[i]
         a.record(stream)
+        if g is not None:
+            g.close()          # the previous step's grid, freed in stream order as a user's loop frees it
         g = v.vdbc_encode(vol, w["ratio"], macrocell=w["macrocell"], stream=stream)
         b.record(stream)
         v.vdbc_render(g, cam, med, w["spp"], SEED, img, stream=stream)
         c.record(stream)
-        grids.append(g)
     t_end.record(stream)
     barrier()
     total_ms = t_start.elapsed_time(t_end)
     enc_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
     ren_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(steps)]
-    for g in grids[:-1]:
-        g.close()
-    return total_ms, enc_ms, ren_ms, grids[-1]
+    return total_ms, enc_ms, ren_ms, g
 
 
 def tracker_roofline(v, g, cam, med, w, img, stream, first_kernel_ms, lookups, profile_name):
