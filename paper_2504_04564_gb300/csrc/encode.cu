@@ -181,7 +181,6 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __rest
                                                              Majority* __restrict__ maj, int* __restrict__ nonfinite)
 {
     constexpr int kWarps = kPass1Threads / 32;
-    __shared__ uint32_t s_min[kWarps], s_max[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t c = maj->bits;
     unsigned long long cnt = 0;          // (warp-uniform) voxels holding c
@@ -281,6 +280,8 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __rest
             imin = min(imin, (int)c);
             imax = max(imax, (int)c);
         }
+        // the warp's part of the brick folds into its keys (identity on
+        // entry): no block barrier, warps move on to their next brick at once
         uint32_t kmin = 0xffffffffu, kmax = 0u;
         if (any) {
             kmin = okey((umax & 0x80000000u) ? umax : (uint32_t)imin);
@@ -288,19 +289,14 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __rest
         }
         kmin = __reduce_min_sync(0xffffffffu, kmin);
         kmax = __reduce_max_sync(0xffffffffu, kmax);
-        if (lane == 0) { s_min[warp] = kmin; s_max[warp] = kmax; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t a = s_min[0], e = s_max[0];
-            for (int w = 1; w < kWarps; ++w) { a = min(a, s_min[w]); e = max(e, s_max[w]); }
-            lo_key[b] = a;
-            hi_key[b] = e;
-            if (e >= 0xff800000u || a <= 0x007fffffu) bad = true;   // a NaN or infinity in the brick
+        if (lane == 0 && kmin <= kmax) {
+            atomicMin(lo_key + b, kmin);
+            atomicMax(hi_key + b, kmax);
+            if (kmax >= 0xff800000u || kmin <= 0x007fffffu) bad = true;   // a NaN or infinity in the part
         }
-        __syncthreads();
     }
     if (lane == 0 && cnt) atomicAdd(&maj->count, cnt);
-    if (threadIdx.x == 0 && bad) atomicOr(nonfinite, 1);
+    if (lane == 0 && bad) atomicOr(nonfinite, 1);
 }
 
 // kMode 1: the volume's rows start on 16-byte boundaries (nx % 4 == 0 and an
@@ -820,14 +816,18 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
         // pass counts the byte of every key whose higher bytes equal the
         // prefix chosen so far, and keeps the byte at which the count from the
         // top reaches the rank still wanted
+        // (per-warp digit counts, summed once per pass: the keys share their
+        // top bytes, and one shared count per digit had every warp's adds
+        // collide on a few bins)
         __shared__ unsigned s_hist[256];
+        __shared__ unsigned s_whist[kSelThreads / 32][256];
         __shared__ unsigned long long s_prefix;
         __shared__ long long s_rank;
         unsigned long long prefix = 0, pmask = 0;
         long long rank = take;
-        const int lane = threadIdx.x & 31;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int shift = 56; shift >= 0; shift -= 8) {
-            for (int i = threadIdx.x; i < 256; i += kSelThreads) s_hist[i] = 0u;
+            for (int i = threadIdx.x; i < (kSelThreads / 32) * 256; i += kSelThreads) (&s_whist[0][0])[i] = 0u;
             __syncthreads();
             // kSelBatch keys a thread loaded before any is counted, so that
             // their L2 latencies overlap
@@ -844,8 +844,14 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
                     const bool in = k != 0ull && (k & pmask) == prefix;
                     const unsigned digit = in ? (unsigned)(k >> shift) & 255u : 256u;
                     const unsigned peers = __match_any_sync(0xffffffffu, digit);
-                    if (in && lane == __ffs(peers) - 1) atomicAdd(&s_hist[digit], (unsigned)__popc(peers));
+                    if (in && lane == __ffs(peers) - 1) s_whist[wid][digit] += (unsigned)__popc(peers);
                 }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 256; i += kSelThreads) {
+                unsigned t = 0u;
+                for (int w = 0; w < kSelThreads / 32; ++w) t += s_whist[w][i];
+                s_hist[i] = t;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1511,6 +1517,8 @@ vdbc_status launch_background(const float* v, const Dims& d, int nb, unsigned gr
     const bool aligned = rows_aligned(v, d);
     const Majority* m = shortcut ? maj : nullptr;
     if (shortcut) {
+        VDBC_CUDA(cudaMemsetAsync(lo_key, 0xff, (size_t)nb * 4, s));     // min / max identities
+        VDBC_CUDA(cudaMemsetAsync(hi_key, 0, (size_t)nb * 4, s));
         KLAUNCH(k_candidate<<<1, 1024, 0, s>>>(v, d, maj));
         if (aligned)
             KLAUNCH(k_pass1_maj<1><<<grid, kPass1Threads, 0, s>>>(v, d, nb, lo_key, hi_key, maj, nonfinite));
