@@ -1389,6 +1389,8 @@ __global__ void __launch_bounds__(kGroup == 32 ? 256 : kGroup)
 constexpr int kMcInThreads = 512;
 __global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* __restrict__ v, Dims d,
                                                                    const uint8_t* __restrict__ active,
+                                                                   const uint32_t* __restrict__ lo_key,
+                                                                   const uint32_t* __restrict__ hi_key,
                                                                    const uint32_t* __restrict__ bsel, int mc, int mx,
                                                                    int my, float* __restrict__ mcmin,
                                                                    float* __restrict__ mcmax)
@@ -1406,13 +1408,21 @@ __global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* 
     if (threadIdx.x == 0) { s_nparts = 0; s_hasB = 0; }
     __syncthreads();
     const int nbx = (x1 >> 5) - (x0 >> 5) + 1, nby = (y1 >> 5) - (y0 >> 5) + 1, nbz = (z1 >> 5) - (z0 >> 5) + 1;
+    float bmin = INFINITY, bmax = -INFINITY;   // ranges of the whole active bricks this thread lists
     if ((int)threadIdx.x < nbx * nby * nbz) {
         const int t = threadIdx.x;
         const int bx = (x0 >> 5) + t % nbx, by = (y0 >> 5) + (t / nbx) % nby, bz = (z0 >> 5) + t / (nbx * nby);
         const int ax0 = max(x0, bx * 32), ax1 = min(x1, bx * 32 + 31);
         const int ay0 = max(y0, by * 32), ay1 = min(y1, by * 32 + 31);
         const int az0 = max(z0, bz * 32), az1 = min(z1, bz * 32 + 31);
-        if (__ldg(active + ((size_t)bz * d.by + by) * d.bx + bx)) {
+        const size_t bi = ((size_t)bz * d.by + by) * d.bx + bx;
+        if (__ldg(active + bi) && ax0 == bx * 32 && ay0 == by * 32 && az0 == bz * 32 &&
+            ax1 == min(bx * 32 + 31, d.nx - 1) && ay1 == min(by * 32 + 31, d.ny - 1) && az1 == min(bz * 32 + 31, d.nz - 1)) {
+            // the whole brick: its range from pass 1 (the exact min and max of
+            // its voxels in the total order), no voxel read
+            bmin = __uint_as_float(okey_inv(__ldg(lo_key + bi)));
+            bmax = __uint_as_float(okey_inv(__ldg(hi_key + bi)));
+        } else if (__ldg(active + bi)) {
             const int i = atomicAdd(&s_nparts, 1);
             s_part[i][0] = ax0;
             s_part[i][1] = ax1 - ax0 + 1;
@@ -1427,7 +1437,7 @@ __global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* 
         }
     }
     __syncthreads();
-    float vmin = INFINITY, vmax = -INFINITY;
+    float vmin = bmin, vmax = bmax;
     if (threadIdx.x == 0) {
         if (s_hasB) { const float B = __uint_as_float(bsel[1]); vmin = B; vmax = B; }
         if (x0 == 0 && y0 == 0 && z0 == 0) { vmin = fminf(vmin, __ldg(v)); vmax = fmaxf(vmax, __ldg(v)); }
@@ -1897,7 +1907,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
         const GridView& gv = g->view;
         const long long ncell = (long long)gv.mx * gv.my * gv.mz;
         KLAUNCH(k_macrocells_input<<<(unsigned)ncell, kMcInThreads, 0, s>>>(
-            vol, d, active, bsel, gv.mc, gv.mx, gv.my, reinterpret_cast<float*>(base + g->off_mcmin),
+            vol, d, active, lo_key, hi_key, bsel, gv.mc, gv.mx, gv.my, reinterpret_cast<float*>(base + g->off_mcmin),
             reinterpret_cast<float*>(base + g->off_mcmax)));
         e = cudaGetLastError();
         st = e == cudaSuccess ? VDBC_OK : cuda_status(e, "vdbc_encode: macrocells");

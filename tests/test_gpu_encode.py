@@ -100,10 +100,14 @@ def test_encoder_bit_exact_metrics_and_quantized_payloads(env, metric, payload):
     check_encoding(env, host, 6.0, metric=metric, payload=payload)
 
 
-@pytest.mark.parametrize("macrocell,payload", [(4, 0), (8, 0), (13, 0), (48, 0), (56, 0), (64, 1), (48, 2)])
+@pytest.mark.parametrize("macrocell,payload", [(4, 0), (8, 0), (13, 0), (33, 0), (48, 0), (56, 0), (64, 0), (64, 1),
+                                               (48, 2)])
 def test_macrocell_sizes(env, macrocell, payload):
     """Cells above 4096 dilated voxels take the block-per-cell kernels: the
-    input-based one for FP32 leaves, the tree-based one for FP16/FP8."""
+    input-based one for FP32 leaves (which takes a whole active brick's range
+    from pass 1 and reads only partial bricks; 33, 48, 56 and 64 cover whole
+    bricks, 64 the clipped ones at the volume's edges too), the tree-based one for
+    FP16/FP8."""
     host = env["vg"].generate_host(env["vg"].make_params("turbulence", (150, 97, 131), 2))
     check_encoding(env, host, 2.0, payload=payload, macrocell=macrocell)
 
