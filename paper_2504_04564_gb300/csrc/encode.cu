@@ -599,15 +599,11 @@ __global__ void __launch_bounds__(1024) k_argmax(const unsigned long long* __res
 // empty space and at its edge) adds to a per-warp run in registers instead
 // of an atomic on that one global bin.  kVec: float4 rows, as pass 1 in kMode 1.
 template <bool kVec>
-__global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict__ v, Dims d,
-                                                        const uint32_t* __restrict__ lo_key,
-                                                        const uint32_t* __restrict__ hi_key,
-                                                        const uint32_t* __restrict__ bsel,
-                                                        unsigned long long* __restrict__ hist,
-                                                        const Majority* __restrict__ maj, long long nvox)
+__device__ __forceinline__ void pass2_brick(const float* __restrict__ v, const Dims& d,
+                                            const uint32_t* __restrict__ lo_key, const uint32_t* __restrict__ hi_key,
+                                            const uint32_t* __restrict__ bsel, unsigned long long* __restrict__ hist,
+                                            const int b)
 {
-    if (is_majority(maj, nvox)) return;          // B is the counted candidate
-    const int b = blockIdx.x;
     const uint32_t H = bsel[0];
     // key range of the bit patterns [H<<16, H<<16 | 0xffff]
     const uint32_t p0 = H << 16, p1 = (H << 16) | 0xffffu;
@@ -720,6 +716,21 @@ __global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict_
         }
     }
     if (run_cnt && lane == 0) atomicAdd(hist + run_key, run_cnt);
+}
+
+// blocks take bricks in turn (a few per SM): when the candidate holds the
+// majority every block returns at once, and a block per brick cost 0.1 ms of
+// launches on the full-scale cloud for nothing
+template <bool kVec>
+__global__ void __launch_bounds__(kPassThreads) k_pass2(const float* __restrict__ v, Dims d,
+                                                        const uint32_t* __restrict__ lo_key,
+                                                        const uint32_t* __restrict__ hi_key,
+                                                        const uint32_t* __restrict__ bsel,
+                                                        unsigned long long* __restrict__ hist,
+                                                        const Majority* __restrict__ maj, long long nvox, int nbricks)
+{
+    if (is_majority(maj, nvox)) return;          // B is the counted candidate
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x) pass2_brick<kVec>(v, d, lo_key, hi_key, bsel, hist, b);
 }
 
 // ---------------------------------------------------------------- scores (Eq. f1-f3)
@@ -1547,10 +1558,11 @@ vdbc_status launch_background(const float* v, const Dims& d, int nb, unsigned gr
         KLAUNCH(k_pass1<0><<<grid, kPass1Threads, kPass1Smem, s>>>(v, d, nb, lo_key, hi_key, hist, nonfinite, m, nvox));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 0, m, nvox));
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * sizeof(unsigned long long), s));
+    const unsigned p2grid = (unsigned)std::min<long long>(nb, (long long)grid * 8);   // (grid: one block per SM)
     if (aligned)
-        KLAUNCH(k_pass2<true><<<(unsigned)nb, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox));
+        KLAUNCH(k_pass2<true><<<p2grid, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox, nb));
     else
-        KLAUNCH(k_pass2<false><<<(unsigned)nb, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox));
+        KLAUNCH(k_pass2<false><<<p2grid, kPassThreads, 0, s>>>(v, d, lo_key, hi_key, bsel, hist, m, nvox, nb));
     KLAUNCH(k_argmax<<<1, 1024, 0, s>>>(hist, bsel, 1, m, nvox));
     return VDBC_OK;
 }
