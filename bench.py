@@ -449,8 +449,9 @@ def run_e2e(torch, v, volgen, w, cam, med, dev, args, barrier, world, paths_per_
     H, W = w["height"], w["width"]
     host_vol = volgen.generate_torch(volgen.make_params(w["kind"], w["dims"], w["seed"]), dev).cpu().pin_memory()
     torch.cuda.empty_cache()
+    nlanes = int(os.environ.get("VDBC_E2E_LANES", "2"))
     lanes = [dict(stream=torch.cuda.Stream(device=dev), img=np.empty((H, W, 4), dtype=np.float32))
-             for _ in range(2)]
+             for _ in range(nlanes)]
 
     def e2e_steps(lane, n):
         torch.cuda.set_device(dev)
@@ -468,7 +469,7 @@ def run_e2e(torch, v, volgen, w, cam, med, dev, args, barrier, world, paths_per_
                 e2e_steps(lane, n)
             except Exception as ex:       # surfaced below, on the calling thread
                 errs.append(ex)
-        ts = [threading.Thread(target=body, args=(lanes[i], counts[i])) for i in range(2)]
+        ts = [threading.Thread(target=body, args=(lanes[i], counts[i])) for i in range(len(lanes))]
         for t in ts:
             t.start()
         for t in ts:
@@ -477,15 +478,15 @@ def run_e2e(torch, v, volgen, w, cam, med, dev, args, barrier, world, paths_per_
             raise errs[0]
 
     torch.cuda.synchronize()
-    run_pair((1, 1))
+    run_pair([1] * len(lanes))
     barrier()
     t0 = time.perf_counter()
-    run_pair(((args.steps + 1) // 2, args.steps // 2))
+    run_pair([args.steps // len(lanes) + (1 if i < args.steps % len(lanes) else 0) for i in range(len(lanes))])
     barrier()
     e2e_s = time.perf_counter() - t0
     out = {"value": round(world * paths_per_step * args.steps / e2e_s / 1e6, 3), "unit": "Mpaths/s",
            "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(H * W * 16),
-           "pipeline": "2 host threads, a stream each; one step's upload overlaps the other's tracker"}
+           "pipeline": "%d host threads, a stream each; one step's upload overlaps the others' work" % len(lanes)}
     del host_vol
     torch.cuda.empty_cache()
     return out

@@ -23,9 +23,10 @@
 //                  histogram inside it (a brick of one bit pattern, known
 //                  from its range, is counted without being read)
 //   k_scores       one thread per brick: FP64 f with no contraction
-//   k_select       one CTA: the N-th largest FP64 key (bisection on keys in
-//                  registers up to 4096 bricks, radix selection by bytes
-//                  above), ties by brick index
+//   k_select       one CTA: the N-th largest FP64 key, ties by brick index
+//                  (bisection on keys in registers, up to 4096 bricks)
+//   k_sel_*        the same above 4096 bricks over the whole GPU: radix
+//                  passes by bytes, then ties ranked across CTAs
 //   k_leaf_status  one warp per candidate leaf: constant? (prune) tile value?
 //   scans (one CTA up to 64K entries), k_fill_* tree tables, k_fill_leaves
 //                  payload copy / quantization
@@ -925,6 +926,194 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const unsigned long long
     if (threadIdx.x == 0) { counts[0] = m; counts[1] = take; }
 }
 
+// ---------------------------------------------------------------- selection above 4096 bricks, grid-wide
+// The same selection as k_select's global-memory branch (the N-th largest
+// key by bytes from the top, ties by brick index), over the whole GPU: one
+// CTA on one SM spent most of its time in the warp matches of its eight
+// passes (0.8 ms for the full-scale cloud's 208,593 bricks).  Per pass, the
+// CTAs count the digit of every key under the prefix chosen so far (per-warp
+// counts in shared memory, one global add per digit and CTA) and one thread
+// picks the digit; then the CTAs count the keys equal to the threshold in
+// their brick ranges, and rank them by brick index from those counts.
+constexpr int kSelMaxCtas = 1024;
+struct SelState {
+    unsigned long long prefix, pmask;
+    long long rank, m, take;
+    int done;                     // take == m or take == 0: every non-empty brick, or none
+    int pad;
+    unsigned hist[256];
+    unsigned ties[kSelMaxCtas];   // keys equal to the threshold in each CTA's brick range
+};
+
+__device__ __forceinline__ unsigned long long sel_key1(const unsigned long long* __restrict__ fkey,
+                                                       const uint8_t* __restrict__ empty, int i)
+{
+    return empty[i] ? 0ull : fkey[i] + 1ull;
+}
+
+__global__ void k_sel_init(SelState* st)
+{
+    if (threadIdx.x == 0) {
+        st->prefix = 0ull;
+        st->pmask = 0ull;
+        st->rank = st->m = st->take = 0;
+        st->done = 0;
+    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0u;
+}
+
+// one pass: the digit at `shift` of every non-empty key under the prefix
+__global__ void __launch_bounds__(kSelThreads) k_sel_hist(const unsigned long long* __restrict__ fkey,
+                                                          const uint8_t* __restrict__ empty, int nb,
+                                                          SelState* __restrict__ st, int shift)
+{
+    __shared__ unsigned s_w[kSelThreads / 32][256];
+    if (st->done) return;
+    for (int i = threadIdx.x; i < (kSelThreads / 32) * 256; i += kSelThreads) (&s_w[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, pmask = st->pmask;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = blockIdx.x * kSelThreads * kSelBatch; base < nb; base += gridDim.x * kSelThreads * kSelBatch) {
+        unsigned long long kk[kSelBatch];
+#pragma unroll
+        for (int j = 0; j < kSelBatch; ++j) {
+            const int i = base + j * kSelThreads + threadIdx.x;
+            kk[j] = i < nb ? sel_key1(fkey, empty, i) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kSelBatch; ++j) {
+            const bool in = kk[j] != 0ull && (kk[j] & pmask) == prefix;
+            const unsigned digit = in ? (unsigned)(kk[j] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, digit);
+            if (in && lane == __ffs(peers) - 1) s_w[wid][digit] += (unsigned)__popc(peers);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += kSelThreads) {
+        unsigned t = 0u;
+        for (int w = 0; w < kSelThreads / 32; ++w) t += s_w[w][d];
+        if (t) atomicAdd(&st->hist[d], t);
+    }
+}
+
+// the digit at which the count from the top reaches the rank still wanted
+// (the first pass also fixes m and take); clears the counts for the next pass
+__global__ void k_sel_pick(SelState* st, int shift, long long budget, int first)
+{
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) {
+        s_skip = st->done;
+        if (first) {
+            long long m = 0;
+            for (int d = 0; d < 256; ++d) m += st->hist[d];
+            const long long take = budget < m ? budget : m;
+            st->m = m;
+            st->take = take;
+            st->rank = take;
+            if (take == m || take == 0) st->done = s_skip = 1;
+        }
+        if (!s_skip) {
+            const long long rank = st->rank;
+            long long above = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (above + (long long)st->hist[d] >= rank) break;
+                above += st->hist[d];
+            }
+            st->prefix |= (unsigned long long)d << shift;
+            st->pmask |= 255ull << shift;
+            st->rank = rank - above;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0u;
+}
+
+// keys equal to the threshold V (= the chosen prefix) in each CTA's range
+__global__ void __launch_bounds__(kSelThreads) k_sel_ties(const unsigned long long* __restrict__ fkey,
+                                                          const uint8_t* __restrict__ empty, int nb,
+                                                          SelState* __restrict__ st, int chunk)
+{
+    __shared__ unsigned s[32];
+    __shared__ unsigned s_tot;
+    if (st->done) return;
+    const unsigned long long V = st->prefix;
+    const int lo = blockIdx.x * chunk, hi = min(nb, lo + chunk);
+    unsigned n = 0u;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kSelThreads) n += sel_key1(fkey, empty, i) == V ? 1u : 0u;
+    n = block_count(n, s, &s_tot);
+    if (threadIdx.x == 0) st->ties[blockIdx.x] = n;
+}
+
+// the brick set: keys above V, and the first `need` keys equal to V in brick
+// order (their rank: the ties of earlier CTAs, earlier rounds, warps, lanes)
+__global__ void __launch_bounds__(kSelThreads) k_sel_assign(const unsigned long long* __restrict__ fkey,
+                                                            const uint8_t* __restrict__ empty, int nb,
+                                                            const SelState* __restrict__ st, int chunk,
+                                                            uint8_t* __restrict__ active,
+                                                            long long* __restrict__ counts)
+{
+    __shared__ unsigned s_w[32];
+    __shared__ long long s_base;
+    const int lo = blockIdx.x * chunk, hi = min(nb, lo + chunk);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { counts[0] = st->m; counts[1] = st->take; }
+    if (st->done) {
+        const bool all = st->take > 0;
+        for (int i = lo + (int)threadIdx.x; i < hi; i += kSelThreads) active[i] = (all && !empty[i]) ? 1 : 0;
+        return;
+    }
+    const unsigned long long V = st->prefix;
+    const long long need = st->rank;
+    if (threadIdx.x == 0) {
+        long long b = 0;
+        for (int c = 0; c < (int)blockIdx.x; ++c) b += st->ties[c];
+        s_base = b;
+    }
+    __syncthreads();
+    long long run = s_base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = lo; base < hi; base += kSelThreads) {
+        const int i = base + (int)threadIdx.x;
+        const unsigned long long k = i < hi ? sel_key1(fkey, empty, i) : 0ull;
+        const bool eq = k != 0ull && k == V;
+        const unsigned bal = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0) s_w[w] = (unsigned)__popc(bal);
+        __syncthreads();
+        long long mine = run + __popc(bal & ((1u << lane) - 1u));
+        unsigned tot = 0u;
+        for (int q = 0; q < kSelThreads / 32; ++q) {
+            if (q < w) mine += s_w[q];
+            tot += s_w[q];
+        }
+        if (i < hi) active[i] = (k != 0ull && (k > V || (eq && mine < need))) ? 1 : 0;
+        run += tot;
+        __syncthreads();
+    }
+}
+
+// the brick selection: k_select up to 4096 bricks (keys in registers), the
+// grid-wide passes above; st is scratch for the latter, sms the SM count
+vdbc_status launch_select(const unsigned long long* fkey, const uint8_t* empty, int nb, long long budget,
+                          uint8_t* active, long long* counts, SelState* st, int sms, cudaStream_t s)
+{
+    if (nb <= kSelCache * kSelThreads) {
+        KLAUNCH(k_select<<<1, kSelThreads, 0, s>>>(fkey, empty, nb, budget, active, counts));
+        return VDBC_OK;
+    }
+    const int ctas = std::min(kSelMaxCtas, std::min(2 * std::max(1, sms), (nb + kSelThreads - 1) / kSelThreads));
+    const int chunk = (nb + ctas - 1) / ctas;
+    KLAUNCH(k_sel_init<<<1, 256, 0, s>>>(st));
+    for (int p = 0; p < 8; ++p) {
+        const int shift = 56 - 8 * p;
+        KLAUNCH(k_sel_hist<<<ctas, kSelThreads, 0, s>>>(fkey, empty, nb, st, shift));
+        KLAUNCH(k_sel_pick<<<1, 256, 0, s>>>(st, shift, budget, p == 0));
+    }
+    KLAUNCH(k_sel_ties<<<ctas, kSelThreads, 0, s>>>(fkey, empty, nb, st, chunk));
+    KLAUNCH(k_sel_assign<<<ctas, kSelThreads, 0, s>>>(fkey, empty, nb, st, chunk, active, counts));
+    VDBC_CUDA(cudaGetLastError());
+    return VDBC_OK;
+}
+
 // ---------------------------------------------------------------- exclusive scan (u32)
 constexpr int kScanBlock = 1024, kScanItems = 4;
 
@@ -1799,6 +1988,8 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     VDBC_TRY(sc.get(&total, 8));
     Majority* maj = nullptr;
     VDBC_TRY(sc.get(&maj, 1));
+    SelState* selst = nullptr;
+    VDBC_TRY(sc.get(&selst, 1));
 
     // phase 1: histogram -> B (two levels), brick ranges
     VDBC_CUDA(cudaMemsetAsync(hist, 0, 65536 * 8, s));
@@ -1810,8 +2001,7 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(lo_key, hi_key, nb, bsel, metric, fkey, empty));
     double nbud = std::floor((double)nb * 131072.0 / (ratio * (double)brick_bytes(payload)));
     const long long budget = nbud > (double)nb ? (long long)nb : (long long)nbud;
-    KLAUNCH(k_select<<<1, 1024, 0, s>>>(fkey, empty, nb, budget, active, counts));
-    VDBC_CUDA(cudaGetLastError());
+    VDBC_TRY(launch_select(fkey, empty, nb, budget, active, counts, selst, (int)p1grid, s));
 
     // compact list of active bricks (x-fastest brick order)
     uint32_t *act32, *brank;
@@ -2029,6 +2219,7 @@ struct NoAllocScratch {
     uint32_t bsel[2];
     int nonfinite;
     Majority maj;                            // the background's candidate pattern and its count
+    SelState sel;                            // the grid-wide selection's state
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -2141,8 +2332,8 @@ extern "C" vdbc_status vdbc_select_bricks_noalloc(const vdbc_dense* in, const vd
                                &sc->nonfinite, &sc->maj, s));
     KLAUNCH(k_scores<<<grid1d(nb, 256), 256, 0, s>>>(sc->lo_key, sc->hi_key, (int)nb, sc->bsel, metric, sc->fkey,
                                                      sc->empty));
-    KLAUNCH(k_select<<<1, 1024, 0, s>>>(sc->fkey, sc->empty, (int)nb, budget, active_out,
-                                        reinterpret_cast<long long*>(counts_out)));
+    VDBC_TRY(launch_select(sc->fkey, sc->empty, (int)nb, budget, active_out, reinterpret_cast<long long*>(counts_out),
+                           &sc->sel, (int)p1grid, s));
     KLAUNCH(k_noalloc_finish<<<1, 32, 0, s>>>(sc->bsel, &sc->nonfinite, background_bits_out,
                                               reinterpret_cast<long long*>(counts_out)));
     VDBC_CUDA(cudaGetLastError());
