@@ -555,6 +555,13 @@ struct BatchSource {
 // runs.  Each lane's arithmetic is the same either way (equal images).
 enum : int { kPhLook = 0, kPhFlight = 1, kPhStart = 2, kPhEnd = 3 };
 
+// the walk of a free flight over the macrocells: 1 one flat loop of single
+// cell steps shared by the warp's lanes, 0 a loop of crossings with an inner
+// search (next_cell) per crossing
+#ifndef VDBC_PT_FLAT
+#define VDBC_PT_FLAT 1
+#endif
+
 template <bool kUseCoarse, class Src, bool kPhased = false>
 __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
                                         int chunk, unsigned stride)
@@ -713,14 +720,61 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 tau = -flog(1.0f - u01(r.x));
                 ua = u01(r.y); ub = u01(r.z); uc = u01(r.w);
             }
-            // spend tau over as many cells as it lasts (cheap inner walk), so
-            // that the draw and the lookup below run once per iteration
+            // spend tau over as many cells as it lasts, so that the draw and
+            // the lookup below run once per iteration
+#if VDBC_PT_FLAT
+            // One DDA cell per trip for every lane: a lane standing in an
+            // occupied cell spends tau over it (or stops at its collision
+            // point), a lane between occupied cells examines the next cell as
+            // next_cell does.  The lanes of a warp thus share one loop, whose
+            // trips are the most cells any lane passes, instead of an inner
+            // search loop per crossing; each lane's arithmetic is next_cell's.
+            if (!ended && !parked) {
+                bool have = true;   // the lane stands in an occupied cell (tr.mj, tr.texit, tr.tcur)
+                for (;;) {
+                    float tadv = 0.0f;
+                    if (!have) {
+                        int id;
+                        float tex;
+                        if (!tr.dda.cell(m, id, tex)) { ended = true; break; }
+                        VDBC_EVENT(w, 1);
+                        if (--guard < 0) { ended = true; break; }
+                        if constexpr (kUseCoarse) {
+                            int cid = ((tr.dda.cz / kCoarse) * cy_n + tr.dda.cy / kCoarse) * cx_n + tr.dda.cx / kCoarse;
+                            if (!((cbits[cid >> 5] >> (cid & 31)) & 1u)) {
+                                VDBC_EVENT(w, 2);
+                                if (!tr.dda.skip_block(m, o)) { ended = true; break; }
+                                continue;
+                            }
+                        }
+                        float mj = 0.0f;
+                        if (((bits[id >> 5] >> (id & 31)) & 1u) && tex > tr.dda.t)
+                            mj = __fmul_rn(med.sigma_scale, __ldg(m.mcmax + id));
+                        if (mj > 0.0f) {
+                            tr.mj = mj;
+                            tr.texit = tex;
+                            tr.tcur = tr.dda.t;
+                            have = true;
+                        }
+                        tadv = tex;
+                    }
+                    if (have) {
+                        const float reach = __fmul_rn(tr.mj, __fsub_rn(tr.texit, tr.tcur));
+                        if (tau < reach) break;          // the collision point lies in this cell
+                        tau = __fsub_rn(tau, reach);
+                        tadv = tr.texit;
+                        steps_in_cell = 0;
+                        have = false;
+                    }
+                    tr.dda.advance(m, o, tadv);
+                }
+            }
+#else
+            // (nested form: each crossing searches the next occupied cell in
+            // an inner loop)
             for (int k = 0; !ended && !parked; ++k) {
                 float reach = __fmul_rn(tr.mj, __fsub_rn(tr.texit, tr.tcur));
                 if (tau < reach) break;
-#if VDBC_PT_WALK > 0
-                if (k == VDBC_PT_WALK) { parked = true; break; }   // go on next iteration
-#endif
                 tau = __fsub_rn(tau, reach);
                 tr.dda.advance(m, o, tr.texit);
                 steps_in_cell = 0;
@@ -735,6 +789,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                     break;
                 }
             }
+#endif
             if (ended && guard < 0) w.flags |= kErrDdaSteps;
             if (ended) {
                 mode = -mode;            // ray ended
@@ -832,14 +887,6 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
 #endif
     flush_stats(st, w, paths);
 }
-
-// cell crossings a lane makes per loop iteration before it parks its free
-// flight until the next iteration (0: no limit).  One keeps the warp's lanes
-// in step: 28.2 ms against 30.4 unbounded (2: 28.6, 4: 29.8) on the 512^3
-// medium, with the same images (each lane's arithmetic is unchanged)
-#ifndef VDBC_PT_WALK
-#define VDBC_PT_WALK 1
-#endif
 
 // resident 256-thread blocks per SM the tracker is compiled for: 4 (64
 // registers) measured fastest for the plain samplers without the coarse level
