@@ -561,6 +561,15 @@ enum : int { kPhLook = 0, kPhFlight = 1, kPhStart = 2, kPhEnd = 3 };
 #ifndef VDBC_PT_FLAT
 #define VDBC_PT_FLAT 1
 #endif
+// cells a lane's flat walk examines per loop iteration before it parks the
+// free flight until the next iteration (0: no limit).  Parking measured
+// slower at every limit: 55.7, 50.6 and 52.2 ms at 2, 4 and 8 cells against
+// 37.9 unbounded on the full-scale cloud frame, 10.8, 10.1, 10.3 against 8.33
+// on the 512^3 frame (the iterations it adds cost more than the lanes it
+// keeps in step)
+#ifndef VDBC_PT_WALK
+#define VDBC_PT_WALK 0
+#endif
 
 template <bool kUseCoarse, class Src, bool kPhased = false>
 __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitems, DevStats* __restrict__ st,
@@ -707,7 +716,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
         float3 x = f3(0.f, 0.f, 0.f);
         if ((mode == kDelta || mode == kRatio) && !start && (!kPhased || (P == kPhFlight && !pend_look))) {
             bool ended = false, parked = false;
-            if (searching) {   // the search for the ray's next occupied cell goes on
+            if (!VDBC_PT_FLAT && searching) {   // the search for the ray's next occupied cell goes on
                 const int st = next_cell<kUseCoarse>(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w);
                 if (st == kCellEnded) ended = true;
                 else if (st == kCellSearching) parked = true;
@@ -730,8 +739,18 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             // trips are the most cells any lane passes, instead of an inner
             // search loop per crossing; each lane's arithmetic is next_cell's.
             if (!ended && !parked) {
-                bool have = true;   // the lane stands in an occupied cell (tr.mj, tr.texit, tr.tcur)
-                for (;;) {
+                // the lane stands in an occupied cell (tr.mj, tr.texit, tr.tcur)
+                // unless it resumes a search it was parked in
+                bool have = !searching;
+                searching = false;
+                for (int k = 0;; ++k) {
+#if VDBC_PT_WALK > 0
+                    if (k == VDBC_PT_WALK) {   // go on in the next iteration (tau kept)
+                        parked = true;
+                        searching = !have;
+                        break;
+                    }
+#endif
                     float tadv = 0.0f;
                     if (!have) {
                         int id;
@@ -892,7 +911,10 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
 // registers) measured fastest for the plain samplers without the coarse level
 // (36.4 ms against 40.1 at 2, 44.0 at 3, 37.1 at 5 on the 512^3 medium with
 // 48^3 cells; again with 32-item work chunks and 56^3 cells: 16.1 ms against
-// 16.7 at 5 and 17.0 at 6); with the coarse level (8^3 cells) 2 is faster
+// 16.7 at 5 and 17.0 at 6; with the flat walk, the full-scale cloud frame
+// 42.1 at 3 against 37.9 with 32-item chunks and 35.2 at 5 against 34.9 with
+// adaptive chunks, the 512^3 frame 8.58 at 3 and 8.75 at 5 against 8.30); with
+// the coarse level (8^3 cells) 2 is faster
 // (130.9 against 153.6 ms), and the learned sampler keeps 2 (its tile code
 // needs the registers)
 #ifndef VDBC_PT_MIN_BLOCKS
@@ -1430,19 +1452,27 @@ bool coarse_skipping(int)
     return e && e[0] == '1';
 }
 
-// items a warp takes from the work counter at once: 32, one item a lane (one
-// 8x4 pixel tile of one sample).  Larger chunks leave each warp a longer
-// tail of paths when the counter runs out (measured on the 1024^2 x 16 spp
-// frame: 16.4 ms at 32, 18.1 at 256, 23.9 at 1024); VDBC_PT_CHUNK overrides
+// items a warp takes from the work counter at once.  A chunk is consecutive
+// 8x4 pixel tiles of one sample, which the warp's lanes take in order: larger
+// chunks keep a warp's successive paths next to each other in the image (and
+// so in the volume), smaller ones leave each warp a shorter tail of paths when
+// the counter runs out.  The chunk is the largest of 32, 64 and 128 items that
+// still gives every resident warp 200 chunks, so that its last one is under
+// half a percent of its share.  Measured (ms): the 1920x1080 x 64 spp frame of
+// the full-scale cloud (27,000 items a warp) 37.65 at 32, 35.75 at 64, 34.79 at
+// 128, 34.82 at 192, 35.14 at 256; the 1024^2 x 16 spp frame of the 512^3
+// medium (3,400 items a warp) 8.32 at 32, 8.34 at 64, 8.61 at 128, 9.31 at 256.
+// VDBC_PT_CHUNK overrides.
 int work_chunk(unsigned long long items, long long resident_warps)
 {
-    (void)items;
-    (void)resident_warps;
     if (const char* e = std::getenv("VDBC_PT_CHUNK")) {
         int c = std::atoi(e);
         return c < 32 ? 32 : c;
     }
-    return 32;
+    const unsigned long long w = (unsigned long long)std::max<long long>(resident_warps, 1);
+    int c = 32;
+    while (c < 128 && items >= 200ull * w * (unsigned long long)(2 * c)) c *= 2;
+    return c;
 }
 constexpr size_t kSmemBitsMax = 96 * 1024;
 
@@ -2133,10 +2163,10 @@ vdbc_status batch_autotune(vdbc_batch* b, cudaStream_t s)
         return VDBC_OK;
     }
     // launch shapes: (threads per block, accessor cache depth) pairs, work
-    // items a warp takes per refill (32, 64, 256: one, two or eight paths per
-    // lane per refill), coarse DDA level on or off
+    // items a warp takes per refill (32, 64, 128, 256: one, two, four or eight
+    // paths per lane per refill), coarse DDA level on or off
     const int shapes[][2] = {{128, 1}, {256, 1}, {256, 2}};
-    const int chunks[] = {32, 64, 256};
+    const int chunks[] = {32, 64, 128, 256};
     const int coarses[] = {1, 0};
     cudaEvent_t e0, e1;
     VDBC_CUDA(cudaEventCreate(&e0));

@@ -277,7 +277,12 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 //    each leaf's entry once, the rest go corner by corner.
 // 1 is the default: the second path's extra code costs more than the
 // descents it saves (8.57 against 9.98 ms on the 512^3 frame, 44.01 against
-// 45.28 ms on the cloud; the images are bit-identical).
+// 45.28 ms on the cloud; the images are bit-identical).  A third form, which
+// found the lower node of the first corner's leaf once and took every other
+// corner's leaf entry from it with independent loads (no corner waiting on
+// the previous one's descent), measured 35.4 against 34.9 ms on the cloud and
+// 8.28 against 8.30 on the 512^3 frame: the eight entries in flight cost
+// spills (300 bytes a thread against 152).
 #ifndef VDBC_TRI_STRADDLE
 #define VDBC_TRI_STRADDLE 1
 #endif
