@@ -561,6 +561,13 @@ enum : int { kPhLook = 0, kPhFlight = 1, kPhStart = 2, kPhEnd = 3 };
 #ifndef VDBC_PT_FLAT
 #define VDBC_PT_FLAT 1
 #endif
+// 1: a ray's search for its first occupied cell runs in the flat walk of the
+// free flight, whose draw is then made before the cell is found (its call
+// number counted once it is); 0: the search runs where the ray starts,
+// before the draw
+#ifndef VDBC_PT_SPECDRAW
+#define VDBC_PT_SPECDRAW 1
+#endif
 // cells a lane's flat walk examines per loop iteration before it parks the
 // free flight until the next iteration (0: no limit).  Parking measured
 // slower at every limit: 55.7, 50.6 and 52.2 ms at 2, 4 and 8 cells against
@@ -590,6 +597,7 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
     bool start = false;   // a ray to start before the next free flight
     bool searching = false;   // the ray's next occupied cell is still being searched for
     bool pend_look = false;   // (phased) a lookup waits at o + tcur d
+    bool spec = false;        // the current free flight was drawn ahead of the ray's first occupied cell
     unsigned long long pool_next = 0, pool_end = 0;   // this warp's share of the work counter
     Track tr;
     Accessor acc;
@@ -701,9 +709,13 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 VDBC_EVENT(w, 4);
                 guard = m.mx + m.my + m.mz + 8;
                 steps_in_cell = 0;
+#if VDBC_PT_FLAT && VDBC_PT_SPECDRAW
+                searching = true;   // the flight's walk finds the first occupied cell
+#else
                 const int st = next_cell<kUseCoarse>(tr, m, med, o, bits, cbits, cx_n, cy_n, guard, w);
                 if (st == kCellEnded) mode = -mode;   // leaves at once
                 searching = st == kCellSearching;
+#endif
             } else {
                 mode = -mode;
             }
@@ -724,8 +736,22 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
             }
             if (!ended && !parked && tau < 0.0f) {
                 Rng rng{pixel, J.sample_base + sample, J.k0, J.k1};
+#if VDBC_PT_FLAT && VDBC_PT_SPECDRAW
+                // a lane still looking for its ray's first occupied cell draws
+                // ahead of finding it, and the draw's call number is taken
+                // once the cell is found: a ray that meets no occupied cell
+                // takes no call, as in the oracle
+                spec = searching;
+                U4 r = (mode == kDelta) ? rng.draw(call, 0) : rng.draw(lcall, 1);
+                if (!spec) {
+                    if (mode == kDelta) ++call;
+                    else ++lcall;
+                    VDBC_EVENT(w, 3);
+                }
+#else
                 U4 r = (mode == kDelta) ? rng.draw(call++, 0) : rng.draw(lcall++, 1);
                 VDBC_EVENT(w, 3);
+#endif
                 tau = -flog(1.0f - u01(r.x));
                 ua = u01(r.y); ub = u01(r.z); uc = u01(r.w);
             }
@@ -774,6 +800,14 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                             tr.texit = tex;
                             tr.tcur = tr.dda.t;
                             have = true;
+#if VDBC_PT_SPECDRAW
+                            if (spec) {   // the ray's first occupied cell: its draw counts
+                                if (mode == kDelta) ++call;
+                                else ++lcall;
+                                VDBC_EVENT(w, 3);
+                                spec = false;
+                            }
+#endif
                         }
                         tadv = tex;
                     }
@@ -1768,17 +1802,21 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
     if (g.payload == VDBC_FP8)
         return render_common(VdbSamplerT<2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                              out_on_device, stream);
-    // VDBC_PT_LOOKUP = <depth><straddle> picks another accessor depth (1, 2) and
-    // straddle mode (1, 2) for FP32 grids, for measuring them against each other
+    // VDBC_PT_LOOKUP = <depth><mode> picks another accessor depth (1, 2) and
+    // stencil mode (11, 12, 22, 24; the default is depth 1, mode 4) for FP32
+    // grids, for measuring them against each other
     const char* lk = std::getenv("VDBC_PT_LOOKUP");
-    if (lk && std::strcmp(lk, "22") == 0)
-        return render_common(VdbSamplerT<0, 2, 2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+    if (lk && std::strcmp(lk, "11") == 0)
+        return render_common(VdbSamplerT<0, 1, 1>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
                              rgba_out, out_on_device, stream);
     if (lk && std::strcmp(lk, "12") == 0)
         return render_common(VdbSamplerT<0, 1, 2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
                              rgba_out, out_on_device, stream);
-    if (lk && std::strcmp(lk, "21") == 0)
-        return render_common(VdbSamplerT<0, 2, 1>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+    if (lk && std::strcmp(lk, "22") == 0)
+        return render_common(VdbSamplerT<0, 2, 2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
+                             rgba_out, out_on_device, stream);
+    if (lk && std::strcmp(lk, "24") == 0)
+        return render_common(VdbSamplerT<0, 2, 4>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed,
                              rgba_out, out_on_device, stream);
     return render_common(VdbSamplerT<0>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                          out_on_device, stream);

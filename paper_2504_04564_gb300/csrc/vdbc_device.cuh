@@ -270,21 +270,32 @@ __device__ __forceinline__ float voxel(const GridView& g, Accessor& acc, int i, 
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// corners of a trilinear stencil that straddles a leaf boundary:
-// 1: corner by corner through the accessor (a corner in another leaf than the
-//    previous corner moves the cached leaf);
-// 2: stencils across one face (two leaves, the most frequent straddle) take
-//    each leaf's entry once, the rest go corner by corner.
-// 1 is the default: the second path's extra code costs more than the
-// descents it saves (8.57 against 9.98 ms on the 512^3 frame, 44.01 against
-// 45.28 ms on the cloud; the images are bit-identical).  A third form, which
-// found the lower node of the first corner's leaf once and took every other
-// corner's leaf entry from it with independent loads (no corner waiting on
-// the previous one's descent), measured 35.4 against 34.9 ms on the cloud and
-// 8.28 against 8.30 on the 512^3 frame: the eight entries in flight cost
-// spills (300 bytes a thread against 152).
+// How the eight corners of a trilinear stencil are fetched.  A stencil inside
+// one leaf can take the leaf once and its eight values from it (the one-leaf
+// path); a stencil that straddles a leaf boundary (one in three at random
+// positions) goes corner by corner through the accessor, where a corner in
+// another leaf than the previous corner moves the cached leaf.  The
+// corner-by-corner path also serves one-leaf stencils, with the same values.
+// 1: each lane takes the path its own stencil needs.  A warp whose lookups
+//    include both kinds (nearly every warp) runs the two paths one after the
+//    other.
+// 4: the one-leaf path only when every active lane of the warp has a one-leaf
+//    stencil, else corner by corner for all of them: one path per warp.
+// 0: corner by corner always.
+// 2: as 1, and stencils across one face (two leaves, the most frequent
+//    straddle) take each leaf's entry once.
+// 4 is the default: 33.99 ms against 34.98 (mode 1) and 34.26 (mode 0) on
+// the full-scale cloud frame, 7.87 against 8.31 and 7.83 on the 512^3 frame,
+// images bit-identical.  Mode 2's extra code cost more than the descents it
+// saved (9.98 against 8.57 ms on the 512^3 frame, 45.28 against 44.01 ms on
+// the cloud, against mode 1 on an earlier tracker).  A form which found the
+// lower node of the first corner's leaf once and took every other corner's
+// leaf entry from it with independent loads (no corner waiting on the
+// previous one's descent) measured 35.4 against 34.9 ms on the cloud and 8.28
+// against 8.30 on the 512^3 frame (against mode 1): the eight entries in
+// flight cost spills (300 bytes a thread against 152).
 #ifndef VDBC_TRI_STRADDLE
-#define VDBC_TRI_STRADDLE 1
+#define VDBC_TRI_STRADDLE 4
 #endif
 constexpr int kTriStraddle = VDBC_TRI_STRADDLE;
 
@@ -304,7 +315,10 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
     float v000, v100, v010, v110, v001, v101, v011, v111;
     const int lx0 = x0 >> 3, ly0 = y0 >> 3, lz0 = z0 >> 3;
     const int S = (lx0 != (x1 >> 3) ? 1 : 0) | (ly0 != (y1 >> 3) ? 2 : 0) | (lz0 != (z1 >> 3) ? 4 : 0);
-    if (S == 0) {
+    bool fast = S == 0;
+    if (T == 0) fast = false;
+    if (T == 4) fast = __all_sync(__activemask(), S == 0);
+    if (fast) {
         uint32_t e = acc.leaf<D>(g, lx0, ly0, lz0);
         if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
         int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
