@@ -106,7 +106,7 @@ typedef struct {
     double  ratio;      /* R of the target rate 1:R, R >= 1; 1 keeps every non-empty brick */
     int32_t metric;     /* VDBC_F1, VDBC_F2 (default when 0) or VDBC_F3 */
     int32_t payload;    /* VDBC_FP32, VDBC_FP16 or VDBC_FP8 */
-    int32_t macrocell;  /* edge of a majorant macrocell in voxels, 1..64; 0 means 8 */
+    int32_t macrocell;  /* edge of a majorant macrocell in voxels, 1..128; 0 means 8 */
     int32_t reserved;
 } vdbc_encode_params;
 
@@ -269,7 +269,7 @@ vdbc_status vdbc_render_stats_get(const vdbc_grid* grid, void* stream, vdbc_rend
  * 5.3: the structured volume in a 3D CUDA texture) or, with
  * VDBC_FILTER_LINEAR, a linear device copy sampled by the same software
  * trilinear as the grid.  Builds the same macrocell majorant grid from the
- * dense values.
+ * dense values (macrocell edge 1..128 voxels, 0 means 8).
  */
 vdbc_status vdbc_volume_create(const vdbc_dense* in, int32_t filter, int32_t macrocell,
                                void* stream, vdbc_volume** out);

@@ -1596,7 +1596,10 @@ __global__ void __launch_bounds__(kMcInThreads) k_macrocells_input(const float* 
                                                                    int my, float* __restrict__ mcmin,
                                                                    float* __restrict__ mcmax)
 {
-    constexpr int kW = kMcInThreads / 32, kMaxParts = 64;
+    // a cell of at most kMaxMacrocell voxels, dilated by one, overlaps at most
+    // six bricks along an axis
+    constexpr int kW = kMcInThreads / 32, kMaxParts = 216;
+    static_assert(kMaxMacrocell <= 128 && kMaxParts <= kMcInThreads, "one thread per overlapped brick");
     __shared__ float s_lo[kW], s_hi[kW];
     __shared__ int s_part[kMaxParts][4];       // x0, width, y0 | z0 << 16, ey | ez << 16
     __shared__ int s_nparts, s_hasB;
@@ -1955,7 +1958,8 @@ extern "C" vdbc_status vdbc_encode(const vdbc_dense* in, const vdbc_encode_param
     if (payload < VDBC_FP32 || payload > VDBC_FP8)
         return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: unknown payload %d", payload);
     int mc = params->macrocell == 0 ? 8 : params->macrocell;
-    if (mc < 1 || mc > 64) return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: macrocell %d outside 1..64", mc);
+    if (mc < 1 || mc > kMaxMacrocell)
+        return set_error(VDBC_ERR_INVALID_ARG, "vdbc_encode: macrocell %d outside 1..%d", mc, kMaxMacrocell);
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Scratch sc(s);

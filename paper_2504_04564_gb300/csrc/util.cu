@@ -508,7 +508,7 @@ extern "C" vdbc_status vdbc_grid_load(const char* path, void* stream, vdbc_grid*
     if (c != h.checksum) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: checksum mismatch in %s", path);
     for (int a = 0; a < 3; ++a)
         if (info.dims[a] < 1 || info.dims[a] > kMaxDim) return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: bad dims");
-    if ((long long)active.size() != info.n_bricks || info.macrocell < 1 || info.macrocell > 64 ||
+    if ((long long)active.size() != info.n_bricks || info.macrocell < 1 || info.macrocell > kMaxMacrocell ||
         info.payload < VDBC_FP32 || info.payload > VDBC_LEARNED)
         return set_error(VDBC_ERR_FORMAT, "vdbc_grid_load: inconsistent header");
     for (int i = 0; i < 16; ++i)

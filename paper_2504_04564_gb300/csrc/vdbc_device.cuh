@@ -45,6 +45,8 @@ constexpr uint32_t kTile = 0x80000000u;
 constexpr uint32_t kBackgroundEntry = 0x80000000u;   // tile 0
 constexpr int kUpperN = 32768, kLowerN = 4096, kLeafN = 512;
 constexpr int kMaxDim = 8192;
+// largest macrocell edge in voxels (encode, dense volumes, grid files)
+constexpr int kMaxMacrocell = 128;
 
 struct GridView {
     int nx, ny, nz;

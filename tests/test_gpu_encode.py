@@ -101,15 +101,32 @@ def test_encoder_bit_exact_metrics_and_quantized_payloads(env, metric, payload):
 
 
 @pytest.mark.parametrize("macrocell,payload", [(4, 0), (8, 0), (13, 0), (33, 0), (48, 0), (56, 0), (64, 0), (64, 1),
-                                               (48, 2)])
+                                               (48, 2), (96, 0), (128, 0), (128, 2)])
 def test_macrocell_sizes(env, macrocell, payload):
     """Cells above 4096 dilated voxels take the block-per-cell kernels: the
     input-based one for FP32 leaves (which takes a whole active brick's range
     from pass 1 and reads only partial bricks; 33, 48, 56 and 64 cover whole
-    bricks, 64 the clipped ones at the volume's edges too), the tree-based one for
-    FP16/FP8."""
+    bricks, 64 the clipped ones at the volume's edges too; 96 and 128, the
+    largest, overlap up to five and six bricks along an axis), the tree-based
+    one for FP16/FP8."""
     host = env["vg"].generate_host(env["vg"].make_params("turbulence", (150, 97, 131), 2))
     check_encoding(env, host, 2.0, payload=payload, macrocell=macrocell)
+
+
+def test_macrocell_128_six_bricks_per_axis(env):
+    """A 128-voxel cell dilated by one voxel overlaps six 32^3 bricks along each
+    axis once the volume reaches past 256 voxels: the 216 parts the input-based
+    kernel lists at most.  At 1:2 most bricks are active, cut by the cell
+    faces; the ranges equal the oracle's on the decoded grid."""
+    v, orc = env["v"], env["orc"]
+    host = env["vg"].generate_host(env["vg"].make_params("turbulence", (262, 259, 261), 5))
+    vol, grid, e = encode_both(env, host, 2.0, 2, 0, 128, 0)
+    D = orc.decode_dense(host, e["active"], e["background_bits"], 0)
+    mn, mx = v.vdbc_grid_macrocells(grid)
+    omn, omx = orc.macrocell_minmax(D, 128)
+    assert mn.size == 3 * 3 * 3
+    assert np.array_equal(mn, omn) and np.array_equal(mx, omx)
+    grid.close()
 
 
 def tie_volume(dims, levels=37):

@@ -111,10 +111,11 @@ def test_pt_turbulence_matches_oracle(env, payload):
     assert st.paths == 48 * 40 * 4 and st.error_flags == 0 and st.lookups > 48 * 40 * 4
 
 
-@pytest.mark.parametrize("macrocell", [16, 5, 48, 56])
+@pytest.mark.parametrize("macrocell", [16, 5, 48, 56, 100, 128])
 def test_pt_macrocell_sizes_match_oracle(env, macrocell):
-    """Majorant macrocells of other sizes (the benchmark uses 56^3) change the
-    free flights but not the parity with the oracle."""
+    """Majorant macrocells of other sizes (the benchmarks use 56^3 and 128^3)
+    change the free flights but not the parity with the oracle; 100 and 128
+    leave partial cells at the volume's far faces, 128 one cell across y and z."""
     torch, v, orc, vg, sc = env["torch"], env["v"], env["orc"], env["vg"], env["sc"]
     dims = (112, 96, 80)
     host = vg.generate_host(vg.make_params("turbulence", dims, 4))
