@@ -1075,8 +1075,8 @@ def study_fullscale():
     img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     paths = W * H * spp
     peak, _ = measured_peaks()
-    mc = scenes.CLOUD_994["macrocell"]
-    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, mc)
+    mc = scenes.CLOUD_1987["macrocell"]
+    dense = v.vdbc_volume_create(vol, v.FILTER_TEXTURE, scenes.CLOUD_1987["texture_macrocell"])
     ms_d, lk_d = _timed_render(torch, v, dense, cam, med, spp, img, dense=True)
     ref = img.clone()
     dense.close()

@@ -15,7 +15,7 @@ def test_benchmark_scenes():
     f = scenes.CLOUD_1987
     assert f["dims"] == (1987, 1351, 2449) and f["ratio"] == 10.0 and (f["width"], f["height"], f["spp"]) == (1920, 1080, 64)
     assert f["medium"]["albedo"] == 0.95 and f["medium"]["g"] == 0.8 and f["medium"]["max_bounces"] == 32
-    assert f["kind"] == c["kind"] and (f["macrocell"], f["texture_macrocell"]) == (64, 64)
+    assert f["kind"] == c["kind"] and (f["macrocell"], f["texture_macrocell"]) == (128, 128)
     e = scenes.BLOBS_64_EA
     assert e["dims"] == (64, 64, 64) and e["ratio"] == 4.0 and (e["width"], e["height"]) == (128, 128) and e["step"] == 0.5
 

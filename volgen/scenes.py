@@ -59,9 +59,13 @@ CLOUD_994 = dict(kind="cloud", dims=(994, 676, 1225), seed=0, ratio=10.0, width=
                  learn=dict(steps=200, samples_per_leaf=64, lr=2e-3, lr_latent=2e-2, seed=1))
 # the full-scale cloud: 1987 x 1351 x 2449 voxels (26.3 GB dense; the same
 # generator as the 994 x 676 x 1225 cloud) at 1:10, 1920 x 1080 x 64 spp,
-# albedo 0.95, g 0.8, up to 32 bounces; 64^3 macrocells for grid and texture
+# albedo 0.95, g 0.8, up to 32 bounces; 128^3 macrocells for grid and texture,
+# each its fastest measured size (grid 27.1 ms against 27.3 at 112^3, 28.3 at
+# 96^3, 29.6 at 80^3, 32.3 at 64^3; texture 27.3 ms against 31.7 at 96^3 and
+# 40.8 at 64^3): here a path's walk over the cells costs more than the null
+# collisions the larger cells add
 CLOUD_1987 = dict(kind="cloud", dims=(1987, 1351, 2449), seed=0, ratio=10.0, width=1920, height=1080, spp=64,
-                  medium=pt_medium_args(albedo=0.95, g=0.8, max_bounces=32), macrocell=64, texture_macrocell=64)
+                  medium=pt_medium_args(albedo=0.95, g=0.8, max_bounces=32), macrocell=128, texture_macrocell=128)
 # the 64^3 blobs volume at 1:4, EA, 128^2, step 0.5, ortho +z
 BLOBS_64_EA = dict(kind="blobs", dims=(64, 64, 64), seed=0, ratio=4.0, width=128, height=128, step=0.5)
 
