@@ -505,6 +505,8 @@ struct SingleSource {
     const uint32_t* b;
     const uint32_t* cb;
     const float* box;     // the clip box in index space (shared memory)
+    const float* smaj;    // the macrocells' majorants in shared memory, or null
+    __device__ __forceinline__ const float* maj(int) const { return smaj; }
     // rays are clipped to the box of the cells with a positive majorant: no
     // free flight starts outside it, so starting the walk at its boundary
     // changes no path
@@ -548,6 +550,7 @@ struct BatchSource {
     }
     __device__ __forceinline__ const uint32_t* bits(int i) const { return jobs[i].bits; }
     __device__ __forceinline__ const uint32_t* cbits(int i) const { return jobs[i].cbits; }
+    __device__ __forceinline__ const float* maj(int) const { return nullptr; }
     __device__ __forceinline__ float sample(int i, float x, float y, float z, Accessor& a) const
     {
         // the payload is the group's, fixed at compile time (one kernel with a
@@ -806,8 +809,12 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                             }
                         }
                         float mj = 0.0f;
-                        if (((bits[id >> 5] >> (id & 31)) & 1u) && tex > tr.dda.t)
+                        const float* smaj = src.maj(jb);
+                        if (smaj) {   // the same product, formed at launch (positive exactly where the bit is set)
+                            if (tex > tr.dda.t) mj = smaj[id];
+                        } else if (((bits[id >> 5] >> (id & 31)) & 1u) && tex > tr.dda.t) {
                             mj = __fmul_rn(med.sigma_scale, __ldg(m.mcmax + id));
+                        }
                         if (mj > 0.0f) {
                             tr.mj = mj;
                             tr.texit = tex;
@@ -991,11 +998,13 @@ __device__ __forceinline__ void occupied_clip_box(const Majorants& m, const int*
 }
 
 // gbits: nwords fine occupancy words followed by ncwords coarse words; the
-// parts that fit in `smem_words` are staged in shared memory (coarse first)
+// parts that fit in `smem_words` are staged in shared memory (coarse first);
+// smaj_cells > 0: the majorant of every macrocell (sigma_scale x max, the
+// product the walk forms) follows them in shared memory
 template <class S, bool kUseCoarse, bool kPhased = false, int kBlocks = pt_min_blocks<S, kUseCoarse>()>
 __global__ void __launch_bounds__(256, kBlocks)
     k_pt(S smp, JobView job, const uint32_t* __restrict__ gbits, int nwords, int ncwords, int smem_words,
-         DevStats* __restrict__ st, int chunk)
+         int smaj_cells, DevStats* __restrict__ st, int chunk)
 {
     extern __shared__ uint32_t s_bits[];
     __shared__ float s_box[6];
@@ -1010,8 +1019,14 @@ __global__ void __launch_bounds__(256, kBlocks)
             bits = s_bits + ncwords;
         }
     }
+    float* s_maj = nullptr;
+    if (smaj_cells > 0) {
+        s_maj = reinterpret_cast<float*>(s_bits + smem_words);
+        for (int i = threadIdx.x; i < smaj_cells; i += blockDim.x)
+            s_maj[i] = __fmul_rn(job.med.sigma_scale, __ldg(job.m.mcmax + i));
+    }
     __syncthreads();
-    SingleSource<S> src{job, smp, bits, cbits, s_box};
+    SingleSource<S> src{job, smp, bits, cbits, s_box, s_maj};
     pt_loop<kUseCoarse, SingleSource<S>, kPhased>(src, job.items, st, chunk, 1u);
 }
 
@@ -1522,6 +1537,13 @@ int work_chunk(unsigned long long items, long long resident_warps)
     return c;
 }
 constexpr size_t kSmemBitsMax = 96 * 1024;
+// dynamic shared memory a tracker block may take for occupancy words and the
+// majorant table together, leaving room for four blocks per SM
+constexpr size_t kSmemMajMax = 40 * 1024;
+// 1: stage the majorant table in shared memory when it fits (kSmemMajMax)
+#ifndef VDBC_PT_SMEM_MAJ
+#define VDBC_PT_SMEM_MAJ 1
+#endif
 
 // the job's constants for the tracker (bits are filled in by the caller)
 JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int spp, uint64_t seed,
@@ -1556,7 +1578,15 @@ vdbc_status launch_pt_t(const S& smp, const JobView& job, const uint32_t* bits, 
 {
     int smem_words = std::min<int>(nwords + ncwords, (int)(kSmemBitsMax / 4));
     if (smem_words < ncwords) smem_words = 0;
-    size_t smem = (size_t)smem_words * 4;
+    // the majorants go to shared memory when the whole table fits beside the
+    // occupancy words within kSmemMajMax: the walk then reads a found cell's
+    // majorant there instead of from global memory
+    const long long ncell = (long long)job.m.mx * job.m.my * job.m.mz;
+    int smaj_cells = 0;
+#if VDBC_PT_SMEM_MAJ
+    if (smem_words == nwords + ncwords && (size_t)(smem_words + ncell) * 4 <= kSmemMajMax) smaj_cells = (int)ncell;
+#endif
+    size_t smem = (size_t)(smem_words + smaj_cells) * 4;
     auto kern = k_pt<S, kUseCoarse, kPhased, kBlocks>;
     if (smem > 48 * 1024) VDBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -1565,8 +1595,8 @@ vdbc_status launch_pt_t(const S& smp, const JobView& job, const uint32_t* bits, 
     long long want = (long long)((job.items + kPtThreads - 1) / kPtThreads);
     long long blocks = std::min<long long>((long long)sm_count() * per_sm, std::max<long long>(want, 1));
     if (chunk <= 0) chunk = work_chunk(job.items, blocks * (kPtThreads / 32));
-    KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, job, bits, nwords, ncwords, smem_words, stats,
-                                                            chunk));
+    KLAUNCH(kern<<<(unsigned)blocks, kPtThreads, smem, s>>>(smp, job, bits, nwords, ncwords, smem_words, smaj_cells,
+                                                            stats, chunk));
     VDBC_CUDA(cudaGetLastError());
     return VDBC_OK;
 }
@@ -1816,7 +1846,7 @@ extern "C" vdbc_status vdbc_render(const vdbc_grid* grid, const vdbc_camera* cam
         return render_common(VdbSamplerT<2>{g}, mj, grid->info.dims, grid->stats, camera, medium, spp, seed, rgba_out,
                              out_on_device, stream);
     // VDBC_PT_LOOKUP = <depth><mode> picks another accessor depth (1, 2) and
-    // stencil mode (11, 12, 22, 24; the default is depth 1, mode 4) for FP32
+    // stencil mode (11, 12, 22, 24; the default is depth 1, mode 5) for FP32
     // grids, for measuring them against each other
     const char* lk = std::getenv("VDBC_PT_LOOKUP");
     if (lk && std::strcmp(lk, "11") == 0)

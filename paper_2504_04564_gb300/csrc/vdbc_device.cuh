@@ -276,28 +276,36 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 // one leaf can take the leaf once and its eight values from it (the one-leaf
 // path); a stencil that straddles a leaf boundary (one in three at random
 // positions) goes corner by corner through the accessor, where a corner in
-// another leaf than the previous corner moves the cached leaf.  The
-// corner-by-corner path also serves one-leaf stencils, with the same values.
+// another leaf than the previous corner moves the cached leaf (a stencil
+// across an x face alternates leaves corner by corner: up to eight descents,
+// each waiting on the last).  The corner-by-corner path also serves one-leaf
+// stencils, with the same values.
 // 1: each lane takes the path its own stencil needs.  A warp whose lookups
 //    include both kinds (nearly every warp) runs the two paths one after the
 //    other.
 // 4: the one-leaf path only when every active lane of the warp has a one-leaf
 //    stencil, else corner by corner for all of them: one path per warp.
+// 5: every stencil that straddles at most two axes (all but 0.2 % at random
+//    positions) takes its up to four leaves at once: the first corner's
+//    through the accessor, the others by descents that do not wait on each
+//    other; corner by corner for the whole warp only when one of its lanes
+//    straddles all three axes.
 // 0: corner by corner always.
 // 2: as 1, and stencils across one face (two leaves, the most frequent
 //    straddle) take each leaf's entry once.
-// 4 is the default: 33.99 ms against 34.98 (mode 1) and 34.26 (mode 0) on
-// the full-scale cloud frame, 7.87 against 8.31 and 7.83 on the 512^3 frame,
-// images bit-identical.  Mode 2's extra code cost more than the descents it
-// saved (9.98 against 8.57 ms on the 512^3 frame, 45.28 against 44.01 ms on
-// the cloud, against mode 1 on an earlier tracker).  A form which found the
-// lower node of the first corner's leaf once and took every other corner's
-// leaf entry from it with independent loads (no corner waiting on the
-// previous one's descent) measured 35.4 against 34.9 ms on the cloud and 8.28
-// against 8.30 on the 512^3 frame (against mode 1): the eight entries in
+// 5 is the default: 24.5 ms against 27.1 (mode 4) on the full-scale cloud
+// frame, 7.15 against 7.70 on the 512^3 frame; mode 4 had measured 33.99 ms
+// against 34.98 (mode 1) and 34.26 (mode 0) on the cloud at 64^3 cells, 7.87
+// against 8.31 and 7.83 on the 512^3 frame.  Images are bit-identical in
+// every mode.  Mode 2's extra code cost more than the descents it saved (9.98
+// against 8.57 ms on the 512^3 frame, 45.28 against 44.01 ms on the cloud,
+// against mode 1 on an earlier tracker).  A form which found the lower node of
+// the first corner's leaf once and took every other corner's leaf entry from
+// it with independent loads measured 35.4 against 34.9 ms on the cloud and
+// 8.28 against 8.30 on the 512^3 frame (against mode 1): the eight entries in
 // flight cost spills (300 bytes a thread against 152).
 #ifndef VDBC_TRI_STRADDLE
-#define VDBC_TRI_STRADDLE 4
+#define VDBC_TRI_STRADDLE 5
 #endif
 constexpr int kTriStraddle = VDBC_TRI_STRADDLE;
 
@@ -318,9 +326,48 @@ __device__ __forceinline__ float vdb_trilinear(const GridView& g, float px, floa
     const int lx0 = x0 >> 3, ly0 = y0 >> 3, lz0 = z0 >> 3;
     const int S = (lx0 != (x1 >> 3) ? 1 : 0) | (ly0 != (y1 >> 3) ? 2 : 0) | (lz0 != (z1 >> 3) ? 4 : 0);
     bool fast = S == 0;
-    if (T == 0) fast = false;
+    if (T == 0 || T == 5) fast = false;
     if (T == 4) fast = __all_sync(__activemask(), S == 0);
-    if (fast) {
+    if (T == 5 && __all_sync(__activemask(), __popc(S) <= 2)) {
+        // Up to four leaves: the stencil straddles at most two axes, a1 and
+        // a2 (bit masks of x, y, z; zero when absent).  The first corner's
+        // leaf comes through the accessor, the leaves across a1, a2 and both
+        // from their own descents, which do not wait on each other; each
+        // corner then takes the entry of the leaf its straddling bits name.
+        const int a1 = S & -S, a2 = S & ~a1;
+        const int lx1 = x1 >> 3, ly1 = y1 >> 3, lz1 = z1 >> 3;
+        const int pay = P >= 0 ? P : g.payload;
+        uint32_t e[4];
+        float2 sm[4];
+        e[0] = acc.leaf<D>(g, lx0, ly0, lz0);
+        sm[0] = acc.sm;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            const int m = (k & 1 ? a1 : 0) | (k & 2 ? a2 : 0);
+            e[k] = e[0];
+            sm[k] = sm[0];
+            if (k == 1 ? a1 != 0 : a2 != 0) {   // a2 != 0 implies a1 != 0
+                e[k] = descend_to_leaf(g, m & 1 ? lx1 : lx0, m & 2 ? ly1 : ly0, m & 4 ? lz1 : lz0);
+                if (pay != 0 && !(e[k] & kTile)) sm[k] = __ldg(g.meta + e[k]);
+#ifdef VDBC_STATS
+                ++acc.queries;
+                ++acc.descents;
+#endif
+            }
+        }
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int x = (c & 1) ? x1 : x0, y = (c & 2) ? y1 : y0, z = (c & 4) ? z1 : z0;
+            const int k = ((c & a1) ? 1 : 0) | ((c & a2) ? 2 : 0);
+            const uint32_t ek = k == 0 ? e[0] : k == 1 ? e[1] : k == 2 ? e[2] : e[3];
+            const float2 smk = k == 0 ? sm[0] : k == 1 ? sm[1] : k == 2 ? sm[2] : sm[3];
+            v[c] = (ek & kTile) ? __ldg(g.tiles + (ek & ~kTile))
+                                : leaf_value_t<P>(g, ek, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7), smk);
+        }
+        v000 = v[0]; v100 = v[1]; v010 = v[2]; v110 = v[3];
+        v001 = v[4]; v101 = v[5]; v011 = v[6]; v111 = v[7];
+    } else if (fast) {
         uint32_t e = acc.leaf<D>(g, lx0, ly0, lz0);
         if (e & kTile) return __ldg(g.tiles + (e & ~kTile));
         int ax = x0 & 7, bx = x1 & 7, ay = (y0 & 7) << 3, by = (y1 & 7) << 3;
