@@ -196,7 +196,12 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __rest
         bool any = false, seen = false;
         if constexpr (kMode == 2) {
             constexpr int U = 32;          // a brick row's 32 slices in flight (16: 8.80 ms, 32: 8.06 on the
-                                           // full-scale cloud encode; 24 splits the rows: 9.73)
+                                           // full-scale cloud encode; 24 splits the rows: 9.73).  Groups of
+                                           // 2 or 4 bricks along x per warp row (256- or 512-byte runs, 8 to
+                                           // 16 loads in flight within 64 registers) measured 9.5 against
+                                           // 7.8 ms for the whole encode, and loads asking L2 for the
+                                           // 256-byte block around them 7.80 against 7.81: the pass is
+                                           // bound by the loads it keeps in flight, not by run length
             const bool valid = lane < ex;
             if (warp < ey) {
                 const size_t slice = (size_t)d.nx * d.ny;
