@@ -192,6 +192,54 @@ struct LearnedSampler {
             xs[0] = min(max(i0, 0), g.nx - 1); xs[1] = min(max(i0 + 1, 0), g.nx - 1);
             ys[0] = min(max(j0, 0), g.ny - 1); ys[1] = min(max(j0 + 1, 0), g.ny - 1);
             zs[0] = min(max(k0, 0), g.nz - 1); zs[1] = min(max(k0 + 1, 0), g.nz - 1);
+        }
+        // As the plain sampler's default stencil mode: a stencil that
+        // straddles at most two axes takes its up to four leaves at once (the
+        // first corner's through the accessor, the others by descents that do
+        // not wait on each other), for the whole warp unless one of its
+        // lanes straddles all three axes; corner by corner otherwise.
+        const int lx0 = xs[0] >> 3, ly0 = ys[0] >> 3, lz0 = zs[0] >> 3;
+        const int S = (lx0 != (xs[1] >> 3) ? 1 : 0) | (ly0 != (ys[1] >> 3) ? 2 : 0) | (lz0 != (zs[1] >> 3) ? 4 : 0);
+        if (__all_sync(0xffffffffu, !look || __popc(S) <= 2)) {
+            if (look) {
+                const int a1 = S & -S, a2 = S & ~a1;
+                uint32_t e[4];
+                float2 sm[4];
+                e[0] = leaf(acc, lx0, ly0, lz0);
+                sm[0] = acc.sm;
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    const int m = (k & 1 ? a1 : 0) | (k & 2 ? a2 : 0);
+                    e[k] = e[0];
+                    sm[k] = sm[0];
+                    if (k == 1 ? a1 != 0 : a2 != 0) {   // a2 != 0 implies a1 != 0
+                        e[k] = descend_to_leaf(g, m & 1 ? xs[1] >> 3 : lx0, m & 2 ? ys[1] >> 3 : ly0,
+                                               m & 4 ? zs[1] >> 3 : lz0);
+                        if (!(e[k] & kTile))
+                            sm[k] = (e[k] & kNeural) ? __ldg(g.nmeta + (e[k] & ~kNeural)) : __ldg(g.meta + e[k]);
+#ifdef VDBC_STATS
+                        ++acc.queries;
+                        ++acc.descents;
+#endif
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
+                    const int k = ((c & a1) ? 1 : 0) | ((c & a2) ? 2 : 0);
+                    const uint32_t ek = k == 0 ? e[0] : k == 1 ? e[1] : k == 2 ? e[2] : e[3];
+                    const float2 smk = k == 0 ? sm[0] : k == 1 ? sm[1] : k == 2 ? sm[2] : sm[3];
+                    if (ek & kTile) {
+                        v[c] = __ldg(g.tiles + (ek & ~kTile));
+                    } else if (ek & kNeural) {
+                        v[c] = __uint_as_float(ek & ~kNeural);      // the rank, until the network answers
+                        nmask |= 1u << c;
+                    } else {
+                        v[c] = leaf_value_t<1>(g, ek, ((z & 7) << 6) | ((y & 7) << 3) | (x & 7), smk);
+                    }
+                }
+            }
+        } else if (look) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int x = xs[c & 1], y = ys[(c >> 1) & 1], z = zs[c >> 2];
