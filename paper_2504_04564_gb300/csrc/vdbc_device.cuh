@@ -303,7 +303,12 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 // the first corner's leaf once and took every other corner's leaf entry from
 // it with independent loads measured 35.4 against 34.9 ms on the cloud and
 // 8.28 against 8.30 on the 512^3 frame (against mode 1): the eight entries in
-// flight cost spills (300 bytes a thread against 152).
+// flight cost spills (300 bytes a thread against 152).  Mode 5 with the lanes
+// whose first corner shares a leaf taking its entry from one of them
+// (__match_any_sync, one accessor lookup per leaf and warp, shuffles to the
+// others) measured 25.5 against 23.9 ms on the cloud and 7.53 against 6.96 on
+// the 512^3 frame: lanes that share a leaf already share its loads, which
+// the memory system merges, and the match and shuffles cost every lookup.
 #ifndef VDBC_TRI_STRADDLE
 #define VDBC_TRI_STRADDLE 5
 #endif
