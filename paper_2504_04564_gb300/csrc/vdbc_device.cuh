@@ -309,6 +309,9 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return __fma
 // others) measured 25.5 against 23.9 ms on the cloud and 7.53 against 6.96 on
 // the 512^3 frame: lanes that share a leaf already share its loads, which
 // the memory system merges, and the match and shuffles cost every lookup.
+// Mode 5 with the extra leaves taken from the first corner's lower node (one
+// node descent, then one load per extra leaf) measured 24.4 against 23.9 ms
+// on the cloud and 7.16 against 6.95 on the 512^3 frame.
 #ifndef VDBC_TRI_STRADDLE
 #define VDBC_TRI_STRADDLE 5
 #endif
