@@ -201,7 +201,11 @@ __global__ void __launch_bounds__(kPass1Threads) k_pass1_maj(const float* __rest
                                            // 16 loads in flight within 64 registers) measured 9.5 against
                                            // 7.8 ms for the whole encode, and loads asking L2 for the
                                            // 256-byte block around them 7.80 against 7.81: the pass is
-                                           // bound by the loads it keeps in flight, not by run length
+                                           // bound by the loads it keeps in flight, not by run length.
+                                           // Four-byte cp.async copies into shared memory, one stage of
+                                           // 16 slices in flight while the last is worked on, took 9.85
+                                           // against 7.80 ms (the same grid): a four-byte asynchronous
+                                           // copy costs more than the register it saves
             const bool valid = lane < ex;
             if (warp < ey) {
                 const size_t slice = (size_t)d.nx * d.ny;
