@@ -493,6 +493,9 @@ struct JobView {
     uint32_t per;              // work items per sample (8x4 tiles x 32)
     int items32;               // items < 2^32: item decode by the invariant divisions below
     DivU32 div_per, div_tiles_x;
+    int tile_major;            // items ordered (tile, sample, pixel) instead of (sample, tile, pixel)
+    uint32_t spp32;            // work items per tile over all samples (tile-major order)
+    DivU32 div_spp32;
 };
 
 // one job: constants in kernel parameters, the grid's payload fixed at compile time
@@ -642,14 +645,25 @@ __device__ __forceinline__ void pt_loop(const Src& src, unsigned long long nitem
                 if (item >= nitems) {
                     mode = kDone;
                 } else {
-                    // item -> (job, sample, 8x4 pixel tile, pixel in tile): a warp's paths are neighbours
+                    // item -> (job, 8x4 pixel tile, sample, pixel in tile), or (job,
+                    // sample, tile, pixel) with the sample-first order: a warp's paths are neighbours
                     // (the divisions by invariants take one high multiply each;
                     // 64-bit division only for frames of 2^32 items or more)
                     jb = src.find(item, jb);
                     const JobView& F = src.job(jb);
                     const unsigned long long local = item - F.item_begin;
                     uint32_t q, ty, tx;
-                    if (F.items32) {
+                    if (F.items32 && F.tile_major) {
+                        // a tile's 32 pixels sample after sample: a warp's
+                        // successive paths start from the same pixels
+                        const uint32_t l32 = (uint32_t)local;
+                        const uint32_t tile = F.div_spp32.div(l32);
+                        const uint32_t r = l32 - tile * F.spp32;
+                        sample = r >> 5;
+                        q = (tile << 5) | (r & 31);
+                        ty = F.div_tiles_x.div(tile);
+                        tx = tile - ty * (uint32_t)F.tiles_x;
+                    } else if (F.items32) {
                         const uint32_t l32 = (uint32_t)local;
                         sample = F.div_per.div(l32);
                         q = l32 - sample * F.per;
@@ -1569,6 +1583,16 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     j.items32 = j.items < (1ull << 32) ? 1 : 0;
     j.div_per.init(j.per);
     j.div_tiles_x.init((uint32_t)j.tiles_x);
+    // Work items ordered by tile first: a tile's 32 pixels for every sample in
+    // turn, so that the warps working at one time start their paths from few
+    // pixels and read the same leaves (full-scale cloud frame 21.99 against
+    // 23.97 ms ordered by sample first, 512^3 frame 6.55 against 6.99; the
+    // per-pixel sums, and so the images, are the same).  VDBC_PT_ORDER=sample
+    // restores the sample-first order.
+    const char* order = std::getenv("VDBC_PT_ORDER");
+    j.tile_major = (order && std::strcmp(order, "sample") == 0) ? 0 : 1;
+    j.spp32 = (uint32_t)((unsigned long long)spp * 32ull);
+    if (j.items32) j.div_spp32.init(j.spp32);
     return j;
 }
 

@@ -285,9 +285,10 @@ def test_pt_coarse_level_changes_no_image(env, monkeypatch):
 def test_pt_lookup_modes_and_work_chunks_change_no_image(env, monkeypatch):
     """The stencil modes (one-leaf path per lane, one path per warp, up to four
     leaves at once, the accessor at depth 2) fetch the same eight values and
-    interpolate them in the same order, and the work chunks only change which
-    lane renders which path (the per-pixel sums are integers): every variant
-    renders the default image bit for bit, with the same lookup count."""
+    interpolate them in the same order, and the work chunks and the work order
+    (tile first or sample first) only change which lane renders which path
+    (the per-pixel sums are integers): every variant renders the default image
+    bit for bit, with the same lookup count."""
     torch, v, vg, sc = env["torch"], env["v"], env["vg"], env["sc"]
     dims = (120, 104, 112)
     host = vg.generate_host(vg.make_params("turbulence", dims, 8))
@@ -296,7 +297,8 @@ def test_pt_lookup_modes_and_work_chunks_change_no_image(env, monkeypatch):
     med = v.make_medium(v.MODE_PT, **sc.pt_medium_args())
     base = gpu_image(env, grid, cam, med, 8, 5)
     lookups = v.vdbc_render_stats_get(grid).lookups
-    for name, values in (("VDBC_PT_LOOKUP", ["11", "12", "22", "24"]), ("VDBC_PT_CHUNK", ["32", "64", "128", "256"])):
+    for name, values in (("VDBC_PT_LOOKUP", ["11", "12", "22", "24"]), ("VDBC_PT_CHUNK", ["32", "64", "128", "256"]),
+                         ("VDBC_PT_ORDER", ["sample"])):
         for val in values:
             monkeypatch.setenv(name, val)
             img = gpu_image(env, grid, cam, med, 8, 5)
