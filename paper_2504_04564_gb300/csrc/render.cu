@@ -1588,7 +1588,10 @@ JobView make_job(const Majorants& mj, const CamDev& cam, const MedDev& med, int 
     // pixels and read the same leaves (full-scale cloud frame 21.99 against
     // 23.97 ms ordered by sample first, 512^3 frame 6.55 against 6.99; the
     // per-pixel sums, and so the images, are the same).  VDBC_PT_ORDER=sample
-    // restores the sample-first order.
+    // restores the sample-first order.  Tiles visited in strips of 8 or 32
+    // tile rows, each strip column by column, instead of row by row measured
+    // 22.3 and 21.8 against 22.0 ms on the cloud, 6.65 and 6.60 against 6.55
+    // on the 512^3 frame.
     const char* order = std::getenv("VDBC_PT_ORDER");
     j.tile_major = (order && std::strcmp(order, "sample") == 0) ? 0 : 1;
     j.spp32 = (uint32_t)((unsigned long long)spp * 32ull);
