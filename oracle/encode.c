@@ -17,9 +17,11 @@
  *  - the tree is root -> 32^3 upper -> 16^3 lower -> 8^3 leaf, prune collapses
  *    a leaf whose 512 values are bitwise equal into a tile, and a lower/upper
  *    node whose entries are all equal tiles into a tile of its parent;
- *  - FP16/FP8 payloads (a project extension, parity unpinned against the
- *    paper): per leaf offset = min, scale = max - min, code = round to
- *    nearest even of (v - off) / scale in FP32, decode = fmaf(scale, code, off).
+ *  - FP16/FP8 payloads (a project extension: the paper stores FP32 leaves and
+ *    prints no quantized value; the rounding is pinned to the IEEE 754 binary16
+ *    and OCP E4M3 definitions instead): per leaf offset = min, scale = max -
+ *    min, code = round to nearest even of (v - off) / scale in FP32, decode =
+ *    fmaf(scale, code, off).
  */
 #include <math.h>
 #include <stdlib.h>

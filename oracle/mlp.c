@@ -1,9 +1,9 @@
 /*
  * mlp.c -- the learned leaf decoder (a project extension; the paper only
  * cites NeuralVDB as related work in Section 2.3, where inference is too slow
- * for real time).  Parity against the paper is unpinned: there is nothing in
- * the paper to pin it to; it is pinned to calculus instead (finite
- * differences, closed-form networks, Adam's first step).
+ * for real time).  The paper prints nothing for it to be compared with, so
+ * it is pinned to calculus instead (finite differences, closed-form networks,
+ * Adam's steps in closed form).
  *
  * Network (shared by all leaves): input x = (u, v, w, z_0 .. z_15), with
  * (u, v, w) = the voxel's position in its 8^3 leaf divided by 7 and z the

@@ -1,5 +1,5 @@
-"""Pins of the oracle's FP16 / FP8(E4M3) leaf codecs (a project extension;
-parity against the paper is unpinned because the paper stores FP32 leaves).
+"""Pins of the oracle's FP16 / FP8(E4M3) leaf codecs (a project extension:
+the paper stores FP32 leaves, so the pins are the formats' own definitions).
 
 The rounding is checked against the format definitions decoded bit field by
 bit field (IEEE 754 binary16; OCP FP8 E4M3 with no infinities), exhaustively

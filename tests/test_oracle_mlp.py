@@ -1,5 +1,5 @@
-"""Pins of the oracle's learned leaf decoder (a project extension: parity
-against the paper is unpinned).  The backward pass is pinned to the forward
+"""Pins of the oracle's learned leaf decoder (a project extension the paper
+prints no values for).  The backward pass is pinned to the forward
 by central finite differences, the forward to networks built by hand whose
 output is known in closed form, and Adam to the closed form of its first
 step."""
